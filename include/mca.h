@@ -1,0 +1,172 @@
+/*
+ * mca.h — C ABI of the GB300 steady-state memristor-crossbar (MCA) solver.
+ *
+ * The library computes the steady state of a memristor crossbar array: two resistive
+ * wire grids (top rows = word lines, bottom columns = bit lines) coupled at every cross
+ * point (i, j) by a memristor, driven at the left end of every top row.  It solves the
+ * modified-nodal-analysis system of Xie et al., "A Fast Method for Steady-State
+ * Memristor Crossbar Array Circuit Simulation" (arXiv 2109.07929):
+ *
+ *   Section 2, eq. (MNA) / eq. (F):  G_t V_t + I(V_t - V_b) - Y_t = 0,
+ *                                    G_b V_b - I(V_t - V_b) - Y_b = 0,
+ *   eqs. (Gt), (Gb):                 G_t = I (x) G_r,  G_b = G_c (x) I,
+ *   eq. (Newton3), eq. (J):          Newton's method on F with the MNA Jacobian,
+ *   Section 3, eqs. (P), (block), (M):  each Newton system is solved by GMRES,
+ *                                    preconditioned with P = [[G_t + a1 I, -a1 I],
+ *                                    [-a2 I, G_b + a2 I]], a1 = a2 = mean device
+ *                                    conductance, inverted through the Kronecker
+ *                                    structure of G_t and G_b.
+ *
+ * Device model: i = (g_ij / b) sinh(b * dV) (b = 0 selects the linear device i = g dV).
+ *
+ * Conventions for every array argument:
+ *   - node voltages are row-major m x n (cell (i, j) at i*n + j), one block per input
+ *     vector: v_top[v][i][j], v_bot[v][i][j];
+ *   - input vectors are v_in[v][i] (volts at the left end of top row i);
+ *   - output currents are i_out[v][j] (amperes into the sense amplifier of column j).
+ *   - pointers may be host or device memory (CUDA unified addressing tells them apart);
+ *     the caller owns every buffer it passes in and may free it when the call returns.
+ *
+ * Errors: every int-returning call returns MCA_OK (0) or a negative MCA_ERR_* code and
+ * never throws.  mca_last_error_message() gives a human-readable detail of the most
+ * recent failure in the calling thread.  One handle must not be used from two threads at
+ * the same time.
+ */
+#ifndef MCA_H_
+#define MCA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------------- */
+#define MCA_OK 0
+#define MCA_ERR_INVALID_ARG (-1)   /* bad size, NULL pointer, non-positive conductance  */
+#define MCA_ERR_CUDA (-2)          /* a CUDA runtime call failed                        */
+#define MCA_ERR_NONFINITE (-3)     /* NaN/Inf in the inputs or in the residual          */
+#define MCA_ERR_NOT_CONVERGED (-4) /* Newton stopped at max_newton; outputs still valid */
+#define MCA_ERR_TIMEOUT (-5)       /* a bounded device-side wait gave up                */
+#define MCA_ERR_OOM (-6)           /* device memory allocation failed                   */
+#define MCA_ERR_UNSUPPORTED (-7)   /* precision mode not available on this device       */
+
+/* ---- precision of the preconditioner apply (Section 3.2) -------------------------- */
+#define MCA_PREC_FP64 0        /* all four eigenbasis transforms in FP64 (CUDA cores)     */
+#define MCA_PREC_BF16 1        /* all four transforms on tcgen05 tensor cores, BF16 in,
+                                  FP32 accumulate                                        */
+#define MCA_PREC_BF16_SPLIT 2  /* forward transforms BF16; back transforms with hi+lo
+                                  BF16 splitting of both operands (3 tensor-core
+                                  products, FP32 accumulate)                             */
+
+typedef struct mca_params {
+  int32_t rows;              /* m >= 1: number of top-layer rows (word lines)            */
+  int32_t cols;              /* n >= 1: number of bottom-layer columns (bit lines)       */
+  double g_wire_top;         /* S, top-layer segment conductance (Section 2)             */
+  double g_wire_bot;         /* S, bottom-layer segment conductance                      */
+  double g_src;              /* S, driver conductance at the left end of each top row    */
+  double g_term_top_right;   /* S, right end of each top row to ground                   */
+  double g_term_bot_top;     /* S, row-0 end of each bottom column to ground             */
+  double g_sense;            /* S, row-(m-1) end of each bottom column to virtual ground */
+  double b;                  /* 1/V, memristor sinh nonlinearity (0 = linear)            */
+  int32_t precision;         /* MCA_PREC_*                                               */
+  int32_t gmres_restart;     /* 1..30 (flexible GMRES restart length)                    */
+  int32_t max_newton;        /* Newton iteration limit (>= 1)                            */
+  int32_t max_batch;         /* input vectors solved together per pass (>= 1)            */
+  double newton_rtol;        /* stop when ||F||_2 / ||Y||_2 <= newton_rtol               */
+  double eta0;               /* relative tolerance of the first linear solve             */
+  double eta_max;            /* upper bound of later forcing terms                       */
+} mca_params;
+
+typedef struct mca_stats {
+  int32_t status;            /* MCA_OK, MCA_ERR_NOT_CONVERGED or MCA_ERR_NONFINITE       */
+  int32_t newton_iters;      /* Jacobian solves performed                                */
+  int32_t gmres_iters;       /* GMRES iterations summed over the Newton steps            */
+  int32_t reserved;
+  double rel_residual;       /* ||F||_2 / ||Y||_2 at the returned voltages               */
+  double kcl_rel_error;      /* |sum I_in - sum I_out - sum leaks| / sum |I_in|          */
+} mca_stats;
+
+typedef struct mca_handle mca_handle;
+
+/* Fill *p with the defaults: 1 S wires, 10 ohm driver and sense, 1 kohm terminations,
+ * b = 2, MCA_PREC_BF16_SPLIT, restart 30, max_newton 20, max_batch 4, newton_rtol 1e-8,
+ * eta0 1e-4, eta_max 1e-2.  rows/cols are left at 0 and must be set. */
+void mca_default_params(mca_params* p);
+
+/* Create a solver for one crossbar.
+ *   p     : circuit and solver parameters (copied).
+ *   g_map : m*n memristor conductances g_ij in siemens, row-major, host or device,
+ *           every entry > 0 and finite (copied; the caller keeps ownership).
+ *   out   : receives the handle.
+ * Builds the 1-D wire operators G_r (n x n) and G_c (m x m) of eq. (G) with the end
+ * terminations, and their FP64 eigendecompositions on the GPU (separability of eqs.
+ * (Gt)/(Gb), Section 3.1).  Allocates the device workspace for max_batch vectors.
+ * Returns MCA_ERR_INVALID_ARG for bad sizes or values, MCA_ERR_OOM, MCA_ERR_CUDA. */
+int mca_create(const mca_params* p, const double* g_map, mca_handle** out);
+
+/* Solve the steady state for nvec input vectors (Newton, eq. (Newton3), from V = 0).
+ *   v_in  : nvec*m input voltages, row vector per input (host or device).
+ *   v_top : nvec*m*n top-layer node voltages out, or NULL.
+ *   v_bot : nvec*m*n bottom-layer node voltages out, or NULL.
+ *   i_out : nvec*n sensed column currents g_sense * V_b[m-1, j] out, or NULL.
+ *   stats : nvec entries out, or NULL.
+ *   stream: cudaStream_t to run on (NULL = legacy default stream).  The call returns
+ *           after the results are written.
+ * Returns MCA_OK when every vector met newton_rtol, else the first failing status
+ * (MCA_ERR_NOT_CONVERGED / MCA_ERR_NONFINITE; outputs are still written), or
+ * MCA_ERR_INVALID_ARG / MCA_ERR_CUDA / MCA_ERR_TIMEOUT. */
+int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, double* v_bot,
+              double* i_out, mca_stats* stats, void* stream);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void mca_destroy(mca_handle* h);
+
+/* Static description of a status code. */
+const char* mca_strerror(int code);
+
+/* Detail of the most recent failure in this thread ("" if none). */
+const char* mca_last_error_message(void);
+
+/* ---- single-operation entry points (device pointers only; used by tests/bench) ----- */
+
+/* Residual and Jacobian diagonal (eq. (F), eq. (J)) at nvec states.
+ *   x     : device, nvec * 2*m*n, [V_t ; V_b] per vector.
+ *   v_in  : device, nvec * m.
+ *   F     : device out, nvec * 2*m*n, [F_t ; F_b] per vector.
+ *   D     : device out, nvec * m*n, g_ij cosh(b (V_t - V_b)).
+ *   fnorm : host out, nvec values of ||F||_2 (may be NULL).
+ *   dmean : host out, nvec values of mean(D) = a1 = a2 of eq. (P) (may be NULL). */
+int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nvec,
+                 double* F, double* D, double* fnorm, double* dmean, void* stream);
+
+/* Jacobian apply w = J z with J = [[G_t + D, -D], [-D, G_b + D]] (eq. (J)).
+ *   D : device, nvec * m*n;  z, w : device, nvec * 2*m*n. */
+int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* w,
+                       int32_t nvec, void* stream);
+
+/* Preconditioner apply z = P^-1 r (eqs. (P), (block), (M)) with a1 = a2 = a[v] per
+ * vector, in the given MCA_PREC_* precision.
+ *   a : host, nvec values (> 0);  r, z : device, nvec * 2*m*n. */
+int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z,
+                      int32_t nvec, int32_t precision, void* stream);
+
+/* Copy out the FP64 eigenpairs of the wire operators (host or device buffers):
+ * mu[n], Q_r[n*n] (column k is eigenvector k, row-major storage Q_r[j*n + k]) for G_r;
+ * nu[m], Q_c[m*m] for G_c.  Eigenvalues ascending.  NULL outputs are skipped. */
+int mca_eigenpairs(mca_handle* h, double* mu, double* q_r, double* nu, double* q_c);
+
+/* One flexible-GMRES(restart) cycle for J dx = rhs (Section 4) with the handle's
+ * preconditioner (a1 = a2 = a[v]), at the Jacobian diagonal D, from dx = 0.  Stops when
+ * the Givens residual estimate reaches rtol * ||rhs|| or after gmres_restart iterations.
+ *   D : device nvec*m*n;  a : host nvec (> 0);  rhs, dx : device nvec*2*m*n;
+ *   iters : host out, nvec iteration counts (may be NULL);
+ *   res   : host out, nvec final residual estimates ||rhs - J dx|| (may be NULL). */
+int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const double* rhs,
+                    double* dx, int32_t nvec, double rtol, int32_t* iters, double* res,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCA_H_ */

@@ -1,0 +1,242 @@
+"""GB300 steady-state memristor-crossbar solver: Python binding of libmca.so.
+
+Argument marshalling only; every step of the solve runs in the library's CUDA kernels.
+The binding takes NumPy arrays (host) or torch CUDA tensors (device) and passes their
+pointers through the C ABI declared in include/mca.h.  It fails loudly when the library
+is missing or no GPU is present; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+PREC_FP64 = 0
+PREC_BF16 = 1
+PREC_BF16_SPLIT = 2
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_NONFINITE = -3
+ERR_NOT_CONVERGED = -4
+ERR_TIMEOUT = -5
+ERR_OOM = -6
+ERR_UNSUPPORTED = -7
+
+EXPORTED = (
+    "mca_default_params", "mca_create", "mca_solve", "mca_destroy", "mca_strerror",
+    "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_precond_apply",
+    "mca_eigenpairs", "mca_gmres_solve",
+)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("rows", ctypes.c_int32), ("cols", ctypes.c_int32),
+        ("g_wire_top", ctypes.c_double), ("g_wire_bot", ctypes.c_double),
+        ("g_src", ctypes.c_double), ("g_term_top_right", ctypes.c_double),
+        ("g_term_bot_top", ctypes.c_double), ("g_sense", ctypes.c_double),
+        ("b", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
+        ("max_newton", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+        ("newton_rtol", ctypes.c_double), ("eta0", ctypes.c_double),
+        ("eta_max", ctypes.c_double),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+        ("gmres_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("rel_residual", ctypes.c_double), ("kcl_rel_error", ctypes.c_double),
+    ]
+
+
+class MCAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libmca.so (building it first if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing:
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmca.so not built ({path})")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.mca_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.mca_default_params.restype = None
+    lib.mca_create.argtypes = [ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+    lib.mca_solve.argtypes = [P, P, ctypes.c_int32, P, P, P, P, P]
+    lib.mca_destroy.argtypes = [P]
+    lib.mca_destroy.restype = None
+    lib.mca_strerror.argtypes = [ctypes.c_int]
+    lib.mca_strerror.restype = ctypes.c_char_p
+    lib.mca_last_error_message.argtypes = []
+    lib.mca_last_error_message.restype = ctypes.c_char_p
+    lib.mca_residual.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P]
+    lib.mca_jacobian_apply.argtypes = [P, P, P, P, ctypes.c_int32, P]
+    lib.mca_precond_apply.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
+    lib.mca_eigenpairs.argtypes = [P, P, P, P, P]
+    lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double, P, P, P]
+    for name in ("mca_create", "mca_solve", "mca_residual", "mca_jacobian_apply",
+                 "mca_precond_apply", "mca_eigenpairs", "mca_gmres_solve"):
+        getattr(lib, name).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        lib = load(False)
+        detail = lib.mca_last_error_message().decode()
+        raise MCAError(rc, f"{lib.mca_strerror(rc).decode()}: {detail}")
+    return rc
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a NumPy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def default_params(rows, cols, **kw):
+    lib = load()
+    p = Params()
+    lib.mca_default_params(ctypes.byref(p))
+    p.rows = rows
+    p.cols = cols
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Solver:
+    """One crossbar: ``Solver(params, gmap)`` then ``solve(vin)``."""
+
+    def __init__(self, params: Params, gmap):
+        self.lib = load()
+        self.params = params
+        self.m, self.n = params.rows, params.cols
+        g = gmap if not isinstance(gmap, np.ndarray) else np.ascontiguousarray(gmap, np.float64)
+        h = ctypes.c_void_p()
+        _check(self.lib.mca_create(ctypes.byref(params), _ptr(g), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, vin, v_top=None, v_bot=None, i_out=None, stream=None,
+              allow_not_converged=False):
+        """Solve for ``nvec`` input vectors.  ``vin`` is (nvec, m) host or device; the
+        output buffers default to host NumPy arrays.  Returns (v_top, v_bot, i_out,
+        stats list)."""
+        nvec = vin.shape[0] if vin.ndim == 2 else 1
+        if isinstance(vin, np.ndarray):
+            vin = np.ascontiguousarray(vin, np.float64)
+        if v_top is None:
+            v_top = np.empty((nvec, self.m, self.n))
+        if v_bot is None:
+            v_bot = np.empty((nvec, self.m, self.n))
+        if i_out is None:
+            i_out = np.empty((nvec, self.n))
+        st = (Stats * nvec)()
+        rc = self.lib.mca_solve(self.h, _ptr(vin), nvec, _ptr(v_top), _ptr(v_bot), _ptr(i_out),
+                                ctypes.cast(st, ctypes.c_void_p), _stream_ptr(stream))
+        allow = (ERR_NOT_CONVERGED, ERR_NONFINITE) if allow_not_converged else ()
+        _check(rc, allow)
+        stats = [dict(status=s.status, newton_iters=s.newton_iters, gmres_iters=s.gmres_iters,
+                      rel_residual=s.rel_residual, kcl_rel_error=s.kcl_rel_error) for s in st]
+        return v_top, v_bot, i_out, stats
+
+    def solve_raw(self, vin_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr=None, stream=None):
+        """Pointer-level call of mca_solve (no allocation, no checks); returns the status."""
+        return self.lib.mca_solve(self.h, vin_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr,
+                                  _stream_ptr(stream))
+
+    # ---- single operations (device tensors) ---------------------------------------
+    def residual(self, x, vin, F, D, stream=None):
+        nvec = x.shape[0]
+        fn = np.zeros(nvec)
+        dm = np.zeros(nvec)
+        _check(self.lib.mca_residual(self.h, _ptr(x), _ptr(vin), nvec, _ptr(F), _ptr(D),
+                                     _ptr(fn), _ptr(dm), _stream_ptr(stream)))
+        return fn, dm
+
+    def jacobian_apply(self, D, z, w, stream=None):
+        _check(self.lib.mca_jacobian_apply(self.h, _ptr(D), _ptr(z), _ptr(w), z.shape[0],
+                                           _stream_ptr(stream)))
+
+    def precond_apply(self, a, r, z, precision=None, stream=None):
+        a = np.ascontiguousarray(a, np.float64)
+        prec = self.params.precision if precision is None else precision
+        _check(self.lib.mca_precond_apply(self.h, _ptr(a), _ptr(r), _ptr(z), r.shape[0], prec,
+                                          _stream_ptr(stream)))
+
+    def eigenpairs(self):
+        mu = np.empty(self.n)
+        qr = np.empty((self.n, self.n))
+        nu = np.empty(self.m)
+        qc = np.empty((self.m, self.m))
+        _check(self.lib.mca_eigenpairs(self.h, _ptr(mu), _ptr(qr), _ptr(nu), _ptr(qc)))
+        return mu, qr, nu, qc
+
+    def gmres_solve(self, D, a, rhs, dx, rtol, stream=None):
+        a = np.ascontiguousarray(a, np.float64)
+        nvec = rhs.shape[0]
+        its = np.zeros(nvec, np.int32)
+        res = np.zeros(nvec)
+        _check(self.lib.mca_gmres_solve(self.h, _ptr(D), _ptr(a), _ptr(rhs), _ptr(dx), nvec,
+                                        rtol, _ptr(its), _ptr(res), _stream_ptr(stream)))
+        return its, res

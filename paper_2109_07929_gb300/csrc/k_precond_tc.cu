@@ -1,0 +1,433 @@
+// Tensor-core form of the preconditioner apply z = P^-1 r (eqs. P, block, M; the
+// tensor-product evaluation of Section 3.2 done in the exact Kronecker eigenbasis).
+//
+// Four block-transposed GEMMs O[blk][c][r] = sum_k A[blk][r][k] B[c][k] on tcgen05
+// (kind::f16, BF16 operands, FP32 accumulators in TMEM), blk = 2*b + layer:
+//   1: T1^T  = (X Q_r)^T            A = X      [blk][i][j]    B = Q_r^T  [k'][j]
+//   2: Y_hat = modes^-1 (Q_c^T T1)  A = T1^T   [blk][k'][i]   B = Q_c^T  [i'][i]
+//      (stored [blk][i'][k']; the per-mode 2x2 inverse of eq. P is the epilogue, which
+//       needs both layers of one mode, so each CTA owns the two layers' tiles)
+//   3: E^T   = (Y_hat Q_r^T)^T      A = Y_hat  [blk][i'][k']  B = Q_r    [j][k']
+//   4: Z     = (E^T Q_c^T)^T        A = E^T    [blk][j][i']   B = Q_c    [i][i']
+// Every operand is K-major, so TMA tiles land in the canonical 128-byte-swizzled layout
+// the MMA descriptors expect, and every epilogue writes its tile transposed, which makes
+// the TMEM lane = output row mapping store coalesced.
+//
+// Precision: the back transforms (3, 4) multiply the large amplified low modes of Y_hat;
+// with MCA_PREC_BF16_SPLIT both of their operands are split as hi + lo BF16 pairs and
+// the three products hi*hi + hi*lo + lo*hi accumulate in the same FP32 tile.
+//
+// All device-side waits are bounded by a wall-clock limit; on expiry the CTA records
+// MCA_ERR_TIMEOUT in a device flag, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "mca_internal.cuh"
+#include "precond_tc.h"
+
+namespace mca {
+namespace tc {
+
+namespace {
+
+constexpr int BM = 128;          // accumulator rows (TMEM lanes)
+constexpr int BK = 64;           // K elements per stage: one 128-byte swizzle row
+constexpr int kThreads = 128;    // 4 warps: TMA producer, MMA issuer, all 4 run the epilogue
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase parity; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with 128-byte
+// swizzling: 8-row x 128-byte atoms, 1024 bytes between consecutive 8-row groups.
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a & 0x3FFFFu) >> 4);     // start address (16-byte units)
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+      "[%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+        "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+        "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void record_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+template <int BN, bool SPLIT>
+struct Layout {
+  static constexpr int A_BYTES = BM * BK * 2;       // 16 KB
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int HALF = 2 * A_BYTES + B_BYTES;
+  static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
+  static constexpr int STAGES = SPLIT ? 2 : 4;
+  static constexpr int BAR_OFF = STAGES * STAGE;
+  static constexpr int SMEM = BAR_OFF + 256 + 1024;  // barriers + TMEM slot + alignment
+  static constexpr int TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
+};
+
+template <int BN, bool SPLIT, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
+          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
+          GemmEpi ep) {
+  using L = Layout<BN, SPLIT>;
+  const int rt = blockIdx.x, ct = blockIdx.y, b = blockIdx.z;
+  if (ep.ctl != nullptr && !ep.ctl[b].gm_active) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + L::STAGES;
+  uint64_t* accum = empty + L::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = rt * BM, c0 = ct * BN;
+  const int blk0 = 2 * b, blk1 = 2 * b + 1;
+  const int nkb = ep.K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < L::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)L::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % L::STAGES;
+      const uint32_t ph = (uint32_t)(kb / L::STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        record_error(ep.err, MCA_ERR_TIMEOUT);
+        break;
+      }
+      uint8_t* st = smem + s * L::STAGE;
+      mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
+      const int k0 = kb * BK;
+      tma_load_2d(st, &tmA, k0, blk0 * ep.R + r0, &full[s]);
+      tma_load_2d(st + L::A_BYTES, &tmA, k0, blk1 * ep.R + r0, &full[s]);
+      tma_load_2d(st + 2 * L::A_BYTES, &tmB, k0, c0, &full[s]);
+      if (SPLIT) {
+        uint8_t* sl = st + L::HALF;
+        tma_load_2d(sl, &tmAl, k0, blk0 * ep.R + r0, &full[s]);
+        tma_load_2d(sl + L::A_BYTES, &tmAl, k0, blk1 * ep.R + r0, &full[s]);
+        tma_load_2d(sl + 2 * L::A_BYTES, &tmBl, k0, c0, &full[s]);
+      }
+    }
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer (one thread)
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % L::STAGES;
+      const uint32_t ph = (uint32_t)(kb / L::STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        record_error(ep.err, MCA_ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint8_t* st = smem + s * L::STAGE;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const int off = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
+        const uint64_t a0 = sw128_desc(st + off);
+        const uint64_t a1 = sw128_desc(st + L::A_BYTES + off);
+        const uint64_t bd = sw128_desc(st + 2 * L::A_BYTES + off);
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        umma(tmem, a0, bd, idesc, acc);
+        umma(tmem + BN, a1, bd, idesc, acc);
+        if (SPLIT) {
+          const uint8_t* sl = st + L::HALF;
+          const uint64_t a0l = sw128_desc(sl + off);
+          const uint64_t a1l = sw128_desc(sl + L::A_BYTES + off);
+          const uint64_t bdl = sw128_desc(sl + 2 * L::A_BYTES + off);
+          umma(tmem, a0l, bd, idesc, 1u);
+          umma(tmem, a0, bdl, idesc, 1u);
+          umma(tmem + BN, a1l, bd, idesc, 1u);
+          umma(tmem + BN, a1, bdl, idesc, 1u);
+        }
+      }
+      umma_commit(&empty[s]);
+    }
+    if (ok) umma_commit(accum);
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: thread = TMEM lane = output row r0 + 32*warp + lane
+  bool have = mbar_wait(accum, 0);
+  if (!have) record_error(ep.err, MCA_ERR_TIMEOUT);
+  if (have) {
+    tc_fence_after();
+    const int r = r0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    float a_mode = 0.f, mu_r = 0.f;
+    bool r_ok = r < ep.R_valid;
+    if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+      a_mode = (float)ep.ctl[b].a;
+      mu_r = r_ok ? (float)ep.mu[r] : 0.f;
+    }
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 32; ++cc) {
+      uint32_t v0[32], v1[32];
+      tmem_ld32(lane_base + cc * 32, v0);
+      tmem_ld32(lane_base + BN + cc * 32, v1);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int c = c0 + cc * 32 + q;
+        float x0 = __uint_as_float(v0[q]);
+        float x1 = __uint_as_float(v1[q]);
+        if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+          // [y_t; y_b] = (1/det) [[nu + a, a], [a, mu + a]] [x_t; x_b]
+          float y0 = 0.f, y1 = 0.f;
+          if (r_ok && c < ep.C_valid) {
+            const float nu_c = (float)ep.nu[c];
+            const float det = mu_r * nu_c + mu_r * a_mode + nu_c * a_mode;
+            const float inv = 1.0f / det;
+            y0 = ((nu_c + a_mode) * x0 + a_mode * x1) * inv;
+            y1 = (a_mode * x0 + (mu_r + a_mode) * x1) * inv;
+          }
+          x0 = y0;
+          x1 = y1;
+        }
+        const size_t o0 = (size_t)b * ep.o_bs + (size_t)c * ep.o_ld + r;
+        if (EPI == EPI_F64) {
+          if (r_ok && c < ep.C_valid) {
+            double* out = static_cast<double*>(ep.out);
+            out[o0] = (double)x0;
+            out[o0 + ep.o_ls] = (double)x1;
+          }
+        } else {
+          __nv_bfloat16* out = static_cast<__nv_bfloat16*>(ep.out);
+          const __nv_bfloat16 h0 = __float2bfloat16(x0);
+          const __nv_bfloat16 h1 = __float2bfloat16(x1);
+          out[o0] = h0;
+          out[o0 + ep.o_ls] = h1;
+          if (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) {
+            __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(ep.out_lo);
+            lo[o0] = __float2bfloat16(x0 - __bfloat162float(h0));
+            lo[o0 + ep.o_ls] = __float2bfloat16(x1 - __bfloat162float(h1));
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)L::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// FP64 [b][layer][m][n] -> BF16 padded [b][layer][mp][np] (the pads stay zero).
+__global__ void k_cast_pad(const double* __restrict__ x, size_t xstride,
+                           __nv_bfloat16* __restrict__ xbf, int m, int n, int mp, int np) {
+  const int b = blockIdx.y;
+  const size_t mn = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < 2 * mn;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(e / mn);
+    const size_t cell = e - l * mn;
+    const int i = (int)(cell / n), j = (int)(cell - (size_t)i * n);
+    xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = __double2bfloat16(x[b * xstride + e]);
+  }
+}
+
+template <int BN, bool SPLIT, int EPI>
+cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
+                       const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
+  using L = Layout<BN, SPLIT>;
+  auto kern = k_gemm_tc<BN, SPLIT, EPI>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         L::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid(ep.R / BM, ep.C / BN, B);
+  kern<<<grid, kThreads, L::SMEM, s>>>(a, al, bm, bml, ep);
+  return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+bool encode_available() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || fn == nullptr)
+    return false;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+// 2-D BF16 map over a row-major [rows][cols] matrix with a box of box_rows x 64 elements
+// and 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
+              uint32_t box_rows) {
+  if (!encode_available()) return false;
+  cuuint64_t gdim[2] = {cols, rows};
+  cuuint64_t gstride[1] = {cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
+                        gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
+                 const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
+                 cudaStream_t s) {
+#define MCA_TC_CASE(BN_, SPLIT_, EPI_)                                       \
+  if (bn == BN_ && split == SPLIT_ && epi == EPI_)                           \
+    return launch_one<BN_, SPLIT_, EPI_>(a, al, bm, bml, ep, B, s);
+  MCA_TC_CASE(128, false, EPI_BF16)
+  MCA_TC_CASE(64, false, EPI_BF16)
+  MCA_TC_CASE(128, false, EPI_MODES)
+  MCA_TC_CASE(64, false, EPI_MODES)
+  MCA_TC_CASE(128, false, EPI_MODES_SPLIT)
+  MCA_TC_CASE(64, false, EPI_MODES_SPLIT)
+  MCA_TC_CASE(128, false, EPI_F64)
+  MCA_TC_CASE(64, false, EPI_F64)
+  MCA_TC_CASE(128, true, EPI_SPLIT)
+  MCA_TC_CASE(64, true, EPI_SPLIT)
+  MCA_TC_CASE(128, true, EPI_F64)
+  MCA_TC_CASE(64, true, EPI_F64)
+#undef MCA_TC_CASE
+  return cudaErrorInvalidValue;
+}
+
+void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
+              int np, int B, cudaStream_t s) {
+  const size_t n2 = 2 * (size_t)m * n;
+  int nb = (int)((n2 + 255) / 256);
+  if (nb > 1216) nb = 1216;
+  k_cast_pad<<<dim3(nb, B), 256, 0, s>>>(x, xstride, xbf, m, n, mp, np);
+}
+
+}  // namespace tc
+}  // namespace mca

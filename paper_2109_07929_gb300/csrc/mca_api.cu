@@ -1,0 +1,680 @@
+// C ABI and host orchestration of the steady-state crossbar solve.
+//
+//   mca_create : 1-D wire operators of eq. (G) with terminations, FP64 eigenpairs on the
+//                GPU, BF16 operand copies and TMA maps for the tensor-core transforms,
+//                device workspace for max_batch vectors.
+//   mca_solve  : Newton (eq. Newton3) from V = 0; every Newton system J dx = -F (eq. J)
+//                is solved by one flexible GMRES(restart) cycle right-preconditioned with
+//                P^-1 of eq. (P) (Section 3), inexact-Newton forcing terms.
+//
+// The host only enqueues kernels; the iteration state lives on the device (VecCtl).  The
+// host reads one small flag array per Newton step and polls the GMRES stop flags one
+// iteration behind the launches, so the GPU queue never drains inside a cycle.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mca_internal.cuh"
+#include "precond_tc.h"
+
+namespace mca {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+static void set_error(const char* msg) { g_last_error = msg; }
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace mca
+
+using namespace mca;
+
+struct mca_handle {
+  mca_params p;
+  Grid gr;
+  int m = 0, n = 0, mp = 0, np = 0;
+  size_t mn = 0, n2 = 0;
+  int restart = 30;
+  int Bmax = 1;
+  int device = 0;
+  // crossbar + eigenbasis (FP64)
+  double* g = nullptr;
+  double *mu = nullptr, *nu = nullptr, *Qr = nullptr, *Qc = nullptr, *QrT = nullptr,
+         *QcT = nullptr;
+  // BF16 copies (padded)
+  __nv_bfloat16 *QrT_bf = nullptr, *QcT_bf = nullptr, *Qr_hi = nullptr, *Qr_lo = nullptr,
+                *Qc_hi = nullptr, *Qc_lo = nullptr;
+  // workspace
+  double *x = nullptr, *F = nullptr, *D = nullptr, *V = nullptr, *Z = nullptr, *W = nullptr;
+  double *part = nullptr, *h1 = nullptr, *h2 = nullptr;
+  double *vin = nullptr, *iout = nullptr, *kcl = nullptr;
+  VecCtl* ctl = nullptr;
+  int32_t* hflags = nullptr;      // pinned, mapped
+  int32_t* hflags_dev = nullptr;
+  int* err = nullptr;
+  double *T1_64 = nullptr, *Xh_64 = nullptr, *E_64 = nullptr;
+  __nv_bfloat16 *Xbf = nullptr, *T1bf = nullptr, *Yh = nullptr, *Yl = nullptr, *Eh = nullptr,
+                *El = nullptr;
+  bool tc_ok = false;
+  CUtensorMap mA1, mA2, mA3h, mA3l, mA4h, mA4l;           // A operands
+  CUtensorMap mB1[2], mB2[2], mB3h[2], mB3l[2], mB4h[2], mB4l[2];  // B operands, BN 128/64
+  int bn[4] = {128, 128, 128, 128};
+  std::vector<void*> allocs;
+  cudaEvent_t ev[MCA_KMAX + 1];
+  bool ev_ok = false;
+  // statistics of the last solve pass (host copies)
+  std::vector<VecCtl> ctl_host;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(mca_handle* h, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return MCA_OK;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return MCA_ERR_OOM;
+  }
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return MCA_OK;
+}
+
+#define MCA_TRY(expr)               \
+  do {                              \
+    int _rc = (expr);               \
+    if (_rc != MCA_OK) return _rc;  \
+  } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int validate(const mca_params* p) {
+  if (!p) return MCA_ERR_INVALID_ARG;
+  if (p->rows < 1 || p->cols < 1 || p->rows > 16384 || p->cols > 16384) {
+    set_error("rows/cols must be in 1..16384");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (!finite_pos(p->g_wire_top) || !finite_pos(p->g_wire_bot) || !finite_pos(p->g_src) ||
+      !finite_pos(p->g_term_top_right) || !finite_pos(p->g_term_bot_top) ||
+      !finite_pos(p->g_sense)) {
+    set_error("wire and termination conductances must be finite and > 0");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (!std::isfinite(p->b) || p->b < 0.0) {
+    set_error("b must be finite and >= 0");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (p->precision < MCA_PREC_FP64 || p->precision > MCA_PREC_BF16_SPLIT) {
+    set_error("unknown precision");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (p->gmres_restart < 1 || p->gmres_restart > MCA_KMAX || p->max_newton < 1 ||
+      p->max_batch < 1 || p->max_batch > 64) {
+    set_error("gmres_restart in 1..30, max_newton >= 1, max_batch in 1..64");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (!(p->newton_rtol > 0.0) || !(p->eta0 > 0.0) || !(p->eta_max > 0.0)) {
+    set_error("tolerances must be > 0");
+    return MCA_ERR_INVALID_ARG;
+  }
+  return MCA_OK;
+}
+
+int setup_tc(mca_handle* h) {
+  if (!tc::encode_available()) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return MCA_ERR_UNSUPPORTED;
+  }
+  const size_t B = h->Bmax, mp = h->mp, np = h->np;
+  MCA_TRY(dalloc(h, &h->Xbf, B * 2 * mp * np));
+  MCA_TRY(dalloc(h, &h->T1bf, B * 2 * np * mp));
+  MCA_TRY(dalloc(h, &h->Yh, B * 2 * mp * np));
+  MCA_TRY(dalloc(h, &h->Yl, B * 2 * mp * np));
+  MCA_TRY(dalloc(h, &h->Eh, B * 2 * np * mp));
+  MCA_TRY(dalloc(h, &h->El, B * 2 * np * mp));
+  MCA_CUDA_TRY(cudaMemset(h->Xbf, 0, B * 2 * mp * np * sizeof(__nv_bfloat16)));
+  bool ok = true;
+  ok &= tc::make_map(&h->mA1, h->Xbf, B * 2 * mp, np, 128);
+  ok &= tc::make_map(&h->mA2, h->T1bf, B * 2 * np, mp, 128);
+  ok &= tc::make_map(&h->mA3h, h->Yh, B * 2 * mp, np, 128);
+  ok &= tc::make_map(&h->mA3l, h->Yl, B * 2 * mp, np, 128);
+  ok &= tc::make_map(&h->mA4h, h->Eh, B * 2 * np, mp, 128);
+  ok &= tc::make_map(&h->mA4l, h->El, B * 2 * np, mp, 128);
+  const uint32_t bns[2] = {128, 64};
+  for (int q = 0; q < 2; ++q) {
+    ok &= tc::make_map(&h->mB1[q], h->QrT_bf, np, np, bns[q]);
+    ok &= tc::make_map(&h->mB2[q], h->QcT_bf, mp, mp, bns[q]);
+    ok &= tc::make_map(&h->mB3h[q], h->Qr_hi, np, np, bns[q]);
+    ok &= tc::make_map(&h->mB3l[q], h->Qr_lo, np, np, bns[q]);
+    ok &= tc::make_map(&h->mB4h[q], h->Qc_hi, mp, mp, bns[q]);
+    ok &= tc::make_map(&h->mB4l[q], h->Qc_lo, mp, mp, bns[q]);
+  }
+  if (!ok) {
+    set_error("tensor map encoding failed");
+    return MCA_ERR_UNSUPPORTED;
+  }
+  // tile width: 64 columns when 128 would leave most SMs idle
+  const int R[4] = {h->mp, h->np, h->mp, h->np};
+  const int C[4] = {h->np, h->mp, h->np, h->mp};
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  for (int s = 0; s < 4; ++s) {
+    const long ctas128 = (long)(R[s] / 128) * (C[s] / 128) * h->Bmax;
+    h->bn[s] = (ctas128 < sms) ? 64 : 128;
+  }
+  h->tc_ok = true;
+  return MCA_OK;
+}
+
+int alloc_workspace(mca_handle* h) {
+  const size_t B = h->Bmax, n2 = h->n2, mn = h->mn;
+  const size_t kv = h->restart + 1;
+  MCA_TRY(dalloc(h, &h->x, B * n2));
+  MCA_TRY(dalloc(h, &h->F, B * n2));
+  MCA_TRY(dalloc(h, &h->D, B * mn));
+  MCA_TRY(dalloc(h, &h->V, B * kv * n2));
+  MCA_TRY(dalloc(h, &h->Z, B * h->restart * n2));
+  MCA_TRY(dalloc(h, &h->W, B * n2));
+  MCA_TRY(dalloc(h, &h->part, B * 32 * MCA_NPART));
+  MCA_TRY(dalloc(h, &h->h1, B * 32));
+  MCA_TRY(dalloc(h, &h->h2, B * 32));
+  MCA_TRY(dalloc(h, &h->vin, B * h->m));
+  MCA_TRY(dalloc(h, &h->iout, B * h->n));
+  MCA_TRY(dalloc(h, &h->kcl, B));
+  MCA_TRY(dalloc(h, &h->ctl, B));
+  MCA_TRY(dalloc(h, &h->err, 1));
+  MCA_CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+  MCA_CUDA_TRY(cudaMemset(h->ctl, 0, B * sizeof(VecCtl)));
+  if (h->p.precision == MCA_PREC_FP64) {
+    MCA_TRY(dalloc(h, &h->T1_64, B * n2));
+    MCA_TRY(dalloc(h, &h->Xh_64, B * n2));
+    MCA_TRY(dalloc(h, &h->E_64, B * n2));
+  }
+  MCA_CUDA_TRY(cudaHostAlloc(&h->hflags, 64 * sizeof(int32_t), cudaHostAllocMapped));
+  MCA_CUDA_TRY(cudaHostGetDevicePointer(&h->hflags_dev, h->hflags, 0));
+  for (int k = 0; k <= MCA_KMAX; ++k)
+    MCA_CUDA_TRY(cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming));
+  h->ev_ok = true;
+  h->ctl_host.resize(B);
+  return MCA_OK;
+}
+
+// z = P^-1 r for B vectors: r at rin + b*rstride, z at zout + b*zstride.  For the
+// tensor-core forms the BF16 copy of r must already be in h->Xbf.
+int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstride,
+                  double* zout, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s) {
+  const int m = h->m, n = h->n;
+  const size_t mn = h->mn;
+  if (precision == MCA_PREC_FP64) {
+    if (!h->T1_64) return MCA_ERR_UNSUPPORTED;
+    BlkAddr a1{rstride, mn, (size_t)n}, o1{2 * mn, mn, (size_t)m};
+    launch_gemm64_tstore(rin, a1, h->QrT, h->T1_64, o1, B, m, n, n, ctl, s);
+    BlkAddr a2{2 * mn, mn, (size_t)m}, o2{2 * mn, mn, (size_t)n};
+    launch_gemm64_tstore(h->T1_64, a2, h->QcT, h->Xh_64, o2, B, n, m, m, ctl, s);
+    launch_modes_2x2_f64(h->Xh_64, h->mu, h->nu, m, n, ctl, B, s);
+    BlkAddr a3{2 * mn, mn, (size_t)n}, o3{2 * mn, mn, (size_t)m};
+    launch_gemm64_tstore(h->Xh_64, a3, h->Qr, h->E_64, o3, B, m, n, n, ctl, s);
+    BlkAddr a4{2 * mn, mn, (size_t)m}, o4{zstride, mn, (size_t)n};
+    launch_gemm64_tstore(h->E_64, a4, h->Qc, zout, o4, B, n, m, m, ctl, s);
+    MCA_CUDA_TRY(cudaGetLastError());
+    return MCA_OK;
+  }
+  if (!h->tc_ok) return MCA_ERR_UNSUPPORTED;
+  const bool split = (precision == MCA_PREC_BF16_SPLIT);
+  const size_t mp = h->mp, np = h->np;
+  auto q = [](int bn) { return bn == 128 ? 0 : 1; };
+  tc::GemmEpi e{};
+  e.ctl = ctl;
+  e.err = h->err;
+  // 1: T1^T = (X Q_r)^T
+  e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
+  e.out = h->T1bf; e.out_lo = nullptr; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
+  MCA_CUDA_TRY(tc::gemm(h->bn[0], false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(h->bn[0])],
+                        h->mB1[q(h->bn[0])], e, B, s));
+  // 2: Y_hat = modes^-1 (Q_c^T T1), stored [i'][k']
+  e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
+  e.out = h->Yh; e.out_lo = h->Yl; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
+  e.mu = h->mu; e.nu = h->nu;
+  MCA_CUDA_TRY(tc::gemm(h->bn[1], false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2,
+                        h->mA2, h->mB2[q(h->bn[1])], h->mB2[q(h->bn[1])], e, B, s));
+  // 3: E^T = (Y_hat Q_r^T)^T
+  e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
+  e.out = h->Eh; e.out_lo = h->El; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
+  MCA_CUDA_TRY(tc::gemm(h->bn[2], split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h,
+                        h->mA3l, h->mB3h[q(h->bn[2])], h->mB3l[q(h->bn[2])], e, B, s));
+  // 4: Z = (E^T Q_c^T)^T, FP64 unpadded
+  e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
+  e.out = zout; e.out_lo = nullptr; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
+  MCA_CUDA_TRY(tc::gemm(h->bn[3], split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(h->bn[3])],
+                        h->mB4l[q(h->bn[3])], e, B, s));
+  return MCA_OK;
+}
+
+SolverCfg make_cfg(const mca_handle* h) {
+  SolverCfg c;
+  c.newton_rtol = h->p.newton_rtol;
+  c.eta0 = h->p.eta0;
+  c.eta_max = h->p.eta_max;
+  c.max_newton = h->p.max_newton;
+  c.restart = h->restart;
+  return c;
+}
+
+bool any_flag(const mca_handle* h, int B) {
+  for (int b = 0; b < B; ++b)
+    if (reinterpret_cast<volatile int32_t*>(h->hflags)[b]) return true;
+  return false;
+}
+
+// One flexible GMRES cycle on the vectors whose gm_active flag is set; V[b][0] and its
+// BF16 copy are already in place.
+int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
+  const size_t n2 = h->n2;
+  const size_t vstride = (size_t)(h->restart + 1) * n2;
+  const size_t zstride = (size_t)h->restart * n2;
+  const int nbS = residual_nblk((int)h->mn);
+  const int nbV = vec_nblk(n2);
+  const bool tc = h->p.precision != MCA_PREC_FP64;
+  for (int k = 0; k < h->restart; ++k) {
+    const double* vk = h->V + (size_t)k * n2;
+    double* zk = h->Z + (size_t)k * n2;
+    // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
+    MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s));
+    launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
+                     h->ctl, s);
+    launch_reduce_dots(h->part, nbS, k + 1, h->h1, B, h->ctl, s);
+    launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, s);
+    launch_reduce_dots(h->part, nbV, k + 1, h->h2, B, h->ctl, s);
+    launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, s);
+    launch_givens(h->part, nbV, h->h1, h->h2, k, h->restart, h->ctl, B, h->hflags_dev, s);
+    launch_normalize(h->W, h->V + (size_t)(k + 1) * n2, vstride, n2, tc ? h->Xbf : nullptr,
+                     h->mp, h->np, h->m, h->n, h->ctl, B, s);
+    MCA_CUDA_TRY(cudaGetLastError());
+    MCA_CUDA_TRY(cudaEventRecord(h->ev[k], s));
+    if (k >= 1) {
+      MCA_CUDA_TRY(cudaEventSynchronize(h->ev[k - 1]));
+      if (!any_flag(h, B)) break;
+    }
+  }
+  return MCA_OK;
+}
+
+int check_device_error(mca_handle* h) {
+  int e = 0;
+  MCA_CUDA_TRY(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    cudaMemset(h->err, 0, sizeof(int));
+    set_error("a bounded device wait expired");
+    return e;
+  }
+  return MCA_OK;
+}
+
+// Solve B <= Bmax vectors whose inputs are in h->vin; results stay in h->x / h->iout.
+int solve_pass(mca_handle* h, int B, cudaStream_t s) {
+  const SolverCfg cfg = make_cfg(h);
+  const int nbR = residual_nblk((int)h->mn);
+  const bool tc = h->p.precision != MCA_PREC_FP64;
+  const size_t vstride = (size_t)(h->restart + 1) * h->n2;
+  const size_t zstride = (size_t)h->restart * h->n2;
+  launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
+  MCA_CUDA_TRY(cudaMemsetAsync(h->x, 0, (size_t)B * h->n2 * sizeof(double), s));
+  for (int it = 0; it <= h->p.max_newton; ++it) {
+    launch_residual(h->gr, h->g, h->vin, h->x, h->F, h->D, h->part, nbR, B, h->ctl, s);
+    launch_newton_control(h->part, nbR, (int)h->mn, h->ctl, B, cfg, h->hflags_dev, s);
+    MCA_CUDA_TRY(cudaGetLastError());
+    MCA_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!any_flag(h, B)) break;
+    launch_init_basis(h->F, -1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
+                      h->n, h->ctl, B, s);
+    MCA_TRY(gmres_cycle(h, h->D, B, s));
+    launch_lsq_update(h->x, h->Z, zstride, h->n2, h->ctl, B, s);
+    MCA_CUDA_TRY(cudaGetLastError());
+  }
+  launch_outputs(h->gr, h->vin, h->x, h->iout, h->kcl, B, s);
+  MCA_CUDA_TRY(cudaGetLastError());
+  MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
+                               cudaMemcpyDeviceToHost, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return check_device_error(h);
+}
+
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!dst || bytes == 0) return MCA_OK;
+  MCA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+  return MCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mca_default_params(mca_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->g_wire_top = 1.0;
+  p->g_wire_bot = 1.0;
+  p->g_src = 0.1;
+  p->g_term_top_right = 1e-3;
+  p->g_term_bot_top = 1e-3;
+  p->g_sense = 0.1;
+  p->b = 2.0;
+  p->precision = MCA_PREC_BF16_SPLIT;
+  p->gmres_restart = 30;
+  p->max_newton = 20;
+  p->max_batch = 4;
+  p->newton_rtol = 1e-8;
+  p->eta0 = 1e-4;
+  p->eta_max = 1e-2;
+}
+
+const char* mca_strerror(int code) {
+  switch (code) {
+    case MCA_OK: return "ok";
+    case MCA_ERR_INVALID_ARG: return "invalid argument";
+    case MCA_ERR_CUDA: return "CUDA runtime error";
+    case MCA_ERR_NONFINITE: return "non-finite value in inputs or residual";
+    case MCA_ERR_NOT_CONVERGED: return "Newton did not reach the tolerance";
+    case MCA_ERR_TIMEOUT: return "bounded device wait expired";
+    case MCA_ERR_OOM: return "device memory allocation failed";
+    case MCA_ERR_UNSUPPORTED: return "unsupported on this device";
+    default: return "unknown status";
+  }
+}
+
+const char* mca_last_error_message(void) { return g_last_error.c_str(); }
+
+void mca_destroy(mca_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  for (void* q : h->allocs) cudaFree(q);
+  if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->ev_ok)
+    for (int k = 0; k <= MCA_KMAX; ++k) cudaEventDestroy(h->ev[k]);
+  delete h;
+}
+
+int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
+  g_last_error.clear();
+  if (!out || !g_map) {
+    set_error("NULL argument");
+    return MCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc != MCA_OK) return rc;
+  mca_handle* h = new mca_handle();
+  h->p = *p;
+  cudaGetDevice(&h->device);
+  h->m = p->rows;
+  h->n = p->cols;
+  h->mp = (int)round_up(h->m, 128);
+  h->np = (int)round_up(h->n, 128);
+  h->mn = (size_t)h->m * h->n;
+  h->n2 = 2 * h->mn;
+  h->restart = p->gmres_restart;
+  h->Bmax = p->max_batch;
+  h->gr.m = h->m;
+  h->gr.n = h->n;
+  h->gr.gt = p->g_wire_top;
+  h->gr.gb = p->g_wire_bot;
+  h->gr.g_src = p->g_src;
+  h->gr.g_tr = p->g_term_top_right;
+  h->gr.g_bt = p->g_term_bot_top;
+  h->gr.g_sense = p->g_sense;
+  h->gr.b = p->b;
+  auto fail = [&](int code) {
+    mca_destroy(h);
+    return code;
+  };
+  // conductance map: copy and validate on the host
+  std::vector<double> gh(h->mn);
+  if (cudaMemcpy(gh.data(), g_map, h->mn * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cannot read g_map");
+    return fail(MCA_ERR_INVALID_ARG);
+  }
+  for (size_t i = 0; i < h->mn; ++i) {
+    if (!std::isfinite(gh[i])) {
+      set_error("g_map has a non-finite entry");
+      return fail(MCA_ERR_NONFINITE);
+    }
+    if (!(gh[i] > 0.0)) {
+      set_error("g_map entries must be > 0");
+      return fail(MCA_ERR_INVALID_ARG);
+    }
+  }
+  if ((rc = dalloc(h, &h->g, h->mn)) != MCA_OK) return fail(rc);
+  if (cudaMemcpy(h->g, gh.data(), h->mn * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MCA_ERR_CUDA);
+  // eigenpairs of the two wire operators
+  const size_t nn = (size_t)h->n * h->n, mm = (size_t)h->m * h->m;
+  double* scratch = nullptr;
+  if ((rc = dalloc(h, &h->mu, h->n)) || (rc = dalloc(h, &h->nu, h->m)) ||
+      (rc = dalloc(h, &h->Qr, nn)) || (rc = dalloc(h, &h->Qc, mm)) ||
+      (rc = dalloc(h, &h->QrT, nn)) || (rc = dalloc(h, &h->QcT, mm)) ||
+      (rc = dalloc(h, &scratch, std::max(nn, mm))))
+    return fail(rc);
+  cudaStream_t s = 0;
+  launch_eig_tridiag(h->n, p->g_wire_top, p->g_src, p->g_term_top_right, h->mu, h->Qr,
+                     scratch, s);
+  launch_eig_tridiag(h->m, p->g_wire_bot, p->g_term_bot_top, p->g_sense, h->nu, h->Qc,
+                     scratch, s);
+  launch_transpose64(h->Qr, h->n, h->QrT, s);
+  launch_transpose64(h->Qc, h->m, h->QcT, s);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("eigen setup kernels failed");
+    return fail(MCA_ERR_CUDA);
+  }
+  if (p->precision != MCA_PREC_FP64) {
+    const size_t npp = (size_t)h->np * h->np, mpp = (size_t)h->mp * h->mp;
+    if ((rc = dalloc(h, &h->QrT_bf, npp)) || (rc = dalloc(h, &h->QcT_bf, mpp)) ||
+        (rc = dalloc(h, &h->Qr_hi, npp)) || (rc = dalloc(h, &h->Qr_lo, npp)) ||
+        (rc = dalloc(h, &h->Qc_hi, mpp)) || (rc = dalloc(h, &h->Qc_lo, mpp)))
+      return fail(rc);
+    launch_pack_q_bf16(h->Qr, h->n, h->np, h->Qr_hi, h->Qr_lo, h->QrT_bf, s);
+    launch_pack_q_bf16(h->Qc, h->m, h->mp, h->Qc_hi, h->Qc_lo, h->QcT_bf, s);
+    if (cudaGetLastError() != cudaSuccess) return fail(MCA_ERR_CUDA);
+  }
+  if ((rc = alloc_workspace(h)) != MCA_OK) return fail(rc);
+  if (p->precision != MCA_PREC_FP64) {
+    if ((rc = setup_tc(h)) != MCA_OK) return fail(rc);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("create failed");
+    return fail(MCA_ERR_CUDA);
+  }
+  *out = h;
+  return MCA_OK;
+}
+
+int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, double* v_bot,
+              double* i_out, mca_stats* stats, void* stream) {
+  g_last_error.clear();
+  if (!h || !v_in || nvec < 0) {
+    set_error("NULL handle/input or negative nvec");
+    return MCA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t m = h->m, n = h->n, mn = h->mn;
+  int worst = MCA_OK;
+  for (int v0 = 0; v0 < nvec; v0 += h->Bmax) {
+    const int B = std::min(h->Bmax, nvec - v0);
+    MCA_CUDA_TRY(cudaMemcpyAsync(h->vin, v_in + (size_t)v0 * m, (size_t)B * m * sizeof(double),
+                                 cudaMemcpyDefault, s));
+    int rc = solve_pass(h, B, s);
+    if (rc != MCA_OK) return rc;
+    for (int b = 0; b < B; ++b) {
+      const double* xb = h->x + (size_t)b * h->n2;
+      MCA_TRY(copy_out(v_top ? v_top + (size_t)(v0 + b) * mn : nullptr, xb, mn * sizeof(double), s));
+      MCA_TRY(copy_out(v_bot ? v_bot + (size_t)(v0 + b) * mn : nullptr, xb + mn,
+                       mn * sizeof(double), s));
+    }
+    MCA_TRY(copy_out(i_out ? i_out + (size_t)v0 * n : nullptr, h->iout,
+                     (size_t)B * n * sizeof(double), s));
+    std::vector<double> kcl(B);
+    MCA_CUDA_TRY(cudaMemcpyAsync(kcl.data(), h->kcl, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MCA_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b) {
+      const VecCtl& c = h->ctl_host[b];
+      if (c.status != MCA_OK && worst == MCA_OK) worst = c.status;
+      if (stats) {
+        mca_stats& st = stats[v0 + b];
+        st.status = c.status;
+        st.newton_iters = c.newton_iters;
+        st.gmres_iters = c.gmres_iters;
+        st.reserved = 0;
+        st.rel_residual = (c.ynorm > 0.0) ? c.fnorm / c.ynorm : 0.0;
+        st.kcl_rel_error = kcl[b];
+      }
+    }
+  }
+  return worst;
+}
+
+int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nvec, double* F,
+                 double* D, double* fnorm, double* dmean, void* stream) {
+  g_last_error.clear();
+  if (!h || !x || !v_in || !F || !D || nvec < 1 || nvec > h->Bmax) {
+    set_error("bad arguments (nvec must be in 1..max_batch)");
+    return MCA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = residual_nblk((int)h->mn);
+  launch_residual(h->gr, h->g, v_in, x, F, D, h->part, nb, nvec, nullptr, s);
+  launch_reduce_dots(h->part, nb, 2, h->h1, nvec, nullptr, s);
+  MCA_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hh((size_t)nvec * 32);
+  MCA_CUDA_TRY(cudaMemcpyAsync(hh.data(), h->h1, hh.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int b = 0; b < nvec; ++b) {
+    if (fnorm) fnorm[b] = std::sqrt(hh[(size_t)b * 32]);
+    if (dmean) dmean[b] = hh[(size_t)b * 32 + 1] / (double)h->mn;
+  }
+  return MCA_OK;
+}
+
+int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* w, int32_t nvec,
+                       void* stream) {
+  g_last_error.clear();
+  if (!h || !D || !z || !w || nvec < 1 || nvec > h->Bmax) {
+    set_error("bad arguments (nvec must be in 1..max_batch)");
+    return MCA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  launch_spmv_dots(h->gr, D, z, h->n2, w, nullptr, 0, 0, h->part, residual_nblk((int)h->mn),
+                   nvec, nullptr, s);
+  MCA_CUDA_TRY(cudaGetLastError());
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return MCA_OK;
+}
+
+static int load_ctl_a(mca_handle* h, const double* a, int nvec, cudaStream_t s) {
+  for (int b = 0; b < nvec; ++b) {
+    if (!finite_pos(a[b])) {
+      set_error("a must be finite and > 0");
+      return MCA_ERR_INVALID_ARG;
+    }
+    VecCtl& c = h->ctl_host[b];
+    memset(&c, 0, sizeof(VecCtl));
+    c.a = a[b];
+    c.gm_active = 1;
+    c.newton_active = 1;
+  }
+  MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl, h->ctl_host.data(), (size_t)nvec * sizeof(VecCtl),
+                               cudaMemcpyHostToDevice, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return MCA_OK;
+}
+
+int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z, int32_t nvec,
+                      int32_t precision, void* stream) {
+  g_last_error.clear();
+  if (!h || !a || !r || !z || nvec < 1 || nvec > h->Bmax) {
+    set_error("bad arguments (nvec must be in 1..max_batch)");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (precision != h->p.precision &&
+      !(precision != MCA_PREC_FP64 && h->p.precision != MCA_PREC_FP64)) {
+    set_error("precision not prepared by this handle");
+    return MCA_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MCA_TRY(load_ctl_a(h, a, nvec, s));
+  if (precision != MCA_PREC_FP64)
+    tc::cast_pad(r, h->n2, h->Xbf, h->m, h->n, h->mp, h->np, nvec, s);
+  MCA_TRY(precond_apply(h, precision, r, h->n2, z, h->n2, nvec, h->ctl, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return check_device_error(h);
+}
+
+int mca_eigenpairs(mca_handle* h, double* mu, double* q_r, double* nu, double* q_c) {
+  g_last_error.clear();
+  if (!h) return MCA_ERR_INVALID_ARG;
+  const size_t nn = (size_t)h->n * h->n, mm = (size_t)h->m * h->m;
+  if (mu) MCA_CUDA_TRY(cudaMemcpy(mu, h->mu, h->n * sizeof(double), cudaMemcpyDefault));
+  if (q_r) MCA_CUDA_TRY(cudaMemcpy(q_r, h->Qr, nn * sizeof(double), cudaMemcpyDefault));
+  if (nu) MCA_CUDA_TRY(cudaMemcpy(nu, h->nu, h->m * sizeof(double), cudaMemcpyDefault));
+  if (q_c) MCA_CUDA_TRY(cudaMemcpy(q_c, h->Qc, mm * sizeof(double), cudaMemcpyDefault));
+  return MCA_OK;
+}
+
+int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const double* rhs,
+                    double* dx, int32_t nvec, double rtol, int32_t* iters, double* res,
+                    void* stream) {
+  g_last_error.clear();
+  if (!h || !D || !a || !rhs || !dx || nvec < 1 || nvec > h->Bmax || !(rtol > 0.0)) {
+    set_error("bad arguments (nvec must be in 1..max_batch, rtol > 0)");
+    return MCA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n2 = h->n2;
+  const size_t vstride = (size_t)(h->restart + 1) * n2;
+  const size_t zstride = (size_t)h->restart * n2;
+  const bool tc = h->p.precision != MCA_PREC_FP64;
+  MCA_TRY(load_ctl_a(h, a, nvec, s));
+  // beta = ||rhs||, v_0 = rhs / beta
+  const int nbV = vec_nblk(n2);
+  MCA_CUDA_TRY(cudaMemcpyAsync(h->F, rhs, (size_t)nvec * n2 * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+  MCA_CUDA_TRY(cudaMemcpyAsync(h->W, rhs, (size_t)nvec * n2 * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+  launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, s);
+  launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, s);
+  launch_init_basis(h->F, 1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m, h->n,
+                    h->ctl, nvec, s);
+  MCA_TRY(gmres_cycle(h, D, nvec, s));
+  MCA_CUDA_TRY(cudaMemsetAsync(dx, 0, (size_t)nvec * n2 * sizeof(double), s));
+  launch_lsq_update(dx, h->Z, zstride, n2, h->ctl, nvec, s);
+  MCA_CUDA_TRY(cudaGetLastError());
+  MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)nvec * sizeof(VecCtl),
+                               cudaMemcpyDeviceToHost, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int b = 0; b < nvec; ++b) {
+    if (iters) iters[b] = h->ctl_host[b].k_done;
+    if (res) res[b] = h->ctl_host[b].res_est;
+  }
+  return check_device_error(h);
+}
+
+}  // extern "C"

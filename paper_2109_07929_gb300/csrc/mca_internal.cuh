@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of the crossbar solver.
+//
+// Data layout (device, FP64 unless noted):
+//   one solve vector  x = [V_t ; V_b], each layer m x n row-major (cell (i,j) at i*n+j),
+//   so a vector holds N2 = 2*m*n doubles; a batch of B vectors is contiguous [b][N2].
+//   D (device conductance g*cosh(b dV), the diagonal of the Jacobian's device blocks)
+//   is [b][m*n].
+// Krylov storage for flexible GMRES(restart): V[b][j][N2] (j = 0..restart) and
+// Z[b][j][N2] (j = 0..restart-1).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+#include "../../include/mca.h"
+
+#define MCA_KMAX 30            // largest GMRES restart length
+#define MCA_NPART 1024         // max per-vector partial sums of a reduction kernel
+
+namespace mca {
+
+// Per-vector solver control block, written by the control kernels and read by every
+// iteration kernel (vectors whose flags are cleared skip their work).
+struct VecCtl {
+  double ynorm;        // ||Y||_2
+  double fnorm;        // ||F||_2 at the current Newton iterate
+  double fnorm_prev;   // ||F||_2 at the previous Newton iterate
+  double a;            // a1 = a2 = mean(D)
+  double eta;          // forcing term of the current linear solve
+  double tol_abs;      // GMRES stop: ||r|| <= tol_abs
+  double inv_h;        // 1 / h_{k+1,k} for the basis normalisation
+  double res_est;      // Givens residual estimate |g_{k+1}|
+  int32_t newton_active;
+  int32_t status;
+  int32_t newton_iters;
+  int32_t gmres_iters;
+  int32_t gm_active;   // GMRES cycle running
+  int32_t k_done;      // columns finished in this cycle
+  int32_t pad0, pad1;
+  double H[(MCA_KMAX + 1) * MCA_KMAX];   // column k at H[k*(KMAX+1) + row]
+  double cs[MCA_KMAX];
+  double sn[MCA_KMAX];
+  double g[MCA_KMAX + 1];
+  double y[MCA_KMAX];
+};
+
+// Scalars of one crossbar needed by the stencil kernels.
+struct Grid {
+  int m, n;                 // rows, cols
+  double gt, gb;            // wire segment conductances (top rows, bottom columns)
+  double g_src, g_tr;       // top-row ends: source (j = 0), termination (j = n-1)
+  double g_bt, g_sense;     // bottom-column ends: termination (i = 0), sense (i = m-1)
+  double b;                 // sinh nonlinearity (0 = linear device)
+};
+
+struct SolverCfg {
+  double newton_rtol;
+  double eta0;
+  double eta_max;
+  int max_newton;
+  int restart;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- kernels (launchers)
+// stencil / residual / Jacobian (k_stencil.cu)
+void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
+                          cudaStream_t s);
+void launch_residual(const Grid& gr, const double* gmap, const double* vin, const double* x,
+                     double* F, double* D, double* part, int nblk, int B, const VecCtl* ctl,
+                     cudaStream_t s);
+void launch_newton_control(const double* part, int nblk, int mn, VecCtl* ctl, int B,
+                           SolverCfg cfg, int32_t* host_flags, cudaStream_t s);
+void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
+                       __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
+                       int B, cudaStream_t s);
+void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t zstride,
+                      double* w, const double* V, size_t vstride, int nk, double* part,
+                      int nblk, int B, const VecCtl* ctl, cudaStream_t s);
+void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,
+                    double* kcl, int B, cudaStream_t s);
+int residual_nblk(int mn);
+// Krylov (k_krylov.cu)
+int vec_nblk(size_t n2);
+void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
+                        const VecCtl* ctl, cudaStream_t s);
+void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, int nk,
+                        const double* h, double* part, int nblk, int B, const VecCtl* ctl,
+                        cudaStream_t s);
+void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
+                        const double* h, double* part, int nblk, int B, const VecCtl* ctl,
+                        cudaStream_t s);
+void launch_givens(const double* part_norm, int nblk, const double* h1, const double* h2,
+                   int k, int restart, VecCtl* ctl, int B, int32_t* host_flags,
+                   cudaStream_t s);
+void launch_normalize(const double* w, double* vnext, size_t vstride, size_t n2,
+                      __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
+                      int B, cudaStream_t s);
+void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
+                       int B, cudaStream_t s);
+void launch_gmres_init(const double* part_norm, int nblk, VecCtl* ctl, int B, double rtol,
+                       cudaStream_t s);
+// eigen setup (k_eig.cu)
+void launch_eig_tridiag(int n, double g, double g_first, double g_last, double* lam,
+                        double* Q, double* scratch, cudaStream_t s);
+void launch_pack_q_bf16(const double* Q, int n, int npad, __nv_bfloat16* out_q,
+                        __nv_bfloat16* out_q_lo, __nv_bfloat16* out_qt, cudaStream_t s);
+void launch_transpose64(const double* Q, int n, double* QT, cudaStream_t s);
+// FP64 preconditioner (k_precond64.cu)
+// Block-transposed GEMM used by all four eigenbasis transforms:
+//   O[blk][c][r] = sum_k A[blk][r][k] * Bm[c][k]   (r < R, c < C, k < K)
+// with blk = 2*b + layer; A block blk starts at A + b*a.bs + layer*a.ls (row stride K),
+// O block blk starts at O + b*o.bs + layer*o.ls (row stride o.ld along c).
+struct BlkAddr {
+  size_t bs;   // elements between batch entries
+  size_t ls;   // elements between the two layers of one entry
+  size_t ld;   // leading dimension (A: row stride; O: stride between c)
+};
+void launch_gemm64_tstore(const double* A, BlkAddr a, const double* Bm, double* O, BlkAddr o,
+                          int B, int R, int K, int C, const VecCtl* ctl, cudaStream_t s);
+// Per-mode 2x2 inverse of eq. (P) in place on X_hat[b][layer][i'][k'] (m x n).
+void launch_modes_2x2_f64(double* Xh, const double* mu, const double* nu, int m, int n,
+                          const VecCtl* ctl, int B, cudaStream_t s);
+
+}  // namespace mca
+
+// Report the first CUDA error of a call chain as MCA_ERR_CUDA.
+#define MCA_CUDA_TRY(expr)                                 \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) {                               \
+      mca::set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return MCA_ERR_CUDA;                                 \
+    }                                                      \
+  } while (0)
+
+namespace mca {
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+}

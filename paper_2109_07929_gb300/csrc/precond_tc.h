@@ -1,0 +1,44 @@
+// Host interface of the tcgen05 preconditioner GEMM (k_precond_tc.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "mca_internal.cuh"
+
+namespace mca {
+namespace tc {
+
+enum Epi {
+  EPI_BF16 = 0,         // out = bf16(acc)
+  EPI_MODES = 1,        // out = bf16(per-mode 2x2 inverse of eq. P applied to (acc_t, acc_b))
+  EPI_SPLIT = 2,        // out = bf16(acc), out_lo = bf16(acc - out)
+  EPI_F64 = 3,          // out = (double)acc for r < R_valid, c < C_valid (unpadded)
+  EPI_MODES_SPLIT = 4,  // EPI_MODES with a hi/lo pair
+};
+
+// Output addressing: element (blk = 2b + layer, c, r) is written to
+//   out[b*o_bs + layer*o_ls + c*o_ld + r].
+struct GemmEpi {
+  int R, K, C;              // padded extents: rows per block (x128), K (x64), cols (xBN)
+  int R_valid, C_valid;     // logical extents
+  void* out;
+  void* out_lo;
+  size_t o_bs, o_ls, o_ld;
+  const double* mu;         // eigenvalue per r (EPI_MODES*)
+  const double* nu;         // eigenvalue per c (EPI_MODES*)
+  const VecCtl* ctl;        // per-vector a and activity flag (NULL: all active)
+  int* err;                 // device status flag (MCA_ERR_TIMEOUT on an expired wait)
+};
+
+bool encode_available();
+bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
+              uint32_t box_rows);
+cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
+                 const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
+                 cudaStream_t s);
+void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
+              int np, int B, cudaStream_t s);
+
+}  // namespace tc
+}  // namespace mca

@@ -1,0 +1,294 @@
+"""GPU parity of every step of the solve against the CPU FP64 oracle, through the C ABI.
+
+Tolerances:
+* FP64 kernels (residual, Jacobian apply, eigenpairs, FP64 preconditioner, GMRES): FP64
+  rounding, scaled by the magnitude of the terms that cancel.
+* Whole solves: relative KCL residual <= the requested tolerance (recomputed here by the
+  oracle's own residual) and node-voltage max relative error <= 1e-7 against the oracle
+  solution, both solved tight.
+* Tensor-core preconditioner: BF16 operands (unit roundoff 2^-9) with FP32 accumulation;
+  the forward transforms carry a relative error of a few 1e-3 in the mode coefficients,
+  so z agrees with the FP64 oracle to 3e-2 in relative 2-norm (a transposed or misplaced
+  tile gives O(1) errors).
+"""
+import numpy as np
+import pytest
+
+import mca_inputs as mi
+from oracle import mca_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2109_07929_gb300 as mca  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _params(p, **kw):
+    base = dict(g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot, g_src=p.g_src,
+                g_term_top_right=p.g_term_top_right, g_term_bot_top=p.g_term_bot_top,
+                g_sense=p.g_sense, b=p.b)
+    base.update(kw)
+    return mca.default_params(p.rows, p.cols, **base)
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+SHAPES = [(1, 1), (1, 9), (7, 1), (33, 47), (64, 64), (130, 70)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES + [(257, 129)])
+def test_eigenpairs(m, n):
+    cb = mi.make_crossbar(m, n, 1, g_wire_bot=0.5)
+    with mca.Solver(_params(cb.params, precision=mca.PREC_FP64, max_batch=1), cb.gmap) as s:
+        mu, qr, nu, qc = s.eigenpairs()
+    mu_r, qr_r, nu_r, qc_r = O.eig_setup(cb.params)
+    for lam, Q, lam_r, Q_r in ((mu, qr, mu_r, qr_r), (nu, qc, nu_r, qc_r)):
+        k = lam.size
+        np.testing.assert_allclose(lam, lam_r, rtol=0, atol=5e-15 * np.abs(lam_r).max())
+        sign = np.sign(np.sum(Q * Q_r, axis=0))
+        np.testing.assert_allclose(Q * sign[None, :], Q_r, atol=1e-9)
+        np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-10)
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_residual_and_jacobian_diagonal(m, n):
+    cb = mi.make_crossbar(m, n, 2, nvec=2)
+    p = cb.params
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-0.1, 0.35, size=(2, 2 * m * n))
+    with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=2), cb.gmap) as s:
+        F = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
+        D = torch.empty(2, m * n, dtype=torch.float64, device=DEV)
+        fn, dm = s.residual(_t(x), _t(cb.vin), F, D)
+        F = F.cpu().numpy()
+        D = D.cpu().numpy()
+    Gt, Gb = O.layer_operators(p)
+    for v in range(2):
+        Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], x[v, :m * n], x[v, m * n:])
+        scale = 4 * max(p.g_wire_top, p.g_wire_bot) * np.abs(x[v]).max() + p.g_src * 0.3
+        np.testing.assert_allclose(F[v], np.concatenate([Ft, Fb]), rtol=0, atol=1e-14 * scale)
+        Dr = O.device_conductance(cb.gmap.ravel(), p.b, x[v, :m * n] - x[v, m * n:])
+        np.testing.assert_allclose(D[v], Dr, rtol=1e-14)
+        np.testing.assert_allclose(fn[v], np.linalg.norm(np.concatenate([Ft, Fb])), rtol=1e-12)
+        np.testing.assert_allclose(dm[v], Dr.mean(), rtol=1e-13)
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_jacobian_apply(m, n):
+    cb = mi.make_crossbar(m, n, 3)
+    p = cb.params
+    rng = np.random.default_rng(6)
+    xt = rng.uniform(0, 0.3, size=m * n)
+    xb = rng.uniform(0, 0.1, size=m * n)
+    z = rng.standard_normal((2, 2 * m * n))
+    Dr = O.device_conductance(cb.gmap.ravel(), p.b, xt - xb)
+    J = O.jacobian(p, cb.gmap, xt, xb)
+    with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=2), cb.gmap) as s:
+        w = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
+        s.jacobian_apply(_t(np.stack([Dr, Dr])), _t(z), w)
+        w = w.cpu().numpy()
+    for v in range(2):
+        ref = J @ z[v]
+        np.testing.assert_allclose(w[v], ref, rtol=0, atol=1e-14 * 8 * np.abs(z[v]).max())
+
+
+@pytest.mark.parametrize("m,n", SHAPES + [(256, 256)])
+def test_precond_fp64(m, n):
+    cb = mi.make_crossbar(m, n, 4, g_wire_bot=0.5)
+    p = cb.params
+    rng = np.random.default_rng(7)
+    r = rng.standard_normal((2, 2 * m * n))
+    a = np.array([2.1e-5, 7.0e-5])
+    eig = O.eig_setup(p)
+    with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=2), cb.gmap) as s:
+        z = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
+        s.precond_apply(a, _t(r), z)
+        z = z.cpu().numpy()
+    for v in range(2):
+        zt, zb = O.precond_apply_modes(eig, a[v], a[v], r[v, :m * n], r[v, m * n:], (m, n))
+        ref = np.concatenate([zt, zb])
+        assert _rel_err(z[v], ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [mca.PREC_BF16, mca.PREC_BF16_SPLIT], ids=["bf16", "bf16split"])
+@pytest.mark.parametrize("m,n", [(1, 1), (33, 47), (128, 128), (130, 70), (256, 384)])
+def test_precond_tensor_core(m, n, prec):
+    cb = mi.make_crossbar(m, n, 4, g_wire_bot=0.5)
+    p = cb.params
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal((3, 2 * m * n))
+    a = np.array([2.1e-5, 7.0e-5, 3.3e-4])
+    eig = O.eig_setup(p)
+    with mca.Solver(_params(p, precision=prec, max_batch=3), cb.gmap) as s:
+        z = torch.empty(3, 2 * m * n, dtype=torch.float64, device=DEV)
+        s.precond_apply(a, _t(r), z)
+        z = z.cpu().numpy()
+    for v in range(3):
+        zt, zb = O.precond_apply_modes(eig, a[v], a[v], r[v, :m * n], r[v, m * n:], (m, n))
+        ref = np.concatenate([zt, zb])
+        err = np.linalg.norm(z[v] - ref) / np.linalg.norm(ref)
+        assert err < 3e-2, (v, err)
+
+
+@pytest.mark.parametrize("prec", [mca.PREC_FP64, mca.PREC_BF16_SPLIT], ids=["fp64", "bf16split"])
+def test_gmres_cycle(prec):
+    cb = mi.make_crossbar(40, 56, 9)
+    p = cb.params
+    m, n = p.rows, p.cols
+    N = m * n
+    rng = np.random.default_rng(3)
+    xt = rng.uniform(0, 0.3, N)
+    xb = rng.uniform(0, 0.05, N)
+    J = O.jacobian(p, cb.gmap, xt, xb)
+    Dr = O.device_conductance(cb.gmap.ravel(), p.b, xt - xb)
+    a = Dr.mean()
+    rhs = rng.standard_normal(2 * N)
+    with mca.Solver(_params(p, precision=prec, max_batch=1), cb.gmap) as s:
+        dx = torch.empty(1, 2 * N, dtype=torch.float64, device=DEV)
+        its, res = s.gmres_solve(_t(Dr[None]), [a], _t(rhs[None]), dx, 1e-9)
+        dx = dx.cpu().numpy()[0]
+    true_res = np.linalg.norm(rhs - J @ dx)
+    assert true_res <= 1.5e-9 * np.linalg.norm(rhs)
+    np.testing.assert_allclose(res[0], true_res, rtol=1e-3, atol=1e-13 * np.linalg.norm(rhs))
+    eig = O.eig_setup(p)
+    pc = lambda v: np.concatenate(O.precond_apply_modes(eig, a, a, v[:N], v[N:], (m, n)))
+    _, its_ref, _ = O.gmres_right(lambda v: J @ v, rhs, pc, restart=30, rtol=1e-9)
+    if prec == mca.PREC_FP64:
+        assert abs(int(its[0]) - its_ref) <= 1
+    else:
+        assert its[0] <= its_ref + 4
+
+
+def _check_solve(cb, prec, tol, vtol=1e-7, nvec=None, ref_tol=1e-13):
+    p = cb.params
+    vin = cb.vin if nvec is None else cb.vin[:nvec]
+    with mca.Solver(_params(p, precision=prec, newton_rtol=tol, max_batch=min(4, len(vin))),
+                    cb.gmap) as s:
+        vt, vb, io, st = s.solve(vin)
+    for v in range(len(vin)):
+        assert st[v]["status"] == 0, st[v]
+        Ft, Fb = O.residual(p, cb.gmap, vin[v], vt[v].ravel(), vb[v].ravel())
+        Yt, _ = O.source_vector(p, vin[v])
+        rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
+        assert rel <= tol * 1.01, (v, rel)
+        np.testing.assert_allclose(st[v]["rel_residual"], rel, rtol=1e-3, atol=tol * 1e-3)
+        ref = O.newton_solve(p, cb.gmap, vin[v], tol=ref_tol, linear="direct")
+        assert _rel_err(vt[v], ref.Vt) <= vtol and _rel_err(vb[v], ref.Vb) <= vtol
+        np.testing.assert_allclose(io[v], p.g_sense * vb[v][-1], rtol=1e-15)
+        assert st[v]["kcl_rel_error"] <= 1e-6
+    return st
+
+
+@pytest.mark.parametrize("prec", [mca.PREC_FP64, mca.PREC_BF16_SPLIT, mca.PREC_BF16],
+                         ids=["fp64", "bf16split", "bf16"])
+def test_solve_small_config(prec):
+    """32x32, log-uniform g, Newton to 1e-10 (seed 0)."""
+    _check_solve(mi.config_small(0), prec, 1e-10)
+
+
+@pytest.mark.parametrize("prec", [mca.PREC_FP64, mca.PREC_BF16_SPLIT], ids=["fp64", "bf16split"])
+@pytest.mark.parametrize("m,n", [(1, 1), (1, 17), (5, 1), (33, 47), (130, 70)])
+def test_solve_ragged_shapes(m, n, prec):
+    cb = mi.make_crossbar(m, n, 11, nvec=3, g_wire_bot=0.5)
+    _check_solve(cb, prec, 1e-11)
+
+
+@pytest.mark.parametrize("prec", [mca.PREC_FP64, mca.PREC_BF16_SPLIT], ids=["fp64", "bf16split"])
+def test_solve_bimodal_256(prec):
+    """256x256 bimodal conductances, eight seeds (map s with input vector s)."""
+    for seed in range(8):
+        _check_solve(mi.config_bimodal(seed), prec, 1e-10, ref_tol=1e-13)
+
+
+def test_batch_matches_single_solves():
+    cb = mi.make_crossbar(48, 40, 21, nvec=6)
+    p = cb.params
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=4,
+                            newton_rtol=1e-11), cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=1,
+                            newton_rtol=1e-11), cb.gmap) as s:
+        for v in range(6):
+            vt1, vb1, io1, st1 = s.solve(cb.vin[v:v + 1])
+            assert _rel_err(vt[v], vt1[0]) < 1e-9 and _rel_err(vb[v], vb1[0]) < 1e-8
+
+
+def test_device_buffers_in_and_out():
+    cb = mi.make_crossbar(20, 30, 5, nvec=2)
+    p = cb.params
+    vin = _t(cb.vin)
+    vt = torch.empty(2, 20, 30, dtype=torch.float64, device=DEV)
+    vb = torch.empty_like(vt)
+    io = torch.empty(2, 30, dtype=torch.float64, device=DEV)
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=2), cb.gmap) as s:
+        s.solve(vin, vt, vb, io, stream=torch.cuda.current_stream())
+        vt_h, vb_h, io_h, _ = s.solve(cb.vin)
+    assert _rel_err(vt.cpu().numpy(), vt_h) < 1e-12
+    assert _rel_err(io.cpu().numpy(), io_h) < 1e-12
+
+
+def test_linear_uniform_single_iteration():
+    """Linear devices of one conductance: P = J, so one GMRES iteration and one Newton
+    step solve the circuit."""
+    cb = mi.make_crossbar(24, 36, 6, b=0.0)
+    g = np.full((24, 36), 4e-5)
+    p = cb.params
+    with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=1, newton_rtol=1e-11), g) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+    assert st[0]["newton_iters"] == 1 and st[0]["gmres_iters"] == 1, st
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=1,
+                            newton_rtol=1e-9), g) as s:
+        vt2, vb2, io2, st2 = s.solve(cb.vin)
+    assert st2[0]["status"] == 0 and st2[0]["gmres_iters"] <= 4, st2
+
+
+def test_zero_input_and_status_codes():
+    cb = mi.make_crossbar(8, 9, 1)
+    p = cb.params
+    with mca.Solver(_params(p, max_batch=2), cb.gmap) as s:
+        vt, vb, io, st = s.solve(np.zeros((1, 8)))
+        assert st[0]["status"] == 0 and np.all(vt == 0) and np.all(vb == 0)
+        vt, vb, io, st = s.solve(np.full((1, 8), np.nan), allow_not_converged=True)
+        assert st[0]["status"] == mca.ERR_NONFINITE
+    with mca.Solver(_params(p, max_batch=1, max_newton=1, newton_rtol=1e-14), cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin, allow_not_converged=True)
+        assert st[0]["status"] == mca.ERR_NOT_CONVERGED and st[0]["newton_iters"] == 1
+        assert np.all(np.isfinite(vt))
+    bad = cb.gmap.copy()
+    bad[2, 3] = np.nan
+    with pytest.raises(mca.MCAError) as e:
+        mca.Solver(_params(p), bad)
+    assert e.value.code == mca.ERR_NONFINITE
+    bad[2, 3] = -1.0
+    with pytest.raises(mca.MCAError) as e:
+        mca.Solver(_params(p), bad)
+    assert e.value.code == mca.ERR_INVALID_ARG
+
+
+def test_full_size_1024_sampled():
+    """1024x1024 (2.1M unknowns), log-uniform g, wires 1 S / 0.5 S, BF16 split
+    preconditioner, Newton to 1e-8: the oracle recomputes the FP64 residual of the
+    returned voltages, and the voltages match the oracle's preconditioned-GMRES solve."""
+    cb = mi.config_large(1024, 0)
+    p = cb.params
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, newton_rtol=1e-8, max_batch=1),
+                    cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+    assert st[0]["status"] == 0
+    Ft, Fb = O.residual(p, cb.gmap, cb.vin[0], vt[0].ravel(), vb[0].ravel())
+    Yt, _ = O.source_vector(p, cb.vin[0])
+    rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
+    assert rel <= 1e-8 * 1.01
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, newton_rtol=1e-12, max_batch=1),
+                    cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+    ref = O.newton_solve(p, cb.gmap, cb.vin[0], tol=1e-12, linear="pgmres")
+    assert _rel_err(vt[0], ref.Vt) <= 1e-7 and _rel_err(vb[0], ref.Vb) <= 1e-7
