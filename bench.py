@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Throughput of the steady-state crossbar solve on one GB300.
+
+Workload: the 1024 x 1024 memristor crossbar (2.1M unknowns), log-uniform device
+conductances in [1e-6, 1e-4] S, top wires 1 S, bottom wires 0.5 S, 10 ohm drivers and
+sense, 1 kohm terminations, sinh devices (b = 2), V_in ~ U[0, 0.3] V.  One step solves a
+batch of input vectors to a relative KCL residual ||F||/||Y|| <= 1e-8 with Newton +
+flexible GMRES(30) preconditioned by the Kronecker/block preconditioner (tensor-core BF16
+transforms, split back transforms); value = solves per second.
+
+The JSON line also carries: the end-to-end figure through the C ABI with host buffers,
+the roofline of the dominant kernel family (CUDA events on the solve stream), the same
+workload in the plain FP64 GPU form, the preconditioner TFLOP/s (dense eigenbasis count
+8 m n (m + n) per apply), and the CPU oracle on the host cores.
+
+--impl reference times the CPU oracle itself on the same workload (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import mca_inputs as mi  # noqa: E402
+
+METRIC = "solves/s at 1e-8 rel. KCL residual (1024² MCA) vs plain FP64; precond TFLOP/s"
+TOL = 1e-8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--precision", default="bf16split", choices=["bf16split", "bf16", "fp64"])
+    ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(
+            ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+             "-lms", "200", "-i", str(self.gpu)], stdout=self.fh, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                     hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        sm = sorted(r["sm"] for r in rows)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0]["smax"],
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def oracle_solves(cb, count, start=0):
+    """Time `count` oracle solves (Newton + preconditioned GMRES, FP64, NumPy/SciPy)."""
+    from oracle import mca_oracle as O
+    t0 = time.perf_counter()
+    for v in range(start, start + count):
+        r = O.newton_solve(cb.params, cb.gmap, cb.vin[v % len(cb.vin)], tol=TOL, linear="pgmres")
+        assert r.rel_residual <= TOL
+    return time.perf_counter() - t0
+
+
+def workload_config(args, batch):
+    return {
+        "workload": f"{args.size}x{args.size} MCA, log-uniform g in [1e-6,1e-4] S, wires "
+                    "1 S top / 0.5 S bottom, sinh devices b=2, V_in~U[0,0.3] V, "
+                    f"Newton to {TOL:g} rel. KCL residual, FGMRES(30)",
+        "rows": args.size, "cols": args.size, "batch_per_step": batch,
+        "precision": args.precision, "newton_rtol": TOL,
+        "cache": "inputs larger than L2: the Krylov basis of one solve is ~1 GB",
+    }
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return
+    cb = mi.config_large(args.size, 0, nvec=args.warmup + args.steps)
+    oracle_solves(cb, args.warmup)
+    t = oracle_solves(cb, args.steps, start=args.warmup)
+    value = args.steps / t
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, 1),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle solves of the {args.size}^2 crossbar, "
+                                   "one input vector each"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2109_07929_gb300 as mca
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    prec = {"bf16split": mca.PREC_BF16_SPLIT, "bf16": mca.PREC_BF16,
+            "fp64": mca.PREC_FP64}[args.precision]
+    B = args.batch
+    W, K = args.warmup, args.steps
+    m = n = args.size
+    cb = mi.config_large(args.size, 1000 + rank, nvec=(W + K) * B)
+    p = cb.params
+    params = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
+                                g_src=p.g_src, g_term_top_right=p.g_term_top_right,
+                                g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
+                                precision=prec, newton_rtol=TOL, max_batch=B)
+    solver = mca.Solver(params, cb.gmap)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    vin = torch.as_tensor(cb.vin, device=dev)
+    vt = torch.empty(B, m, n, dtype=torch.float64, device=dev)
+    vb = torch.empty_like(vt)
+    io = torch.empty(B, n, dtype=torch.float64, device=dev)
+    stats = (mca.Stats * B)()
+    sp = mca.ctypes.cast(stats, mca.ctypes.c_void_p)
+
+    def step(i, check):
+        rc = solver.solve_raw(vin[i * B:(i + 1) * B].data_ptr(), B, vt.data_ptr(), vb.data_ptr(),
+                              io.data_ptr(), sp, stream)
+        if rc != 0:
+            raise RuntimeError(f"solve failed with status {rc}")
+        if check is not None:
+            for s in stats:
+                assert s.status == 0 and s.rel_residual <= TOL, (s.status, s.rel_residual)
+                check.append((s.newton_iters, s.gmres_iters, s.rel_residual))
+
+    warm = []
+    for i in range(W):
+        step(i, warm)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = mca.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    timed = []
+    for i in range(W, W + K):
+        step(i, timed)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = mca.kernel_launches() - launches0
+    clocks = sampler.stop()
+    t = ev0.elapsed_time(ev1) / 1000.0
+    if pg:
+        tt = torch.tensor([t], dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t = float(tt[0])
+        pg.barrier()
+    value = world * K * B / t
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies included
+    vin_h = torch.as_tensor(cb.vin).pin_memory()
+    vt_h = torch.empty(B, m, n, dtype=torch.float64).pin_memory()
+    vb_h = torch.empty_like(vt_h).pin_memory()
+    io_h = torch.empty(B, n, dtype=torch.float64).pin_memory()
+
+    def step_host(i):
+        rc = solver.solve_raw(vin_h[i * B:(i + 1) * B].data_ptr(), B, vt_h.data_ptr(),
+                              vb_h.data_ptr(), io_h.data_ptr(), sp, stream)
+        if rc != 0:
+            raise RuntimeError(f"solve failed with status {rc}")
+
+    step_host(0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ke = max(1, K // 2)
+    e0.record(stream)
+    for i in range(W, W + ke):
+        step_host(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = e0.elapsed_time(e1) / 1000.0
+    if pg:
+        tt = torch.tensor([te], dtype=torch.float64)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        te = float(tt[0])
+    e2e = {"value": world * ke * B / te, "unit": "solves/s",
+           "h2d_bytes_per_step": B * m * 8,
+           "d2h_bytes_per_step": B * (2 * m * n + n) * 8 + B * mca.ctypes.sizeof(mca.Stats)}
+
+    # ---- per-family kernel timing (CUDA events on the solve stream, separate pass)
+    solver.profile(True)
+    for i in range(W, W + min(K, 4)):
+        step(i, None)
+    prof = solver.profile_read()
+    solver.profile(False)
+    peaks, peak_src = load_peaks()
+    fam = max(prof, key=lambda f: prof[f]["ms"])
+    fp = prof[fam]
+    gemm = fam.startswith("precond")
+    if gemm and prec != mca.PREC_FP64:
+        ach = fp["flops"] / (fp["ms"] / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s"}
+    elif gemm:
+        ach = fp["flops"] / (fp["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    else:
+        ach = fp["bytes"] / (fp["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = fam
+    roof["launches"] = fp["launches"]
+    roof["avg_launch_us"] = 1e3 * fp["ms"] / max(1, fp["launches"])
+    roof["peak_source"] = f"{peak_src} ({'sustained bf16' if roof['bound'] == 'tensor' else roof['bound']})"
+    roof["traffic"] = committed_traffic(fam, fp)
+    total_ms = sum(v["ms"] for v in prof.values())
+    breakdown = {f: {"share": v["ms"] / total_ms, "launches": v["launches"],
+                     "GB/s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
+                     "TFLOP/s": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
+                 for f, v in prof.items() if v["launches"] > 0}
+    # precond TFLOP/s in the dense eigenbasis count, 8 m n (m + n) per apply
+    pc_ms = sum(prof[f]["ms"] for f in ("precond_1", "precond_2", "precond_3", "precond_4"))
+    applies = prof["precond_1"]["flops"] / (4.0 * m * n * n) if prof["precond_1"]["flops"] else 0
+    precond_tflops = applies * 8.0 * m * n * (m + n) / (pc_ms / 1e3) / 1e12 if pc_ms else 0.0
+
+    iters = np.array([(a, b_) for a, b_, _ in timed])
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": 1000 * t / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+bf16" if prec != mca.PREC_FP64 else "f64",
+        "data": "synthetic", "config": workload_config(args, B),
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+        "precond_tflops": precond_tflops, "kernel_breakdown": breakdown,
+        "newton_iters_per_solve": float(iters[:, 0].mean()),
+        "gmres_iters_per_solve": float(iters[:, 1].mean()),
+        "max_rel_residual": float(max(r for _, _, r in timed)),
+    }
+    solver.close()
+    del vt, vb, io
+
+    # ---- the same workload in the plain FP64 GPU form (one vector)
+    if not args.no_fp64_form and prec != mca.PREC_FP64:
+        p64 = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
+                                 g_src=p.g_src, g_term_top_right=p.g_term_top_right,
+                                 g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
+                                 precision=mca.PREC_FP64, newton_rtol=TOL, max_batch=1)
+        with mca.Solver(p64, cb.gmap) as s64:
+            vt1 = torch.empty(1, m, n, dtype=torch.float64, device=dev)
+            vb1 = torch.empty_like(vt1)
+            io1 = torch.empty(1, n, dtype=torch.float64, device=dev)
+            st1 = (mca.Stats * 1)()
+            sp1 = mca.ctypes.cast(st1, mca.ctypes.c_void_p)
+            s64.solve_raw(vin[0:1].data_ptr(), 1, vt1.data_ptr(), vb1.data_ptr(), io1.data_ptr(),
+                          sp1, stream)
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            nf = 2
+            for i in range(nf):
+                rc = s64.solve_raw(vin[1 + i:2 + i].data_ptr(), 1, vt1.data_ptr(), vb1.data_ptr(),
+                                   io1.data_ptr(), sp1, stream)
+                assert rc == 0 and st1[0].rel_residual <= TOL
+            b_.record(stream)
+            torch.cuda.synchronize()
+            t64 = a.elapsed_time(b_) / 1000.0
+            out["fp64_form"] = {"value": nf / t64, "unit": "solves/s",
+                                "gmres_iters_per_solve": st1[0].gmres_iters,
+                                "speedup_of_mixed": value / (world * nf / t64)}
+
+    # ---- CPU oracle on the host cores (rank 0, one GPU only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tcpu = oracle_solves(cb, 1)
+        out["cpu_baseline"] = {"value": 1.0 / tcpu, "unit": "solves/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"1 oracle solve (Newton + FP64 preconditioned GMRES, "
+                                         f"NumPy/SciPy) of the {m}^2 crossbar, vector 0"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+# FP64 CUDA-core peak used for the FP64 form: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def committed_traffic(fam, fp):
+    """Per-launch DRAM bytes of this family from the committed ncu summary, if it was
+    taken on the current kernels; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(fam)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2109_07929_gb300", "csrc", ent.get("source", ""))
+    if not os.path.exists(src):
+        return None
+    import hashlib
+    with open(src, "rb") as f:
+        h = hashlib.sha1(f.read()).hexdigest()
+    if h != ent.get("sha1"):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

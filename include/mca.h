@@ -166,6 +166,35 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
                     double* dx, int32_t nvec, double rtol, int32_t* iters, double* res,
                     void* stream);
 
+/* ---- per-kernel-family timing (measurement support) -------------------------------- */
+#define MCA_FAM_RESIDUAL 0      /* residual + Jacobian diagonal (eq. F, eq. J)              */
+#define MCA_FAM_SPMV_DOTS 1     /* Jacobian apply fused with the first Gram-Schmidt pass    */
+#define MCA_FAM_UPDATE_DOTS 2   /* second Gram-Schmidt pass                                 */
+#define MCA_FAM_UPDATE_NORM 3   /* third Gram-Schmidt pass with the norm                    */
+#define MCA_FAM_NORMALIZE 4     /* basis normalisation (+ BF16 copy)                         */
+#define MCA_FAM_SMALL 5         /* reductions, Givens, Newton control, least squares        */
+#define MCA_FAM_UPDATE_X 6      /* x += Z y                                                 */
+#define MCA_FAM_PRECOND_1 7     /* preconditioner transform 1 (X Q_r)                       */
+#define MCA_FAM_PRECOND_2 8     /* transform 2 (Q_c^T T1) + per-mode 2x2 inverse            */
+#define MCA_FAM_PRECOND_3 9     /* transform 3 (Y_hat Q_r^T)                                */
+#define MCA_FAM_PRECOND_4 10    /* transform 4 (Q_c E), FP64 output                         */
+#define MCA_NUM_FAMILIES 11
+
+/* Enable (1) or disable (0) timing of the handle's kernel launches with CUDA events on
+ * the solve stream; enabling resets the counters.  Timing adds host synchronisation per
+ * GMRES cycle, so timed throughput runs keep it off. */
+int mca_profile(mca_handle* h, int32_t enable);
+
+/* Totals of one family since the last enable: launches that did work, their summed
+ * device time in ms, and their algorithmic DRAM bytes and FLOPs (counting only the
+ * vectors still iterating in each launch; the tensor-core transforms count the MMA
+ * FLOPs they execute, 3 products per split transform).  Any output may be NULL. */
+int mca_profile_read(mca_handle* h, int32_t family, int64_t* launches, double* ms,
+                     double* bytes, double* flops);
+
+/* Number of CUDA kernel launches this library has made in the calling process. */
+int64_t mca_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

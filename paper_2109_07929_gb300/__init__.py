@@ -30,8 +30,12 @@ ERR_UNSUPPORTED = -7
 EXPORTED = (
     "mca_default_params", "mca_create", "mca_solve", "mca_destroy", "mca_strerror",
     "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_precond_apply",
-    "mca_eigenpairs", "mca_gmres_solve",
+    "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
+    "mca_kernel_launches",
 )
+
+FAMILIES = ("residual", "spmv_dots", "update_dots", "update_norm", "normalize", "small",
+            "update_x", "precond_1", "precond_2", "precond_3", "precond_4")
 
 
 class Params(ctypes.Structure):
@@ -97,8 +101,13 @@ def load(build_if_missing=True):
     lib.mca_precond_apply.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
     lib.mca_eigenpairs.argtypes = [P, P, P, P, P]
     lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double, P, P, P]
+    lib.mca_profile.argtypes = [P, ctypes.c_int32]
+    lib.mca_profile_read.argtypes = [P, ctypes.c_int32, P, P, P, P]
+    lib.mca_kernel_launches.argtypes = []
+    lib.mca_kernel_launches.restype = ctypes.c_int64
     for name in ("mca_create", "mca_solve", "mca_residual", "mca_jacobian_apply",
-                 "mca_precond_apply", "mca_eigenpairs", "mca_gmres_solve"):
+                 "mca_precond_apply", "mca_eigenpairs", "mca_gmres_solve", "mca_profile",
+                 "mca_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -133,6 +142,11 @@ def _stream_ptr(stream):
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+def kernel_launches():
+    """Kernel launches made by the library in this process."""
+    return int(load().mca_kernel_launches())
 
 
 def default_params(rows, cols, **kw):
@@ -204,6 +218,20 @@ class Solver:
         """Pointer-level call of mca_solve (no allocation, no checks); returns the status."""
         return self.lib.mca_solve(self.h, vin_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr,
                                   _stream_ptr(stream))
+
+    def profile(self, enable=True):
+        _check(self.lib.mca_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{family: dict(launches, ms, bytes, flops)} since profiling was enabled."""
+        out = {}
+        for f, name in enumerate(FAMILIES):
+            n = ctypes.c_int64()
+            ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _check(self.lib.mca_profile_read(self.h, f, ctypes.addressof(n), ctypes.addressof(ms),
+                                             ctypes.addressof(by), ctypes.addressof(fl)))
+            out[name] = dict(launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value)
+        return out
 
     # ---- single operations (device tensors) ---------------------------------------
     def residual(self, x, vin, F, D, stream=None):

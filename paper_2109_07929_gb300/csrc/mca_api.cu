@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,7 +28,12 @@ namespace mca {
 
 namespace {
 thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
 }
+
+// Every kernel launch of the library goes through one of the launch_* wrappers; their
+// call sites add to this counter.
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
@@ -78,6 +84,19 @@ struct mca_handle {
   bool ev_ok = false;
   // statistics of the last solve pass (host copies)
   std::vector<VecCtl> ctl_host;
+  // kernel-family timing
+  struct ProfRec {
+    int fam, k;
+    cudaEvent_t a, b;
+    double bytes_pv, flops_pv;  // per vector still iterating
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_next = 0;
+  std::vector<ProfRec> prof_pending;
+  int64_t prof_launches[MCA_NUM_FAMILIES] = {};
+  double prof_ms[MCA_NUM_FAMILIES] = {}, prof_bytes[MCA_NUM_FAMILIES] = {},
+         prof_flops[MCA_NUM_FAMILIES] = {};
 };
 
 namespace {
@@ -217,23 +236,85 @@ int alloc_workspace(mca_handle* h) {
   return MCA_OK;
 }
 
+// ---- kernel-family timing -------------------------------------------------------------
+cudaEvent_t prof_event(mca_handle* h) {
+  if (h->prof_next == h->prof_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->prof_pool.push_back(e);
+  }
+  return h->prof_pool[h->prof_next++];
+}
+
+// Record a start event when timing is on; returns it (or NULL).
+cudaEvent_t prof_begin(mca_handle* h, cudaStream_t s) {
+  if (!h->prof_on) return nullptr;
+  cudaEvent_t a = prof_event(h);
+  if (a) cudaEventRecord(a, s);
+  return a;
+}
+
+void prof_end(mca_handle* h, cudaEvent_t a, int fam, int k, double bytes_pv, double flops_pv,
+              cudaStream_t s) {
+  if (!h->prof_on || !a) return;
+  cudaEvent_t b = prof_event(h);
+  if (!b) return;
+  cudaEventRecord(b, s);
+  h->prof_pending.push_back({fam, k, a, b, bytes_pv, flops_pv});
+}
+
+// Fold the pending records into the family totals.  active(k) is the number of vectors
+// that did work in GMRES iteration k (k < 0: launches outside the Krylov loop).
+template <typename F>
+void prof_flush(mca_handle* h, F active) {
+  if (!h->prof_on) return;
+  for (auto& r : h->prof_pending) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) continue;
+    const int act = active(r.k);
+    if (act <= 0) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    h->prof_launches[r.fam] += 1;
+    h->prof_ms[r.fam] += ms;
+    h->prof_bytes[r.fam] += r.bytes_pv * act;
+    h->prof_flops[r.fam] += r.flops_pv * act;
+  }
+  h->prof_pending.clear();
+  h->prof_next = 0;
+}
+
 // z = P^-1 r for B vectors: r at rin + b*rstride, z at zout + b*zstride.  For the
 // tensor-core forms the BF16 copy of r must already be in h->Xbf.
 int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstride,
-                  double* zout, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s) {
+                  double* zout, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s,
+                  int prof_k = -1) {
   const int m = h->m, n = h->n;
   const size_t mn = h->mn;
   if (precision == MCA_PREC_FP64) {
     if (!h->T1_64) return MCA_ERR_UNSUPPORTED;
+    const double f_r = 4.0 * m * (double)n * n, f_c = 4.0 * n * (double)m * m;
     BlkAddr a1{rstride, mn, (size_t)n}, o1{2 * mn, mn, (size_t)m};
+    cudaEvent_t t0 = prof_begin(h, s);
     launch_gemm64_tstore(rin, a1, h->QrT, h->T1_64, o1, B, m, n, n, ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 32.0 * mn, f_r, s);
     BlkAddr a2{2 * mn, mn, (size_t)m}, o2{2 * mn, mn, (size_t)n};
+    t0 = prof_begin(h, s);
     launch_gemm64_tstore(h->T1_64, a2, h->QcT, h->Xh_64, o2, B, n, m, m, ctl, s);
+    count_launches(1);
     launch_modes_2x2_f64(h->Xh_64, h->mu, h->nu, m, n, ctl, B, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, 64.0 * mn, f_c, s);
     BlkAddr a3{2 * mn, mn, (size_t)n}, o3{2 * mn, mn, (size_t)m};
+    t0 = prof_begin(h, s);
     launch_gemm64_tstore(h->Xh_64, a3, h->Qr, h->E_64, o3, B, m, n, n, ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, 32.0 * mn, f_r, s);
     BlkAddr a4{2 * mn, mn, (size_t)m}, o4{zstride, mn, (size_t)n};
+    t0 = prof_begin(h, s);
     launch_gemm64_tstore(h->E_64, a4, h->Qc, zout, o4, B, n, m, m, ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k, 32.0 * mn, f_c, s);
     MCA_CUDA_TRY(cudaGetLastError());
     return MCA_OK;
   }
@@ -247,24 +328,40 @@ int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstrid
   // 1: T1^T = (X Q_r)^T
   e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
   e.out = h->T1bf; e.out_lo = nullptr; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
+  // executed MMA FLOPs per vector: 2 layers x 2 M N K, three products when split
+  const double f_r = 4.0 * m * (double)n * n, f_c = 4.0 * n * (double)m * m;
+  const double sp = split ? 3.0 : 1.0;
+  cudaEvent_t t0 = prof_begin(h, s);
   MCA_CUDA_TRY(tc::gemm(h->bn[0], false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(h->bn[0])],
                         h->mB1[q(h->bn[0])], e, B, s));
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 16.0 * mn * 0.25 + 4.0 * mn, f_r, s);
   // 2: Y_hat = modes^-1 (Q_c^T T1), stored [i'][k']
   e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
   e.out = h->Yh; e.out_lo = h->Yl; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
   e.mu = h->mu; e.nu = h->nu;
+  t0 = prof_begin(h, s);
   MCA_CUDA_TRY(tc::gemm(h->bn[1], false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2,
                         h->mA2, h->mB2[q(h->bn[1])], h->mB2[q(h->bn[1])], e, B, s));
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, (split ? 12.0 : 8.0) * mn, f_c, s);
   // 3: E^T = (Y_hat Q_r^T)^T
   e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
   e.out = h->Eh; e.out_lo = h->El; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
+  t0 = prof_begin(h, s);
   MCA_CUDA_TRY(tc::gemm(h->bn[2], split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h,
                         h->mA3l, h->mB3h[q(h->bn[2])], h->mB3l[q(h->bn[2])], e, B, s));
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, (split ? 16.0 : 8.0) * mn, sp * f_r, s);
   // 4: Z = (E^T Q_c^T)^T, FP64 unpadded
   e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
   e.out = zout; e.out_lo = nullptr; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
+  t0 = prof_begin(h, s);
   MCA_CUDA_TRY(tc::gemm(h->bn[3], split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(h->bn[3])],
                         h->mB4l[q(h->bn[3])], e, B, s));
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k, (split ? 8.0 : 4.0) * mn + 16.0 * mn,
+           sp * f_c, s);
   return MCA_OK;
 }
 
@@ -288,6 +385,7 @@ bool any_flag(const mca_handle* h, int B) {
 // BF16 copy are already in place.
 int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
   const size_t n2 = h->n2;
+  const double cells = (double)h->mn;
   const size_t vstride = (size_t)(h->restart + 1) * n2;
   const size_t zstride = (size_t)h->restart * n2;
   const int nbS = residual_nblk((int)h->mn);
@@ -296,23 +394,59 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
   for (int k = 0; k < h->restart; ++k) {
     const double* vk = h->V + (size_t)k * n2;
     double* zk = h->Z + (size_t)k * n2;
+    const double nk = k + 1;
     // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
-    MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s));
+    MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k));
+    cudaEvent_t t0 = prof_begin(h, s);
     launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
                      h->ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (14.0 + 4.0 * nk), s);
+    t0 = prof_begin(h, s);
     launch_reduce_dots(h->part, nbS, k + 1, h->h1, B, h->ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_SMALL, k, 0.0, 0.0, s);
+    t0 = prof_begin(h, s);
     launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k, cells * (32.0 + 16.0 * nk), cells * 8.0 * nk, s);
+    t0 = prof_begin(h, s);
     launch_reduce_dots(h->part, nbV, k + 1, h->h2, B, h->ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_SMALL, k, 0.0, 0.0, s);
+    t0 = prof_begin(h, s);
     launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk), cells * (4.0 * nk + 4.0), s);
+    t0 = prof_begin(h, s);
     launch_givens(h->part, nbV, h->h1, h->h2, k, h->restart, h->ctl, B, h->hflags_dev, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_SMALL, k, 0.0, 0.0, s);
+    t0 = prof_begin(h, s);
     launch_normalize(h->W, h->V + (size_t)(k + 1) * n2, vstride, n2, tc ? h->Xbf : nullptr,
                      h->mp, h->np, h->m, h->n, h->ctl, B, s);
+    count_launches(1);
+    // the last iteration of a cycle normalises nothing: counted with iteration k + 1
+    prof_end(h, t0, MCA_FAM_NORMALIZE, k + 1, cells * (tc ? 36.0 : 32.0), cells * 2.0, s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaEventRecord(h->ev[k], s));
     if (k >= 1) {
       MCA_CUDA_TRY(cudaEventSynchronize(h->ev[k - 1]));
       if (!any_flag(h, B)) break;
     }
+  }
+  if (h->prof_on) {
+    // iterations done per vector in this cycle decide which launches did work
+    MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
+                                 cudaMemcpyDeviceToHost, s));
+    MCA_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<int> kd(B);
+    for (int b = 0; b < B; ++b) kd[b] = h->ctl_host[b].k_done;
+    prof_flush(h, [&](int k) {
+      int c = 0;
+      for (int b = 0; b < B; ++b) c += (k < kd[b]) ? 1 : 0;
+      return c;
+    });
   }
   return MCA_OK;
 }
@@ -336,20 +470,48 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s) {
   const size_t vstride = (size_t)(h->restart + 1) * h->n2;
   const size_t zstride = (size_t)h->restart * h->n2;
   launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
+  count_launches(1);
   MCA_CUDA_TRY(cudaMemsetAsync(h->x, 0, (size_t)B * h->n2 * sizeof(double), s));
+  const double cells = (double)h->mn;
+  int n_active = B;  // vectors entering the current Newton step
   for (int it = 0; it <= h->p.max_newton; ++it) {
+    cudaEvent_t t0 = prof_begin(h, s);
     launch_residual(h->gr, h->g, h->vin, h->x, h->F, h->D, h->part, nbR, B, h->ctl, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * 48.0, cells * 30.0, s);
+    t0 = prof_begin(h, s);
     launch_newton_control(h->part, nbR, (int)h->mn, h->ctl, B, cfg, h->hflags_dev, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_SMALL, -1, 0.0, 0.0, s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
-    if (!any_flag(h, B)) break;
+    const int entering = n_active;
+    n_active = 0;
+    for (int b = 0; b < B; ++b) n_active += reinterpret_cast<volatile int32_t*>(h->hflags)[b] ? 1 : 0;
+    prof_flush(h, [&](int) { return entering; });
+    if (n_active == 0) break;
+    t0 = prof_begin(h, s);
     launch_init_basis(h->F, -1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
                       h->n, h->ctl, B, s);
+    count_launches(1);
+    prof_end(h, t0, MCA_FAM_SMALL, -1, 0.0, 0.0, s);
     MCA_TRY(gmres_cycle(h, h->D, B, s));
+    t0 = prof_begin(h, s);
     launch_lsq_update(h->x, h->Z, zstride, h->n2, h->ctl, B, s);
+    count_launches(2);
+    double kbar = 0.0;
+    if (h->prof_on) {
+      int c = 0;
+      for (int b = 0; b < B; ++b)
+        if (h->ctl_host[b].k_done > 0) { kbar += h->ctl_host[b].k_done; ++c; }
+      kbar = c ? kbar / c : 0.0;
+    }
+    prof_end(h, t0, MCA_FAM_UPDATE_X, -1, cells * 16.0 * (2.0 + kbar), cells * 4.0 * kbar, s);
+    prof_flush(h, [&](int) { return n_active; });
     MCA_CUDA_TRY(cudaGetLastError());
   }
   launch_outputs(h->gr, h->vin, h->x, h->iout, h->kcl, B, s);
+  count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
   MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
                                cudaMemcpyDeviceToHost, s));
@@ -410,6 +572,7 @@ void mca_destroy(mca_handle* h) {
   if (h->hflags) cudaFreeHost(h->hflags);
   if (h->ev_ok)
     for (int k = 0; k <= MCA_KMAX; ++k) cudaEventDestroy(h->ev[k]);
+  for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
   delete h;
 }
 
@@ -477,10 +640,14 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
   cudaStream_t s = 0;
   launch_eig_tridiag(h->n, p->g_wire_top, p->g_src, p->g_term_top_right, h->mu, h->Qr,
                      scratch, s);
+  count_launches(2);
   launch_eig_tridiag(h->m, p->g_wire_bot, p->g_term_bot_top, p->g_sense, h->nu, h->Qc,
                      scratch, s);
+  count_launches(2);
   launch_transpose64(h->Qr, h->n, h->QrT, s);
+  count_launches(1);
   launch_transpose64(h->Qc, h->m, h->QcT, s);
+  count_launches(1);
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     set_error("eigen setup kernels failed");
     return fail(MCA_ERR_CUDA);
@@ -492,7 +659,9 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
         (rc = dalloc(h, &h->Qc_hi, mpp)) || (rc = dalloc(h, &h->Qc_lo, mpp)))
       return fail(rc);
     launch_pack_q_bf16(h->Qr, h->n, h->np, h->Qr_hi, h->Qr_lo, h->QrT_bf, s);
+    count_launches(1);
     launch_pack_q_bf16(h->Qc, h->m, h->mp, h->Qc_hi, h->Qc_lo, h->QcT_bf, s);
+    count_launches(1);
     if (cudaGetLastError() != cudaSuccess) return fail(MCA_ERR_CUDA);
   }
   if ((rc = alloc_workspace(h)) != MCA_OK) return fail(rc);
@@ -561,7 +730,9 @@ int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nve
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = residual_nblk((int)h->mn);
   launch_residual(h->gr, h->g, v_in, x, F, D, h->part, nb, nvec, nullptr, s);
+  count_launches(1);
   launch_reduce_dots(h->part, nb, 2, h->h1, nvec, nullptr, s);
+  count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
   std::vector<double> hh((size_t)nvec * 32);
   MCA_CUDA_TRY(cudaMemcpyAsync(hh.data(), h->h1, hh.size() * sizeof(double),
@@ -584,6 +755,7 @@ int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_spmv_dots(h->gr, D, z, h->n2, w, nullptr, 0, 0, h->part, residual_nblk((int)h->mn),
                    nvec, nullptr, s);
+  count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
   MCA_CUDA_TRY(cudaStreamSynchronize(s));
   return MCA_OK;
@@ -623,6 +795,7 @@ int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z
   MCA_TRY(load_ctl_a(h, a, nvec, s));
   if (precision != MCA_PREC_FP64)
     tc::cast_pad(r, h->n2, h->Xbf, h->m, h->n, h->mp, h->np, nvec, s);
+    count_launches(1);
   MCA_TRY(precond_apply(h, precision, r, h->n2, z, h->n2, nvec, h->ctl, s));
   MCA_CUDA_TRY(cudaStreamSynchronize(s));
   return check_device_error(h);
@@ -660,12 +833,16 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
   MCA_CUDA_TRY(cudaMemcpyAsync(h->W, rhs, (size_t)nvec * n2 * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
   launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, s);
+  count_launches(1);
   launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, s);
+  count_launches(1);
   launch_init_basis(h->F, 1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m, h->n,
                     h->ctl, nvec, s);
+  count_launches(1);
   MCA_TRY(gmres_cycle(h, D, nvec, s));
   MCA_CUDA_TRY(cudaMemsetAsync(dx, 0, (size_t)nvec * n2 * sizeof(double), s));
   launch_lsq_update(dx, h->Z, zstride, n2, h->ctl, nvec, s);
+  count_launches(2);
   MCA_CUDA_TRY(cudaGetLastError());
   MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)nvec * sizeof(VecCtl),
                                cudaMemcpyDeviceToHost, s));
@@ -675,6 +852,30 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
     if (res) res[b] = h->ctl_host[b].res_est;
   }
   return check_device_error(h);
+}
+
+int64_t mca_kernel_launches(void) { return g_launches.load(); }
+
+int mca_profile(mca_handle* h, int32_t enable) {
+  if (!h) return MCA_ERR_INVALID_ARG;
+  h->prof_on = enable != 0;
+  h->prof_pending.clear();
+  h->prof_next = 0;
+  for (int f = 0; f < MCA_NUM_FAMILIES; ++f) {
+    h->prof_launches[f] = 0;
+    h->prof_ms[f] = h->prof_bytes[f] = h->prof_flops[f] = 0.0;
+  }
+  return MCA_OK;
+}
+
+int mca_profile_read(mca_handle* h, int32_t family, int64_t* launches, double* ms,
+                     double* bytes, double* flops) {
+  if (!h || family < 0 || family >= MCA_NUM_FAMILIES) return MCA_ERR_INVALID_ARG;
+  if (launches) *launches = h->prof_launches[family];
+  if (ms) *ms = h->prof_ms[family];
+  if (bytes) *bytes = h->prof_bytes[family];
+  if (flops) *flops = h->prof_flops[family];
+  return MCA_OK;
 }
 
 }  // extern "C"
