@@ -192,6 +192,30 @@ int mca_profile(mca_handle* h, int32_t enable);
 int mca_profile_read(mca_handle* h, int32_t family, int64_t* launches, double* ms,
                      double* bytes, double* flops);
 
+/* ---- residual without device allocation ------------------------------------------- */
+
+/* Residual, Jacobian diagonal and their norms for callers that cannot allocate device
+ * memory: code running inside CUDA graph stream capture (allocation cannot be captured),
+ * services that forbid allocator calls after start-up, and hosts whose device memory is
+ * owned by another framework's pool.  The paper has no counterpart; this is a usage
+ * variant of mca_residual() that needs no handle and makes no cudaMalloc/cudaFree.
+ *   p      : circuit parameters (rows, cols, wire/termination conductances, b).
+ *   g_map  : device, m*n memristor conductances.
+ *   x      : device, nvec * 2*m*n states [V_t ; V_b].
+ *   v_in   : device, nvec * m input voltages.
+ *   F, D   : device outputs as in mca_residual().
+ *   fnorm  : device output, nvec values ||F||_2 (may be NULL).
+ *   dmean  : device output, nvec values mean(D) (may be NULL).
+ *   stream : the call only enqueues work on it (no synchronisation).
+ * Limits: 1 <= nvec <= 8, else MCA_ERR_INVALID_ARG.  Scratch lives in a fixed 1.2 MiB
+ * device array that every GPU loading the library keeps until exit; all calls on a
+ * device share it, so calls that overlap on the GPU race (order them on one stream).
+ * The first call on a device looks up that array's address; make it before any stream
+ * capture. */
+int mca_residual_noalloc(const mca_params* p, const double* g_map, const double* x,
+                         const double* v_in, int32_t nvec, double* F, double* D,
+                         double* fnorm, double* dmean, void* stream);
+
 /* Number of CUDA kernel launches this library has made in the calling process. */
 int64_t mca_kernel_launches(void);
 

@@ -31,7 +31,7 @@ EXPORTED = (
     "mca_default_params", "mca_create", "mca_solve", "mca_destroy", "mca_strerror",
     "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_precond_apply",
     "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
-    "mca_kernel_launches",
+    "mca_kernel_launches", "mca_residual_noalloc",
 )
 
 FAMILIES = ("residual", "spmv_dots", "update_dots", "update_norm", "normalize", "small",
@@ -103,6 +103,9 @@ def load(build_if_missing=True):
     lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double, P, P, P]
     lib.mca_profile.argtypes = [P, ctypes.c_int32]
     lib.mca_profile_read.argtypes = [P, ctypes.c_int32, P, P, P, P]
+    lib.mca_residual_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P, ctypes.c_int32, P, P,
+                                         P, P, P]
+    lib.mca_residual_noalloc.restype = ctypes.c_int
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
     for name in ("mca_create", "mca_solve", "mca_residual", "mca_jacobian_apply",
@@ -147,6 +150,14 @@ def _stream_ptr(stream):
 def kernel_launches():
     """Kernel launches made by the library in this process."""
     return int(load().mca_kernel_launches())
+
+
+def residual_noalloc(params, gmap, x, vin, F, D, fnorm=None, dmean=None, stream=None):
+    """mca_residual_noalloc on device tensors (no handle, no device allocation)."""
+    rc = load().mca_residual_noalloc(ctypes.byref(params), _ptr(gmap), _ptr(x), _ptr(vin),
+                                     x.shape[0], _ptr(F), _ptr(D), _ptr(fnorm), _ptr(dmean),
+                                     _stream_ptr(stream))
+    return _check(rc)
 
 
 def default_params(rows, cols, **kw):

@@ -42,6 +42,7 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 }
 
 static void set_error(const char* msg) { g_last_error = msg; }
+void set_error_message(const char* msg) { g_last_error = msg; }
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
