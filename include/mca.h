@@ -91,7 +91,7 @@ typedef struct mca_handle mca_handle;
 
 /* Fill *p with the defaults: 1 S wires, 10 ohm driver and sense, 1 kohm terminations,
  * b = 2, MCA_PREC_BF16_SPLIT, restart 30, max_newton 20, max_batch 4, newton_rtol 1e-8,
- * eta0 1e-4, eta_max 1e-2.  rows/cols are left at 0 and must be set. */
+ * eta0 1e-3, eta_max 1e-2.  rows/cols are left at 0 and must be set. */
 void mca_default_params(mca_params* p);
 
 /* Create a solver for one crossbar.

@@ -34,7 +34,71 @@ __device__ __forceinline__ void block_store_partials(double (&acc)[KP], int nk,
 #pragma unroll
     for (int q = 0; q < kThreads / 32; ++q) s += red[q][threadIdx.x];
     part[((size_t)b * 32 + threadIdx.x) * nblk + blockIdx.x] = s;
+    __threadfence();
   }
+}
+
+// True in every thread of the block that finished last among the nblk blocks of vector b
+// (its partial sums are then all visible); the counter is reset by the caller.
+__device__ __forceinline__ bool last_block(unsigned int* cnt, int b, int nblk) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&cnt[b], 1u) == (unsigned)nblk - 1);
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Fixed-order reduction of part[b][j][0..nblk) into h[b][j] (j < nk), warp w taking rows
+// w, w + 8, ...
+__device__ __forceinline__ void block_reduce_rows(const double* __restrict__ part, int b,
+                                                  int nblk, int nk, double* __restrict__ h) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int j = w; j < nk; j += kThreads / 32) {
+    double s = 0.0;
+    for (int t = l; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32 + j) * nblk + t]);
+    s = warp_sum(s);
+    if (l == 0) h[(size_t)b * 32 + j] = s;
+  }
+}
+
+// Givens rotation of Hessenberg column k (h = h1 + h2, h_{k+1,k} = sqrt(hn2)), residual
+// estimate |g_{k+1}| and the stop test of the GMRES cycle.  One thread.
+__device__ void givens_column(VecCtl& c, int b, double hn2, const double* __restrict__ h1,
+                              const double* __restrict__ h2, int k, int restart,
+                              int32_t* host_flags) {
+  const int ld = MCA_KMAX + 1;
+  double* col = c.H + (size_t)k * ld;
+  for (int j = 0; j <= k; ++j) col[j] = __ldcg(&h1[(size_t)b * 32 + j]) + __ldcg(&h2[(size_t)b * 32 + j]);
+  const double hk1 = sqrt(hn2);
+  col[k + 1] = hk1;
+  for (int j = 0; j < k; ++j) {
+    const double t = c.cs[j] * col[j] + c.sn[j] * col[j + 1];
+    col[j + 1] = -c.sn[j] * col[j] + c.cs[j] * col[j + 1];
+    col[j] = t;
+  }
+  const double rho = hypot(col[k], col[k + 1]);
+  double cs = 1.0, sn = 0.0;
+  if (rho > 0.0) {
+    cs = col[k] / rho;
+    sn = col[k + 1] / rho;
+  }
+  c.cs[k] = cs;
+  c.sn[k] = sn;
+  col[k] = rho;
+  col[k + 1] = 0.0;
+  c.g[k + 1] = -sn * c.g[k];
+  c.g[k] = cs * c.g[k];
+  const double res = fabs(c.g[k + 1]);
+  c.res_est = res;
+  c.k_done = k + 1;
+  c.gmres_iters += 1;
+  c.inv_h = (hk1 > 0.0) ? 1.0 / hk1 : 0.0;
+  const bool stop = !(res > c.tol_abs) || (k + 1 >= restart) || !(hk1 > 0.0) ||
+                    !(rho > 0.0) || !isfinite(res);
+  if (stop) c.gm_active = 0;
+  if (host_flags) host_flags[b] = c.gm_active;
+  __threadfence_system();
 }
 
 // h[b][j] = sum over blocks of part[b][j][:] for j < nk.
@@ -56,7 +120,7 @@ template <int KP>
 __global__ void __launch_bounds__(kThreads)
 k_update_dots(double* __restrict__ w, const double* __restrict__ V, size_t vstride, size_t n2,
               int nk, const double* __restrict__ h, double* __restrict__ part, int nblk,
-              const VecCtl* __restrict__ ctl) {
+              const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h2) {
   const int b = blockIdx.y;
   if (ctl != nullptr && !ctl[b].gm_active) return;
   double hj[KP], acc[KP];
@@ -82,6 +146,10 @@ k_update_dots(double* __restrict__ w, const double* __restrict__ V, size_t vstri
       if (j < nk) acc[j] = fma(v[j], x, acc[j]);
   }
   block_store_partials<KP>(acc, nk, part, b, nblk);
+  if (cnt != nullptr && last_block(cnt, b, nblk)) {
+    block_reduce_rows(part, b, nblk, nk, h2);
+    if (threadIdx.x == 0) cnt[b] = 0;
+  }
 }
 
 // pass 3: w <- w - sum_j h_j v_j, then the partial ||w||^2 (stored at part[b][0][blk]).
@@ -89,7 +157,8 @@ template <int KP>
 __global__ void __launch_bounds__(kThreads)
 k_update_norm(double* __restrict__ w, const double* __restrict__ V, size_t vstride, size_t n2,
               int nk, const double* __restrict__ h, double* __restrict__ part, int nblk,
-              const VecCtl* __restrict__ ctl) {
+              VecCtl* ctl, unsigned int* cnt, const double* __restrict__ h1, int restart,
+              int32_t* host_flags) {
   const int b = blockIdx.y;
   if (ctl != nullptr && !ctl[b].gm_active) return;
   double hj[KP];
@@ -108,56 +177,20 @@ k_update_norm(double* __restrict__ w, const double* __restrict__ V, size_t vstri
     acc[0] = fma(x, x, acc[0]);
   }
   block_store_partials<1>(acc, 1, part, b, nblk);
-}
-
-// Givens rotation of Hessenberg column k (h = h1 + h2, h_{k+1,k} = ||w||), residual
-// estimate |g_{k+1}| and the stop test of the GMRES cycle.
-__global__ void k_givens(const double* __restrict__ part_norm, int nblk,
-                         const double* __restrict__ h1, const double* __restrict__ h2, int k,
-                         int restart, VecCtl* ctl, int32_t* host_flags) {
-  const int b = blockIdx.x;
-  VecCtl& c = ctl[b];
-  if (!c.gm_active) {
-    if (threadIdx.x == 0 && host_flags) host_flags[b] = 0;
-    return;
-  }
-  const int l = threadIdx.x;
-  double s = 0.0;
-  for (int t = l; t < nblk; t += 32) s += part_norm[((size_t)b * 32) * nblk + t];
-  s = warp_sum(s);
-  if (l == 0) {
-    const int ld = MCA_KMAX + 1;
-    double* col = c.H + (size_t)k * ld;
-    for (int j = 0; j <= k; ++j) col[j] = h1[(size_t)b * 32 + j] + h2[(size_t)b * 32 + j];
-    const double hk1 = sqrt(s);
-    col[k + 1] = hk1;
-    for (int j = 0; j < k; ++j) {
-      const double t = c.cs[j] * col[j] + c.sn[j] * col[j + 1];
-      col[j + 1] = -c.sn[j] * col[j] + c.cs[j] * col[j + 1];
-      col[j] = t;
+  if (cnt == nullptr) return;
+  if (last_block(cnt, b, nblk)) {
+    __shared__ double hn2;
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+      for (int t = threadIdx.x; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32) * nblk + t]);
+      s = warp_sum(s);
+      if (threadIdx.x == 0) hn2 = s;
     }
-    const double rho = hypot(col[k], col[k + 1]);
-    double cs = 1.0, sn = 0.0;
-    if (rho > 0.0) {
-      cs = col[k] / rho;
-      sn = col[k + 1] / rho;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      cnt[b] = 0;
+      givens_column(ctl[b], b, hn2, h1, h, nk - 1, restart, host_flags);
     }
-    c.cs[k] = cs;
-    c.sn[k] = sn;
-    col[k] = rho;
-    col[k + 1] = 0.0;
-    c.g[k + 1] = -sn * c.g[k];
-    c.g[k] = cs * c.g[k];
-    const double res = fabs(c.g[k + 1]);
-    c.res_est = res;
-    c.k_done = k + 1;
-    c.gmres_iters += 1;
-    c.inv_h = (hk1 > 0.0) ? 1.0 / hk1 : 0.0;
-    const bool stop = !(res > c.tol_abs) || (k + 1 >= restart) || !(hk1 > 0.0) ||
-                      !(rho > 0.0) || !isfinite(res);
-    if (stop) c.gm_active = 0;
-    if (host_flags) host_flags[b] = c.gm_active;
-    __threadfence_system();
   }
 }
 
@@ -271,23 +304,19 @@ void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
   } while (0)
 
 void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h, double* part, int nblk, int B, const VecCtl* ctl,
-                        cudaStream_t s) {
+                        const double* h1, double* part, int nblk, int B, const VecCtl* ctl,
+                        unsigned int* cnt, double* h2, cudaStream_t s) {
   dim3 grid(nblk, B);
-  MCA_KP_DISPATCH(k_update_dots, nk, grid, w, V, vstride, n2, nk, h, part, nblk, ctl);
+  MCA_KP_DISPATCH(k_update_dots, nk, grid, w, V, vstride, n2, nk, h1, part, nblk, ctl, cnt, h2);
 }
 
 void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h, double* part, int nblk, int B, const VecCtl* ctl,
-                        cudaStream_t s) {
+                        const double* h2, double* part, int nblk, int B, VecCtl* ctl,
+                        unsigned int* cnt, const double* h1, int restart,
+                        int32_t* host_flags, cudaStream_t s) {
   dim3 grid(nblk, B);
-  MCA_KP_DISPATCH(k_update_norm, nk, grid, w, V, vstride, n2, nk, h, part, nblk, ctl);
-}
-
-void launch_givens(const double* part_norm, int nblk, const double* h1, const double* h2,
-                   int k, int restart, VecCtl* ctl, int B, int32_t* host_flags,
-                   cudaStream_t s) {
-  k_givens<<<B, 32, 0, s>>>(part_norm, nblk, h1, h2, k, restart, ctl, host_flags);
+  MCA_KP_DISPATCH(k_update_norm, nk, grid, w, V, vstride, n2, nk, h2, part, nblk, ctl, cnt,
+                  h1, restart, host_flags);
 }
 
 void launch_normalize(const double* w, double* vnext, size_t vstride, size_t n2,

@@ -7,9 +7,34 @@
 // along bottom column j, node i has diagonal (i > 0 ? g_b : g_term_top) +
 //   (i < m-1 ? g_b : g_sense) and couplings -g_b to i +- 1 (eqs. Gt, Gb: G_t = I (x) G_r,
 //   G_b = G_c (x) I in the row-major node order shared by both layers, Section 3.1).
+//
+// FP64 arithmetic is the scarce resource on this GPU (about 1/64 of the FP32 rate), so the
+// kernels keep FP64 instructions per cell low: diagonals are precomputed per position
+// class, and the device model uses short Taylor polynomials instead of library sinh/cosh.
 #include "mca_internal.cuh"
 
 namespace mca {
+
+Grid make_grid(const mca_params& p) {
+  Grid g;
+  g.m = p.rows;
+  g.n = p.cols;
+  g.gt = p.g_wire_top;
+  g.gb = p.g_wire_bot;
+  g.g_src = p.g_src;
+  g.g_tr = p.g_term_top_right;
+  g.g_bt = p.g_term_bot_top;
+  g.g_sense = p.g_sense;
+  g.b = p.b;
+  g.inv_b = (p.b != 0.0) ? 1.0 / p.b : 0.0;
+  g.dt0 = (g.n == 1) ? g.g_src + g.g_tr : g.g_src + g.gt;
+  g.dtm = 2.0 * g.gt;
+  g.dtl = g.gt + g.g_tr;
+  g.db0 = (g.m == 1) ? g.g_bt + g.g_sense : g.g_bt + g.gb;
+  g.dbm = 2.0 * g.gb;
+  g.dbl = g.gb + g.g_sense;
+  return g;
+}
 
 namespace {
 
@@ -29,6 +54,74 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
     a = warp_sum(a);
     b = warp_sum(b);
   }
+}
+
+// sinh(x) and cosh(x) for the memristor model.  For |x| <= 1 the Taylor series
+//   sinh(x) = x sum_k x^2k / (2k+1)!,  cosh(x) = sum_k x^2k / (2k)!
+// truncated after x^18/19! and x^20/20! (next terms below 2e-20 relative), evaluated by
+// Horner in t = x^2 (20 FMAs); outside that range the CUDA math library.
+__device__ __forceinline__ void sinh_cosh(double x, double& sh, double& ch) {
+  if (fabs(x) <= 1.0) {
+    const double t = x * x;
+    double ps = 1.0 / 121645100408832000.0;                 // 1/19!
+    ps = fma(ps, t, 1.0 / 355687428096000.0);               // 1/17!
+    ps = fma(ps, t, 1.0 / 1307674368000.0);                 // 1/15!
+    ps = fma(ps, t, 1.0 / 6227020800.0);                    // 1/13!
+    ps = fma(ps, t, 1.0 / 39916800.0);                      // 1/11!
+    ps = fma(ps, t, 1.0 / 362880.0);                        // 1/9!
+    ps = fma(ps, t, 1.0 / 5040.0);                          // 1/7!
+    ps = fma(ps, t, 1.0 / 120.0);                           // 1/5!
+    ps = fma(ps, t, 1.0 / 6.0);                             // 1/3!
+    ps = fma(ps, t, 1.0);
+    double pc = 1.0 / 2432902008176640000.0;                // 1/20!
+    pc = fma(pc, t, 1.0 / 6402373705728000.0);              // 1/18!
+    pc = fma(pc, t, 1.0 / 20922789888000.0);                // 1/16!
+    pc = fma(pc, t, 1.0 / 87178291200.0);                   // 1/14!
+    pc = fma(pc, t, 1.0 / 479001600.0);                     // 1/12!
+    pc = fma(pc, t, 1.0 / 3628800.0);                       // 1/10!
+    pc = fma(pc, t, 1.0 / 40320.0);                         // 1/8!
+    pc = fma(pc, t, 1.0 / 720.0);                           // 1/6!
+    pc = fma(pc, t, 1.0 / 24.0);                            // 1/4!
+    pc = fma(pc, t, 0.5);                                   // 1/2!
+    pc = fma(pc, t, 1.0);
+    sh = x * ps;
+    ch = pc;
+  } else {
+    sh = sinh(x);
+    ch = cosh(x);
+  }
+}
+
+// One cell of eq. (F) and the Jacobian diagonal; returns (F_t, F_b, D).
+__device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
+                                              const double* __restrict__ Vt,
+                                              const double* __restrict__ Vb, double g,
+                                              double vin_i, double& ft, double& fb,
+                                              double& dg) {
+  const int m = gr.m, n = gr.n;
+  const double vt = Vt[c], vb = Vb[c];
+  const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
+  const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
+  const double tl = (j > 0) ? Vt[c - 1] : 0.0;
+  const double tr = (j < n - 1) ? Vt[c + 1] : 0.0;
+  const double bu = (i > 0) ? Vb[c - n] : 0.0;
+  const double bd = (i < m - 1) ? Vb[c + n] : 0.0;
+  ft = fma(dt, vt, -gr.gt * (tl + tr));
+  if (j == 0) ft = fma(-gr.g_src, vin_i, ft);
+  fb = fma(db, vb, -gr.gb * (bu + bd));
+  const double dv = vt - vb;
+  double cur;
+  if (gr.b != 0.0) {
+    double sh, ch;
+    sinh_cosh(gr.b * dv, sh, ch);
+    cur = (g * gr.inv_b) * sh;
+    dg = g * ch;
+  } else {
+    cur = g * dv;
+    dg = g;
+  }
+  ft += cur;
+  fb -= cur;
 }
 
 __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl* ctl) {
@@ -86,31 +179,13 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int j = c - i * n;
-    const double vt = Vt[c], vb = Vb[c];
-    double ft = ((j > 0 ? gr.gt : gr.g_src) + (j < n - 1 ? gr.gt : gr.g_tr)) * vt;
-    if (j > 0) ft -= gr.gt * Vt[c - 1];
-    if (j < n - 1) ft -= gr.gt * Vt[c + 1];
-    if (j == 0) ft -= gr.g_src * vinb[i];
-    double fb = ((i > 0 ? gr.gb : gr.g_bt) + (i < m - 1 ? gr.gb : gr.g_sense)) * vb;
-    if (i > 0) fb -= gr.gb * Vb[c - n];
-    if (i < m - 1) fb -= gr.gb * Vb[c + n];
-    const double g = gmap[c];
-    const double dv = vt - vb;
-    double cur, dg;
-    if (gr.b != 0.0) {
-      const double zz = gr.b * dv;
-      cur = (g / gr.b) * sinh(zz);
-      dg = g * cosh(zz);
-    } else {
-      cur = g * dv;
-      dg = g;
-    }
-    ft += cur;
-    fb -= cur;
+    double ft, fb, dg;
+    cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg);
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
-    sf += ft * ft + fb * fb;
+    sf = fma(ft, ft, sf);
+    sf = fma(fb, fb, sf);
     sd += dg;
   }
   block_sum2(sf, sd);
@@ -120,64 +195,116 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
   }
 }
 
-// Newton control (eq. Newton3): ||F||, a = mean(D), convergence test, forcing term of
-// the next linear solve (first: eta0; then Eisenstat-Walker 0.9 (|F_k|/|F_k-1|)^2 capped
-// by eta_max, and never tighter than needed to reach the target), GMRES cycle start.
-__global__ void k_newton_control(const double* __restrict__ part, int nblk, int mn,
-                                 VecCtl* ctl, SolverCfg cfg, int32_t* host_flags) {
-  const int b = blockIdx.x;
-  VecCtl& c = ctl[b];
-  if (!c.newton_active) {
-    if (threadIdx.x == 0 && host_flags) host_flags[b] = 0;
-    return;
+// Newton control (eq. Newton3) for one vector from the reduced sums: ||F||, a = mean(D),
+// convergence test, forcing term of the next linear solve (first: eta0; then
+// Eisenstat-Walker 0.9 (|F_k|/|F_k-1|)^2 capped by eta_max, and never tighter than needed
+// to reach the target), GMRES cycle start.  Runs in one thread.
+__device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const SolverCfg& cfg,
+                               int32_t* host_flag) {
+  const double fn = sqrt(sf);
+  const double a = sd / (double)mn;
+  c.fnorm_prev = c.fnorm;
+  c.fnorm = fn;
+  c.a = a;
+  c.gm_active = 0;
+  c.k_done = 0;
+  if (!isfinite(fn) || !isfinite(a)) {
+    c.status = MCA_ERR_NONFINITE;
+    c.newton_active = 0;
+  } else if (fn <= cfg.newton_rtol * c.ynorm) {
+    c.status = MCA_OK;
+    c.newton_active = 0;
+  } else if (c.newton_iters >= cfg.max_newton) {
+    c.status = MCA_ERR_NOT_CONVERGED;
+    c.newton_active = 0;
+  } else {
+    double eta;
+    if (c.newton_iters == 0 || c.fnorm_prev <= 0.0) {
+      eta = cfg.eta0;
+    } else {
+      const double r = fn / c.fnorm_prev;
+      eta = fmin(cfg.eta_max, 0.9 * r * r);
+    }
+    eta = fmax(eta, 0.5 * cfg.newton_rtol * c.ynorm / fn);
+    eta = fmin(eta, 0.5);
+    c.eta = eta;
+    c.tol_abs = eta * fn;
+    c.g[0] = fn;
+    c.res_est = fn;
+    c.gm_active = 1;
+    c.newton_iters += 1;
   }
+  if (host_flag) *host_flag = c.newton_active;
+  __threadfence_system();
+}
+
+// Residual of the solver loop with the Newton control in the last block of each vector.
+// ZERO: the state is x = 0 (first Newton step from V = 0), where F = -Y and D = g.
+template <bool ZERO>
+__global__ void __launch_bounds__(kThreads)
+k_residual_newton(Grid gr, const double* __restrict__ gmap, const double* __restrict__ vin,
+                  const double* __restrict__ x, double* __restrict__ F,
+                  double* __restrict__ D, double* __restrict__ part, int nblk, VecCtl* ctl,
+                  SolverCfg cfg, unsigned int* cnt, int32_t* host_flags) {
+  const int b = blockIdx.y;
+  if (!ctl[b].newton_active) return;
+  const int m = gr.m, n = gr.n;
+  const int mn = m * n;
+  const double* Vt = x + (size_t)b * 2 * mn;
+  const double* Vb = Vt + mn;
+  double* Ft = F + (size_t)b * 2 * mn;
+  double* Fb = Ft + mn;
+  double* Db = D + (size_t)b * mn;
+  const double* vinb = vin + (size_t)b * m;
   double sf = 0.0, sd = 0.0;
-  for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
-    sf += part[((size_t)b * 32 + 0) * nblk + t];
-    sd += part[((size_t)b * 32 + 1) * nblk + t];
+  for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
+    const int i = c / n;
+    const int j = c - i * n;
+    double ft, fb, dg;
+    if (ZERO) {
+      ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
+      fb = 0.0;
+      dg = gmap[c];
+    } else {
+      cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg);
+    }
+    Ft[c] = ft;
+    Fb[c] = fb;
+    Db[c] = dg;
+    sf = fma(ft, ft, sf);
+    sf = fma(fb, fb, sf);
+    sd += dg;
   }
   block_sum2(sf, sd);
+  __shared__ bool last;
   if (threadIdx.x == 0) {
-    const double fn = sqrt(sf);
-    const double a = sd / (double)mn;
-    c.fnorm_prev = c.fnorm;
-    c.fnorm = fn;
-    c.a = a;
-    c.gm_active = 0;
-    c.k_done = 0;
-    if (!isfinite(fn) || !isfinite(a)) {
-      c.status = MCA_ERR_NONFINITE;
-      c.newton_active = 0;
-    } else if (fn <= cfg.newton_rtol * c.ynorm) {
-      c.status = MCA_OK;
-      c.newton_active = 0;
-    } else if (c.newton_iters >= cfg.max_newton) {
-      c.status = MCA_ERR_NOT_CONVERGED;
-      c.newton_active = 0;
-    } else {
-      double eta;
-      if (c.newton_iters == 0 || c.fnorm_prev <= 0.0) {
-        eta = cfg.eta0;
-      } else {
-        const double r = fn / c.fnorm_prev;
-        eta = fmin(cfg.eta_max, 0.9 * r * r);
-      }
-      eta = fmax(eta, 0.5 * cfg.newton_rtol * c.ynorm / fn);
-      eta = fmin(eta, 0.5);
-      c.eta = eta;
-      c.tol_abs = eta * fn;
-      c.g[0] = fn;
-      c.res_est = fn;
-      c.gm_active = 1;
-      c.newton_iters += 1;
-    }
-    if (host_flags) host_flags[b] = c.newton_active;
-    __threadfence_system();
+    part[((size_t)b * 32 + 0) * nblk + blockIdx.x] = sf;
+    part[((size_t)b * 32 + 1) * nblk + blockIdx.x] = sd;
+    __threadfence();
+    last = (atomicAdd(&cnt[b], 1u) == (unsigned)nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // fixed-order sum over blocks: warp 0 -> ||F||^2, warp 1 -> sum(D)
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __shared__ double tot[2];
+  if (w < 2) {
+    double s = 0.0;
+    for (int t = l; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32 + w) * nblk + t]);
+    s = warp_sum(s);
+    if (l == 0) tot[w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cnt[b] = 0;
+    newton_control(ctl[b], tot[0], tot[1], mn, cfg, host_flags ? &host_flags[b] : nullptr);
   }
 }
 
-// v_0 = sign * F / ||F|| (GMRES from dx = 0; sign = -1 for the Newton system J dx = -F) and its BF16 copy in the padded [layer][mp][np]
-// layout read by the tensor-core preconditioner.
+// v_0 = sign * F / ||F|| (GMRES from dx = 0; sign = -1 for the Newton system J dx = -F)
+// and its BF16 copy in the padded [layer][mp][np] layout read by the tensor-core
+// preconditioner.
 __global__ void k_init_basis(const double* __restrict__ F, double sign, double* __restrict__ V0,
                              size_t vstride, __nv_bfloat16* __restrict__ xbf, int mp, int np,
                              int m, int n, const VecCtl* __restrict__ ctl) {
@@ -197,19 +324,33 @@ __global__ void k_init_basis(const double* __restrict__ F, double sign, double* 
       const int l = (int)(e / mn);
       const int cell = (int)(e - (size_t)l * mn);
       const int i = cell / n, j = cell - (cell / n) * n;
-      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = __double2bfloat16(val);
+      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = __float2bfloat16((float)val);
     }
   }
 }
 
+// Deterministic reduction of part[b][j][0..nblk) (j < nk) into h[b][j] by the whole
+// block (warp w sums rows w, w + 8, ...).
+__device__ __forceinline__ void block_reduce_rows(const double* __restrict__ part, int b,
+                                                  int nblk, int nk, double* __restrict__ h) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int j = w; j < nk; j += kThreads / 32) {
+    double s = 0.0;
+    for (int t = l; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32 + j) * nblk + t]);
+    s = warp_sum(s);
+    if (l == 0) h[(size_t)b * 32 + j] = s;
+  }
+}
+
 // K2 fused with the first classical Gram-Schmidt pass: w = J z for one cell (both
-// layers), then partial dots <V_j, w> for j < nk.
+// layers), then partial dots <V_j, w> for j < nk; the last block of each vector reduces
+// the partials into h.
 template <int KP>
 __global__ void __launch_bounds__(kThreads)
 k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
             size_t zstride, double* __restrict__ w, const double* __restrict__ V,
             size_t vstride, int nk, double* __restrict__ part, int nblk,
-            const VecCtl* __restrict__ ctl) {
+            const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h) {
   const int b = blockIdx.y;
   if (ctl != nullptr && !ctl[b].gm_active) return;
   const int m = gr.m, n = gr.n, mn = m * n;
@@ -228,14 +369,14 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
     const int jj = c - i * n;
     const double a = zt[c], bb = zb[c];
     const double cpl = Db[c] * (a - bb);
-    double ot = ((jj > 0 ? gr.gt : gr.g_src) + (jj < n - 1 ? gr.gt : gr.g_tr)) * a;
-    if (jj > 0) ot -= gr.gt * zt[c - 1];
-    if (jj < n - 1) ot -= gr.gt * zt[c + 1];
-    ot += cpl;
-    double ob = ((i > 0 ? gr.gb : gr.g_bt) + (i < m - 1 ? gr.gb : gr.g_sense)) * bb;
-    if (i > 0) ob -= gr.gb * zb[c - n];
-    if (i < m - 1) ob -= gr.gb * zb[c + n];
-    ob -= cpl;
+    const double dt = (jj == 0) ? gr.dt0 : ((jj == n - 1) ? gr.dtl : gr.dtm);
+    const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
+    const double tl = (jj > 0) ? zt[c - 1] : 0.0;
+    const double tr = (jj < n - 1) ? zt[c + 1] : 0.0;
+    const double bu = (i > 0) ? zb[c - n] : 0.0;
+    const double bd = (i < m - 1) ? zb[c + n] : 0.0;
+    const double ot = fma(dt, a, fma(-gr.gt, tl + tr, cpl));
+    const double ob = fma(db, bb, fma(-gr.gb, bu + bd, -cpl));
     wt[c] = ot;
     wb[c] = ob;
     if (V != nullptr) {
@@ -263,7 +404,17 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
 #pragma unroll
     for (int q = 0; q < kThreads / 32; ++q) s += red[q][threadIdx.x];
     part[((size_t)b * 32 + threadIdx.x) * nblk + blockIdx.x] = s;
+    __threadfence();
   }
+  if (cnt == nullptr) return;
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&cnt[b], 1u) == (unsigned)nblk - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  block_reduce_rows(part, b, nblk, nk, h);
+  if (threadIdx.x == 0) cnt[b] = 0;
 }
 
 // Output currents and the Kirchhoff balance per vector.
@@ -313,9 +464,17 @@ void launch_residual(const Grid& gr, const double* gmap, const double* vin, cons
   k_residual<<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
 }
 
-void launch_newton_control(const double* part, int nblk, int mn, VecCtl* ctl, int B,
-                           SolverCfg cfg, int32_t* host_flags, cudaStream_t s) {
-  k_newton_control<<<B, kThreads, 0, s>>>(part, nblk, mn, ctl, cfg, host_flags);
+void launch_residual_newton(const Grid& gr, const double* gmap, const double* vin,
+                            const double* x, bool zero_state, double* F, double* D,
+                            double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
+                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s) {
+  dim3 grid(nblk, B);
+  if (zero_state)
+    k_residual_newton<true><<<grid, kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl,
+                                                      cfg, cnt, host_flags);
+  else
+    k_residual_newton<false><<<grid, kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl,
+                                                       cfg, cnt, host_flags);
 }
 
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
@@ -329,22 +488,21 @@ void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
 
 void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
-                      int nblk, int B, const VecCtl* ctl, cudaStream_t s) {
+                      int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
+                      cudaStream_t s) {
   // z: the vector of batch entry 0, later entries zstride doubles apart; V: basis vector
   // 0 of batch entry 0 (nk vectors N2 apart, entries vstride apart), or NULL.
   dim3 grid(nblk, B);
-  if (nk <= 1)
-    k_spmv_dots<1><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, ctl);
-  else if (nk <= 2)
-    k_spmv_dots<2><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, ctl);
-  else if (nk <= 4)
-    k_spmv_dots<4><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, ctl);
-  else if (nk <= 8)
-    k_spmv_dots<8><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, ctl);
-  else if (nk <= 16)
-    k_spmv_dots<16><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, ctl);
-  else
-    k_spmv_dots<32><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, ctl);
+#define MCA_SPMV(KP_)                                                                    \
+  k_spmv_dots<KP_><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, \
+                                             nblk, ctl, cnt, h)
+  if (nk <= 1) MCA_SPMV(1);
+  else if (nk <= 2) MCA_SPMV(2);
+  else if (nk <= 4) MCA_SPMV(4);
+  else if (nk <= 8) MCA_SPMV(8);
+  else if (nk <= 16) MCA_SPMV(16);
+  else MCA_SPMV(32);
+#undef MCA_SPMV
 }
 
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,

@@ -70,6 +70,7 @@ struct mca_handle {
   double *part = nullptr, *h1 = nullptr, *h2 = nullptr;
   double *vin = nullptr, *iout = nullptr, *kcl = nullptr;
   VecCtl* ctl = nullptr;
+  unsigned int* cnt = nullptr;    // per-vector block counters of the fused reductions
   int32_t* hflags = nullptr;      // pinned, mapped
   int32_t* hflags_dev = nullptr;
   int* err = nullptr;
@@ -221,7 +222,9 @@ int alloc_workspace(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->kcl, B));
   MCA_TRY(dalloc(h, &h->ctl, B));
   MCA_TRY(dalloc(h, &h->err, 1));
+  MCA_TRY(dalloc(h, &h->cnt, B));
   MCA_CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+  MCA_CUDA_TRY(cudaMemset(h->cnt, 0, B * sizeof(unsigned int)));
   MCA_CUDA_TRY(cudaMemset(h->ctl, 0, B * sizeof(VecCtl)));
   if (h->p.precision == MCA_PREC_FP64) {
     MCA_TRY(dalloc(h, &h->T1_64, B * n2));
@@ -400,29 +403,19 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
     MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k));
     cudaEvent_t t0 = prof_begin(h, s);
     launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
-                     h->ctl, s);
+                     h->ctl, h->cnt, h->h1, s);
     count_launches(1);
-    prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (14.0 + 4.0 * nk), s);
+    prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (12.0 + 4.0 * nk), s);
     t0 = prof_begin(h, s);
-    launch_reduce_dots(h->part, nbS, k + 1, h->h1, B, h->ctl, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_SMALL, k, 0.0, 0.0, s);
-    t0 = prof_begin(h, s);
-    launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, s);
+    launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, h->cnt,
+                       h->h2, s);
     count_launches(1);
     prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k, cells * (32.0 + 16.0 * nk), cells * 8.0 * nk, s);
     t0 = prof_begin(h, s);
-    launch_reduce_dots(h->part, nbV, k + 1, h->h2, B, h->ctl, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_SMALL, k, 0.0, 0.0, s);
-    t0 = prof_begin(h, s);
-    launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, s);
+    launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, h->cnt,
+                       h->h1, h->restart, h->hflags_dev, s);
     count_launches(1);
     prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk), cells * (4.0 * nk + 4.0), s);
-    t0 = prof_begin(h, s);
-    launch_givens(h->part, nbV, h->h1, h->h2, k, h->restart, h->ctl, B, h->hflags_dev, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_SMALL, k, 0.0, 0.0, s);
     t0 = prof_begin(h, s);
     launch_normalize(h->W, h->V + (size_t)(k + 1) * n2, vstride, n2, tc ? h->Xbf : nullptr,
                      h->mp, h->np, h->m, h->n, h->ctl, B, s);
@@ -477,13 +470,13 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s) {
   int n_active = B;  // vectors entering the current Newton step
   for (int it = 0; it <= h->p.max_newton; ++it) {
     cudaEvent_t t0 = prof_begin(h, s);
-    launch_residual(h->gr, h->g, h->vin, h->x, h->F, h->D, h->part, nbR, B, h->ctl, s);
+    launch_residual_newton(h->gr, h->g, h->vin, h->x, it == 0, h->F, h->D, h->part, nbR, B,
+                           h->ctl, cfg, h->cnt, h->hflags_dev, s);
     count_launches(1);
-    prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * 48.0, cells * 30.0, s);
-    t0 = prof_begin(h, s);
-    launch_newton_control(h->part, nbR, (int)h->mn, h->ctl, B, cfg, h->hflags_dev, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_SMALL, -1, 0.0, 0.0, s);
+    // FP64 flops per cell: stencils 12, Taylor sinh/cosh 42, current/conductance 6,
+    // norms 5 (the zero state only the norms)
+    prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * (it == 0 ? 32.0 : 48.0),
+             cells * (it == 0 ? 5.0 : 65.0), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
     const int entering = n_active;
@@ -545,7 +538,7 @@ void mca_default_params(mca_params* p) {
   p->max_newton = 20;
   p->max_batch = 4;
   p->newton_rtol = 1e-8;
-  p->eta0 = 1e-4;
+  p->eta0 = 1e-3;
   p->eta_max = 1e-2;
 }
 
@@ -597,15 +590,7 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
   h->n2 = 2 * h->mn;
   h->restart = p->gmres_restart;
   h->Bmax = p->max_batch;
-  h->gr.m = h->m;
-  h->gr.n = h->n;
-  h->gr.gt = p->g_wire_top;
-  h->gr.gb = p->g_wire_bot;
-  h->gr.g_src = p->g_src;
-  h->gr.g_tr = p->g_term_top_right;
-  h->gr.g_bt = p->g_term_bot_top;
-  h->gr.g_sense = p->g_sense;
-  h->gr.b = p->b;
+  h->gr = make_grid(*p);
   auto fail = [&](int code) {
     mca_destroy(h);
     return code;
@@ -755,7 +740,7 @@ int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* 
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_spmv_dots(h->gr, D, z, h->n2, w, nullptr, 0, 0, h->part, residual_nblk((int)h->mn),
-                   nvec, nullptr, s);
+                   nvec, nullptr, nullptr, nullptr, s);
   count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
   MCA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -833,7 +818,8 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
                                cudaMemcpyDeviceToDevice, s));
   MCA_CUDA_TRY(cudaMemcpyAsync(h->W, rhs, (size_t)nvec * n2 * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
-  launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, s);
+  launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, nullptr,
+                     nullptr, h->restart, nullptr, s);
   count_launches(1);
   launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, s);
   count_launches(1);

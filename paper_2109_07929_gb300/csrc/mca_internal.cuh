@@ -51,7 +51,14 @@ struct Grid {
   double g_src, g_tr;       // top-row ends: source (j = 0), termination (j = n-1)
   double g_bt, g_sense;     // bottom-column ends: termination (i = 0), sense (i = m-1)
   double b;                 // sinh nonlinearity (0 = linear device)
+  double inv_b;             // 1 / b (0 when b = 0)
+  // diagonals of the wire operators (eq. G with terminations): first / inside / last node
+  double dt0, dtm, dtl;     // top row, along j
+  double db0, dbm, dbl;     // bottom column, along i
 };
+
+// Fill a Grid from the circuit parameters.
+Grid make_grid(const mca_params& p);
 
 struct SolverCfg {
   double newton_rtol;
@@ -74,14 +81,22 @@ void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
 void launch_residual(const Grid& gr, const double* gmap, const double* vin, const double* x,
                      double* F, double* D, double* part, int nblk, int B, const VecCtl* ctl,
                      cudaStream_t s);
-void launch_newton_control(const double* part, int nblk, int mn, VecCtl* ctl, int B,
-                           SolverCfg cfg, int32_t* host_flags, cudaStream_t s);
+// Residual of the solver loop: zero_state skips the device model at x = 0 (F = -Y,
+// D = g); the last block of each vector runs the Newton control (convergence test,
+// forcing term, start of the GMRES cycle).
+void launch_residual_newton(const Grid& gr, const double* gmap, const double* vin,
+                            const double* x, bool zero_state, double* F, double* D,
+                            double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
+                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s);
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
                        __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
                        int B, cudaStream_t s);
+// w = J z fused with the partial dots <V_j, w> (j < nk); with cnt != NULL the last block
+// of each vector also reduces them into h[b][j].
 void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
-                      int nblk, int B, const VecCtl* ctl, cudaStream_t s);
+                      int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
+                      cudaStream_t s);
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,
                     double* kcl, int B, cudaStream_t s);
 int residual_nblk(int mn);
@@ -89,15 +104,16 @@ int residual_nblk(int mn);
 int vec_nblk(size_t n2);
 void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
                         const VecCtl* ctl, cudaStream_t s);
+// pass 2: w -= V h1, partial dots <V_j, w>; the last block reduces them into h2.
 void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h, double* part, int nblk, int B, const VecCtl* ctl,
-                        cudaStream_t s);
+                        const double* h1, double* part, int nblk, int B, const VecCtl* ctl,
+                        unsigned int* cnt, double* h2, cudaStream_t s);
+// pass 3: w -= V h2 and ||w||^2; with cnt != NULL the last block of each vector applies
+// the Givens rotation of column nk-1 (restart = cycle length) and updates the flags.
 void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h, double* part, int nblk, int B, const VecCtl* ctl,
-                        cudaStream_t s);
-void launch_givens(const double* part_norm, int nblk, const double* h1, const double* h2,
-                   int k, int restart, VecCtl* ctl, int B, int32_t* host_flags,
-                   cudaStream_t s);
+                        const double* h2, double* part, int nblk, int B, VecCtl* ctl,
+                        unsigned int* cnt, const double* h1, int restart,
+                        int32_t* host_flags, cudaStream_t s);
 void launch_normalize(const double* w, double* vnext, size_t vstride, size_t n2,
                       __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
                       int B, cudaStream_t s);

@@ -100,16 +100,7 @@ extern "C" int mca_residual_noalloc(const mca_params* p, const double* g_map, co
   double* part = nullptr;
   int rc = scratch_address(&part);
   if (rc != MCA_OK) return rc;
-  Grid gr;
-  gr.m = p->rows;
-  gr.n = p->cols;
-  gr.gt = p->g_wire_top;
-  gr.gb = p->g_wire_bot;
-  gr.g_src = p->g_src;
-  gr.g_tr = p->g_term_top_right;
-  gr.g_bt = p->g_term_bot_top;
-  gr.g_sense = p->g_sense;
-  gr.b = p->b;
+  const Grid gr = make_grid(*p);
   const int mn = gr.m * gr.n;
   const int nblk = residual_nblk(mn);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

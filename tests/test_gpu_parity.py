@@ -58,12 +58,15 @@ def test_eigenpairs(m, n):
         np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-10)
 
 
+@pytest.mark.parametrize("vrange", [0.35, 2.0], ids=["series", "wide"])
 @pytest.mark.parametrize("m,n", SHAPES)
-def test_residual_and_jacobian_diagonal(m, n):
+def test_residual_and_jacobian_diagonal(m, n, vrange):
+    """|b dV| <= 1 uses the Taylor form of sinh/cosh, larger |b dV| the library
+    functions; both must agree with NumPy's sinh/cosh to FP64 rounding."""
     cb = mi.make_crossbar(m, n, 2, nvec=2)
     p = cb.params
     rng = np.random.default_rng(5)
-    x = rng.uniform(-0.1, 0.35, size=(2, 2 * m * n))
+    x = rng.uniform(-vrange / 3.5, vrange, size=(2, 2 * m * n))
     with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=2), cb.gmap) as s:
         F = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
         D = torch.empty(2, m * n, dtype=torch.float64, device=DEV)
@@ -73,7 +76,9 @@ def test_residual_and_jacobian_diagonal(m, n):
     Gt, Gb = O.layer_operators(p)
     for v in range(2):
         Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], x[v, :m * n], x[v, m * n:])
-        scale = 4 * max(p.g_wire_top, p.g_wire_bot) * np.abs(x[v]).max() + p.g_src * 0.3
+        dv = x[v, :m * n] - x[v, m * n:]
+        cur = np.abs(cb.gmap.ravel() / p.b * np.sinh(p.b * dv)).max()
+        scale = 4 * max(p.g_wire_top, p.g_wire_bot) * np.abs(x[v]).max() + p.g_src * 0.3 + cur
         np.testing.assert_allclose(F[v], np.concatenate([Ft, Fb]), rtol=0, atol=1e-14 * scale)
         Dr = O.device_conductance(cb.gmap.ravel(), p.b, x[v, :m * n] - x[v, m * n:])
         np.testing.assert_allclose(D[v], Dr, rtol=1e-14)
