@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--precision", default="bf16split", choices=["bf16split", "bf16", "fp64"])
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -356,6 +357,10 @@ def run_ours(args):
                                 "gmres_iters_per_solve": st1[0].gmres_iters,
                                 "speedup_of_mixed": value / (world * nf / t64)}
 
+    # ---- the batched statistical-characterisation workload (secondary figure)
+    if not args.no_batched and args.size == 1024:
+        out["batched_c4"] = run_batched_c4(mca, torch)
+
     # ---- CPU oracle on the host cores (rank 0, one GPU only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         tcpu = oracle_solves(cb, 1)
@@ -367,6 +372,74 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
+    """Statistical characterisation: `count` crossbars with rows/cols drawn from
+    {64,128,256,512}, log-uniform g with lognormal 0.1 variation, `nvec` input vectors
+    each, solved to 1e-8.  Crossbars of one shape share a multi-map handle (one batch,
+    one eigenbasis); the shape groups run concurrently on `threads` streams with CUDA-graph
+    replay and autotuned tiles.  Baseline: one handle per crossbar, solved one after the
+    other.  Wall-clock time of the solves only (handles are created beforehand)."""
+    cbs = mi.config_batched(count=count, nvec=nvec)
+    groups = {}
+    for k, cb in enumerate(cbs):
+        groups.setdefault((cb.params.rows, cb.params.cols), []).append(k)
+
+    def params_for(p, B):
+        return mca.default_params(p.rows, p.cols, g_wire_top=p.g_wire_top,
+                                  g_wire_bot=p.g_wire_bot, g_src=p.g_src,
+                                  g_term_top_right=p.g_term_top_right,
+                                  g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
+                                  newton_rtol=TOL, max_batch=B, gmres_restart=16)
+
+    solvers, vins, maps = [], [], []
+    for (m, n), ks in sorted(groups.items()):
+        p = cbs[ks[0]].params
+        B = min(64, len(ks) * nvec)   # one pass per shape group where it fits
+        solvers.append(mca.Solver(params_for(p, B), np.stack([cbs[k].gmap for k in ks])))
+        vins.append(np.concatenate([cbs[k].vin for k in ks]))
+        maps.append(np.repeat(np.arange(len(ks)), nvec))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vins_d = [torch.as_tensor(v, device=dev) for v in vins]
+    outs_d = [(torch.empty(v.shape[0], s.m, s.n, dtype=torch.float64, device=dev),
+               torch.empty(v.shape[0], s.m, s.n, dtype=torch.float64, device=dev),
+               torch.empty(v.shape[0], s.n, dtype=torch.float64, device=dev))
+              for s, v in zip(solvers, vins)]
+    mca.solve_many(solvers, vins_d, map_indices=maps, n_threads=threads, outs=outs_d)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = mca.solve_many(solvers, vins_d, map_indices=maps, n_threads=threads, outs=outs_d)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    worst = max(x["rel_residual"] for o in out for x in o[3])
+    its = np.mean([x["gmres_iters"] for o in out for x in o[3]])
+    for s in solvers:
+        s.close()
+    # baseline: one handle per crossbar, sequential (a sample of 16 crossbars, scaled)
+    sample = list(range(0, count, max(1, count // 16)))
+    tb = 0.0
+    for k in sample:
+        cb = cbs[k]
+        with mca.Solver(params_for(cb.params, nvec), cb.gmap) as s1:
+            vin_d = torch.as_tensor(cb.vin, device=dev)
+            vt = torch.empty(nvec, s1.m, s1.n, dtype=torch.float64, device=dev)
+            vb = torch.empty_like(vt)
+            io = torch.empty(nvec, s1.n, dtype=torch.float64, device=dev)
+            s1.solve(vin_d, vt, vb, io)
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            s1.solve(vin_d, vt, vb, io)
+            torch.cuda.synchronize()
+            tb += time.perf_counter() - a
+    return {"value": count * nvec / t, "unit": "solves/s", "solves": count * nvec,
+            "crossbars": count, "shape_groups": len(groups), "threads": threads,
+            "max_rel_residual": worst, "gmres_iters_per_solve": float(its),
+            "one_handle_per_crossbar_value": len(sample) * nvec / tb,
+            "workload": "128 crossbars, rows/cols from {64,128,256,512}, 16 V_in each, "
+                        "log-uniform g x lognormal(0.1), BF16-split preconditioner, "
+                        "CUDA graphs, autotuned tiles, device-resident inputs and outputs, "
+                        "wall clock of the solves"}
 
 
 # FP64 CUDA-core peak used for the FP64 form: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.

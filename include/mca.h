@@ -76,7 +76,13 @@ typedef struct mca_params {
   double newton_rtol;        /* stop when ||F||_2 / ||Y||_2 <= newton_rtol               */
   double eta0;               /* relative tolerance of the first linear solve             */
   double eta_max;            /* upper bound of later forcing terms                       */
+  int32_t flags;             /* MCA_FLAG_* bit set                                       */
+  int32_t reserved;
 } mca_params;
+
+/* ---- flags --------------------------------------------------------------------------- */
+#define MCA_FLAG_GRAPHS 1      /* replay each GMRES iteration as a captured CUDA graph      */
+#define MCA_FLAG_AUTOTUNE 2    /* time the tensor-core tile widths at create, keep the best */
 
 typedef struct mca_stats {
   int32_t status;            /* MCA_OK, MCA_ERR_NOT_CONVERGED or MCA_ERR_NONFINITE       */
@@ -91,7 +97,8 @@ typedef struct mca_handle mca_handle;
 
 /* Fill *p with the defaults: 1 S wires, 10 ohm driver and sense, 1 kohm terminations,
  * b = 2, MCA_PREC_BF16_SPLIT, restart 30, max_newton 20, max_batch 4, newton_rtol 1e-8,
- * eta0 1e-3, eta_max 1e-2.  rows/cols are left at 0 and must be set. */
+ * eta0 1e-3, eta_max 1e-2, flags MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE.  rows/cols are
+ * left at 0 and must be set. */
 void mca_default_params(mca_params* p);
 
 /* Create a solver for one crossbar.
@@ -118,6 +125,31 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out);
  * MCA_ERR_INVALID_ARG / MCA_ERR_CUDA / MCA_ERR_TIMEOUT. */
 int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, double* v_bot,
               double* i_out, mca_stats* stats, void* stream);
+
+/* Several crossbars of one shape and wiring in one handle (the statistical-
+ * characterisation workload): n_maps conductance maps share the eigenbasis and the
+ * tensor-core operands, and every input vector picks its map, so vectors of different
+ * crossbars run in the same batched kernels.
+ *   g_maps : n_maps * m*n conductances (host or device), map k at k*m*n.
+ * mca_create(p, g, out) equals mca_create_multi(p, g, 1, out). */
+int mca_create_multi(const mca_params* p, const double* g_maps, int32_t n_maps,
+                     mca_handle** out);
+
+/* mca_solve for a handle with several maps: map_index (host, nvec entries, each in
+ * 0..n_maps-1) selects vector v's crossbar; NULL means map 0 for every vector.  Output
+ * layouts as in mca_solve. */
+int mca_solve_multi(mca_handle* h, const double* v_in, const int32_t* map_index, int32_t nvec,
+                    double* v_top, double* v_bot, double* i_out, mca_stats* stats,
+                    void* stream);
+
+/* Solve nh handles concurrently: worker k of n_threads host threads takes handles in turn
+ * and runs mca_solve_multi on a stream of its own, so crossbars of different shapes
+ * overlap on the GPU.  Arrays are indexed by handle; entries of the output arrays may be
+ * NULL.  Returns MCA_OK or the first failing status. */
+int mca_solve_many(mca_handle* const* hs, int32_t nh, const double* const* v_in,
+                   const int32_t* const* map_index, const int32_t* nvec,
+                   double* const* v_top, double* const* v_bot, double* const* i_out,
+                   mca_stats* const* stats, int32_t n_threads);
 
 /* Release the handle and its device memory.  NULL is ignored. */
 void mca_destroy(mca_handle* h);

@@ -18,6 +18,9 @@ PREC_FP64 = 0
 PREC_BF16 = 1
 PREC_BF16_SPLIT = 2
 
+FLAG_GRAPHS = 1
+FLAG_AUTOTUNE = 2
+
 OK = 0
 ERR_INVALID_ARG = -1
 ERR_CUDA = -2
@@ -31,7 +34,8 @@ EXPORTED = (
     "mca_default_params", "mca_create", "mca_solve", "mca_destroy", "mca_strerror",
     "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_precond_apply",
     "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
-    "mca_kernel_launches", "mca_residual_noalloc",
+    "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
+    "mca_solve_many",
 )
 
 FAMILIES = ("residual", "spmv_dots", "update_dots", "update_norm", "normalize", "small",
@@ -49,6 +53,7 @@ class Params(ctypes.Structure):
         ("max_newton", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("newton_rtol", ctypes.c_double), ("eta0", ctypes.c_double),
         ("eta_max", ctypes.c_double),
+        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -89,6 +94,9 @@ def load(build_if_missing=True):
     lib.mca_default_params.argtypes = [ctypes.POINTER(Params)]
     lib.mca_default_params.restype = None
     lib.mca_create.argtypes = [ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+    lib.mca_create_multi.argtypes = [ctypes.POINTER(Params), P, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.mca_solve_multi.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P]
+    lib.mca_solve_many.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P, ctypes.c_int32]
     lib.mca_solve.argtypes = [P, P, ctypes.c_int32, P, P, P, P, P]
     lib.mca_destroy.argtypes = [P]
     lib.mca_destroy.restype = None
@@ -108,7 +116,8 @@ def load(build_if_missing=True):
     lib.mca_residual_noalloc.restype = ctypes.c_int
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
-    for name in ("mca_create", "mca_solve", "mca_residual", "mca_jacobian_apply",
+    for name in ("mca_create", "mca_create_multi", "mca_solve_multi", "mca_solve_many",
+                 "mca_solve", "mca_residual", "mca_jacobian_apply",
                  "mca_precond_apply", "mca_eigenpairs", "mca_gmres_solve", "mca_profile",
                  "mca_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
@@ -152,6 +161,40 @@ def kernel_launches():
     return int(load().mca_kernel_launches())
 
 
+def solve_many(solvers, vins, map_indices=None, n_threads=4, outs=None):
+    """Solve several Solver objects concurrently (host threads, one stream each).  vins[k]
+    is a host array or device tensor (nvec_k, m_k); outs[k] = (v_top, v_bot, i_out)
+    buffers (host or device, default host NumPy).  Returns per solver (v_top, v_bot,
+    i_out, stats)."""
+    lib = load()
+    nh = len(solvers)
+    H = (ctypes.c_void_p * nh)(*[s.h.value for s in solvers])
+    vins = [np.ascontiguousarray(v, np.float64) if isinstance(v, np.ndarray) else v
+            for v in vins]
+    if outs is None:
+        outs = [(np.empty((v.shape[0], s.m, s.n)), np.empty((v.shape[0], s.m, s.n)),
+                 np.empty((v.shape[0], s.n))) for s, v in zip(solvers, vins)]
+    outs = [tuple(o) + ((Stats * v.shape[0])(),) for o, v in zip(outs, vins)]
+    PA = ctypes.c_void_p * nh
+    VIN = PA(*[_ptr(v) for v in vins])
+    mis = None
+    if map_indices is not None:
+        keep = [np.ascontiguousarray(x, np.int32) for x in map_indices]
+        mis = PA(*[x.ctypes.data for x in keep])
+    NV = (ctypes.c_int32 * nh)(*[v.shape[0] for v in vins])
+    VT = PA(*[_ptr(o[0]) for o in outs])
+    VB = PA(*[_ptr(o[1]) for o in outs])
+    IO = PA(*[_ptr(o[2]) for o in outs])
+    ST = PA(*[ctypes.cast(o[3], ctypes.c_void_p).value for o in outs])
+    _check(lib.mca_solve_many(H, nh, VIN, mis, NV, VT, VB, IO, ST, n_threads))
+    res = []
+    for o in outs:
+        stats = [dict(status=x.status, newton_iters=x.newton_iters, gmres_iters=x.gmres_iters,
+                      rel_residual=x.rel_residual, kcl_rel_error=x.kcl_rel_error) for x in o[3]]
+        res.append((o[0], o[1], o[2], stats))
+    return res
+
+
 def residual_noalloc(params, gmap, x, vin, F, D, fnorm=None, dmean=None, stream=None):
     """mca_residual_noalloc on device tensors (no handle, no device allocation)."""
     rc = load().mca_residual_noalloc(ctypes.byref(params), _ptr(gmap), _ptr(x), _ptr(vin),
@@ -177,12 +220,15 @@ class Solver:
     """One crossbar: ``Solver(params, gmap)`` then ``solve(vin)``."""
 
     def __init__(self, params: Params, gmap):
+        """gmap: (m, n) for one crossbar, or (k, m, n) for k crossbars of this shape."""
         self.lib = load()
         self.params = params
         self.m, self.n = params.rows, params.cols
         g = gmap if not isinstance(gmap, np.ndarray) else np.ascontiguousarray(gmap, np.float64)
+        self.n_maps = int(g.shape[0]) if g.ndim == 3 else 1
         h = ctypes.c_void_p()
-        _check(self.lib.mca_create(ctypes.byref(params), _ptr(g), ctypes.byref(h)))
+        _check(self.lib.mca_create_multi(ctypes.byref(params), _ptr(g), self.n_maps,
+                                         ctypes.byref(h)))
         self.h = h
 
     def close(self):
@@ -203,11 +249,12 @@ class Solver:
         self.close()
 
     def solve(self, vin, v_top=None, v_bot=None, i_out=None, stream=None,
-              allow_not_converged=False):
+              allow_not_converged=False, map_index=None):
         """Solve for ``nvec`` input vectors.  ``vin`` is (nvec, m) host or device; the
-        output buffers default to host NumPy arrays.  Returns (v_top, v_bot, i_out,
-        stats list)."""
+        output buffers default to host NumPy arrays; ``map_index`` (nvec ints) picks each
+        vector's crossbar in a multi-map solver.  Returns (v_top, v_bot, i_out, stats)."""
         nvec = vin.shape[0] if vin.ndim == 2 else 1
+        mi = None if map_index is None else np.ascontiguousarray(map_index, np.int32)
         if isinstance(vin, np.ndarray):
             vin = np.ascontiguousarray(vin, np.float64)
         if v_top is None:
@@ -217,8 +264,9 @@ class Solver:
         if i_out is None:
             i_out = np.empty((nvec, self.n))
         st = (Stats * nvec)()
-        rc = self.lib.mca_solve(self.h, _ptr(vin), nvec, _ptr(v_top), _ptr(v_bot), _ptr(i_out),
-                                ctypes.cast(st, ctypes.c_void_p), _stream_ptr(stream))
+        rc = self.lib.mca_solve_multi(self.h, _ptr(vin), _ptr(mi), nvec, _ptr(v_top),
+                                      _ptr(v_bot), _ptr(i_out), ctypes.cast(st, ctypes.c_void_p),
+                                      _stream_ptr(stream))
         allow = (ERR_NOT_CONVERGED, ERR_NONFINITE) if allow_not_converged else ()
         _check(rc, allow)
         stats = [dict(status=s.status, newton_iters=s.newton_iters, gmres_iters=s.gmres_iters,

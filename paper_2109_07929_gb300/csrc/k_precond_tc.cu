@@ -421,6 +421,34 @@ cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtens
   return cudaErrorInvalidValue;
 }
 
+// Set the dynamic shared-memory limit of every GEMM instantiation up front, so no
+// attribute call happens later inside a stream capture.
+cudaError_t configure_all() {
+  const CUtensorMap* none = nullptr;
+  (void)none;
+#define MCA_TC_CFG(BN_, SPLIT_, EPI_)                                                   \
+  {                                                                                     \
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN_, SPLIT_, EPI_>,                  \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         Layout<BN_, SPLIT_>::SMEM);                    \
+    if (e != cudaSuccess) return e;                                                     \
+  }
+  MCA_TC_CFG(128, false, EPI_BF16)
+  MCA_TC_CFG(64, false, EPI_BF16)
+  MCA_TC_CFG(128, false, EPI_MODES)
+  MCA_TC_CFG(64, false, EPI_MODES)
+  MCA_TC_CFG(128, false, EPI_MODES_SPLIT)
+  MCA_TC_CFG(64, false, EPI_MODES_SPLIT)
+  MCA_TC_CFG(128, false, EPI_F64)
+  MCA_TC_CFG(64, false, EPI_F64)
+  MCA_TC_CFG(128, true, EPI_SPLIT)
+  MCA_TC_CFG(64, true, EPI_SPLIT)
+  MCA_TC_CFG(128, true, EPI_F64)
+  MCA_TC_CFG(64, true, EPI_F64)
+#undef MCA_TC_CFG
+  return cudaSuccess;
+}
+
 void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
               int np, int B, cudaStream_t s) {
   const size_t n2 = 2 * (size_t)m * n;

@@ -242,7 +242,8 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
 // ZERO: the state is x = 0 (first Newton step from V = 0), where F = -Y and D = g.
 template <bool ZERO>
 __global__ void __launch_bounds__(kThreads)
-k_residual_newton(Grid gr, const double* __restrict__ gmap, const double* __restrict__ vin,
+k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restrict__ map_of,
+                  const double* __restrict__ vin,
                   const double* __restrict__ x, double* __restrict__ F,
                   double* __restrict__ D, double* __restrict__ part, int nblk, VecCtl* ctl,
                   SolverCfg cfg, unsigned int* cnt, int32_t* host_flags) {
@@ -250,6 +251,8 @@ k_residual_newton(Grid gr, const double* __restrict__ gmap, const double* __rest
   if (!ctl[b].newton_active) return;
   const int m = gr.m, n = gr.n;
   const int mn = m * n;
+  // conductance map of this vector's crossbar (several crossbars of one shape share a batch)
+  const double* gmap = gmaps + (map_of ? (size_t)map_of[b] * mn : (size_t)0);
   const double* Vt = x + (size_t)b * 2 * mn;
   const double* Vb = Vt + mn;
   double* Ft = F + (size_t)b * 2 * mn;
@@ -464,17 +467,18 @@ void launch_residual(const Grid& gr, const double* gmap, const double* vin, cons
   k_residual<<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
 }
 
-void launch_residual_newton(const Grid& gr, const double* gmap, const double* vin,
-                            const double* x, bool zero_state, double* F, double* D,
-                            double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
-                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s) {
+void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
+                            const double* vin, const double* x, bool zero_state, double* F,
+                            double* D, double* part, int nblk, int B, VecCtl* ctl,
+                            SolverCfg cfg, unsigned int* cnt, int32_t* host_flags,
+                            cudaStream_t s) {
   dim3 grid(nblk, B);
   if (zero_state)
-    k_residual_newton<true><<<grid, kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl,
-                                                      cfg, cnt, host_flags);
+    k_residual_newton<true><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, D, part,
+                                                      nblk, ctl, cfg, cnt, host_flags);
   else
-    k_residual_newton<false><<<grid, kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl,
-                                                       cfg, cnt, host_flags);
+    k_residual_newton<false><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, D, part,
+                                                       nblk, ctl, cfg, cnt, host_flags);
 }
 
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,

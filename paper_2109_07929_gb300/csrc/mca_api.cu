@@ -15,6 +15,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <utility>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,11 +33,14 @@ namespace mca {
 namespace {
 thread_local std::string g_last_error;
 std::atomic<int64_t> g_launches{0};
+thread_local bool g_capturing = false;   // launches recorded into a graph are counted on replay
 }
 
 // Every kernel launch of the library goes through one of the launch_* wrappers; their
 // call sites add to this counter.
-void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void count_launches(int n) {
+  if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
@@ -58,8 +65,11 @@ struct mca_handle {
   int restart = 30;
   int Bmax = 1;
   int device = 0;
-  // crossbar + eigenbasis (FP64)
+  // crossbars + eigenbasis (FP64): n_maps conductance maps of this shape
+  int n_maps = 1;
   double* g = nullptr;
+  int* map_of = nullptr;               // device: map of each vector of the current pass
+  std::vector<int> map_host;
   double *mu = nullptr, *nu = nullptr, *Qr = nullptr, *Qc = nullptr, *QrT = nullptr,
          *QcT = nullptr;
   // BF16 copies (padded)
@@ -84,8 +94,13 @@ struct mca_handle {
   std::vector<void*> allocs;
   cudaEvent_t ev[MCA_KMAX + 1];
   bool ev_ok = false;
+  // Work requested on the legacy default stream runs on this blocking stream instead
+  // (same ordering with the legacy stream, and legal to capture into graphs).
+  cudaStream_t own_stream = nullptr;
   // statistics of the last solve pass (host copies)
   std::vector<VecCtl> ctl_host;
+  // captured GMRES iterations, keyed by (iteration k, batch size B)
+  std::map<std::pair<int, int>, std::pair<cudaGraphExec_t, int>> graphs;
   // kernel-family timing
   struct ProfRec {
     int fam, k;
@@ -152,6 +167,10 @@ int validate(const mca_params* p) {
     set_error("gmres_restart in 1..30, max_newton >= 1, max_batch in 1..64");
     return MCA_ERR_INVALID_ARG;
   }
+  if (p->flags & ~(MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE)) {
+    set_error("unknown flag bits");
+    return MCA_ERR_INVALID_ARG;
+  }
   if (!(p->newton_rtol > 0.0) || !(p->eta0 > 0.0) || !(p->eta_max > 0.0)) {
     set_error("tolerances must be > 0");
     return MCA_ERR_INVALID_ARG;
@@ -164,6 +183,7 @@ int setup_tc(mca_handle* h) {
     set_error("cuTensorMapEncodeTiled unavailable");
     return MCA_ERR_UNSUPPORTED;
   }
+  MCA_CUDA_TRY(tc::configure_all());
   const size_t B = h->Bmax, mp = h->mp, np = h->np;
   MCA_TRY(dalloc(h, &h->Xbf, B * 2 * mp * np));
   MCA_TRY(dalloc(h, &h->T1bf, B * 2 * np * mp));
@@ -223,6 +243,9 @@ int alloc_workspace(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->ctl, B));
   MCA_TRY(dalloc(h, &h->err, 1));
   MCA_TRY(dalloc(h, &h->cnt, B));
+  MCA_TRY(dalloc(h, &h->map_of, B));
+  MCA_CUDA_TRY(cudaMemset(h->map_of, 0, B * sizeof(int)));
+  h->map_host.assign(B, 0);
   MCA_CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
   MCA_CUDA_TRY(cudaMemset(h->cnt, 0, B * sizeof(unsigned int)));
   MCA_CUDA_TRY(cudaMemset(h->ctl, 0, B * sizeof(VecCtl)));
@@ -236,6 +259,7 @@ int alloc_workspace(mca_handle* h) {
   for (int k = 0; k <= MCA_KMAX; ++k)
     MCA_CUDA_TRY(cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming));
   h->ev_ok = true;
+  MCA_CUDA_TRY(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamDefault));
   h->ctl_host.resize(B);
   return MCA_OK;
 }
@@ -287,6 +311,120 @@ void prof_flush(mca_handle* h, F active) {
   h->prof_next = 0;
 }
 
+int check_device_error(mca_handle* h) {
+  int e = 0;
+  MCA_CUDA_TRY(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    cudaMemset(h->err, 0, sizeof(int));
+    set_error("a bounded device wait expired");
+    return e;
+  }
+  return MCA_OK;
+}
+
+// Tensor-core transform `step` (0..3) of the preconditioner for B vectors; the input of
+// step 0 is the BF16 copy in h->Xbf, the output of step 3 goes to zout (FP64).
+int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, int B,
+            const VecCtl* ctl, cudaStream_t s, int prof_k) {
+  const int m = h->m, n = h->n;
+  const size_t mn = h->mn, mp = h->mp, np = h->np;
+  auto q = [](int bn) { return bn == 128 ? 0 : 1; };
+  const int bn = h->bn[step];
+  // executed MMA FLOPs per vector: 2 layers x 2 M N K, three products when split
+  const double f_r = 4.0 * m * (double)n * n, f_c = 4.0 * n * (double)m * m;
+  const double sp = split ? 3.0 : 1.0;
+  tc::GemmEpi e{};
+  e.ctl = ctl;
+  e.err = h->err;
+  e.mu = h->mu;
+  e.nu = h->nu;
+  cudaEvent_t t0 = prof_begin(h, s);
+  switch (step) {
+    case 0:  // T1^T = (X Q_r)^T
+      e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
+      e.out = h->T1bf; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
+      MCA_CUDA_TRY(tc::gemm(bn, false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(bn)],
+                            h->mB1[q(bn)], e, B, s));
+      prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 8.0 * mn, f_r, s);
+      break;
+    case 1:  // Y_hat = modes^-1 (Q_c^T T1), stored [i'][k']
+      e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
+      e.out = h->Yh; e.out_lo = h->Yl; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
+      MCA_CUDA_TRY(tc::gemm(bn, false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2,
+                            h->mA2, h->mB2[q(bn)], h->mB2[q(bn)], e, B, s));
+      prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, (split ? 12.0 : 8.0) * mn, f_c, s);
+      break;
+    case 2:  // E^T = (Y_hat Q_r^T)^T
+      e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
+      e.out = h->Eh; e.out_lo = h->El; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
+      MCA_CUDA_TRY(tc::gemm(bn, split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h, h->mA3l,
+                            h->mB3h[q(bn)], h->mB3l[q(bn)], e, B, s));
+      prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, (split ? 16.0 : 8.0) * mn, sp * f_r, s);
+      break;
+    default:  // Z = (E^T Q_c^T)^T, FP64 unpadded
+      e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
+      e.out = zout; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
+      MCA_CUDA_TRY(tc::gemm(bn, split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)],
+                            h->mB4l[q(bn)], e, B, s));
+      prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k, (split ? 8.0 : 4.0) * mn + 16.0 * mn,
+               sp * f_c, s);
+      break;
+  }
+  count_launches(1);
+  return MCA_OK;
+}
+
+// Tile-width autotuner: time each transform with 128- and 64-column tiles at the handle's
+// batch size and keep the faster one (the best width depends on how many CTAs a shape
+// gives against the SM count).
+int autotune_tiles(mca_handle* h) {
+  const int B = h->Bmax;
+  for (int b = 0; b < B; ++b) {
+    VecCtl& c = h->ctl_host[b];
+    memset(&c, 0, sizeof(VecCtl));
+    c.a = 2e-5;
+    c.gm_active = 1;
+    c.newton_active = 1;
+  }
+  MCA_CUDA_TRY(cudaMemcpy(h->ctl, h->ctl_host.data(), (size_t)B * sizeof(VecCtl),
+                          cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  MCA_CUDA_TRY(cudaEventCreate(&e0));
+  MCA_CUDA_TRY(cudaEventCreate(&e1));
+  const bool split = h->p.precision == MCA_PREC_BF16_SPLIT;
+  const size_t zstride = (size_t)h->restart * h->n2;
+  int rc = MCA_OK;
+  for (int step = 0; step < 4 && rc == MCA_OK; ++step) {
+    float best = 1e30f;
+    int best_bn = h->bn[step];
+    for (int bn : {128, 64}) {
+      h->bn[step] = bn;
+      rc = tc_step(h, step, split, h->Z, zstride, B, h->ctl, 0, -1);
+      if (rc != MCA_OK) break;
+      cudaEventRecord(e0, 0);
+      for (int r = 0; r < 3 && rc == MCA_OK; ++r)
+        rc = tc_step(h, step, split, h->Z, zstride, B, h->ctl, 0, -1);
+      cudaEventRecord(e1, 0);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = MCA_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_bn = bn;
+      }
+    }
+    h->bn[step] = best_bn;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaMemset(h->ctl, 0, (size_t)B * sizeof(VecCtl));
+  if (rc == MCA_OK) rc = check_device_error(h);
+  return rc;
+}
+
 // z = P^-1 r for B vectors: r at rin + b*rstride, z at zout + b*zstride.  For the
 // tensor-core forms the BF16 copy of r must already be in h->Xbf.
 int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstride,
@@ -324,48 +462,8 @@ int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstrid
   }
   if (!h->tc_ok) return MCA_ERR_UNSUPPORTED;
   const bool split = (precision == MCA_PREC_BF16_SPLIT);
-  const size_t mp = h->mp, np = h->np;
-  auto q = [](int bn) { return bn == 128 ? 0 : 1; };
-  tc::GemmEpi e{};
-  e.ctl = ctl;
-  e.err = h->err;
-  // 1: T1^T = (X Q_r)^T
-  e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
-  e.out = h->T1bf; e.out_lo = nullptr; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
-  // executed MMA FLOPs per vector: 2 layers x 2 M N K, three products when split
-  const double f_r = 4.0 * m * (double)n * n, f_c = 4.0 * n * (double)m * m;
-  const double sp = split ? 3.0 : 1.0;
-  cudaEvent_t t0 = prof_begin(h, s);
-  MCA_CUDA_TRY(tc::gemm(h->bn[0], false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(h->bn[0])],
-                        h->mB1[q(h->bn[0])], e, B, s));
-  count_launches(1);
-  prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 16.0 * mn * 0.25 + 4.0 * mn, f_r, s);
-  // 2: Y_hat = modes^-1 (Q_c^T T1), stored [i'][k']
-  e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
-  e.out = h->Yh; e.out_lo = h->Yl; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
-  e.mu = h->mu; e.nu = h->nu;
-  t0 = prof_begin(h, s);
-  MCA_CUDA_TRY(tc::gemm(h->bn[1], false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2,
-                        h->mA2, h->mB2[q(h->bn[1])], h->mB2[q(h->bn[1])], e, B, s));
-  count_launches(1);
-  prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, (split ? 12.0 : 8.0) * mn, f_c, s);
-  // 3: E^T = (Y_hat Q_r^T)^T
-  e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
-  e.out = h->Eh; e.out_lo = h->El; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
-  t0 = prof_begin(h, s);
-  MCA_CUDA_TRY(tc::gemm(h->bn[2], split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h,
-                        h->mA3l, h->mB3h[q(h->bn[2])], h->mB3l[q(h->bn[2])], e, B, s));
-  count_launches(1);
-  prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, (split ? 16.0 : 8.0) * mn, sp * f_r, s);
-  // 4: Z = (E^T Q_c^T)^T, FP64 unpadded
-  e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
-  e.out = zout; e.out_lo = nullptr; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
-  t0 = prof_begin(h, s);
-  MCA_CUDA_TRY(tc::gemm(h->bn[3], split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(h->bn[3])],
-                        h->mB4l[q(h->bn[3])], e, B, s));
-  count_launches(1);
-  prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k, (split ? 8.0 : 4.0) * mn + 16.0 * mn,
-           sp * f_c, s);
+  for (int step = 0; step < 4; ++step)
+    MCA_TRY(tc_step(h, step, split, zout, zstride, B, ctl, s, prof_k));
   return MCA_OK;
 }
 
@@ -385,9 +483,9 @@ bool any_flag(const mca_handle* h, int B) {
   return false;
 }
 
-// One flexible GMRES cycle on the vectors whose gm_active flag is set; V[b][0] and its
-// BF16 copy are already in place.
-int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
+// Enqueue GMRES iteration k (preconditioner, Jacobian apply + CGS2 with the fused
+// reductions and Givens column, basis normalisation) for the vectors still iterating.
+int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t s) {
   const size_t n2 = h->n2;
   const double cells = (double)h->mn;
   const size_t vstride = (size_t)(h->restart + 1) * n2;
@@ -395,34 +493,76 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
   const int nbS = residual_nblk((int)h->mn);
   const int nbV = vec_nblk(n2);
   const bool tc = h->p.precision != MCA_PREC_FP64;
+  const double* vk = h->V + (size_t)k * n2;
+  double* zk = h->Z + (size_t)k * n2;
+  const double nk = k + 1;
+  // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
+  MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k));
+  cudaEvent_t t0 = prof_begin(h, s);
+  launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
+                   h->ctl, h->cnt, h->h1, s);
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (12.0 + 4.0 * nk), s);
+  t0 = prof_begin(h, s);
+  launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, h->cnt,
+                     h->h2, s);
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k, cells * (32.0 + 16.0 * nk), cells * 8.0 * nk, s);
+  t0 = prof_begin(h, s);
+  launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, h->cnt,
+                     h->h1, h->restart, h->hflags_dev, s);
+  count_launches(1);
+  prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk), cells * (4.0 * nk + 4.0), s);
+  t0 = prof_begin(h, s);
+  launch_normalize(h->W, h->V + (size_t)(k + 1) * n2, vstride, n2, tc ? h->Xbf : nullptr,
+                   h->mp, h->np, h->m, h->n, h->ctl, B, s);
+  count_launches(1);
+  // the last iteration of a cycle normalises nothing: counted with iteration k + 1
+  prof_end(h, t0, MCA_FAM_NORMALIZE, k + 1, cells * (tc ? 36.0 : 32.0), cells * 2.0, s);
+  MCA_CUDA_TRY(cudaGetLastError());
+  return MCA_OK;
+}
+
+// Capture iteration k for batch size B once and replay it as one graph launch.
+int launch_iteration_graph(mca_handle* h, const double* D, int B, int k, cudaStream_t s) {
+  auto key = std::make_pair(k, B);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    MCA_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    int rc = enqueue_iteration(h, D, B, k, s);
+    g_capturing = false;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc != MCA_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    MCA_CUDA_TRY(e);
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MCA_CUDA_TRY(e);
+    it = h->graphs.emplace(key, std::make_pair(exec, (int)nodes)).first;
+  }
+  MCA_CUDA_TRY(cudaGraphLaunch(it->second.first, s));
+  count_launches(it->second.second);
+  return MCA_OK;
+}
+
+// One flexible GMRES cycle on the vectors whose gm_active flag is set; V[b][0] and its
+// BF16 copy are already in place.  D is the Jacobian diagonal (graphs only for the
+// handle's own D).
+int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
+  const bool graphs = (h->p.flags & MCA_FLAG_GRAPHS) && !h->prof_on && D == h->D;
   for (int k = 0; k < h->restart; ++k) {
-    const double* vk = h->V + (size_t)k * n2;
-    double* zk = h->Z + (size_t)k * n2;
-    const double nk = k + 1;
-    // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
-    MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k));
-    cudaEvent_t t0 = prof_begin(h, s);
-    launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
-                     h->ctl, h->cnt, h->h1, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (12.0 + 4.0 * nk), s);
-    t0 = prof_begin(h, s);
-    launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, h->cnt,
-                       h->h2, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k, cells * (32.0 + 16.0 * nk), cells * 8.0 * nk, s);
-    t0 = prof_begin(h, s);
-    launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, h->cnt,
-                       h->h1, h->restart, h->hflags_dev, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk), cells * (4.0 * nk + 4.0), s);
-    t0 = prof_begin(h, s);
-    launch_normalize(h->W, h->V + (size_t)(k + 1) * n2, vstride, n2, tc ? h->Xbf : nullptr,
-                     h->mp, h->np, h->m, h->n, h->ctl, B, s);
-    count_launches(1);
-    // the last iteration of a cycle normalises nothing: counted with iteration k + 1
-    prof_end(h, t0, MCA_FAM_NORMALIZE, k + 1, cells * (tc ? 36.0 : 32.0), cells * 2.0, s);
-    MCA_CUDA_TRY(cudaGetLastError());
+    if (graphs) {
+      MCA_TRY(launch_iteration_graph(h, D, B, k, s));
+    } else {
+      MCA_TRY(enqueue_iteration(h, D, B, k, s));
+    }
     MCA_CUDA_TRY(cudaEventRecord(h->ev[k], s));
     if (k >= 1) {
       MCA_CUDA_TRY(cudaEventSynchronize(h->ev[k - 1]));
@@ -445,16 +585,6 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
   return MCA_OK;
 }
 
-int check_device_error(mca_handle* h) {
-  int e = 0;
-  MCA_CUDA_TRY(cudaMemcpy(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (e != 0) {
-    cudaMemset(h->err, 0, sizeof(int));
-    set_error("a bounded device wait expired");
-    return e;
-  }
-  return MCA_OK;
-}
 
 // Solve B <= Bmax vectors whose inputs are in h->vin; results stay in h->x / h->iout.
 int solve_pass(mca_handle* h, int B, cudaStream_t s) {
@@ -470,8 +600,9 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s) {
   int n_active = B;  // vectors entering the current Newton step
   for (int it = 0; it <= h->p.max_newton; ++it) {
     cudaEvent_t t0 = prof_begin(h, s);
-    launch_residual_newton(h->gr, h->g, h->vin, h->x, it == 0, h->F, h->D, h->part, nbR, B,
-                           h->ctl, cfg, h->cnt, h->hflags_dev, s);
+    launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
+                           it == 0, h->F, h->D, h->part, nbR, B, h->ctl, cfg, h->cnt,
+                           h->hflags_dev, s);
     count_launches(1);
     // FP64 flops per cell: stencils 12, Taylor sinh/cosh 42, current/conductance 6,
     // norms 5 (the zero state only the norms)
@@ -540,6 +671,7 @@ void mca_default_params(mca_params* p) {
   p->newton_rtol = 1e-8;
   p->eta0 = 1e-3;
   p->eta_max = 1e-2;
+  p->flags = MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE;
 }
 
 const char* mca_strerror(int code) {
@@ -567,13 +699,20 @@ void mca_destroy(mca_handle* h) {
   if (h->ev_ok)
     for (int k = 0; k <= MCA_KMAX; ++k) cudaEventDestroy(h->ev[k]);
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.first);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
 
 int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
+  return mca_create_multi(p, g_map, 1, out);
+}
+
+int mca_create_multi(const mca_params* p, const double* g_map, int32_t n_maps,
+                     mca_handle** out) {
   g_last_error.clear();
-  if (!out || !g_map) {
-    set_error("NULL argument");
+  if (!out || !g_map || n_maps < 1) {
+    set_error("NULL argument or n_maps < 1");
     return MCA_ERR_INVALID_ARG;
   }
   *out = nullptr;
@@ -581,6 +720,7 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
   if (rc != MCA_OK) return rc;
   mca_handle* h = new mca_handle();
   h->p = *p;
+  h->n_maps = n_maps;
   cudaGetDevice(&h->device);
   h->m = p->rows;
   h->n = p->cols;
@@ -595,14 +735,15 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
     mca_destroy(h);
     return code;
   };
-  // conductance map: copy and validate on the host
-  std::vector<double> gh(h->mn);
-  if (cudaMemcpy(gh.data(), g_map, h->mn * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+  // conductance maps: copy and validate on the host
+  const size_t gtot = h->mn * (size_t)n_maps;
+  std::vector<double> gh(gtot);
+  if (cudaMemcpy(gh.data(), g_map, gtot * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
     cudaGetLastError();
     set_error("cannot read g_map");
     return fail(MCA_ERR_INVALID_ARG);
   }
-  for (size_t i = 0; i < h->mn; ++i) {
+  for (size_t i = 0; i < gtot; ++i) {
     if (!std::isfinite(gh[i])) {
       set_error("g_map has a non-finite entry");
       return fail(MCA_ERR_NONFINITE);
@@ -612,8 +753,8 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
       return fail(MCA_ERR_INVALID_ARG);
     }
   }
-  if ((rc = dalloc(h, &h->g, h->mn)) != MCA_OK) return fail(rc);
-  if (cudaMemcpy(h->g, gh.data(), h->mn * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+  if ((rc = dalloc(h, &h->g, gtot)) != MCA_OK) return fail(rc);
+  if (cudaMemcpy(h->g, gh.data(), gtot * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(MCA_ERR_CUDA);
   // eigenpairs of the two wire operators
   const size_t nn = (size_t)h->n * h->n, mm = (size_t)h->m * h->m;
@@ -653,6 +794,7 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
   if ((rc = alloc_workspace(h)) != MCA_OK) return fail(rc);
   if (p->precision != MCA_PREC_FP64) {
     if ((rc = setup_tc(h)) != MCA_OK) return fail(rc);
+    if ((p->flags & MCA_FLAG_AUTOTUNE) && (rc = autotune_tiles(h)) != MCA_OK) return fail(rc);
   }
   if (cudaDeviceSynchronize() != cudaSuccess) {
     set_error("create failed");
@@ -664,18 +806,37 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out) {
 
 int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, double* v_bot,
               double* i_out, mca_stats* stats, void* stream) {
+  return mca_solve_multi(h, v_in, nullptr, nvec, v_top, v_bot, i_out, stats, stream);
+}
+
+int mca_solve_multi(mca_handle* h, const double* v_in, const int32_t* map_index, int32_t nvec,
+                    double* v_top, double* v_bot, double* i_out, mca_stats* stats,
+                    void* stream) {
   g_last_error.clear();
   if (!h || !v_in || nvec < 0) {
     set_error("NULL handle/input or negative nvec");
     return MCA_ERR_INVALID_ARG;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (map_index) {
+    for (int v = 0; v < nvec; ++v) {
+      if (map_index[v] < 0 || map_index[v] >= h->n_maps) {
+        set_error("map_index out of range");
+        return MCA_ERR_INVALID_ARG;
+      }
+    }
+  }
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
   const size_t m = h->m, n = h->n, mn = h->mn;
   int worst = MCA_OK;
   for (int v0 = 0; v0 < nvec; v0 += h->Bmax) {
     const int B = std::min(h->Bmax, nvec - v0);
     MCA_CUDA_TRY(cudaMemcpyAsync(h->vin, v_in + (size_t)v0 * m, (size_t)B * m * sizeof(double),
                                  cudaMemcpyDefault, s));
+    if (h->n_maps > 1) {
+      for (int b = 0; b < B; ++b) h->map_host[b] = map_index ? map_index[v0 + b] : 0;
+      MCA_CUDA_TRY(cudaMemcpyAsync(h->map_of, h->map_host.data(), (size_t)B * sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+    }
     int rc = solve_pass(h, B, s);
     if (rc != MCA_OK) return rc;
     for (int b = 0; b < B; ++b) {
@@ -703,6 +864,52 @@ int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, do
       }
     }
   }
+  return worst;
+}
+
+int mca_solve_many(mca_handle* const* hs, int32_t nh, const double* const* v_in,
+                   const int32_t* const* map_index, const int32_t* nvec,
+                   double* const* v_top, double* const* v_bot, double* const* i_out,
+                   mca_stats* const* stats, int32_t n_threads) {
+  g_last_error.clear();
+  if (!hs || !v_in || !nvec || nh < 0 || n_threads < 1) {
+    set_error("bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  std::atomic<int> next{0};
+  std::mutex mu;
+  int worst = MCA_OK;
+  std::string first_msg;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (worst == MCA_OK) worst = MCA_ERR_CUDA;
+      return;
+    }
+    for (int i = next++; i < nh; i = next++) {
+      int rc = mca_solve_multi(hs[i], v_in[i], map_index ? map_index[i] : nullptr, nvec[i],
+                               v_top ? v_top[i] : nullptr, v_bot ? v_bot[i] : nullptr,
+                               i_out ? i_out[i] : nullptr, stats ? stats[i] : nullptr, s);
+      if (rc != MCA_OK) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (worst == MCA_OK) {
+          worst = rc;
+          first_msg = g_last_error;
+        }
+      }
+    }
+    cudaStreamDestroy(s);
+  };
+  const int nt = std::min<int>(n_threads, std::max(1, nh));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  g_last_error = first_msg;
   return worst;
 }
 

@@ -37,6 +37,7 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
 cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
+cudaError_t configure_all();
 void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
               int np, int B, cudaStream_t s);
 
