@@ -88,7 +88,7 @@ typedef struct mca_stats {
   int32_t status;            /* MCA_OK, MCA_ERR_NOT_CONVERGED or MCA_ERR_NONFINITE       */
   int32_t newton_iters;      /* Jacobian solves performed                                */
   int32_t gmres_iters;       /* GMRES iterations summed over the Newton steps            */
-  int32_t reserved;
+  int32_t fallback;          /* mca_solve_from: 1 when the guess was rejected            */
   double rel_residual;       /* ||F||_2 / ||Y||_2 at the returned voltages               */
   double kcl_rel_error;      /* |sum I_in - sum I_out - sum leaks| / sum |I_in|          */
 } mca_stats;
@@ -150,6 +150,62 @@ int mca_solve_many(mca_handle* const* hs, int32_t nh, const double* const* v_in,
                    const int32_t* const* map_index, const int32_t* nvec,
                    double* const* v_top, double* const* v_bot, double* const* i_out,
                    mca_stats* const* stats, int32_t n_threads);
+
+/* Reprogram the crossbars of a handle: replace its n_maps conductance maps (host or
+ * device, n_maps*m*n, every entry finite and > 0) without redoing the eigen setup,
+ * which depends only on the wires and terminations. */
+int mca_set_conductances(mca_handle* h, const double* g_maps);
+
+/* Newton from a caller's initial guess instead of V = 0 (warm start).
+ *   guess : device, nvec * 2*m*n states [V_t ; V_b] (e.g. from the CNN below).
+ * A guess is rejected (stats.fallback = 1) when its residual is not finite or not
+ * smaller than the residual of V = 0 (||F(guess)|| >= ||Y||); that vector then starts
+ * from V = 0, whose first Newton step is the linear-circuit solve.  The Newton solve is
+ * the judge of the guess: the returned voltages meet newton_rtol either way.  Other
+ * arguments as in mca_solve_multi. */
+int mca_solve_from(mca_handle* h, const double* v_in, const double* guess,
+                   const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
+                   double* i_out, mca_stats* stats, void* stream);
+
+/* ---- learned warm start: kernels of the CNN (not part of the paper) ---------------
+ * Activations are NCHW FP32 device arrays; weights [cout][cin][3][3] are BF16 (uint16_t
+ * bit patterns) with FP32 accumulation; every layer is a 3x3 convolution with dilation d
+ * and zero padding d (output size = input size), then bias and act (0 none, 1 leaky ReLU
+ * with slope 0.1).  cin, cout <= 64.  All calls only enqueue work on the stream. */
+int mca_cnn_conv_forward(const float* x, int32_t n, int32_t cin, int32_t h, int32_t w,
+                         const uint16_t* wt, const float* bias, int32_t cout, int32_t dilation,
+                         int32_t act, float* y, void* stream);
+
+/* Backward of one layer from gy = dL/dy: gz_scratch (n*cout*h*w floats) receives dL/dz,
+ * gx (may be NULL) dL/dx, gw (cout*cin*9) and gb (cout) the parameter gradients;
+ * part holds nchunk*(cout*cin*9 + cout) floats of per-chunk partial sums (the pixel
+ * reduction is split into nchunk chunks and summed in a fixed order). */
+int mca_cnn_conv_backward(const float* x, const float* y, const float* gy, int32_t n,
+                          int32_t cin, int32_t h, int32_t w, const uint16_t* wt, int32_t cout,
+                          int32_t dilation, int32_t act, float* gz_scratch, float* gx,
+                          float* gw, float* gb, float* part, int32_t nchunk, void* stream);
+
+/* Mean squared error over count values; gpred (may be NULL) receives 2 (pred - t)/count,
+ * part holds 256 floats, loss (device, 1 float) the mean. */
+int mca_cnn_mse(const float* pred, const float* target, int64_t count, float* gpred,
+                float* part, float* loss, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on FP32 master weights w; w_bf16 (may be
+ * NULL) receives the BF16 copy used by the convolutions. */
+int mca_cnn_adam(float* w, uint16_t* w_bf16, const float* g, float* m1, float* m2, int64_t count,
+                 float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+
+/* Network input for nvec vectors of one crossbar: x[v] = [log10(g) + 5, V_in[v][i]/vscale
+ * broadcast along row i] and, with nchan = 4, the node position [j/(n-1), i/(m-1)];
+ * nchan x m x n FP32 each (gmap, vin device FP64). */
+int mca_cnn_features(const double* gmap, const double* vin, int32_t nvec, int32_t m, int32_t n,
+                     float vscale, int32_t nchan, float* x, void* stream);
+
+/* Convert between the network's 2-channel output y = [V_t/vscale, V_b*bscale/vscale] and
+ * FP64 solver states x = [V_t ; V_b]: to_state = 1 writes x from y, to_state = 0 writes
+ * y_out from x (training targets). */
+int mca_cnn_state(const float* y, double* x, int32_t nvec, int32_t m, int32_t n, float vscale,
+                  float bscale, int32_t to_state, float* y_out, void* stream);
 
 /* Release the handle and its device memory.  NULL is ignored. */
 void mca_destroy(mca_handle* h);

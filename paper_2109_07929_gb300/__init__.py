@@ -35,7 +35,8 @@ EXPORTED = (
     "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_precond_apply",
     "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
     "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
-    "mca_solve_many",
+    "mca_solve_many", "mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
+    "mca_cnn_mse", "mca_cnn_adam", "mca_cnn_features", "mca_cnn_state", "mca_set_conductances",
 )
 
 FAMILIES = ("residual", "spmv_dots", "update_dots", "update_norm", "normalize", "small",
@@ -60,7 +61,7 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
-        ("gmres_iters", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("gmres_iters", ctypes.c_int32), ("fallback", ctypes.c_int32),
         ("rel_residual", ctypes.c_double), ("kcl_rel_error", ctypes.c_double),
     ]
 
@@ -114,6 +115,19 @@ def load(build_if_missing=True):
     lib.mca_residual_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P, ctypes.c_int32, P, P,
                                          P, P, P]
     lib.mca_residual_noalloc.restype = ctypes.c_int
+    lib.mca_solve_from.argtypes = [P, P, P, P, ctypes.c_int32, P, P, P, P, P]
+    lib.mca_set_conductances.argtypes = [P, P]
+    lib.mca_set_conductances.restype = ctypes.c_int
+    I, F = ctypes.c_int32, ctypes.c_float
+    lib.mca_cnn_conv_forward.argtypes = [P, I, I, I, I, P, P, I, I, I, P, P]
+    lib.mca_cnn_conv_backward.argtypes = [P, P, P, I, I, I, I, P, I, I, I, P, P, P, P, P, I, P]
+    lib.mca_cnn_mse.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
+    lib.mca_cnn_adam.argtypes = [P, P, P, P, P, ctypes.c_int64, F, F, F, F, I, P]
+    lib.mca_cnn_features.argtypes = [P, P, I, I, I, F, I, P, P]
+    lib.mca_cnn_state.argtypes = [P, P, I, I, I, F, F, I, P, P]
+    for name in ("mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
+                 "mca_cnn_mse", "mca_cnn_adam", "mca_cnn_features", "mca_cnn_state"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
     for name in ("mca_create", "mca_create_multi", "mca_solve_multi", "mca_solve_many",
@@ -190,7 +204,8 @@ def solve_many(solvers, vins, map_indices=None, n_threads=4, outs=None):
     res = []
     for o in outs:
         stats = [dict(status=x.status, newton_iters=x.newton_iters, gmres_iters=x.gmres_iters,
-                      rel_residual=x.rel_residual, kcl_rel_error=x.kcl_rel_error) for x in o[3]]
+                      rel_residual=x.rel_residual, kcl_rel_error=x.kcl_rel_error,
+                      fallback=x.fallback) for x in o[3]]
         res.append((o[0], o[1], o[2], stats))
     return res
 
@@ -270,7 +285,37 @@ class Solver:
         allow = (ERR_NOT_CONVERGED, ERR_NONFINITE) if allow_not_converged else ()
         _check(rc, allow)
         stats = [dict(status=s.status, newton_iters=s.newton_iters, gmres_iters=s.gmres_iters,
-                      rel_residual=s.rel_residual, kcl_rel_error=s.kcl_rel_error) for s in st]
+                      rel_residual=s.rel_residual, kcl_rel_error=s.kcl_rel_error,
+                      fallback=s.fallback) for s in st]
+        return v_top, v_bot, i_out, stats
+
+    def set_conductances(self, gmaps):
+        """Replace the crossbars' conductance maps (same count and shape)."""
+        g = gmaps if not isinstance(gmaps, np.ndarray) else np.ascontiguousarray(gmaps, np.float64)
+        _check(self.lib.mca_set_conductances(self.h, _ptr(g)))
+
+    def solve_from(self, vin, guess, v_top=None, v_bot=None, i_out=None, stream=None,
+                   map_index=None, allow_not_converged=False):
+        """Newton from a device guess (nvec, 2*m*n) FP64 with the fallback rule of
+        mca_solve_from; returns (v_top, v_bot, i_out, stats)."""
+        nvec = vin.shape[0]
+        mi = None if map_index is None else np.ascontiguousarray(map_index, np.int32)
+        if isinstance(vin, np.ndarray):
+            vin = np.ascontiguousarray(vin, np.float64)
+        if v_top is None:
+            v_top = np.empty((nvec, self.m, self.n))
+        if v_bot is None:
+            v_bot = np.empty((nvec, self.m, self.n))
+        if i_out is None:
+            i_out = np.empty((nvec, self.n))
+        st = (Stats * nvec)()
+        rc = self.lib.mca_solve_from(self.h, _ptr(vin), _ptr(guess), _ptr(mi), nvec, _ptr(v_top),
+                                     _ptr(v_bot), _ptr(i_out), ctypes.cast(st, ctypes.c_void_p),
+                                     _stream_ptr(stream))
+        _check(rc, (ERR_NOT_CONVERGED, ERR_NONFINITE) if allow_not_converged else ())
+        stats = [dict(status=s.status, newton_iters=s.newton_iters, gmres_iters=s.gmres_iters,
+                      rel_residual=s.rel_residual, kcl_rel_error=s.kcl_rel_error,
+                      fallback=s.fallback) for s in st]
         return v_top, v_bot, i_out, stats
 
     def solve_raw(self, vin_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr=None, stream=None):

@@ -587,7 +587,8 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
 
 
 // Solve B <= Bmax vectors whose inputs are in h->vin; results stay in h->x / h->iout.
-int solve_pass(mca_handle* h, int B, cudaStream_t s) {
+// from_guess: h->x already holds the initial states (otherwise Newton starts at x = 0).
+int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
   const SolverCfg cfg = make_cfg(h);
   const int nbR = residual_nblk((int)h->mn);
   const bool tc = h->p.precision != MCA_PREC_FP64;
@@ -595,19 +596,21 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s) {
   const size_t zstride = (size_t)h->restart * h->n2;
   launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
   count_launches(1);
-  MCA_CUDA_TRY(cudaMemsetAsync(h->x, 0, (size_t)B * h->n2 * sizeof(double), s));
+  if (!from_guess)
+    MCA_CUDA_TRY(cudaMemsetAsync(h->x, 0, (size_t)B * h->n2 * sizeof(double), s));
   const double cells = (double)h->mn;
   int n_active = B;  // vectors entering the current Newton step
   for (int it = 0; it <= h->p.max_newton; ++it) {
     cudaEvent_t t0 = prof_begin(h, s);
+    const bool zero_state = (it == 0) && !from_guess;
     launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
-                           it == 0, h->F, h->D, h->part, nbR, B, h->ctl, cfg, h->cnt,
+                           zero_state, h->F, h->D, h->part, nbR, B, h->ctl, cfg, h->cnt,
                            h->hflags_dev, s);
     count_launches(1);
     // FP64 flops per cell: stencils 12, Taylor sinh/cosh 42, current/conductance 6,
     // norms 5 (the zero state only the norms)
-    prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * (it == 0 ? 32.0 : 48.0),
-             cells * (it == 0 ? 5.0 : 65.0), s);
+    prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * (zero_state ? 32.0 : 48.0),
+             cells * (zero_state ? 5.0 : 65.0), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
     const int entering = n_active;
@@ -809,9 +812,52 @@ int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, do
   return mca_solve_multi(h, v_in, nullptr, nvec, v_top, v_bot, i_out, stats, stream);
 }
 
+static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
+                      const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
+                      double* i_out, mca_stats* stats, void* stream);
+
 int mca_solve_multi(mca_handle* h, const double* v_in, const int32_t* map_index, int32_t nvec,
                     double* v_top, double* v_bot, double* i_out, mca_stats* stats,
                     void* stream) {
+  return solve_impl(h, v_in, nullptr, map_index, nvec, v_top, v_bot, i_out, stats, stream);
+}
+
+int mca_set_conductances(mca_handle* h, const double* g_maps) {
+  g_last_error.clear();
+  if (!h || !g_maps) {
+    set_error("NULL argument");
+    return MCA_ERR_INVALID_ARG;
+  }
+  const size_t gtot = h->mn * (size_t)h->n_maps;
+  std::vector<double> gh(gtot);
+  MCA_CUDA_TRY(cudaMemcpy(gh.data(), g_maps, gtot * sizeof(double), cudaMemcpyDefault));
+  for (size_t i = 0; i < gtot; ++i) {
+    if (!std::isfinite(gh[i])) {
+      set_error("g_maps has a non-finite entry");
+      return MCA_ERR_NONFINITE;
+    }
+    if (!(gh[i] > 0.0)) {
+      set_error("g_maps entries must be > 0");
+      return MCA_ERR_INVALID_ARG;
+    }
+  }
+  MCA_CUDA_TRY(cudaMemcpy(h->g, gh.data(), gtot * sizeof(double), cudaMemcpyHostToDevice));
+  return MCA_OK;
+}
+
+int mca_solve_from(mca_handle* h, const double* v_in, const double* guess,
+                   const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
+                   double* i_out, mca_stats* stats, void* stream) {
+  if (!guess) {
+    set_error("NULL guess");
+    return MCA_ERR_INVALID_ARG;
+  }
+  return solve_impl(h, v_in, guess, map_index, nvec, v_top, v_bot, i_out, stats, stream);
+}
+
+static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
+                      const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
+                      double* i_out, mca_stats* stats, void* stream) {
   g_last_error.clear();
   if (!h || !v_in || nvec < 0) {
     set_error("NULL handle/input or negative nvec");
@@ -837,7 +883,35 @@ int mca_solve_multi(mca_handle* h, const double* v_in, const int32_t* map_index,
       MCA_CUDA_TRY(cudaMemcpyAsync(h->map_of, h->map_host.data(), (size_t)B * sizeof(int),
                                    cudaMemcpyHostToDevice, s));
     }
-    int rc = solve_pass(h, B, s);
+    std::vector<int> fell(B, 0);
+    if (guess) {
+      // judge the guess: keep it only if its residual is finite and below ||F(0)|| = ||Y||
+      MCA_CUDA_TRY(cudaMemcpyAsync(h->x, guess + (size_t)v0 * h->n2,
+                                   (size_t)B * h->n2 * sizeof(double), cudaMemcpyDefault, s));
+      const int nb = residual_nblk((int)h->mn);
+      launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
+      count_launches(1);
+      // residual of the guess (map-aware through the Newton kernel with max_newton = 0)
+      SolverCfg probe = make_cfg(h);
+      probe.max_newton = 0;
+      probe.newton_rtol = 0.0;
+      launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
+                             false, h->F, h->D, h->part, nb, B, h->ctl, probe, h->cnt,
+                             nullptr, s);
+      count_launches(1);
+      MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
+                                   cudaMemcpyDeviceToHost, s));
+      MCA_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int b = 0; b < B; ++b) {
+        const VecCtl& c = h->ctl_host[b];
+        const bool ok = std::isfinite(c.fnorm) && c.fnorm < c.ynorm;
+        if (!ok && c.ynorm > 0.0) {
+          fell[b] = 1;
+          MCA_CUDA_TRY(cudaMemsetAsync(h->x + (size_t)b * h->n2, 0, h->n2 * sizeof(double), s));
+        }
+      }
+    }
+    int rc = solve_pass(h, B, s, guess != nullptr);
     if (rc != MCA_OK) return rc;
     for (int b = 0; b < B; ++b) {
       const double* xb = h->x + (size_t)b * h->n2;
@@ -858,7 +932,7 @@ int mca_solve_multi(mca_handle* h, const double* v_in, const int32_t* map_index,
         st.status = c.status;
         st.newton_iters = c.newton_iters;
         st.gmres_iters = c.gmres_iters;
-        st.reserved = 0;
+        st.fallback = fell[b];
         st.rel_residual = (c.ynorm > 0.0) ? c.fnorm / c.ynorm : 0.0;
         st.kcl_rel_error = kcl[b];
       }

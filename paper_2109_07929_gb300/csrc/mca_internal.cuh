@@ -161,4 +161,5 @@ void launch_modes_2x2_f64(double* Xh, const double* mu, const double* nu, int m,
 namespace mca {
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void set_error_message(const char* msg);
+void count_launches(int n);
 }
