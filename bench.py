@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--table1", action="store_true",
+                    help="GPU version of the paper's Table 1 (GMRES steps per preconditioner)")
     return ap.parse_args()
 
 
@@ -468,8 +470,49 @@ def committed_traffic(fam, fp):
     return ent.get("bytes_per_launch")
 
 
+def run_table1(args):
+    """Table 1 of the paper on the GPU: GMRES iterations (and time) to relative residual
+    1e-6 on the first Newton system J x = Y in the paper's normalised regime (wires and
+    terminations g = 1, linear devices with g_ij ~ U[0, 0.4]), per preconditioner."""
+    import torch
+    import paper_2109_07929_gb300 as mca
+    from oracle import mca_oracle as O   # source vector only (rhs of the linear system)
+    precs = [("none", mca.PREC_NONE), ("jacobi", mca.PREC_JACOBI), ("paper_mhat", mca.PREC_MHAT),
+             ("exact_fp64", mca.PREC_FP64), ("exact_bf16split", mca.PREC_BF16_SPLIT)]
+    out = {}
+    for n in (16, 32, 64, 128, 256, 512):
+        cb = mi.config_paper_regime(n, 0)
+        p = cb.params
+        g = np.maximum(cb.gmap, 1e-12)
+        Yt, Yb = O.source_vector(p, cb.vin[0])
+        rhs = torch.as_tensor(np.concatenate([Yt, Yb])[None], device="cuda")
+        D = torch.as_tensor(g.ravel()[None], device="cuda")
+        row = {}
+        for name, prec in precs:
+            params = mca.default_params(n, n, g_wire_top=1.0, g_wire_bot=1.0, g_src=1.0,
+                                        g_term_top_right=1.0, g_term_bot_top=1.0, g_sense=1.0,
+                                        b=0.0, precision=prec, max_batch=1)
+            with mca.Solver(params, g) as s:
+                dx = torch.empty(1, 2 * n * n, dtype=torch.float64, device="cuda")
+                s.gmres_solve(D, [g.mean()], rhs, dx, 1e-6, max_iters=60000)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                its, res = s.gmres_solve(D, [g.mean()], rhs, dx, 1e-6, max_iters=60000)
+                torch.cuda.synchronize()
+                row[name] = {"steps": int(its[0]), "ms": 1e3 * (time.perf_counter() - t),
+                             "converged": bool(res[0] <= 1e-6 * float(rhs.norm()) * 1.01)}
+        out[str(n)] = row
+        print(json.dumps({"n": n, **row}), file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "table1_gpu", "restart": 30, "rtol": 1e-6,
+                      "regime": "g = 1 wires and terminations, linear devices U[0,0.4]",
+                      "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.table1:
+        run_table1(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -58,6 +58,11 @@ extern "C" {
 #define MCA_PREC_BF16_SPLIT 2  /* forward transforms BF16; back transforms with hi+lo
                                   BF16 splitting of both operands (3 tensor-core
                                   products, FP32 accumulate)                             */
+#define MCA_PREC_MHAT 3        /* the paper's own evaluation: eq. (block) with the
+                                  approximate Schur complement M_hat of eq. (Mhat), applied
+                                  by tridiagonal solves (eq. 2matrix4), FP64              */
+#define MCA_PREC_JACOBI 4      /* comparison preconditioner of Table 1: diag(J)^-1      */
+#define MCA_PREC_NONE 5        /* no preconditioner (Table 1, "before preconditioned")  */
 
 typedef struct mca_params {
   int32_t rows;              /* m >= 1: number of top-layer rows (word lines)            */
@@ -234,7 +239,8 @@ int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* 
                        int32_t nvec, void* stream);
 
 /* Preconditioner apply z = P^-1 r (eqs. (P), (block), (M)) with a1 = a2 = a[v] per
- * vector, in the given MCA_PREC_* precision.
+ * vector, in the given MCA_PREC_* precision (FP64, BF16, BF16_SPLIT or MHAT; the
+ * tensor-core forms need a handle created with one of them).
  *   a : host, nvec values (> 0);  r, z : device, nvec * 2*m*n. */
 int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z,
                       int32_t nvec, int32_t precision, void* stream);
@@ -244,15 +250,16 @@ int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z
  * nu[m], Q_c[m*m] for G_c.  Eigenvalues ascending.  NULL outputs are skipped. */
 int mca_eigenpairs(mca_handle* h, double* mu, double* q_r, double* nu, double* q_c);
 
-/* One flexible-GMRES(restart) cycle for J dx = rhs (Section 4) with the handle's
+/* Restarted flexible GMRES(restart) for J dx = rhs (Section 4) with the handle's
  * preconditioner (a1 = a2 = a[v]), at the Jacobian diagonal D, from dx = 0.  Stops when
- * the Givens residual estimate reaches rtol * ||rhs|| or after gmres_restart iterations.
+ * the residual reaches rtol * ||rhs|| or after max_iters iterations (max_iters <= 0:
+ * one cycle of gmres_restart iterations).
  *   D : device nvec*m*n;  a : host nvec (> 0);  rhs, dx : device nvec*2*m*n;
  *   iters : host out, nvec iteration counts (may be NULL);
  *   res   : host out, nvec final residual estimates ||rhs - J dx|| (may be NULL). */
 int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const double* rhs,
-                    double* dx, int32_t nvec, double rtol, int32_t* iters, double* res,
-                    void* stream);
+                    double* dx, int32_t nvec, double rtol, int32_t max_iters, int32_t* iters,
+                    double* res, void* stream);
 
 /* ---- per-kernel-family timing (measurement support) -------------------------------- */
 #define MCA_FAM_RESIDUAL 0      /* residual + Jacobian diagonal (eq. F, eq. J)              */

@@ -17,6 +17,9 @@ from . import _build
 PREC_FP64 = 0
 PREC_BF16 = 1
 PREC_BF16_SPLIT = 2
+PREC_MHAT = 3
+PREC_JACOBI = 4
+PREC_NONE = 5
 
 FLAG_GRAPHS = 1
 FLAG_AUTOTUNE = 2
@@ -109,7 +112,8 @@ def load(build_if_missing=True):
     lib.mca_jacobian_apply.argtypes = [P, P, P, P, ctypes.c_int32, P]
     lib.mca_precond_apply.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
     lib.mca_eigenpairs.argtypes = [P, P, P, P, P]
-    lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double, P, P, P]
+    lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double,
+                                    ctypes.c_int32, P, P, P]
     lib.mca_profile.argtypes = [P, ctypes.c_int32]
     lib.mca_profile_read.argtypes = [P, ctypes.c_int32, P, P, P, P]
     lib.mca_residual_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P, ctypes.c_int32, P, P,
@@ -364,11 +368,13 @@ class Solver:
         _check(self.lib.mca_eigenpairs(self.h, _ptr(mu), _ptr(qr), _ptr(nu), _ptr(qc)))
         return mu, qr, nu, qc
 
-    def gmres_solve(self, D, a, rhs, dx, rtol, stream=None):
+    def gmres_solve(self, D, a, rhs, dx, rtol, max_iters=0, stream=None):
+        """Restarted FGMRES on J dx = rhs from dx = 0 (max_iters <= 0: one cycle)."""
         a = np.ascontiguousarray(a, np.float64)
         nvec = rhs.shape[0]
         its = np.zeros(nvec, np.int32)
         res = np.zeros(nvec)
         _check(self.lib.mca_gmres_solve(self.h, _ptr(D), _ptr(a), _ptr(rhs), _ptr(dx), nvec,
-                                        rtol, _ptr(its), _ptr(res), _stream_ptr(stream)))
+                                        rtol, int(max_iters), _ptr(its), _ptr(res),
+                                        _stream_ptr(stream)))
         return its, res

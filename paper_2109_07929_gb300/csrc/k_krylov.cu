@@ -256,7 +256,7 @@ __global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z,
 // Start of a stand-alone linear solve: beta = ||rhs|| from the norm partials, stop at
 // rtol * beta.
 __global__ void k_gmres_init(const double* __restrict__ part_norm, int nblk, VecCtl* ctl,
-                             double rtol) {
+                             double rtol, int first) {
   const int b = blockIdx.x;
   double s = 0.0;
   for (int t = threadIdx.x; t < nblk; t += 32) s += part_norm[((size_t)b * 32) * nblk + t];
@@ -264,22 +264,40 @@ __global__ void k_gmres_init(const double* __restrict__ part_norm, int nblk, Vec
   if (threadIdx.x == 0) {
     VecCtl& c = ctl[b];
     const double beta = sqrt(s);
+    if (first) {
+      c.ynorm = beta;                      // ||rhs|| of the linear system
+      c.tol_abs = rtol * beta;
+      c.gmres_iters = 0;
+    }
     c.g[0] = beta;
     c.res_est = beta;
-    c.tol_abs = rtol * beta;
     c.k_done = 0;
-    c.gmres_iters = 0;
     c.newton_active = 1;
     c.status = MCA_OK;
-    c.gm_active = (beta > 0.0) ? 1 : 0;
+    c.gm_active = (beta > c.tol_abs && beta > 0.0) ? 1 : 0;
   }
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b,
+                      double* __restrict__ out, size_t n2) {
+  const size_t off = (size_t)blockIdx.y * n2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n2;
+       e += (size_t)gridDim.x * blockDim.x)
+    out[off + e] = a[off + e] - b[off + e];
 }
 
 }  // namespace
 
 void launch_gmres_init(const double* part_norm, int nblk, VecCtl* ctl, int B, double rtol,
-                       cudaStream_t s) {
-  k_gmres_init<<<B, 32, 0, s>>>(part_norm, nblk, ctl, rtol);
+                       int first, cudaStream_t s) {
+  k_gmres_init<<<B, 32, 0, s>>>(part_norm, nblk, ctl, rtol, first);
+}
+
+void launch_sub(const double* a, const double* b, double* out, size_t n2, int B,
+                cudaStream_t s) {
+  int nb = (int)((n2 + kThreads - 1) / kThreads);
+  if (nb > 1216) nb = 1216;
+  k_sub<<<dim3(nb, B), kThreads, 0, s>>>(a, b, out, n2);
 }
 
 int vec_nblk(size_t n2) {

@@ -53,6 +53,9 @@ void set_error_message(const char* msg) { g_last_error = msg; }
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Tensor-core preconditioner forms (need the BF16 operands and TMA maps).
+static bool is_tc(int prec) { return prec == MCA_PREC_BF16 || prec == MCA_PREC_BF16_SPLIT; }
+
 }  // namespace mca
 
 using namespace mca;
@@ -85,6 +88,8 @@ struct mca_handle {
   int32_t* hflags_dev = nullptr;
   int* err = nullptr;
   double *T1_64 = nullptr, *Xh_64 = nullptr, *E_64 = nullptr;
+  double* fac = nullptr;          // tridiagonal factors of the paper-literal M_hat
+  int fac_ld = 0;
   __nv_bfloat16 *Xbf = nullptr, *T1bf = nullptr, *Yh = nullptr, *Yl = nullptr, *Eh = nullptr,
                 *El = nullptr;
   bool tc_ok = false;
@@ -158,7 +163,7 @@ int validate(const mca_params* p) {
     set_error("b must be finite and >= 0");
     return MCA_ERR_INVALID_ARG;
   }
-  if (p->precision < MCA_PREC_FP64 || p->precision > MCA_PREC_BF16_SPLIT) {
+  if (p->precision < MCA_PREC_FP64 || p->precision > MCA_PREC_NONE) {
     set_error("unknown precision");
     return MCA_ERR_INVALID_ARG;
   }
@@ -244,6 +249,8 @@ int alloc_workspace(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->err, 1));
   MCA_TRY(dalloc(h, &h->cnt, B));
   MCA_TRY(dalloc(h, &h->map_of, B));
+  h->fac_ld = std::max(h->m, h->n);
+  MCA_TRY(dalloc(h, &h->fac, B * 4 * (size_t)h->fac_ld));
   MCA_CUDA_TRY(cudaMemset(h->map_of, 0, B * sizeof(int)));
   h->map_host.assign(B, 0);
   MCA_CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
@@ -429,7 +436,21 @@ int autotune_tiles(mca_handle* h) {
 // tensor-core forms the BF16 copy of r must already be in h->Xbf.
 int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstride,
                   double* zout, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s,
-                  int prof_k = -1) {
+                  int prof_k = -1, const double* D = nullptr) {
+  if (precision == MCA_PREC_MHAT) {
+    cudaEvent_t t0 = prof_begin(h, s);
+    MCA_TRY(precond_mhat(h->gr, rin, rstride, zout, zstride, B, ctl, h->fac, h->fac_ld, s));
+    prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 112.0 * (double)h->mn, 40.0 * (double)h->mn, s);
+    return MCA_OK;
+  }
+  if (precision == MCA_PREC_JACOBI || precision == MCA_PREC_NONE) {
+    if (precision == MCA_PREC_JACOBI && D == nullptr) return MCA_ERR_UNSUPPORTED;
+    cudaEvent_t t0 = prof_begin(h, s);
+    MCA_TRY(precond_jacobi(h->gr, D, rin, rstride, zout, zstride, B,
+                           precision == MCA_PREC_NONE, ctl, s));
+    prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 40.0 * (double)h->mn, 4.0 * (double)h->mn, s);
+    return MCA_OK;
+  }
   const int m = h->m, n = h->n;
   const size_t mn = h->mn;
   if (precision == MCA_PREC_FP64) {
@@ -492,12 +513,12 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
   const size_t zstride = (size_t)h->restart * n2;
   const int nbS = residual_nblk((int)h->mn);
   const int nbV = vec_nblk(n2);
-  const bool tc = h->p.precision != MCA_PREC_FP64;
+  const bool tc = is_tc(h->p.precision);
   const double* vk = h->V + (size_t)k * n2;
   double* zk = h->Z + (size_t)k * n2;
   const double nk = k + 1;
   // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
-  MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k));
+  MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D));
   cudaEvent_t t0 = prof_begin(h, s);
   launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
                    h->ctl, h->cnt, h->h1, s);
@@ -591,7 +612,7 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
 int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
   const SolverCfg cfg = make_cfg(h);
   const int nbR = residual_nblk((int)h->mn);
-  const bool tc = h->p.precision != MCA_PREC_FP64;
+  const bool tc = is_tc(h->p.precision);
   const size_t vstride = (size_t)(h->restart + 1) * h->n2;
   const size_t zstride = (size_t)h->restart * h->n2;
   launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
@@ -782,7 +803,7 @@ int mca_create_multi(const mca_params* p, const double* g_map, int32_t n_maps,
     set_error("eigen setup kernels failed");
     return fail(MCA_ERR_CUDA);
   }
-  if (p->precision != MCA_PREC_FP64) {
+  if (is_tc(p->precision)) {
     const size_t npp = (size_t)h->np * h->np, mpp = (size_t)h->mp * h->mp;
     if ((rc = dalloc(h, &h->QrT_bf, npp)) || (rc = dalloc(h, &h->QcT_bf, mpp)) ||
         (rc = dalloc(h, &h->Qr_hi, npp)) || (rc = dalloc(h, &h->Qr_lo, npp)) ||
@@ -795,7 +816,7 @@ int mca_create_multi(const mca_params* p, const double* g_map, int32_t n_maps,
     if (cudaGetLastError() != cudaSuccess) return fail(MCA_ERR_CUDA);
   }
   if ((rc = alloc_workspace(h)) != MCA_OK) return fail(rc);
-  if (p->precision != MCA_PREC_FP64) {
+  if (is_tc(p->precision)) {
     if ((rc = setup_tc(h)) != MCA_OK) return fail(rc);
     if ((p->flags & MCA_FLAG_AUTOTUNE) && (rc = autotune_tiles(h)) != MCA_OK) return fail(rc);
   }
@@ -1053,14 +1074,16 @@ int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z
     set_error("bad arguments (nvec must be in 1..max_batch)");
     return MCA_ERR_INVALID_ARG;
   }
-  if (precision != h->p.precision &&
-      !(precision != MCA_PREC_FP64 && h->p.precision != MCA_PREC_FP64)) {
+  const bool ok = (precision == MCA_PREC_MHAT) ||
+                  (precision == MCA_PREC_FP64 && h->p.precision == MCA_PREC_FP64) ||
+                  (is_tc(precision) && is_tc(h->p.precision));
+  if (!ok) {
     set_error("precision not prepared by this handle");
     return MCA_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MCA_TRY(load_ctl_a(h, a, nvec, s));
-  if (precision != MCA_PREC_FP64)
+  if (is_tc(precision))
     tc::cast_pad(r, h->n2, h->Xbf, h->m, h->n, h->mp, h->np, nvec, s);
     count_launches(1);
   MCA_TRY(precond_apply(h, precision, r, h->n2, z, h->n2, nvec, h->ctl, s));
@@ -1080,43 +1103,60 @@ int mca_eigenpairs(mca_handle* h, double* mu, double* q_r, double* nu, double* q
 }
 
 int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const double* rhs,
-                    double* dx, int32_t nvec, double rtol, int32_t* iters, double* res,
-                    void* stream) {
+                    double* dx, int32_t nvec, double rtol, int32_t max_iters, int32_t* iters,
+                    double* res, void* stream) {
   g_last_error.clear();
   if (!h || !D || !a || !rhs || !dx || nvec < 1 || nvec > h->Bmax || !(rtol > 0.0)) {
     set_error("bad arguments (nvec must be in 1..max_batch, rtol > 0)");
     return MCA_ERR_INVALID_ARG;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
   const size_t n2 = h->n2;
   const size_t vstride = (size_t)(h->restart + 1) * n2;
   const size_t zstride = (size_t)h->restart * n2;
-  const bool tc = h->p.precision != MCA_PREC_FP64;
-  MCA_TRY(load_ctl_a(h, a, nvec, s));
-  // beta = ||rhs||, v_0 = rhs / beta
+  const bool tc = is_tc(h->p.precision);
   const int nbV = vec_nblk(n2);
+  const int nbS = residual_nblk((int)h->mn);
+  const int cap = (max_iters > 0) ? max_iters : h->restart;
+  MCA_TRY(load_ctl_a(h, a, nvec, s));
+  MCA_CUDA_TRY(cudaMemsetAsync(dx, 0, (size_t)nvec * n2 * sizeof(double), s));
+  // r = rhs (dx = 0)
   MCA_CUDA_TRY(cudaMemcpyAsync(h->F, rhs, (size_t)nvec * n2 * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
-  MCA_CUDA_TRY(cudaMemcpyAsync(h->W, rhs, (size_t)nvec * n2 * sizeof(double),
-                               cudaMemcpyDeviceToDevice, s));
-  launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, nullptr,
-                     nullptr, h->restart, nullptr, s);
-  count_launches(1);
-  launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, s);
-  count_launches(1);
-  launch_init_basis(h->F, 1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m, h->n,
-                    h->ctl, nvec, s);
-  count_launches(1);
-  MCA_TRY(gmres_cycle(h, D, nvec, s));
-  MCA_CUDA_TRY(cudaMemsetAsync(dx, 0, (size_t)nvec * n2 * sizeof(double), s));
-  launch_lsq_update(dx, h->Z, zstride, n2, h->ctl, nvec, s);
-  count_launches(2);
-  MCA_CUDA_TRY(cudaGetLastError());
-  MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)nvec * sizeof(VecCtl),
-                               cudaMemcpyDeviceToHost, s));
-  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int> total(nvec, 0);
+  for (int cycle = 0;; ++cycle) {
+    // beta = ||r||, v_0 = r / beta
+    MCA_CUDA_TRY(cudaMemcpyAsync(h->W, h->F, (size_t)nvec * n2 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+    launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, nullptr,
+                       nullptr, h->restart, nullptr, s);
+    launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, cycle == 0 ? 1 : 0, s);
+    launch_init_basis(h->F, 1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
+                      h->n, h->ctl, nvec, s);
+    count_launches(3);
+    MCA_TRY(gmres_cycle(h, D, nvec, s));
+    launch_lsq_update(dx, h->Z, zstride, n2, h->ctl, nvec, s);
+    count_launches(2);
+    MCA_CUDA_TRY(cudaGetLastError());
+    MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)nvec * sizeof(VecCtl),
+                                 cudaMemcpyDeviceToHost, s));
+    MCA_CUDA_TRY(cudaStreamSynchronize(s));
+    bool more = false;
+    for (int b = 0; b < nvec; ++b) {
+      const VecCtl& c = h->ctl_host[b];
+      total[b] += c.k_done;
+      if (c.res_est > c.tol_abs && total[b] < cap) more = true;
+    }
+    if (!more || max_iters <= 0) break;
+    // restart from the true residual r = rhs - J dx (vectors already converged restart
+    // with a residual below their tolerance and do no further work)
+    launch_spmv_dots(h->gr, D, dx, n2, h->W, nullptr, 0, 0, h->part, nbS, nvec, nullptr,
+                     nullptr, nullptr, s);
+    launch_sub(rhs, h->W, h->F, n2, nvec, s);
+    count_launches(2);
+  }
   for (int b = 0; b < nvec; ++b) {
-    if (iters) iters[b] = h->ctl_host[b].k_done;
+    if (iters) iters[b] = total[b];
     if (res) res[b] = h->ctl_host[b].res_est;
   }
   return check_device_error(h);

@@ -122,14 +122,24 @@ void launch_normalize(const double* w, double* vnext, size_t vstride, size_t n2,
                       int B, cudaStream_t s);
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
                        int B, cudaStream_t s);
+// first = 1: remember beta = ||rhs|| and stop at rtol * beta; first = 0 (a restart): keep
+// the tolerance of the first cycle.
 void launch_gmres_init(const double* part_norm, int nblk, VecCtl* ctl, int B, double rtol,
-                       cudaStream_t s);
+                       int first, cudaStream_t s);
 // eigen setup (k_eig.cu)
 void launch_eig_tridiag(int n, double g, double g_first, double g_last, double* lam,
                         double* Q, double* scratch, cudaStream_t s);
 void launch_pack_q_bf16(const double* Q, int n, int npad, __nv_bfloat16* out_q,
                         __nv_bfloat16* out_q_lo, __nv_bfloat16* out_qt, cudaStream_t s);
 void launch_transpose64(const double* Q, int n, double* QT, cudaStream_t s);
+// paper-literal M_hat, Jacobi and identity preconditioners (k_precond_mhat.cu); fac holds
+// 4 * ld doubles per vector, ld = max(m, n)
+int precond_mhat(const Grid& gr, const double* r, size_t rstride, double* z, size_t zstride,
+                 int B, const VecCtl* ctl, double* fac, int ld, cudaStream_t s);
+int precond_jacobi(const Grid& gr, const double* D, const double* r, size_t rstride, double* z,
+                   size_t zstride, int B, bool none, const VecCtl* ctl, cudaStream_t s);
+// element-wise out = a - b on nvec vectors of n2 doubles (k_krylov.cu)
+void launch_sub(const double* a, const double* b, double* out, size_t n2, int B, cudaStream_t s);
 // FP64 preconditioner (k_precond64.cu)
 // Block-transposed GEMM used by all four eigenbasis transforms:
 //   O[blk][c][r] = sum_k A[blk][r][k] * Bm[c][k]   (r < R, c < C, k < K)
