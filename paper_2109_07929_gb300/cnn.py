@@ -288,6 +288,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--eval256", type=int, default=8)
     ap.add_argument("--eval512", type=int, default=8)
     ap.add_argument("--eval1024", type=int, default=4)
     ap.add_argument("--out", default=WEIGHTS)
@@ -306,6 +307,7 @@ def main():
                       final_loss=losses[-1], train_seconds=ttrain)
     else:
         model.load(a.out)
+    report["eval_256_in_distribution"] = evaluate(model, 256, a.eval256)
     report["eval_512"] = evaluate(model, 512, a.eval512)
     report["eval_1024"] = evaluate(model, 1024, a.eval1024)
     print(json.dumps(report))

@@ -269,14 +269,24 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __syncwarp();
 
   // ---------------- epilogue: thread = TMEM lane = output row r0 + 32*warp + lane
-  bool have = mbar_wait(accum, 0);
-  if (!have) record_error(ep.err, MCA_ERR_TIMEOUT);
+  // (the vote makes a timed-out wait uniform, so every thread meets the same barriers)
+  const bool have = __syncthreads_and(mbar_wait(accum, 0) ? 1 : 0) != 0;
+  if (!have && threadIdx.x == 0) record_error(ep.err, MCA_ERR_TIMEOUT);
+  constexpr bool kBf16Out = (EPI != EPI_F64);
+  constexpr bool kLo = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
+  constexpr int kOuts = kLo ? 4 : 2;            // [hi t, hi b, lo t, lo b]
+  // BF16 outputs are staged transposed in the (now idle) pipeline buffers as
+  // stage[o][c][r] and leave in 16-byte chunks along r; FP64 outputs go straight out
+  // (one 8-byte store per thread and column is already a full 256-byte warp segment).
+  __nv_bfloat16* stage = reinterpret_cast<__nv_bfloat16*>(smem);
+  static_assert(!kBf16Out || kOuts * BN * BM * 2 <= L::BAR_OFF, "staging exceeds smem");
   if (have) {
     tc_fence_after();
-    const int r = r0 + warp * 32 + lane;
+    const int rl = warp * 32 + lane;             // row inside the tile
+    const int r = r0 + rl;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     float a_mode = 0.f, mu_r = 0.f;
-    bool r_ok = r < ep.R_valid;
+    const bool r_ok = r < ep.R_valid;
     if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
       a_mode = (float)ep.ctl[b].a;
       mu_r = r_ok ? (float)ep.mu[r] : 0.f;
@@ -288,7 +298,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       tmem_ld32(lane_base + BN + cc * 32, v1);
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        const int c = c0 + cc * 32 + q;
+        const int cl = cc * 32 + q;
+        const int c = c0 + cl;
         float x0 = __uint_as_float(v0[q]);
         float x1 = __uint_as_float(v1[q]);
         if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
@@ -297,31 +308,46 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (r_ok && c < ep.C_valid) {
             const float nu_c = (float)ep.nu[c];
             const float det = mu_r * nu_c + mu_r * a_mode + nu_c * a_mode;
-            const float inv = 1.0f / det;
+            const float inv = __frcp_rn(det);
             y0 = ((nu_c + a_mode) * x0 + a_mode * x1) * inv;
             y1 = (a_mode * x0 + (mu_r + a_mode) * x1) * inv;
           }
           x0 = y0;
           x1 = y1;
         }
-        const size_t o0 = (size_t)b * ep.o_bs + (size_t)c * ep.o_ld + r;
         if (EPI == EPI_F64) {
           if (r_ok && c < ep.C_valid) {
+            const size_t o0 = (size_t)b * ep.o_bs + (size_t)c * ep.o_ld + r;
             double* out = static_cast<double*>(ep.out);
             out[o0] = (double)x0;
             out[o0 + ep.o_ls] = (double)x1;
           }
         } else {
-          __nv_bfloat16* out = static_cast<__nv_bfloat16*>(ep.out);
           const __nv_bfloat16 h0 = __float2bfloat16(x0);
           const __nv_bfloat16 h1 = __float2bfloat16(x1);
-          out[o0] = h0;
-          out[o0 + ep.o_ls] = h1;
-          if (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) {
-            __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(ep.out_lo);
-            lo[o0] = __float2bfloat16(x0 - __bfloat162float(h0));
-            lo[o0 + ep.o_ls] = __float2bfloat16(x1 - __bfloat162float(h1));
+          stage[((size_t)0 * BN + cl) * BM + rl] = h0;
+          stage[((size_t)1 * BN + cl) * BM + rl] = h1;
+          if (kLo) {
+            stage[((size_t)2 * BN + cl) * BM + rl] = __float2bfloat16(x0 - __bfloat162float(h0));
+            stage[((size_t)3 * BN + cl) * BM + rl] = __float2bfloat16(x1 - __bfloat162float(h1));
           }
+        }
+      }
+    }
+  }
+  if (kBf16Out) {
+    __syncthreads();
+    if (have) {
+      // 16-byte chunks: 16 per staged column of 128 rows; thread t takes t, t + 128, ...
+      constexpr int kChunks = BN * (BM / 8);
+#pragma unroll 1
+      for (int o = 0; o < kOuts; ++o) {
+        __nv_bfloat16* out = static_cast<__nv_bfloat16*>((o < 2) ? ep.out : ep.out_lo);
+        const size_t base = (size_t)b * ep.o_bs + (size_t)(o & 1) * ep.o_ls + r0;
+        for (int q = threadIdx.x; q < kChunks; q += kThreads) {
+          const int cl = q >> 4, rc = (q & 15) * 8;
+          const uint4 v = *reinterpret_cast<const uint4*>(&stage[((size_t)o * BN + cl) * BM + rc]);
+          *reinterpret_cast<uint4*>(&out[base + (size_t)(c0 + cl) * ep.o_ld + rc]) = v;
         }
       }
     }
