@@ -1,0 +1,62 @@
+// Conversions between FP64 and FP32/BF16 done with integer bit operations.
+//
+// On this GPU every FP64<->FP32 conversion instruction issues on the FP64 pipe, which
+// runs at 1/64 of the FP32 rate and is the bottleneck of the solver's FP64 kernels.
+// These helpers rebuild the IEEE encodings on the integer pipe instead.  Values below
+// the FP32 normal range (|x| < 2^-126) flush to a signed zero; Inf and NaN are kept.
+#pragma once
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace mca {
+
+// Exact widening of a normal (or zero / Inf / NaN) float; subnormals flush to zero.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint32_t m = u & 0x7FFFFFu;
+  uint32_t hi, lo;
+  if (e == 0u) {
+    hi = sign;
+    lo = 0u;
+  } else if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3);
+    lo = m << 29;
+  } else {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);   // 896 = 1023 - 127
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Narrowing to float by truncating the mantissa (relative error < 2^-23); out-of-range
+// magnitudes become zero or infinity.
+__device__ __forceinline__ float d2f_trunc(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v);
+  const uint32_t lo = (uint32_t)__double2loint(v);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // top 23 mantissa bits
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  const int ef = e - 896;
+  if (ef <= 0) return __uint_as_float(sign);
+  if (ef >= 0xFF) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((uint32_t)ef << 23) | m);
+}
+
+// BF16 with round-to-nearest-even on the truncated float (the discarded low 29 bits of
+// the double only matter for exact BF16 ties).
+__device__ __forceinline__ __nv_bfloat16 d2bf16_bits(double v) {
+  const uint32_t f = __float_as_uint(d2f_trunc(v));
+  uint32_t r;
+  if ((f & 0x7F800000u) == 0x7F800000u)
+    r = (f >> 16) | ((f & 0xFFFFu) ? 0x40u : 0u);            // Inf / NaN
+  else
+    r = (f + 0x7FFFu + ((f >> 16) & 1u)) >> 16;
+  __nv_bfloat16_raw raw;
+  raw.x = (unsigned short)r;
+  return __nv_bfloat16(raw);
+}
+
+}  // namespace mca

@@ -9,6 +9,7 @@
 //   pass 3: w <- w - V h2, and ||w||^2 in the same sweep
 // so the nk = k+1 basis vectors are read three times.  All reductions are two-level
 // (per-block partials, then one fixed-order sum per vector), hence deterministic.
+#include "bits.cuh"
 #include "mca_internal.cuh"
 
 namespace mca {
@@ -213,7 +214,7 @@ __global__ void k_normalize(const double* __restrict__ w, double* __restrict__ v
       const int l = (int)(e / mn);
       const int cell = (int)(e - (size_t)l * mn);
       const int i = cell / n, j = cell - (cell / n) * n;
-      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = __double2bfloat16(val);
+      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = d2bf16_bits(val);
     }
   }
 }

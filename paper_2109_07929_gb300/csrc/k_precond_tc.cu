@@ -25,6 +25,7 @@
 
 #include <cstring>
 
+#include "bits.cuh"
 #include "mca_internal.cuh"
 #include "precond_tc.h"
 
@@ -289,7 +290,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const bool r_ok = r < ep.R_valid;
     if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
       a_mode = (float)ep.ctl[b].a;
-      mu_r = r_ok ? (float)ep.mu[r] : 0.f;
+      mu_r = r_ok ? ep.mu_f[r] : 0.f;
     }
 #pragma unroll 1
     for (int cc = 0; cc < BN / 32; ++cc) {
@@ -306,7 +307,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           // [y_t; y_b] = (1/det) [[nu + a, a], [a, mu + a]] [x_t; x_b]
           float y0 = 0.f, y1 = 0.f;
           if (r_ok && c < ep.C_valid) {
-            const float nu_c = (float)ep.nu[c];
+            const float nu_c = ep.nu_f[c];
             const float det = mu_r * nu_c + mu_r * a_mode + nu_c * a_mode;
             const float inv = __frcp_rn(det);
             y0 = ((nu_c + a_mode) * x0 + a_mode * x1) * inv;
@@ -319,8 +320,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (r_ok && c < ep.C_valid) {
             const size_t o0 = (size_t)b * ep.o_bs + (size_t)c * ep.o_ld + r;
             double* out = static_cast<double*>(ep.out);
-            out[o0] = (double)x0;
-            out[o0 + ep.o_ls] = (double)x1;
+            out[o0] = f2d_bits(x0);
+            out[o0 + ep.o_ls] = f2d_bits(x1);
           }
         } else {
           const __nv_bfloat16 h0 = __float2bfloat16(x0);

@@ -11,6 +11,7 @@
 // FP64 arithmetic is the scarce resource on this GPU (about 1/64 of the FP32 rate), so the
 // kernels keep FP64 instructions per cell low: diagonals are precomputed per position
 // class, and the device model uses short Taylor polynomials instead of library sinh/cosh.
+#include "bits.cuh"
 #include "mca_internal.cuh"
 
 namespace mca {
@@ -56,10 +57,12 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
-// sinh(x) and cosh(x) for the memristor model.  For |x| <= 1 the Taylor series
-//   sinh(x) = x sum_k x^2k / (2k+1)!,  cosh(x) = sum_k x^2k / (2k)!
-// truncated after x^18/19! and x^20/20! (next terms below 2e-20 relative), evaluated by
-// Horner in t = x^2 (20 FMAs); outside that range the CUDA math library.
+// Memristor current and conductance.  The current enters the KCL residual and is kept in
+// FP64: for |x| <= 1, sinh(x) = x sum_k x^2k / (2k+1)! truncated after x^18/19! (next term
+// below 2e-20 relative), Horner in t = x^2 (10 FMAs); outside that range the CUDA math
+// library.  The conductance cosh(x) only shapes the Newton matrix (the Jacobian diagonal
+// and a = mean(D)), so it is evaluated in FP32 (relative error ~1e-7, which changes the
+// inexact Newton steps but not the solution the FP64 residual drives them to).
 __device__ __forceinline__ void sinh_cosh(double x, double& sh, double& ch) {
   if (fabs(x) <= 1.0) {
     const double t = x * x;
@@ -73,19 +76,8 @@ __device__ __forceinline__ void sinh_cosh(double x, double& sh, double& ch) {
     ps = fma(ps, t, 1.0 / 120.0);                           // 1/5!
     ps = fma(ps, t, 1.0 / 6.0);                             // 1/3!
     ps = fma(ps, t, 1.0);
-    double pc = 1.0 / 2432902008176640000.0;                // 1/20!
-    pc = fma(pc, t, 1.0 / 6402373705728000.0);              // 1/18!
-    pc = fma(pc, t, 1.0 / 20922789888000.0);                // 1/16!
-    pc = fma(pc, t, 1.0 / 87178291200.0);                   // 1/14!
-    pc = fma(pc, t, 1.0 / 479001600.0);                     // 1/12!
-    pc = fma(pc, t, 1.0 / 3628800.0);                       // 1/10!
-    pc = fma(pc, t, 1.0 / 40320.0);                         // 1/8!
-    pc = fma(pc, t, 1.0 / 720.0);                           // 1/6!
-    pc = fma(pc, t, 1.0 / 24.0);                            // 1/4!
-    pc = fma(pc, t, 0.5);                                   // 1/2!
-    pc = fma(pc, t, 1.0);
     sh = x * ps;
-    ch = pc;
+    ch = f2d_bits(coshf(d2f_trunc(x)));
   } else {
     sh = sinh(x);
     ch = cosh(x);
@@ -327,7 +319,7 @@ __global__ void k_init_basis(const double* __restrict__ F, double sign, double* 
       const int l = (int)(e / mn);
       const int cell = (int)(e - (size_t)l * mn);
       const int i = cell / n, j = cell - (cell / n) * n;
-      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = __float2bfloat16((float)val);
+      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = d2bf16_bits(val);
     }
   }
 }

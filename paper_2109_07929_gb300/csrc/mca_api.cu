@@ -75,6 +75,7 @@ struct mca_handle {
   std::vector<int> map_host;
   double *mu = nullptr, *nu = nullptr, *Qr = nullptr, *Qc = nullptr, *QrT = nullptr,
          *QcT = nullptr;
+  float *mu_f = nullptr, *nu_f = nullptr;   // FP32 eigenvalues for the GEMM epilogue
   // BF16 copies (padded)
   __nv_bfloat16 *QrT_bf = nullptr, *QcT_bf = nullptr, *Qr_hi = nullptr, *Qr_lo = nullptr,
                 *Qc_hi = nullptr, *Qc_lo = nullptr;
@@ -345,6 +346,8 @@ int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, i
   e.err = h->err;
   e.mu = h->mu;
   e.nu = h->nu;
+  e.mu_f = h->mu_f;
+  e.nu_f = h->nu_f;
   cudaEvent_t t0 = prof_begin(h, s);
   switch (step) {
     case 0:  // T1^T = (X Q_r)^T
@@ -809,6 +812,18 @@ int mca_create_multi(const mca_params* p, const double* g_map, int32_t n_maps,
         (rc = dalloc(h, &h->Qr_hi, npp)) || (rc = dalloc(h, &h->Qr_lo, npp)) ||
         (rc = dalloc(h, &h->Qc_hi, mpp)) || (rc = dalloc(h, &h->Qc_lo, mpp)))
       return fail(rc);
+    // FP32 copies of the eigenvalues (host-side rounding of n + m values)
+    std::vector<double> ev(std::max(h->m, h->n));
+    std::vector<float> evf(ev.size());
+    if ((rc = dalloc(h, &h->mu_f, h->n)) || (rc = dalloc(h, &h->nu_f, h->m))) return fail(rc);
+    if (cudaMemcpy(ev.data(), h->mu, h->n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(MCA_ERR_CUDA);
+    for (int i = 0; i < h->n; ++i) evf[i] = (float)ev[i];
+    cudaMemcpy(h->mu_f, evf.data(), h->n * sizeof(float), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(ev.data(), h->nu, h->m * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(MCA_ERR_CUDA);
+    for (int i = 0; i < h->m; ++i) evf[i] = (float)ev[i];
+    cudaMemcpy(h->nu_f, evf.data(), h->m * sizeof(float), cudaMemcpyHostToDevice);
     launch_pack_q_bf16(h->Qr, h->n, h->np, h->Qr_hi, h->Qr_lo, h->QrT_bf, s);
     count_launches(1);
     launch_pack_q_bf16(h->Qc, h->m, h->mp, h->Qc_hi, h->Qc_lo, h->QcT_bf, s);

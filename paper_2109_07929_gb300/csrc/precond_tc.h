@@ -27,6 +27,8 @@ struct GemmEpi {
   size_t o_bs, o_ls, o_ld;
   const double* mu;         // eigenvalue per r (EPI_MODES*)
   const double* nu;         // eigenvalue per c (EPI_MODES*)
+  const float* mu_f;        // the same in FP32 (the epilogue arithmetic is FP32)
+  const float* nu_f;
   const VecCtl* ctl;        // per-vector a and activity flag (NULL: all active)
   int* err;                 // device status flag (MCA_ERR_TIMEOUT on an expired wait)
 };

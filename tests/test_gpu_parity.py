@@ -61,8 +61,9 @@ def test_eigenpairs(m, n):
 @pytest.mark.parametrize("vrange", [0.35, 2.0], ids=["series", "wide"])
 @pytest.mark.parametrize("m,n", SHAPES)
 def test_residual_and_jacobian_diagonal(m, n, vrange):
-    """|b dV| <= 1 uses the Taylor form of sinh/cosh, larger |b dV| the library
-    functions; both must agree with NumPy's sinh/cosh to FP64 rounding."""
+    """|b dV| <= 1 uses the Taylor form of sinh, larger |b dV| the library function;
+    both must give the residual to FP64 rounding.  D (cosh, the Jacobian diagonal) is
+    evaluated in FP32 for |b dV| <= 1: it only shapes the Newton matrix."""
     cb = mi.make_crossbar(m, n, 2, nvec=2)
     p = cb.params
     rng = np.random.default_rng(5)
@@ -81,9 +82,9 @@ def test_residual_and_jacobian_diagonal(m, n, vrange):
         scale = 4 * max(p.g_wire_top, p.g_wire_bot) * np.abs(x[v]).max() + p.g_src * 0.3 + cur
         np.testing.assert_allclose(F[v], np.concatenate([Ft, Fb]), rtol=0, atol=1e-14 * scale)
         Dr = O.device_conductance(cb.gmap.ravel(), p.b, x[v, :m * n] - x[v, m * n:])
-        np.testing.assert_allclose(D[v], Dr, rtol=1e-14)
+        np.testing.assert_allclose(D[v], Dr, rtol=3e-7)
         np.testing.assert_allclose(fn[v], np.linalg.norm(np.concatenate([Ft, Fb])), rtol=1e-12)
-        np.testing.assert_allclose(dm[v], Dr.mean(), rtol=1e-13)
+        np.testing.assert_allclose(dm[v], Dr.mean(), rtol=3e-7)
 
 
 @pytest.mark.parametrize("m,n", SHAPES)
