@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=1024)
-    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--precision", default="bf16split", choices=["bf16split", "bf16", "fp64"])
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -467,6 +467,8 @@ def committed_traffic(fam, fp):
         h = hashlib.sha1(f.read()).hexdigest()
     if h != ent.get("sha1"):
         return None
+    if "ratio_to_algorithmic" in ent:
+        return ent["ratio_to_algorithmic"] * fp["bytes"] / max(1, fp["launches"])
     return ent.get("bytes_per_launch")
 
 

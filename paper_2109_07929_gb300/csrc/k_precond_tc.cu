@@ -154,24 +154,31 @@ __device__ __forceinline__ void record_error(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
 
-template <int BN, bool SPLIT>
+// Shared-memory plan.  Single-product GEMMs keep two stages (<= 113 KB) so two CTAs share
+// an SM and one CTA's epilogue overlaps the other's main loop; the split GEMMs need two
+// 96/80 KB stages and run one CTA per SM.  A staged BF16 epilogue reuses the stage buffers
+// (4 outputs of 128 x BN in the MODES_SPLIT case), which sets the floor on their size.
+template <int BN, bool SPLIT, int EPI>
 struct Layout {
   static constexpr int A_BYTES = BM * BK * 2;       // 16 KB
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int HALF = 2 * A_BYTES + B_BYTES;
   static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
-  static constexpr int STAGES = SPLIT ? 2 : 4;
+  static constexpr int STAGE_OUT = ((EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) ? 4 : 2) * BN * BM * 2;
+  static constexpr int STAGES_MIN = (STAGE_OUT + STAGE - 1) / STAGE;
+  static constexpr int STAGES = SPLIT ? 2 : (STAGES_MIN > 2 ? STAGES_MIN : 2);
+  static constexpr int CTAS = (STAGES * STAGE <= 110 * 1024) ? 2 : 1;
   static constexpr int BAR_OFF = STAGES * STAGE;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;  // barriers + TMEM slot + alignment
   static constexpr int TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
 };
 
 template <int BN, bool SPLIT, int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, Layout<BN, SPLIT, EPI>::CTAS)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
           GemmEpi ep) {
-  using L = Layout<BN, SPLIT>;
+  using L = Layout<BN, SPLIT, EPI>;
   const int rt = blockIdx.x, ct = blockIdx.y, b = blockIdx.z;
   if (ep.ctl != nullptr && !ep.ctl[b].gm_active) return;
   extern __shared__ uint8_t smem_raw[];
@@ -380,7 +387,7 @@ __global__ void k_cast_pad(const double* __restrict__ x, size_t xstride,
 template <int BN, bool SPLIT, int EPI>
 cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
                        const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
-  using L = Layout<BN, SPLIT>;
+  using L = Layout<BN, SPLIT, EPI>;
   auto kern = k_gemm_tc<BN, SPLIT, EPI>;
   static bool configured = false;
   if (!configured) {
@@ -457,7 +464,7 @@ cudaError_t configure_all() {
   {                                                                                     \
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN_, SPLIT_, EPI_>,                  \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                         Layout<BN_, SPLIT_>::SMEM);                    \
+                                         Layout<BN_, SPLIT_, EPI_>::SMEM);              \
     if (e != cudaSuccess) return e;                                                     \
   }
   MCA_TC_CFG(128, false, EPI_BF16)

@@ -337,3 +337,21 @@ def test_full_size_1024_sampled():
         vt, vb, io, st = s.solve(cb.vin)
     ref = O.newton_solve(p, cb.gmap, cb.vin[0], tol=1e-12, linear="pgmres")
     assert _rel_err(vt[0], ref.Vt) <= 1e-7 and _rel_err(vb[0], ref.Vb) <= 1e-7
+
+
+def test_full_size_2048_residual():
+    """2048x2048 (8.4M unknowns), log-uniform g, wires 1 S / 0.5 S, BF16 split
+    preconditioner, Newton to 1e-8: the oracle recomputes the FP64 KCL residual of the
+    returned voltages and the Kirchhoff balance."""
+    cb = mi.config_large(2048, 0)
+    p = cb.params
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, newton_rtol=1e-8, max_batch=1),
+                    cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+    assert st[0]["status"] == 0 and st[0]["gmres_iters"] <= 20
+    Ft, Fb = O.residual(p, cb.gmap, cb.vin[0], vt[0].ravel(), vb[0].ravel())
+    Yt, _ = O.source_vector(p, cb.vin[0])
+    rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
+    assert rel <= 1e-8 * 1.01
+    assert abs(O.kcl_balance(p, cb.vin[0], vt[0], vb[0])) <= 1e-6 * O.outputs(
+        p, cb.vin[0], vt[0], vb[0])["i_in"].sum()
