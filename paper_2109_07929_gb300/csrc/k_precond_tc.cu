@@ -35,7 +35,8 @@ namespace tc {
 namespace {
 
 constexpr int BM = 128;          // accumulator rows (TMEM lanes)
-constexpr int BK = 64;           // K elements per stage: one 128-byte swizzle row
+constexpr int BK = 64;           // K elements per stage with 128-byte swizzling
+constexpr int BK_SPLIT = 32;     // split GEMMs: 64-byte swizzle rows, half-size stages
 constexpr int kThreads = 128;    // 4 warps: TMA producer, MMA issuer, all 4 run the epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
@@ -111,6 +112,24 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* p) {
   return d;
 }
 
+// The same for 64-byte swizzling (K tiles of 32 BF16): 8-row x 64-byte atoms, 512 bytes
+// between consecutive 8-row groups.
+__device__ __forceinline__ uint64_t sw64_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                    // 64-byte swizzle
+  return d;
+}
+
+template <int BKT>
+__device__ __forceinline__ uint64_t tile_desc(const void* p) {
+  return BKT == 64 ? sw128_desc(p) : sw64_desc(p);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -154,20 +173,25 @@ __device__ __forceinline__ void record_error(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
 
-// Shared-memory plan.  Single-product GEMMs keep two stages (<= 113 KB) so two CTAs share
-// an SM and one CTA's epilogue overlaps the other's main loop; the split GEMMs need two
-// 96/80 KB stages and run one CTA per SM.  A staged BF16 epilogue reuses the stage buffers
-// (4 outputs of 128 x BN in the MODES_SPLIT case), which sets the floor on their size.
+// Shared-memory plan.  A configuration that fits two CTAs per SM (<= 110 KB) keeps two
+// stages so one CTA's epilogue overlaps the other's main loop; otherwise one CTA uses up
+// to ~200 KB of stages.  A staged BF16 epilogue reuses the stage buffers (2 or 4 output
+// tiles of 128 x BN), which sets the floor on their size.  Split GEMMs use 32-wide K
+// tiles (64-byte swizzle) to make their stages small enough to pair up.
 template <int BN, bool SPLIT, int EPI>
 struct Layout {
-  static constexpr int A_BYTES = BM * BK * 2;       // 16 KB
-  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int BKT = SPLIT ? BK_SPLIT : BK;
+  static constexpr int A_BYTES = BM * BKT * 2;
+  static constexpr int B_BYTES = BN * BKT * 2;
   static constexpr int HALF = 2 * A_BYTES + B_BYTES;
   static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
-  static constexpr int STAGE_OUT = ((EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) ? 4 : 2) * BN * BM * 2;
+  static constexpr int STAGE_OUT = (EPI == EPI_F64) ? 0 :
+      ((EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) ? 4 : 2) * BN * BM * 2;
   static constexpr int STAGES_MIN = (STAGE_OUT + STAGE - 1) / STAGE;
-  static constexpr int STAGES = SPLIT ? 2 : (STAGES_MIN > 2 ? STAGES_MIN : 2);
-  static constexpr int CTAS = (STAGES * STAGE <= 110 * 1024) ? 2 : 1;
+  static constexpr int STAGES_2 = STAGES_MIN > 2 ? STAGES_MIN : 2;
+  static constexpr int CTAS = (STAGES_2 * STAGE <= 110 * 1024) ? 2 : 1;
+  static constexpr int STAGES_1 = (200 * 1024) / STAGE;
+  static constexpr int STAGES = (CTAS == 2) ? STAGES_2 : (STAGES_1 > STAGES_MIN ? STAGES_1 : STAGES_MIN);
   static constexpr int BAR_OFF = STAGES * STAGE;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;  // barriers + TMEM slot + alignment
   static constexpr int TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
@@ -192,7 +216,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = rt * BM, c0 = ct * BN;
   const int blk0 = 2 * b, blk1 = 2 * b + 1;
-  const int nkb = ep.K / BK;
+  constexpr int BKT = L::BKT;
+  const int nkb = ep.K / BKT;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < L::STAGES; ++s) {
@@ -225,7 +250,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
       uint8_t* st = smem + s * L::STAGE;
       mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
-      const int k0 = kb * BK;
+      const int k0 = kb * BKT;
       tma_load_2d(st, &tmA, k0, blk0 * ep.R + r0, &full[s]);
       tma_load_2d(st + L::A_BYTES, &tmA, k0, blk1 * ep.R + r0, &full[s]);
       tma_load_2d(st + 2 * L::A_BYTES, &tmB, k0, c0, &full[s]);
@@ -251,19 +276,19 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       tc_fence_after();
       const uint8_t* st = smem + s * L::STAGE;
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
+      for (int kk = 0; kk < BKT / 16; ++kk) {
         const int off = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzle row
-        const uint64_t a0 = sw128_desc(st + off);
-        const uint64_t a1 = sw128_desc(st + L::A_BYTES + off);
-        const uint64_t bd = sw128_desc(st + 2 * L::A_BYTES + off);
+        const uint64_t a0 = tile_desc<BKT>(st + off);
+        const uint64_t a1 = tile_desc<BKT>(st + L::A_BYTES + off);
+        const uint64_t bd = tile_desc<BKT>(st + 2 * L::A_BYTES + off);
         const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
         umma(tmem, a0, bd, idesc, acc);
         umma(tmem + BN, a1, bd, idesc, acc);
         if (SPLIT) {
           const uint8_t* sl = st + L::HALF;
-          const uint64_t a0l = sw128_desc(sl + off);
-          const uint64_t a1l = sw128_desc(sl + L::A_BYTES + off);
-          const uint64_t bdl = sw128_desc(sl + 2 * L::A_BYTES + off);
+          const uint64_t a0l = tile_desc<BKT>(sl + off);
+          const uint64_t a1l = tile_desc<BKT>(sl + L::A_BYTES + off);
+          const uint64_t bdl = tile_desc<BKT>(sl + 2 * L::A_BYTES + off);
           umma(tmem, a0l, bd, idesc, 1u);
           umma(tmem, a0, bdl, idesc, 1u);
           umma(tmem + BN, a1l, bd, idesc, 1u);
@@ -417,19 +442,21 @@ bool encode_available() {
   return true;
 }
 
-// 2-D BF16 map over a row-major [rows][cols] matrix with a box of box_rows x 64 elements
-// and 128-byte swizzle.
+// 2-D BF16 map over a row-major [rows][cols] matrix with a box of box_rows x box_k
+// elements: box_k = 64 with 128-byte swizzle, box_k = 32 with 64-byte swizzle.
 bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
-              uint32_t box_rows) {
+              uint32_t box_rows, uint32_t box_k) {
   if (!encode_available()) return false;
+  if (box_k != (uint32_t)BK && box_k != (uint32_t)BK_SPLIT) return false;
   cuuint64_t gdim[2] = {cols, rows};
   cuuint64_t gstride[1] = {cols * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  cuuint32_t box[2] = {box_k, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
                         gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        box_k == (uint32_t)BK ? CU_TENSOR_MAP_SWIZZLE_128B
+                                              : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

@@ -199,20 +199,24 @@ int setup_tc(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->El, B * 2 * np * mp));
   MCA_CUDA_TRY(cudaMemset(h->Xbf, 0, B * 2 * mp * np * sizeof(__nv_bfloat16)));
   bool ok = true;
-  ok &= tc::make_map(&h->mA1, h->Xbf, B * 2 * mp, np, 128);
-  ok &= tc::make_map(&h->mA2, h->T1bf, B * 2 * np, mp, 128);
-  ok &= tc::make_map(&h->mA3h, h->Yh, B * 2 * mp, np, 128);
-  ok &= tc::make_map(&h->mA3l, h->Yl, B * 2 * mp, np, 128);
-  ok &= tc::make_map(&h->mA4h, h->Eh, B * 2 * np, mp, 128);
-  ok &= tc::make_map(&h->mA4l, h->El, B * 2 * np, mp, 128);
+  // K tiles: 64 wide for the single-product transforms, 32 wide for the split
+  // back transforms, which also hold both operands in hi/lo pairs (split precision)
+  const bool split = h->p.precision == MCA_PREC_BF16_SPLIT;
+  const uint32_t kb = split ? 32u : 64u;
+  ok &= tc::make_map(&h->mA1, h->Xbf, B * 2 * mp, np, 128, 64);
+  ok &= tc::make_map(&h->mA2, h->T1bf, B * 2 * np, mp, 128, 64);
+  ok &= tc::make_map(&h->mA3h, h->Yh, B * 2 * mp, np, 128, kb);
+  ok &= tc::make_map(&h->mA3l, h->Yl, B * 2 * mp, np, 128, kb);
+  ok &= tc::make_map(&h->mA4h, h->Eh, B * 2 * np, mp, 128, kb);
+  ok &= tc::make_map(&h->mA4l, h->El, B * 2 * np, mp, 128, kb);
   const uint32_t bns[2] = {128, 64};
   for (int q = 0; q < 2; ++q) {
-    ok &= tc::make_map(&h->mB1[q], h->QrT_bf, np, np, bns[q]);
-    ok &= tc::make_map(&h->mB2[q], h->QcT_bf, mp, mp, bns[q]);
-    ok &= tc::make_map(&h->mB3h[q], h->Qr_hi, np, np, bns[q]);
-    ok &= tc::make_map(&h->mB3l[q], h->Qr_lo, np, np, bns[q]);
-    ok &= tc::make_map(&h->mB4h[q], h->Qc_hi, mp, mp, bns[q]);
-    ok &= tc::make_map(&h->mB4l[q], h->Qc_lo, mp, mp, bns[q]);
+    ok &= tc::make_map(&h->mB1[q], h->QrT_bf, np, np, bns[q], 64);
+    ok &= tc::make_map(&h->mB2[q], h->QcT_bf, mp, mp, bns[q], 64);
+    ok &= tc::make_map(&h->mB3h[q], h->Qr_hi, np, np, bns[q], kb);
+    ok &= tc::make_map(&h->mB3l[q], h->Qr_lo, np, np, bns[q], kb);
+    ok &= tc::make_map(&h->mB4h[q], h->Qc_hi, mp, mp, bns[q], kb);
+    ok &= tc::make_map(&h->mB4l[q], h->Qc_lo, mp, mp, bns[q], kb);
   }
   if (!ok) {
     set_error("tensor map encoding failed");

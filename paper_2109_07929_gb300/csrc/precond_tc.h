@@ -34,8 +34,9 @@ struct GemmEpi {
 };
 
 bool encode_available();
+// box_k: 64 (single-product GEMMs) or 32 (split GEMMs)
 bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
-              uint32_t box_rows);
+              uint32_t box_rows, uint32_t box_k);
 cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
