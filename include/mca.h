@@ -265,8 +265,10 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
 #define MCA_FAM_RESIDUAL 0      /* residual + Jacobian diagonal (eq. F, eq. J)              */
 #define MCA_FAM_SPMV_DOTS 1     /* Jacobian apply fused with the first Gram-Schmidt pass    */
 #define MCA_FAM_UPDATE_DOTS 2   /* second Gram-Schmidt pass                                 */
-#define MCA_FAM_UPDATE_NORM 3   /* third Gram-Schmidt pass with the norm                    */
-#define MCA_FAM_NORMALIZE 4     /* basis normalisation (+ BF16 copy)                         */
+#define MCA_FAM_UPDATE_NORM 3   /* third Gram-Schmidt pass with the norm; writes the next
+                                   (unnormalised) basis vector and its BF16 copy            */
+#define MCA_FAM_NORMALIZE 4     /* reserved: no separate normalisation pass (the basis is
+                                   kept unnormalised with per-vector scales); reads 0       */
 #define MCA_FAM_SMALL 5         /* reductions, Givens, Newton control, least squares        */
 #define MCA_FAM_UPDATE_X 6      /* x += Z y                                                 */
 #define MCA_FAM_PRECOND_1 7     /* preconditioner transform 1 (X Q_r)                       */
@@ -310,6 +312,12 @@ int mca_profile_read(mca_handle* h, int32_t family, int64_t* launches, double* m
 int mca_residual_noalloc(const mca_params* p, const double* g_map, const double* x,
                          const double* v_in, int32_t nvec, double* F, double* D,
                          double* fnorm, double* dmean, void* stream);
+
+/* Self-test of the bounded device waits that guard every mbarrier wait of the
+ * tensor-core kernels: launches one thread that waits on a barrier nothing completes,
+ * with a limit of limit_ns nanoseconds.  Returns MCA_ERR_TIMEOUT (the expected result)
+ * with the CUDA context still usable, or MCA_ERR_CUDA. */
+int mca_wait_selftest(mca_handle* h, int64_t limit_ns);
 
 /* Number of CUDA kernel launches this library has made in the calling process. */
 int64_t mca_kernel_launches(void);

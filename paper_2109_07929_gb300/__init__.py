@@ -40,6 +40,7 @@ EXPORTED = (
     "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
     "mca_solve_many", "mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
     "mca_cnn_mse", "mca_cnn_adam", "mca_cnn_features", "mca_cnn_state", "mca_set_conductances",
+    "mca_wait_selftest",
 )
 
 FAMILIES = ("residual", "spmv_dots", "update_dots", "update_norm", "normalize", "small",
@@ -121,6 +122,8 @@ def load(build_if_missing=True):
     lib.mca_residual_noalloc.restype = ctypes.c_int
     lib.mca_solve_from.argtypes = [P, P, P, P, ctypes.c_int32, P, P, P, P, P]
     lib.mca_set_conductances.argtypes = [P, P]
+    lib.mca_wait_selftest.argtypes = [P, ctypes.c_int64]
+    lib.mca_wait_selftest.restype = ctypes.c_int
     lib.mca_set_conductances.restype = ctypes.c_int
     I, F = ctypes.c_int32, ctypes.c_float
     lib.mca_cnn_conv_forward.argtypes = [P, I, I, I, I, P, P, I, I, I, P, P]

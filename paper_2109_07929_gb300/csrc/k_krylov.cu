@@ -50,16 +50,17 @@ __device__ __forceinline__ bool last_block(unsigned int* cnt, int b, int nblk) {
   return last;
 }
 
-// Fixed-order reduction of part[b][j][0..nblk) into h[b][j] (j < nk), warp w taking rows
-// w, w + 8, ...
+// Fixed-order reduction of part[b][j][0..nblk) into h[b][j] = scale[j] * sum (j < nk),
+// warp w taking rows w, w + 8, ...
 __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ part, int b,
-                                                  int nblk, int nk, double* __restrict__ h) {
+                                                  int nblk, int nk, double* __restrict__ h,
+                                                  const double* scale) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int j = w; j < nk; j += kThreads / 32) {
     double s = 0.0;
     for (int t = l; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32 + j) * nblk + t]);
     s = warp_sum(s);
-    if (l == 0) h[(size_t)b * 32 + j] = s;
+    if (l == 0) h[(size_t)b * 32 + j] = scale ? s * scale[j] : s;
   }
 }
 
@@ -95,6 +96,7 @@ __device__ void givens_column(VecCtl& c, int b, double hn2, const double* __rest
   c.k_done = k + 1;
   c.gmres_iters += 1;
   c.inv_h = (hk1 > 0.0) ? 1.0 / hk1 : 0.0;
+  c.s[k + 1] = c.inv_h;
   const bool stop = !(res > c.tol_abs) || (k + 1 >= restart) || !(hk1 > 0.0) ||
                     !(rho > 0.0) || !isfinite(res);
   if (stop) c.gm_active = 0;
@@ -125,9 +127,10 @@ k_update_dots(double* __restrict__ w, const double* __restrict__ V, size_t vstri
   const int b = blockIdx.y;
   if (ctl != nullptr && !ctl[b].gm_active) return;
   double hj[KP], acc[KP];
+  const double* sc = ctl ? ctl[b].s : nullptr;
 #pragma unroll
   for (int j = 0; j < KP; ++j) {
-    hj[j] = (j < nk) ? h[(size_t)b * 32 + j] : 0.0;
+    hj[j] = (j < nk) ? h[(size_t)b * 32 + j] * (sc ? sc[j] : 1.0) : 0.0;
     acc[j] = 0.0;
   }
   double* wb = w + (size_t)b * n2;
@@ -148,25 +151,32 @@ k_update_dots(double* __restrict__ w, const double* __restrict__ V, size_t vstri
   }
   block_store_partials<KP>(acc, nk, part, b, nblk);
   if (cnt != nullptr && last_block(cnt, b, nblk)) {
-    block_reduce_rows(part, b, nblk, nk, h2);
+    block_reduce_rows(part, b, nblk, nk, h2, sc);
     if (threadIdx.x == 0) cnt[b] = 0;
   }
 }
 
-// pass 3: w <- w - sum_j h_j v_j, then the partial ||w||^2 (stored at part[b][0][blk]).
+// pass 3: out <- w - sum_j h_j v_j (the next, unnormalised basis vector, with its BF16
+// copy for the tensor-core preconditioner), then the partial ||out||^2; the last block
+// of each vector turns the norm into h_{k+1,k}, the Givens column and the new scale.
 template <int KP>
 __global__ void __launch_bounds__(kThreads)
-k_update_norm(double* __restrict__ w, const double* __restrict__ V, size_t vstride, size_t n2,
+k_update_norm(const double* w, const double* __restrict__ V, size_t vstride, size_t n2,
               int nk, const double* __restrict__ h, double* __restrict__ part, int nblk,
               VecCtl* ctl, unsigned int* cnt, const double* __restrict__ h1, int restart,
-              int32_t* host_flags) {
+              int32_t* host_flags, double* out, size_t ostride,
+              __nv_bfloat16* __restrict__ xbf, int mp, int np, int m, int n) {
   const int b = blockIdx.y;
   if (ctl != nullptr && !ctl[b].gm_active) return;
+  const double* sc = ctl ? ctl[b].s : nullptr;
   double hj[KP];
 #pragma unroll
-  for (int j = 0; j < KP; ++j) hj[j] = (j < nk) ? h[(size_t)b * 32 + j] : 0.0;
-  double* wb = w + (size_t)b * n2;
+  for (int j = 0; j < KP; ++j)
+    hj[j] = (j < nk) ? h[(size_t)b * 32 + j] * (sc ? sc[j] : 1.0) : 0.0;
+  const double* wb = w + (size_t)b * n2;
+  double* ob = out + (size_t)b * ostride;
   const double* Vb = V + (size_t)b * vstride;
+  const size_t mn = n2 / 2;
   double acc[1] = {0.0};
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n2;
        e += (size_t)nblk * kThreads) {
@@ -174,7 +184,13 @@ k_update_norm(double* __restrict__ w, const double* __restrict__ V, size_t vstri
 #pragma unroll
     for (int j = 0; j < KP; ++j)
       if (j < nk) x = fma(-hj[j], Vb[(size_t)j * n2 + e], x);
-    wb[e] = x;
+    ob[e] = x;
+    if (xbf != nullptr) {
+      const int l = (e >= mn) ? 1 : 0;
+      const int cell = (int)(e - (size_t)l * mn);
+      const int i = cell / n, jj = cell - i * n;
+      xbf[(((size_t)b * 2 + l) * mp + i) * np + jj] = d2bf16_bits(x);
+    }
     acc[0] = fma(x, x, acc[0]);
   }
   block_store_partials<1>(acc, 1, part, b, nblk);
@@ -191,30 +207,6 @@ k_update_norm(double* __restrict__ w, const double* __restrict__ V, size_t vstri
     if (threadIdx.x == 0) {
       cnt[b] = 0;
       givens_column(ctl[b], b, hn2, h1, h, nk - 1, restart, host_flags);
-    }
-  }
-}
-
-// v_{k+1} = w / h_{k+1,k} and its BF16 copy for the tensor-core preconditioner.
-__global__ void k_normalize(const double* __restrict__ w, double* __restrict__ vnext,
-                            size_t vstride, size_t n2, __nv_bfloat16* __restrict__ xbf,
-                            int mp, int np, int m, int n, const VecCtl* __restrict__ ctl) {
-  const int b = blockIdx.y;
-  const VecCtl& c = ctl[b];
-  if (!c.gm_active) return;
-  const double s = c.inv_h;
-  const int mn = m * n;
-  const double* wb = w + (size_t)b * n2;
-  double* v = vnext + (size_t)b * vstride;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n2;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const double val = wb[e] * s;
-    v[e] = val;
-    if (xbf != nullptr) {
-      const int l = (int)(e / mn);
-      const int cell = (int)(e - (size_t)l * mn);
-      const int i = cell / n, j = cell - (cell / n) * n;
-      xbf[(((size_t)b * 2 + l) * mp + i) * np + j] = d2bf16_bits(val);
     }
   }
 }
@@ -271,6 +263,7 @@ __global__ void k_gmres_init(const double* __restrict__ part_norm, int nblk, Vec
       c.gmres_iters = 0;
     }
     c.g[0] = beta;
+    c.s[0] = 1.0;
     c.res_est = beta;
     c.k_done = 0;
     c.newton_active = 1;
@@ -332,18 +325,11 @@ void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, i
 void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
                         const double* h2, double* part, int nblk, int B, VecCtl* ctl,
                         unsigned int* cnt, const double* h1, int restart,
-                        int32_t* host_flags, cudaStream_t s) {
+                        int32_t* host_flags, double* out, size_t ostride,
+                        __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s) {
   dim3 grid(nblk, B);
   MCA_KP_DISPATCH(k_update_norm, nk, grid, w, V, vstride, n2, nk, h2, part, nblk, ctl, cnt,
-                  h1, restart, host_flags);
-}
-
-void launch_normalize(const double* w, double* vnext, size_t vstride, size_t n2,
-                      __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
-                      int B, cudaStream_t s) {
-  int nb = (int)((n2 + kThreads - 1) / kThreads);
-  if (nb > 1216) nb = 1216;
-  k_normalize<<<dim3(nb, B), kThreads, 0, s>>>(w, vnext, vstride, n2, xbf, mp, np, m, n, ctl);
+                  h1, restart, host_flags, out, ostride, xbf, mp, np, m, n);
 }
 
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,

@@ -75,10 +75,12 @@ k_gemm64_tstore(const double* __restrict__ A, BlkAddr a, const double* __restric
 // det = mu nu + mu a2 + nu a1 = (mu + a1)(nu + a2) - a1 a2, with a1 = a2 = a.
 __global__ void k_modes_2x2(double* __restrict__ Xh, const double* __restrict__ mu,
                             const double* __restrict__ nu, int m, int n,
-                            const VecCtl* __restrict__ ctl) {
+                            const VecCtl* __restrict__ ctl, int kidx) {
   const int b = blockIdx.y;
   if (!ctl[b].gm_active) return;
   const double a = ctl[b].a;
+  // scale of the unnormalised input basis vector (kidx < 0: none)
+  const double sc = (kidx >= 0) ? ctl[b].s[kidx] : 1.0;
   const size_t mn = (size_t)m * n;
   double* xt = Xh + (size_t)b * 2 * mn;
   double* xb = xt + mn;
@@ -86,10 +88,10 @@ __global__ void k_modes_2x2(double* __restrict__ Xh, const double* __restrict__ 
        e += (size_t)gridDim.x * blockDim.x) {
     const int ip = (int)(e / n), kp = (int)(e - (size_t)ip * n);
     const double M = mu[kp], N = nu[ip];
-    const double det = M * N + M * a + N * a;
+    const double f = sc / (M * N + M * a + N * a);
     const double u = xt[e], v = xb[e];
-    xt[e] = ((N + a) * u + a * v) / det;
-    xb[e] = (a * u + (M + a) * v) / det;
+    xt[e] = ((N + a) * u + a * v) * f;
+    xb[e] = (a * u + (M + a) * v) * f;
   }
 }
 
@@ -102,11 +104,11 @@ void launch_gemm64_tstore(const double* A, BlkAddr a, const double* Bm, double* 
 }
 
 void launch_modes_2x2_f64(double* Xh, const double* mu, const double* nu, int m, int n,
-                          const VecCtl* ctl, int B, cudaStream_t s) {
+                          const VecCtl* ctl, int B, int kidx, cudaStream_t s) {
   const size_t mn = (size_t)m * n;
   int nb = (int)((mn + 255) / 256);
   if (nb > 1216) nb = 1216;
-  k_modes_2x2<<<dim3(nb, B), 256, 0, s>>>(Xh, mu, nu, m, n, ctl);
+  k_modes_2x2<<<dim3(nb, B), 256, 0, s>>>(Xh, mu, nu, m, n, ctl, kidx);
 }
 
 }  // namespace mca

@@ -44,12 +44,14 @@ __global__ void k_mhat_factor(int m, int n, Grid gr, const VecCtl* __restrict__ 
 }
 
 // w = r_b + (G_b r_t + a2 r_t) / a1  (G_b acts along columns: neighbours i +- 1)
+// (times the scale sc of the unnormalised input basis vector; the whole apply is linear)
 __global__ void k_mhat_rhs(Grid gr, const double* __restrict__ r, size_t rstride,
                            double* __restrict__ z, size_t zstride,
-                           const VecCtl* __restrict__ ctl) {
+                           const VecCtl* __restrict__ ctl, int kidx) {
   const int b = blockIdx.y;
   if (!ctl[b].gm_active) return;
   const double a = ctl[b].a, inv_a = 1.0 / a;
+  const double sc = (kidx >= 0) ? ctl[b].s[kidx] : 1.0;
   const int m = gr.m, n = gr.n, mn = m * n;
   const double* rt = r + (size_t)b * rstride;
   const double* rb = rt + mn;
@@ -60,7 +62,7 @@ __global__ void k_mhat_rhs(Grid gr, const double* __restrict__ r, size_t rstride
     double s = db * rt[c];
     if (i > 0) s -= gr.gb * rt[c - n];
     if (i < m - 1) s -= gr.gb * rt[c + n];
-    w[c] = fma(s, inv_a, rb[c]);
+    w[c] = sc * fma(s, inv_a, rb[c]);
   }
 }
 
@@ -152,10 +154,11 @@ __global__ void k_mhat_rows(int m, int n, double* __restrict__ z, size_t zstride
 // z_b = ((G_t + a1 I) z_t - r_t) / a1  (G_t acts along rows: neighbours j +- 1)
 __global__ void k_mhat_back(Grid gr, const double* __restrict__ r, size_t rstride,
                             double* __restrict__ z, size_t zstride,
-                            const VecCtl* __restrict__ ctl) {
+                            const VecCtl* __restrict__ ctl, int kidx) {
   const int b = blockIdx.y;
   if (!ctl[b].gm_active) return;
   const double a = ctl[b].a, inv_a = 1.0 / a;
+  const double sc = (kidx >= 0) ? ctl[b].s[kidx] : 1.0;
   const int m = gr.m, n = gr.n, mn = m * n;
   const double* rt = r + (size_t)b * rstride;
   double* zt = z + (size_t)b * zstride;
@@ -166,31 +169,32 @@ __global__ void k_mhat_back(Grid gr, const double* __restrict__ r, size_t rstrid
     double s = dt * zt[c];
     if (j > 0) s -= gr.gt * zt[c - 1];
     if (j < n - 1) s -= gr.gt * zt[c + 1];
-    zb[c] = (s - rt[c]) * inv_a;
+    zb[c] = fma(-sc, rt[c], s) * inv_a;
   }
 }
 
 // Jacobi: z = r / diag(J), diag(J) = wire diagonal + D; none: z = r.
 __global__ void k_jacobi(Grid gr, const double* __restrict__ D, const double* __restrict__ r,
                          size_t rstride, double* __restrict__ z, size_t zstride, int none,
-                         const VecCtl* __restrict__ ctl) {
+                         const VecCtl* __restrict__ ctl, int kidx) {
   const int b = blockIdx.y;
   if (ctl && !ctl[b].gm_active) return;
+  const double sc = (ctl && kidx >= 0) ? ctl[b].s[kidx] : 1.0;
   const int m = gr.m, n = gr.n, mn = m * n;
   const double* rb = r + (size_t)b * rstride;
   double* zb = z + (size_t)b * zstride;
   const double* Db = D + (size_t)b * mn;
   for (int c = blockIdx.x * kT + threadIdx.x; c < mn; c += gridDim.x * kT) {
     if (none) {
-      zb[c] = rb[c];
-      zb[mn + c] = rb[mn + c];
+      zb[c] = sc * rb[c];
+      zb[mn + c] = sc * rb[mn + c];
       continue;
     }
     const int i = c / n, j = c - i * n;
     const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
     const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
-    zb[c] = rb[c] / (dt + Db[c]);
-    zb[mn + c] = rb[mn + c] / (db + Db[c]);
+    zb[c] = sc * rb[c] / (dt + Db[c]);
+    zb[mn + c] = sc * rb[mn + c] / (db + Db[c]);
   }
 }
 
@@ -203,22 +207,24 @@ int nblocks(size_t count) {
 }  // namespace
 
 int precond_mhat(const Grid& gr, const double* r, size_t rstride, double* z, size_t zstride,
-                 int B, const VecCtl* ctl, double* fac, int ld, cudaStream_t s) {
+                 int B, const VecCtl* ctl, double* fac, int ld, int kidx, cudaStream_t s) {
   const int m = gr.m, n = gr.n;
   const size_t mn = (size_t)m * n;
   k_mhat_factor<<<B, 32, 0, s>>>(m, n, gr, ctl, fac, ld);
-  k_mhat_rhs<<<dim3(nblocks(mn), B), kT, 0, s>>>(gr, r, rstride, z, zstride, ctl);
+  k_mhat_rhs<<<dim3(nblocks(mn), B), kT, 0, s>>>(gr, r, rstride, z, zstride, ctl, kidx);
   k_mhat_cols<<<dim3((n + 127) / 128, B), 128, 0, s>>>(m, n, z, zstride, fac, ld, gr.gb, ctl);
   k_mhat_rows<<<dim3((m + 31) / 32, B), 256, 0, s>>>(m, n, z, zstride, fac, ld, gr.gt, ctl);
-  k_mhat_back<<<dim3(nblocks(mn), B), kT, 0, s>>>(gr, r, rstride, z, zstride, ctl);
+  k_mhat_back<<<dim3(nblocks(mn), B), kT, 0, s>>>(gr, r, rstride, z, zstride, ctl, kidx);
   count_launches(5);
   return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
 }
 
 int precond_jacobi(const Grid& gr, const double* D, const double* r, size_t rstride, double* z,
-                   size_t zstride, int B, bool none, const VecCtl* ctl, cudaStream_t s) {
+                   size_t zstride, int B, bool none, const VecCtl* ctl, int kidx,
+                   cudaStream_t s) {
   const size_t mn = (size_t)gr.m * gr.n;
-  k_jacobi<<<dim3(nblocks(mn), B), kT, 0, s>>>(gr, D, r, rstride, z, zstride, none ? 1 : 0, ctl);
+  k_jacobi<<<dim3(nblocks(mn), B), kT, 0, s>>>(gr, D, r, rstride, z, zstride, none ? 1 : 0, ctl,
+                                               kidx);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
 }

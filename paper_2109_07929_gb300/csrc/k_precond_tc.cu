@@ -320,9 +320,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     float a_mode = 0.f, mu_r = 0.f;
     const bool r_ok = r < ep.R_valid;
+    float sc = 1.f;          // scale of the unnormalised input basis vector
     if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
       a_mode = (float)ep.ctl[b].a;
       mu_r = r_ok ? ep.mu_f[r] : 0.f;
+      if (ep.kidx >= 0) sc = (float)ep.ctl[b].s[ep.kidx];
     }
 #pragma unroll 1
     for (int cc = 0; cc < BN / 32; ++cc) {
@@ -341,7 +343,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           if (r_ok && c < ep.C_valid) {
             const float nu_c = ep.nu_f[c];
             const float det = mu_r * nu_c + mu_r * a_mode + nu_c * a_mode;
-            const float inv = __frcp_rn(det);
+            const float inv = sc * __frcp_rn(det);
             y0 = ((nu_c + a_mode) * x0 + a_mode * x1) * inv;
             y1 = (a_mode * x0 + (mu_r + a_mode) * x1) * inv;
           }
@@ -392,6 +394,25 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)L::TMEM_COLS)
                  : "memory");
+  }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at,
+// with a limit of limit_ns, and records MCA_ERR_TIMEOUT when the wait gives up.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    bool ok = false;
+    while (!(ok = mbar_try_wait(&bar, 0))) {
+      if (global_ns() - t0 > limit_ns) break;
+    }
+    if (!ok) record_error(err, MCA_ERR_TIMEOUT);
   }
 }
 
@@ -508,6 +529,11 @@ cudaError_t configure_all() {
   MCA_TC_CFG(64, true, EPI_F64)
 #undef MCA_TC_CFG
   return cudaSuccess;
+}
+
+cudaError_t wait_selftest(unsigned long long limit_ns, int* err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, err);
+  return cudaGetLastError();
 }
 
 void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,

@@ -222,6 +222,7 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
     c.eta = eta;
     c.tol_abs = eta * fn;
     c.g[0] = fn;
+    c.s[0] = 1.0;
     c.res_est = fn;
     c.gm_active = 1;
     c.newton_iters += 1;
@@ -327,13 +328,14 @@ __global__ void k_init_basis(const double* __restrict__ F, double sign, double* 
 // Deterministic reduction of part[b][j][0..nblk) (j < nk) into h[b][j] by the whole
 // block (warp w sums rows w, w + 8, ...).
 __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ part, int b,
-                                                  int nblk, int nk, double* __restrict__ h) {
+                                                  int nblk, int nk, double* __restrict__ h,
+                                                  const double* scale) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int j = w; j < nk; j += kThreads / 32) {
     double s = 0.0;
     for (int t = l; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32 + j) * nblk + t]);
     s = warp_sum(s);
-    if (l == 0) h[(size_t)b * 32 + j] = s;
+    if (l == 0) h[(size_t)b * 32 + j] = scale ? s * scale[j] : s;
   }
 }
 
@@ -408,7 +410,8 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
   __syncthreads();
   if (!last) return;
   __threadfence();
-  block_reduce_rows(part, b, nblk, nk, h);
+  // the stored basis is unnormalised: <v_j, w> = s_j <V_j, w>
+  block_reduce_rows(part, b, nblk, nk, h, ctl ? ctl[b].s : nullptr);
   if (threadIdx.x == 0) cnt[b] = 0;
 }
 

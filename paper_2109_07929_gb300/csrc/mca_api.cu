@@ -337,7 +337,7 @@ int check_device_error(mca_handle* h) {
 // Tensor-core transform `step` (0..3) of the preconditioner for B vectors; the input of
 // step 0 is the BF16 copy in h->Xbf, the output of step 3 goes to zout (FP64).
 int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, int B,
-            const VecCtl* ctl, cudaStream_t s, int prof_k) {
+            const VecCtl* ctl, cudaStream_t s, int prof_k, int kidx = -1) {
   const int m = h->m, n = h->n;
   const size_t mn = h->mn, mp = h->mp, np = h->np;
   auto q = [](int bn) { return bn == 128 ? 0 : 1; };
@@ -347,6 +347,7 @@ int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, i
   const double sp = split ? 3.0 : 1.0;
   tc::GemmEpi e{};
   e.ctl = ctl;
+  e.kidx = kidx;
   e.err = h->err;
   e.mu = h->mu;
   e.nu = h->nu;
@@ -440,13 +441,15 @@ int autotune_tiles(mca_handle* h) {
 }
 
 // z = P^-1 r for B vectors: r at rin + b*rstride, z at zout + b*zstride.  For the
-// tensor-core forms the BF16 copy of r must already be in h->Xbf.
+// tensor-core forms the BF16 copy of r must already be in h->Xbf.  kidx >= 0: r is the
+// unnormalised basis vector k, and z = P^-1 (ctl[b].s[kidx] r).
 int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstride,
                   double* zout, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s,
-                  int prof_k = -1, const double* D = nullptr) {
+                  int prof_k = -1, const double* D = nullptr, int kidx = -1) {
   if (precision == MCA_PREC_MHAT) {
     cudaEvent_t t0 = prof_begin(h, s);
-    MCA_TRY(precond_mhat(h->gr, rin, rstride, zout, zstride, B, ctl, h->fac, h->fac_ld, s));
+    MCA_TRY(precond_mhat(h->gr, rin, rstride, zout, zstride, B, ctl, h->fac, h->fac_ld, kidx,
+                         s));
     prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 112.0 * (double)h->mn, 40.0 * (double)h->mn, s);
     return MCA_OK;
   }
@@ -454,7 +457,7 @@ int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstrid
     if (precision == MCA_PREC_JACOBI && D == nullptr) return MCA_ERR_UNSUPPORTED;
     cudaEvent_t t0 = prof_begin(h, s);
     MCA_TRY(precond_jacobi(h->gr, D, rin, rstride, zout, zstride, B,
-                           precision == MCA_PREC_NONE, ctl, s));
+                           precision == MCA_PREC_NONE, ctl, kidx, s));
     prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 40.0 * (double)h->mn, 4.0 * (double)h->mn, s);
     return MCA_OK;
   }
@@ -472,7 +475,7 @@ int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstrid
     t0 = prof_begin(h, s);
     launch_gemm64_tstore(h->T1_64, a2, h->QcT, h->Xh_64, o2, B, n, m, m, ctl, s);
     count_launches(1);
-    launch_modes_2x2_f64(h->Xh_64, h->mu, h->nu, m, n, ctl, B, s);
+    launch_modes_2x2_f64(h->Xh_64, h->mu, h->nu, m, n, ctl, B, kidx, s);
     count_launches(1);
     prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, 64.0 * mn, f_c, s);
     BlkAddr a3{2 * mn, mn, (size_t)n}, o3{2 * mn, mn, (size_t)m};
@@ -491,7 +494,7 @@ int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstrid
   if (!h->tc_ok) return MCA_ERR_UNSUPPORTED;
   const bool split = (precision == MCA_PREC_BF16_SPLIT);
   for (int step = 0; step < 4; ++step)
-    MCA_TRY(tc_step(h, step, split, zout, zstride, B, ctl, s, prof_k));
+    MCA_TRY(tc_step(h, step, split, zout, zstride, B, ctl, s, prof_k, kidx));
   return MCA_OK;
 }
 
@@ -512,7 +515,9 @@ bool any_flag(const mca_handle* h, int B) {
 }
 
 // Enqueue GMRES iteration k (preconditioner, Jacobian apply + CGS2 with the fused
-// reductions and Givens column, basis normalisation) for the vectors still iterating.
+// reductions and Givens column) for the vectors still iterating.  The basis vectors after
+// v_0 are kept unnormalised with their scales in VecCtl::s, so the third pass writes
+// v_{k+1} (and its BF16 copy) directly.
 int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t s) {
   const size_t n2 = h->n2;
   const double cells = (double)h->mn;
@@ -525,7 +530,7 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
   double* zk = h->Z + (size_t)k * n2;
   const double nk = k + 1;
   // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
-  MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D));
+  MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k));
   cudaEvent_t t0 = prof_begin(h, s);
   launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
                    h->ctl, h->cnt, h->h1, s);
@@ -538,15 +543,11 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
   prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k, cells * (32.0 + 16.0 * nk), cells * 8.0 * nk, s);
   t0 = prof_begin(h, s);
   launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, h->cnt,
-                     h->h1, h->restart, h->hflags_dev, s);
+                     h->h1, h->restart, h->hflags_dev, h->V + (size_t)(k + 1) * n2, vstride,
+                     tc ? h->Xbf : nullptr, h->mp, h->np, h->m, h->n, s);
   count_launches(1);
-  prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk), cells * (4.0 * nk + 4.0), s);
-  t0 = prof_begin(h, s);
-  launch_normalize(h->W, h->V + (size_t)(k + 1) * n2, vstride, n2, tc ? h->Xbf : nullptr,
-                   h->mp, h->np, h->m, h->n, h->ctl, B, s);
-  count_launches(1);
-  // the last iteration of a cycle normalises nothing: counted with iteration k + 1
-  prof_end(h, t0, MCA_FAM_NORMALIZE, k + 1, cells * (tc ? 36.0 : 32.0), cells * 2.0, s);
+  prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk + (tc ? 4.0 : 0.0)),
+           cells * (4.0 * nk + 4.0), s);
   MCA_CUDA_TRY(cudaGetLastError());
   return MCA_OK;
 }
@@ -1148,7 +1149,7 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
     MCA_CUDA_TRY(cudaMemcpyAsync(h->W, h->F, (size_t)nvec * n2 * sizeof(double),
                                  cudaMemcpyDeviceToDevice, s));
     launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, nullptr,
-                       nullptr, h->restart, nullptr, s);
+                       nullptr, h->restart, nullptr, h->W, n2, nullptr, 0, 0, h->m, h->n, s);
     launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, cycle == 0 ? 1 : 0, s);
     launch_init_basis(h->F, 1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
                       h->n, h->ctl, nvec, s);
@@ -1182,6 +1183,16 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
 }
 
 int64_t mca_kernel_launches(void) { return g_launches.load(); }
+
+int mca_wait_selftest(mca_handle* h, int64_t limit_ns) {
+  g_last_error.clear();
+  if (!h || limit_ns < 0) return MCA_ERR_INVALID_ARG;
+  MCA_CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
+  MCA_CUDA_TRY(tc::wait_selftest((unsigned long long)limit_ns, h->err, h->own_stream));
+  count_launches(1);
+  MCA_CUDA_TRY(cudaStreamSynchronize(h->own_stream));
+  return check_device_error(h);
+}
 
 int mca_profile(mca_handle* h, int32_t enable) {
   if (!h) return MCA_ERR_INVALID_ARG;

@@ -42,6 +42,9 @@ struct VecCtl {
   double sn[MCA_KMAX];
   double g[MCA_KMAX + 1];
   double y[MCA_KMAX];
+  // The basis is stored unnormalised: v_j = s[j] * V[j] (s[0] = 1; s[j+1] = 1/h_{j+1,j}
+  // is set with the Givens column, saving a separate normalisation pass over the vector).
+  double s[MCA_KMAX + 1];
 };
 
 // Scalars of one crossbar needed by the stencil kernels.
@@ -111,15 +114,15 @@ void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
 void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, int nk,
                         const double* h1, double* part, int nblk, int B, const VecCtl* ctl,
                         unsigned int* cnt, double* h2, cudaStream_t s);
-// pass 3: w -= V h2 and ||w||^2; with cnt != NULL the last block of each vector applies
-// the Givens rotation of column nk-1 (restart = cycle length) and updates the flags.
+// pass 3: out = w - V h2 (out[b] at out + b*ostride; out = w for in place) with its BF16
+// copy in xbf (may be NULL), and ||out||^2; with cnt != NULL the last block of each
+// vector applies the Givens rotation of column nk-1 (restart = cycle length), sets the
+// scale of the new basis vector and updates the flags.
 void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
                         const double* h2, double* part, int nblk, int B, VecCtl* ctl,
                         unsigned int* cnt, const double* h1, int restart,
-                        int32_t* host_flags, cudaStream_t s);
-void launch_normalize(const double* w, double* vnext, size_t vstride, size_t n2,
-                      __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
-                      int B, cudaStream_t s);
+                        int32_t* host_flags, double* out, size_t ostride,
+                        __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s);
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
                        int B, cudaStream_t s);
 // first = 1: remember beta = ||rhs|| and stop at rtol * beta; first = 0 (a restart): keep
@@ -134,10 +137,12 @@ void launch_pack_q_bf16(const double* Q, int n, int npad, __nv_bfloat16* out_q,
 void launch_transpose64(const double* Q, int n, double* QT, cudaStream_t s);
 // paper-literal M_hat, Jacobi and identity preconditioners (k_precond_mhat.cu); fac holds
 // 4 * ld doubles per vector, ld = max(m, n)
+// (the outputs carry the scale s[kidx] of the input basis vector)
 int precond_mhat(const Grid& gr, const double* r, size_t rstride, double* z, size_t zstride,
-                 int B, const VecCtl* ctl, double* fac, int ld, cudaStream_t s);
+                 int B, const VecCtl* ctl, double* fac, int ld, int kidx, cudaStream_t s);
 int precond_jacobi(const Grid& gr, const double* D, const double* r, size_t rstride, double* z,
-                   size_t zstride, int B, bool none, const VecCtl* ctl, cudaStream_t s);
+                   size_t zstride, int B, bool none, const VecCtl* ctl, int kidx,
+                   cudaStream_t s);
 // element-wise out = a - b on nvec vectors of n2 doubles (k_krylov.cu)
 void launch_sub(const double* a, const double* b, double* out, size_t n2, int B, cudaStream_t s);
 // FP64 preconditioner (k_precond64.cu)
@@ -152,9 +157,10 @@ struct BlkAddr {
 };
 void launch_gemm64_tstore(const double* A, BlkAddr a, const double* Bm, double* O, BlkAddr o,
                           int B, int R, int K, int C, const VecCtl* ctl, cudaStream_t s);
-// Per-mode 2x2 inverse of eq. (P) in place on X_hat[b][layer][i'][k'] (m x n).
+// Per-mode 2x2 inverse of eq. (P) in place on X_hat[b][layer][i'][k'] (m x n), times the
+// scale s[kidx] of the (unnormalised) input basis vector.
 void launch_modes_2x2_f64(double* Xh, const double* mu, const double* nu, int m, int n,
-                          const VecCtl* ctl, int B, cudaStream_t s);
+                          const VecCtl* ctl, int B, int kidx, cudaStream_t s);
 
 }  // namespace mca
 

@@ -30,6 +30,7 @@ struct GemmEpi {
   const float* mu_f;        // the same in FP32 (the epilogue arithmetic is FP32)
   const float* nu_f;
   const VecCtl* ctl;        // per-vector a and activity flag (NULL: all active)
+  int kidx;                 // EPI_MODES*: scale the modes by ctl[b].s[kidx] (-1: none)
   int* err;                 // device status flag (MCA_ERR_TIMEOUT on an expired wait)
 };
 
@@ -41,6 +42,7 @@ cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtens
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
 cudaError_t configure_all();
+cudaError_t wait_selftest(unsigned long long limit_ns, int* err, cudaStream_t s);
 void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
               int np, int B, cudaStream_t s);
 

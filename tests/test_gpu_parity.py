@@ -295,6 +295,17 @@ def test_linear_uniform_single_iteration():
     assert st2[0]["status"] == 0 and st2[0]["gmres_iters"] <= 4, st2
 
 
+def test_bounded_wait_gives_up_and_context_survives():
+    """A device wait on a barrier that nothing completes gives up after its limit and
+    reports MCA_ERR_TIMEOUT; the context stays usable (a solve afterwards succeeds)."""
+    cb = mi.make_crossbar(16, 12, 2)
+    with mca.Solver(_params(cb.params, max_batch=1), cb.gmap) as s:
+        rc = s.lib.mca_wait_selftest(s.h, 20_000_000)      # 20 ms
+        assert rc == mca.ERR_TIMEOUT
+        vt, vb, io, st = s.solve(cb.vin)
+        assert st[0]["status"] == 0
+
+
 def test_zero_input_and_status_codes():
     cb = mi.make_crossbar(8, 9, 1)
     p = cb.params
