@@ -264,8 +264,9 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
 /* ---- per-kernel-family timing (measurement support) -------------------------------- */
 #define MCA_FAM_RESIDUAL 0      /* residual + Jacobian diagonal (eq. F, eq. J)              */
 #define MCA_FAM_SPMV_DOTS 1     /* Jacobian apply fused with the first Gram-Schmidt pass    */
-#define MCA_FAM_UPDATE_DOTS 2   /* second Gram-Schmidt pass                                 */
-#define MCA_FAM_UPDATE_NORM 3   /* third Gram-Schmidt pass with the norm; writes the next
+#define MCA_FAM_UPDATE_DOTS 2   /* reorthogonalisation (dots, then update + norm), only for
+                                   the vectors whose orthogonality estimate asks for it      */
+#define MCA_FAM_UPDATE_NORM 3   /* Gram-Schmidt update with the norm; writes the next
                                    (unnormalised) basis vector and its BF16 copy            */
 #define MCA_FAM_NORMALIZE 4     /* reserved: no separate normalisation pass (the basis is
                                    kept unnormalised with per-vector scales); reads 0       */

@@ -43,7 +43,7 @@ EXPORTED = (
     "mca_wait_selftest",
 )
 
-FAMILIES = ("residual", "spmv_dots", "update_dots", "update_norm", "normalize", "small",
+FAMILIES = ("residual", "spmv_dots", "reorth", "update_norm", "normalize", "small",
             "update_x", "precond_1", "precond_2", "precond_3", "precond_4")
 
 

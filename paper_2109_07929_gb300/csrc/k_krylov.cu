@@ -1,14 +1,21 @@
 // Flexible GMRES kernels (Section 4: GMRES on each Newton system; right preconditioned,
-// Saad, Iterative Methods for Sparse Linear Systems, Alg. 9.6): classical Gram-Schmidt
-// with one reorthogonalisation (CGS2) in FP64, Givens rotations on the Hessenberg column,
-// back substitution and the solution update dx = Z y.
+// Saad, Iterative Methods for Sparse Linear Systems, Alg. 9.6): classical Gram-Schmidt in
+// FP64 with a second pass when a running estimate of the loss of orthogonality asks for
+// it (the Daniel-Gragg-Kaufman-Stewart selective reorthogonalisation), Givens rotations
+// on the Hessenberg column, back substitution and the solution update dx = Z y.
 //
 // Per iteration k the orthogonalisation runs as
 //   pass 1 (fused into the Jacobian apply): h1 = V^T w
-//   pass 2: w <- w - V h1, and h2 = V^T w in the same sweep
-//   pass 3: w <- w - V h2, and ||w||^2 in the same sweep
-// so the nk = k+1 basis vectors are read three times.  All reductions are two-level
-// (per-block partials, then one fixed-order sum per vector), hence deterministic.
+//   pass 2: u = w - V h1 (the next basis vector) and ||u||^2 in the same sweep
+//   only when the estimate asks for it:
+//   pass 3: h2 = V^T u;  pass 4: u <- u - V h2 and ||u||^2
+// The estimate follows u = (I - V V^T) w: if V^T V = I + E with |E| <= delta, then
+// |V^T u| <= delta |V^T w| plus rounding of order nk eps |w|, so the new vector keeps a
+// loss of about (sqrt(nk) delta + c nk eps) / rho with rho = |u| / |w| (the cancellation
+// of the pass, |w|^2 = |u|^2 + |h1|^2).  While that stays below kOrthTol the second pass
+// is skipped; the GMRES residual estimate is then exact up to a factor 1 + O(k kOrthTol).
+// All reductions are two-level (per-block partials, then one fixed-order sum per vector),
+// hence deterministic.
 #include "bits.cuh"
 #include "mca_internal.cuh"
 
@@ -17,6 +24,8 @@ namespace mca {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr double kEps = 1.1102230246251565e-16;   // 2^-53, unit roundoff of FP64
+constexpr double kOrthTol = 1e-8;                 // largest accepted loss of orthogonality
 
 template <int KP>
 __device__ __forceinline__ void block_store_partials(double (&acc)[KP], int nk,
@@ -64,14 +73,16 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
   }
 }
 
-// Givens rotation of Hessenberg column k (h = h1 + h2, h_{k+1,k} = sqrt(hn2)), residual
+// Givens rotation of Hessenberg column k (h = h1 + h2, h2 may be NULL; h_{k+1,k} =
+// sqrt(hn2)), residual
 // estimate |g_{k+1}| and the stop test of the GMRES cycle.  One thread.
 __device__ void givens_column(VecCtl& c, int b, double hn2, const double* __restrict__ h1,
                               const double* __restrict__ h2, int k, int restart,
                               int32_t* host_flags) {
   const int ld = MCA_KMAX + 1;
   double* col = c.H + (size_t)k * ld;
-  for (int j = 0; j <= k; ++j) col[j] = __ldcg(&h1[(size_t)b * 32 + j]) + __ldcg(&h2[(size_t)b * 32 + j]);
+  for (int j = 0; j <= k; ++j)
+    col[j] = __ldcg(&h1[(size_t)b * 32 + j]) + (h2 ? __ldcg(&h2[(size_t)b * 32 + j]) : 0.0);
   const double hk1 = sqrt(hn2);
   col[k + 1] = hk1;
   for (int j = 0; j < k; ++j) {
@@ -118,62 +129,53 @@ __global__ void k_reduce_dots(const double* __restrict__ part, int nblk, int nk,
   }
 }
 
-// pass 2: w <- w - sum_j h_j v_j, then partial dots <v_j, w>.
+// pass 3 (marked vectors only): partial dots <V_j, u> of the new vector u, reduced by the
+// last block into h2_j = s_j <V_j, u>.
 template <int KP>
 __global__ void __launch_bounds__(kThreads)
-k_update_dots(double* __restrict__ w, const double* __restrict__ V, size_t vstride, size_t n2,
-              int nk, const double* __restrict__ h, double* __restrict__ part, int nblk,
+k_reorth_dots(const double* __restrict__ u, const double* __restrict__ V, size_t vstride,
+              size_t n2, int nk, double* __restrict__ part, int nblk,
               const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h2) {
   const int b = blockIdx.y;
-  if (ctl != nullptr && !ctl[b].gm_active) return;
-  double hj[KP], acc[KP];
-  const double* sc = ctl ? ctl[b].s : nullptr;
+  if (!ctl[b].gm_active || !ctl[b].reorth) return;
+  double acc[KP];
 #pragma unroll
-  for (int j = 0; j < KP; ++j) {
-    hj[j] = (j < nk) ? h[(size_t)b * 32 + j] * (sc ? sc[j] : 1.0) : 0.0;
-    acc[j] = 0.0;
-  }
-  double* wb = w + (size_t)b * n2;
+  for (int j = 0; j < KP; ++j) acc[j] = 0.0;
+  const double* ub = u + (size_t)b * vstride;
   const double* Vb = V + (size_t)b * vstride;
   for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n2;
        e += (size_t)nblk * kThreads) {
-    double v[KP];
-#pragma unroll
-    for (int j = 0; j < KP; ++j) v[j] = (j < nk) ? Vb[(size_t)j * n2 + e] : 0.0;
-    double x = wb[e];
+    const double x = ub[e];
 #pragma unroll
     for (int j = 0; j < KP; ++j)
-      if (j < nk) x = fma(-hj[j], v[j], x);
-    wb[e] = x;
-#pragma unroll
-    for (int j = 0; j < KP; ++j)
-      if (j < nk) acc[j] = fma(v[j], x, acc[j]);
+      if (j < nk) acc[j] = fma(Vb[(size_t)j * n2 + e], x, acc[j]);
   }
   block_store_partials<KP>(acc, nk, part, b, nblk);
-  if (cnt != nullptr && last_block(cnt, b, nblk)) {
-    block_reduce_rows(part, b, nblk, nk, h2, sc);
+  if (last_block(cnt, b, nblk)) {
+    block_reduce_rows(part, b, nblk, nk, h2, ctl[b].s);
     if (threadIdx.x == 0) cnt[b] = 0;
   }
 }
 
-// pass 3: out <- w - sum_j h_j v_j (the next, unnormalised basis vector, with its BF16
-// copy for the tensor-core preconditioner), then the partial ||out||^2; the last block
-// of each vector turns the norm into h_{k+1,k}, the Givens column and the new scale.
+// Passes 2 and 4: out <- w - sum_j hc_j v_j (the next, unnormalised basis vector, with
+// its BF16 copy for the tensor-core preconditioner), then the partial ||out||^2; the last
+// block of each vector runs the phase's control step (UpdPhase).
 template <int KP>
 __global__ void __launch_bounds__(kThreads)
-k_update_norm(const double* w, const double* __restrict__ V, size_t vstride, size_t n2,
-              int nk, const double* __restrict__ h, double* __restrict__ part, int nblk,
-              VecCtl* ctl, unsigned int* cnt, const double* __restrict__ h1, int restart,
-              int32_t* host_flags, double* out, size_t ostride,
-              __nv_bfloat16* __restrict__ xbf, int mp, int np, int m, int n) {
+k_update_norm(int phase, const double* w, size_t wstride, const double* __restrict__ V,
+              size_t vstride, size_t n2, int nk, const double* __restrict__ hc,
+              double* __restrict__ part, int nblk, VecCtl* ctl, unsigned int* cnt,
+              const double* __restrict__ h1, int restart, int32_t* host_flags, double* out,
+              size_t ostride, __nv_bfloat16* __restrict__ xbf, int mp, int np, int m, int n) {
   const int b = blockIdx.y;
-  if (ctl != nullptr && !ctl[b].gm_active) return;
-  const double* sc = ctl ? ctl[b].s : nullptr;
+  if (phase != UPD_PLAIN && (!ctl[b].gm_active || (phase == UPD_REORTH && !ctl[b].reorth)))
+    return;
+  const double* sc = (phase != UPD_PLAIN) ? ctl[b].s : nullptr;
   double hj[KP];
 #pragma unroll
   for (int j = 0; j < KP; ++j)
-    hj[j] = (j < nk) ? h[(size_t)b * 32 + j] * (sc ? sc[j] : 1.0) : 0.0;
-  const double* wb = w + (size_t)b * n2;
+    hj[j] = (j < nk) ? hc[(size_t)b * 32 + j] * (sc ? sc[j] : 1.0) : 0.0;
+  const double* wb = w + (size_t)b * wstride;
   double* ob = out + (size_t)b * ostride;
   const double* Vb = V + (size_t)b * vstride;
   const size_t mn = n2 / 2;
@@ -194,7 +196,7 @@ k_update_norm(const double* w, const double* __restrict__ V, size_t vstride, siz
     acc[0] = fma(x, x, acc[0]);
   }
   block_store_partials<1>(acc, 1, part, b, nblk);
-  if (cnt == nullptr) return;
+  if (phase == UPD_PLAIN) return;
   if (last_block(cnt, b, nblk)) {
     __shared__ double hn2;
     if (threadIdx.x < 32) {
@@ -206,7 +208,35 @@ k_update_norm(const double* w, const double* __restrict__ V, size_t vstride, siz
     __syncthreads();
     if (threadIdx.x == 0) {
       cnt[b] = 0;
-      givens_column(ctl[b], b, hn2, h1, h, nk - 1, restart, host_flags);
+      VecCtl& c = ctl[b];
+      const int k = nk - 1;
+      const double grow = sqrt((double)nk) * c.orth;
+      if (phase == UPD_FIRST) {
+        double proj = 0.0;                      // |h1|^2 = |w|^2 - |u|^2
+        for (int j = 0; j < nk; ++j) {
+          const double t = __ldcg(&hc[(size_t)b * 32 + j]);
+          proj = fma(t, t, proj);
+        }
+        const double rho = (hn2 > 0.0) ? sqrt(hn2 / (hn2 + proj)) : 0.0;
+        const double est = (grow + 4.0 * nk * kEps) / rho;
+        if (hn2 > 0.0 && !(est <= kOrthTol)) {
+          c.reorth = 1;
+          c.reorth_mask |= 1u << k;
+          c.orth1 = est;
+          c.wn2 = hn2;
+          __threadfence();
+        } else {
+          if (hn2 > 0.0) c.orth = est;
+          givens_column(c, b, hn2, hc, nullptr, k, restart, host_flags);
+        }
+      } else {
+        // after the second pass: what is left of the first pass' loss orth1 is scaled by
+        // the basis' own loss, plus rounding, relative to the new norm
+        const double rho2 = (c.wn2 > 0.0 && hn2 > 0.0) ? sqrt(hn2 / c.wn2) : 0.0;
+        if (rho2 > 0.0) c.orth = fmax(c.orth, (grow * c.orth1 + 4.0 * nk * kEps) / rho2);
+        c.reorth = 0;
+        givens_column(c, b, hn2, h1, hc, k, restart, host_flags);
+      }
     }
   }
 }
@@ -264,6 +294,9 @@ __global__ void k_gmres_init(const double* __restrict__ part_norm, int nblk, Vec
     }
     c.g[0] = beta;
     c.s[0] = 1.0;
+    c.orth = 0.0;
+    c.reorth = 0;
+    c.reorth_mask = 0u;
     c.res_est = beta;
     c.k_done = 0;
     c.newton_active = 1;
@@ -315,21 +348,21 @@ void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
     else KERN<32><<<grid, kThreads, 0, s>>>(__VA_ARGS__);                     \
   } while (0)
 
-void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h1, double* part, int nblk, int B, const VecCtl* ctl,
-                        unsigned int* cnt, double* h2, cudaStream_t s) {
+void launch_reorth_dots(const double* u, const double* V, size_t vstride, size_t n2, int nk,
+                        double* part, int nblk, int B, const VecCtl* ctl, unsigned int* cnt,
+                        double* h2, cudaStream_t s) {
   dim3 grid(nblk, B);
-  MCA_KP_DISPATCH(k_update_dots, nk, grid, w, V, vstride, n2, nk, h1, part, nblk, ctl, cnt, h2);
+  MCA_KP_DISPATCH(k_reorth_dots, nk, grid, u, V, vstride, n2, nk, part, nblk, ctl, cnt, h2);
 }
 
-void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h2, double* part, int nblk, int B, VecCtl* ctl,
-                        unsigned int* cnt, const double* h1, int restart,
-                        int32_t* host_flags, double* out, size_t ostride,
+void launch_update_norm(int phase, const double* w, size_t wstride, const double* V,
+                        size_t vstride, size_t n2, int nk, const double* hc, double* part,
+                        int nblk, int B, VecCtl* ctl, unsigned int* cnt, const double* h1,
+                        int restart, int32_t* host_flags, double* out, size_t ostride,
                         __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s) {
   dim3 grid(nblk, B);
-  MCA_KP_DISPATCH(k_update_norm, nk, grid, w, V, vstride, n2, nk, h2, part, nblk, ctl, cnt,
-                  h1, restart, host_flags, out, ostride, xbf, mp, np, m, n);
+  MCA_KP_DISPATCH(k_update_norm, nk, grid, phase, w, wstride, V, vstride, n2, nk, hc, part,
+                  nblk, ctl, cnt, h1, restart, host_flags, out, ostride, xbf, mp, np, m, n);
 }
 
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,

@@ -223,6 +223,9 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
     c.tol_abs = eta * fn;
     c.g[0] = fn;
     c.s[0] = 1.0;
+    c.orth = 0.0;
+    c.reorth = 0;
+    c.reorth_mask = 0u;
     c.res_est = fn;
     c.gm_active = 1;
     c.newton_iters += 1;

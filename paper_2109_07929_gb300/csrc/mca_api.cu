@@ -110,6 +110,7 @@ struct mca_handle {
   // kernel-family timing
   struct ProfRec {
     int fam, k;
+    bool reorth;                // second Gram-Schmidt pass: only the vectors that took it
     cudaEvent_t a, b;
     double bytes_pv, flops_pv;  // per vector still iterating
   };
@@ -295,22 +296,23 @@ cudaEvent_t prof_begin(mca_handle* h, cudaStream_t s) {
 }
 
 void prof_end(mca_handle* h, cudaEvent_t a, int fam, int k, double bytes_pv, double flops_pv,
-              cudaStream_t s) {
+              cudaStream_t s, bool reorth = false) {
   if (!h->prof_on || !a) return;
   cudaEvent_t b = prof_event(h);
   if (!b) return;
   cudaEventRecord(b, s);
-  h->prof_pending.push_back({fam, k, a, b, bytes_pv, flops_pv});
+  h->prof_pending.push_back({fam, k, reorth, a, b, bytes_pv, flops_pv});
 }
 
-// Fold the pending records into the family totals.  active(k) is the number of vectors
-// that did work in GMRES iteration k (k < 0: launches outside the Krylov loop).
+// Fold the pending records into the family totals.  active(k, reorth) is the number of
+// vectors that did work in GMRES iteration k (k < 0: launches outside the Krylov loop;
+// reorth: the conditional second Gram-Schmidt pass).
 template <typename F>
 void prof_flush(mca_handle* h, F active) {
   if (!h->prof_on) return;
   for (auto& r : h->prof_pending) {
     if (cudaEventSynchronize(r.b) != cudaSuccess) continue;
-    const int act = active(r.k);
+    const int act = active(r.k, r.reorth);
     if (act <= 0) continue;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, r.a, r.b);
@@ -514,10 +516,10 @@ bool any_flag(const mca_handle* h, int B) {
   return false;
 }
 
-// Enqueue GMRES iteration k (preconditioner, Jacobian apply + CGS2 with the fused
-// reductions and Givens column) for the vectors still iterating.  The basis vectors after
-// v_0 are kept unnormalised with their scales in VecCtl::s, so the third pass writes
-// v_{k+1} (and its BF16 copy) directly.
+// Enqueue GMRES iteration k (preconditioner, Jacobian apply + classical Gram-Schmidt with
+// the fused reductions, the conditional second pass and the Givens column) for the vectors
+// still iterating.  The basis vectors after v_0 are kept unnormalised with their scales in
+// VecCtl::s, so the update pass writes v_{k+1} (and its BF16 copy) directly.
 int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t s) {
   const size_t n2 = h->n2;
   const double cells = (double)h->mn;
@@ -536,18 +538,26 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
                    h->ctl, h->cnt, h->h1, s);
   count_launches(1);
   prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (12.0 + 4.0 * nk), s);
+  double* vnext = h->V + (size_t)(k + 1) * n2;
+  __nv_bfloat16* xbf = tc ? h->Xbf : nullptr;
   t0 = prof_begin(h, s);
-  launch_update_dots(h->W, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B, h->ctl, h->cnt,
-                     h->h2, s);
-  count_launches(1);
-  prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k, cells * (32.0 + 16.0 * nk), cells * 8.0 * nk, s);
-  t0 = prof_begin(h, s);
-  launch_update_norm(h->W, h->V, vstride, n2, k + 1, h->h2, h->part, nbV, B, h->ctl, h->cnt,
-                     h->h1, h->restart, h->hflags_dev, h->V + (size_t)(k + 1) * n2, vstride,
-                     tc ? h->Xbf : nullptr, h->mp, h->np, h->m, h->n, s);
+  launch_update_norm(UPD_FIRST, h->W, n2, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B,
+                     h->ctl, h->cnt, h->h1, h->restart, h->hflags_dev, vnext, vstride, xbf,
+                     h->mp, h->np, h->m, h->n, s);
   count_launches(1);
   prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk + (tc ? 4.0 : 0.0)),
            cells * (4.0 * nk + 4.0), s);
+  // second pass, a no-op for the vectors whose orthogonality estimate did not ask for it
+  t0 = prof_begin(h, s);
+  launch_reorth_dots(vnext, h->V, vstride, n2, k + 1, h->part, nbV, B, h->ctl, h->cnt, h->h2,
+                     s);
+  launch_update_norm(UPD_REORTH, vnext, vstride, h->V, vstride, n2, k + 1, h->h2, h->part,
+                     nbV, B, h->ctl, h->cnt, h->h1, h->restart, h->hflags_dev, vnext, vstride,
+                     xbf, h->mp, h->np, h->m, h->n, s);
+  count_launches(2);
+  prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k,
+           cells * (48.0 + 32.0 * nk + (tc ? 4.0 : 0.0)),
+           cells * (8.0 * nk + 4.0), s, true);
   MCA_CUDA_TRY(cudaGetLastError());
   return MCA_OK;
 }
@@ -604,10 +614,15 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
                                  cudaMemcpyDeviceToHost, s));
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<int> kd(B);
-    for (int b = 0; b < B; ++b) kd[b] = h->ctl_host[b].k_done;
-    prof_flush(h, [&](int k) {
+    std::vector<uint32_t> rm(B);
+    for (int b = 0; b < B; ++b) {
+      kd[b] = h->ctl_host[b].k_done;
+      rm[b] = h->ctl_host[b].reorth_mask;
+    }
+    prof_flush(h, [&](int k, bool reorth) {
       int c = 0;
-      for (int b = 0; b < B; ++b) c += (k < kd[b]) ? 1 : 0;
+      for (int b = 0; b < B; ++b)
+        c += (k < kd[b] && (!reorth || ((rm[b] >> k) & 1u))) ? 1 : 0;
       return c;
     });
   }
@@ -645,7 +660,7 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     const int entering = n_active;
     n_active = 0;
     for (int b = 0; b < B; ++b) n_active += reinterpret_cast<volatile int32_t*>(h->hflags)[b] ? 1 : 0;
-    prof_flush(h, [&](int) { return entering; });
+    prof_flush(h, [&](int, bool) { return entering; });
     if (n_active == 0) break;
     t0 = prof_begin(h, s);
     launch_init_basis(h->F, -1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
@@ -664,7 +679,7 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
       kbar = c ? kbar / c : 0.0;
     }
     prof_end(h, t0, MCA_FAM_UPDATE_X, -1, cells * 16.0 * (2.0 + kbar), cells * 4.0 * kbar, s);
-    prof_flush(h, [&](int) { return n_active; });
+    prof_flush(h, [&](int, bool) { return n_active; });
     MCA_CUDA_TRY(cudaGetLastError());
   }
   launch_outputs(h->gr, h->vin, h->x, h->iout, h->kcl, B, s);
@@ -1148,8 +1163,9 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
     // beta = ||r||, v_0 = r / beta
     MCA_CUDA_TRY(cudaMemcpyAsync(h->W, h->F, (size_t)nvec * n2 * sizeof(double),
                                  cudaMemcpyDeviceToDevice, s));
-    launch_update_norm(h->W, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec, nullptr, nullptr,
-                       nullptr, h->restart, nullptr, h->W, n2, nullptr, 0, 0, h->m, h->n, s);
+    launch_update_norm(UPD_PLAIN, h->W, n2, h->V, vstride, n2, 0, h->h2, h->part, nbV, nvec,
+                       nullptr, nullptr, nullptr, h->restart, nullptr, h->W, n2, nullptr, 0, 0,
+                       h->m, h->n, s);
     launch_gmres_init(h->part, nbV, h->ctl, nvec, rtol, cycle == 0 ? 1 : 0, s);
     launch_init_basis(h->F, 1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
                       h->n, h->ctl, nvec, s);

@@ -36,7 +36,11 @@ struct VecCtl {
   int32_t gmres_iters;
   int32_t gm_active;   // GMRES cycle running
   int32_t k_done;      // columns finished in this cycle
-  int32_t pad0, pad1;
+  int32_t reorth;      // the current iteration needs the second Gram-Schmidt pass
+  uint32_t reorth_mask;  // bit k: iteration k of this cycle took the second pass
+  double orth;         // running estimate of the basis' loss of orthogonality
+  double orth1;        // estimate for the new vector after the first pass (when reorth)
+  double wn2;          // its squared norm after the first pass (when reorth)
   double H[(MCA_KMAX + 1) * MCA_KMAX];   // column k at H[k*(KMAX+1) + row]
   double cs[MCA_KMAX];
   double sn[MCA_KMAX];
@@ -111,17 +115,25 @@ int vec_nblk(size_t n2);
 void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
                         const VecCtl* ctl, cudaStream_t s);
 // pass 2: w -= V h1, partial dots <V_j, w>; the last block reduces them into h2.
-void launch_update_dots(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h1, double* part, int nblk, int B, const VecCtl* ctl,
-                        unsigned int* cnt, double* h2, cudaStream_t s);
-// pass 3: out = w - V h2 (out[b] at out + b*ostride; out = w for in place) with its BF16
-// copy in xbf (may be NULL), and ||out||^2; with cnt != NULL the last block of each
-// vector applies the Givens rotation of column nk-1 (restart = cycle length), sets the
-// scale of the new basis vector and updates the flags.
-void launch_update_norm(double* w, const double* V, size_t vstride, size_t n2, int nk,
-                        const double* h2, double* part, int nblk, int B, VecCtl* ctl,
-                        unsigned int* cnt, const double* h1, int restart,
-                        int32_t* host_flags, double* out, size_t ostride,
+// Update passes of the Gram-Schmidt step (phase of launch_update_norm):
+//   UPD_PLAIN  out = w - V hc and ||out||^2 partials only (cnt, ctl unused)
+//   UPD_FIRST  out = w - V h1 (hc = h1); the last block of each vector estimates the loss
+//              of orthogonality of out and either finishes Hessenberg column nk-1 (Givens
+//              rotation, scale of the new basis vector, flags) or marks the vector for the
+//              second pass
+//   UPD_REORTH only for marked vectors: out = w - V h2 (hc = h2, w = out in place), then
+//              column nk-1 = h1 + h2 is finished as above
+enum UpdPhase { UPD_PLAIN = 0, UPD_FIRST = 1, UPD_REORTH = 2 };
+// second-pass dots h2 = V^T u (j < nk) of the new vector u (u[b] at u + b*vstride), only
+// for the vectors marked by UPD_FIRST
+void launch_reorth_dots(const double* u, const double* V, size_t vstride, size_t n2, int nk,
+                        double* part, int nblk, int B, const VecCtl* ctl, unsigned int* cnt,
+                        double* h2, cudaStream_t s);
+// out[b] at out + b*ostride, w[b] at w + b*wstride; BF16 copy of out in xbf (may be NULL)
+void launch_update_norm(int phase, const double* w, size_t wstride, const double* V,
+                        size_t vstride, size_t n2, int nk, const double* hc, double* part,
+                        int nblk, int B, VecCtl* ctl, unsigned int* cnt, const double* h1,
+                        int restart, int32_t* host_flags, double* out, size_t ostride,
                         __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s);
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
                        int B, cudaStream_t s);

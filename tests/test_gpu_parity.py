@@ -253,6 +253,34 @@ def test_restarted_gmres_other_preconditioners(prec):
     assert its[0] >= 1
 
 
+def test_selective_reorthogonalisation_long_cycle():
+    """A 30-iteration cycle without preconditioning loses orthogonality fast enough that
+    the second Gram-Schmidt pass is taken; the GMRES minimum residual still matches the
+    oracle's modified Gram-Schmidt GMRES, and the Givens estimate matches the true
+    residual (which needs an orthonormal basis)."""
+    cb = mi.make_crossbar(24, 20, 12)
+    p = cb.params
+    N = 24 * 20
+    Dr = cb.gmap.ravel().copy()
+    J = O.jacobian(p, cb.gmap, np.zeros(N), np.zeros(N))
+    rhs = np.random.default_rng(2).standard_normal(2 * N)
+    with mca.Solver(_params(p, precision=mca.PREC_NONE, max_batch=1), cb.gmap) as s:
+        s.profile(True)
+        dx = torch.empty(1, 2 * N, dtype=torch.float64, device=DEV)
+        its, res = s.gmres_solve(_t(Dr[None]), [Dr.mean()], _t(rhs[None]), dx, 1e-15)
+        prof = s.profile_read()
+        s.profile(False)
+        dx = dx.cpu().numpy()[0]
+    assert its[0] == 30
+    assert prof["reorth"]["launches"] > 0
+    assert prof["reorth"]["launches"] < prof["update_norm"]["launches"]
+    true_res = np.linalg.norm(rhs - J @ dx)
+    np.testing.assert_allclose(res[0], true_res, rtol=1e-6)
+    x_ref, _, _ = O.gmres_right(lambda v: J @ v, rhs, lambda v: v, restart=30, rtol=1e-15,
+                                maxiter=30)
+    np.testing.assert_allclose(true_res, np.linalg.norm(rhs - J @ x_ref), rtol=1e-6)
+
+
 def test_batch_matches_single_solves():
     cb = mi.make_crossbar(48, 40, 21, nvec=6)
     p = cb.params
