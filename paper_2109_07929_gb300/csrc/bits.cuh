@@ -45,6 +45,16 @@ __device__ __forceinline__ float d2f_trunc(double v) {
   return __uint_as_float(sign | ((uint32_t)ef << 23) | m);
 }
 
+// Narrowing to float with rounding to nearest (ties away from zero): half an FP32 ulp
+// (bit 28 of the FP64 mantissa) is added to the magnitude before truncating; a carry into
+// the exponent is the correct rounding up into the next binade.  Inf and NaN are passed to
+// the truncation unchanged.
+__device__ __forceinline__ float d2f_round(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  if (((u >> 52) & 0x7FFull) == 0x7FFull) return d2f_trunc(v);
+  return d2f_trunc(__longlong_as_double((long long)(u + (1ull << 28))));
+}
+
 // BF16 with round-to-nearest-even on the truncated float (the discarded low 29 bits of
 // the double only matter for exact BF16 ties).
 __device__ __forceinline__ __nv_bfloat16 d2bf16_bits(double v) {

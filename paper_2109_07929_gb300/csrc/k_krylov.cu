@@ -33,11 +33,8 @@ __device__ __forceinline__ void block_store_partials(double (&acc)[KP], int nk,
                                                      int nblk) {
   __shared__ double red[kThreads / 32][KP];
   const int wv = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < KP; ++j) {
-    const double s = warp_sum(acc[j]);
-    if (l == 0) red[wv][j] = s;
-  }
+  const double tot = warp_sum_scatter<KP>(acc);
+  if (warp_scatter_writer<KP>(l)) red[wv][warp_scatter_index<KP>(l)] = tot;
   __syncthreads();
   if (threadIdx.x < nk && threadIdx.x < KP) {
     double s = 0.0;

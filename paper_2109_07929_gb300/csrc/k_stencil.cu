@@ -10,7 +10,8 @@
 //
 // FP64 arithmetic is the scarce resource on this GPU (about 1/64 of the FP32 rate), so the
 // kernels keep FP64 instructions per cell low: diagonals are precomputed per position
-// class, and the device model uses short Taylor polynomials instead of library sinh/cosh.
+// class, and the device model uses a short economised polynomial for sinh and FP32 cosh
+// instead of the FP64 library functions.
 #include "bits.cuh"
 #include "mca_internal.cuh"
 
@@ -57,30 +58,33 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
-// Memristor current and conductance.  The current enters the KCL residual and is kept in
-// FP64: for |x| <= 1, sinh(x) = x sum_k x^2k / (2k+1)! truncated after x^18/19! (next term
-// below 2e-20 relative), Horner in t = x^2 (10 FMAs); outside that range the CUDA math
-// library.  The conductance cosh(x) only shapes the Newton matrix (the Jacobian diagonal
-// and a = mean(D)), so it is evaluated in FP32 (relative error ~1e-7, which changes the
-// inexact Newton steps but not the solution the FP64 residual drives them to).
-__device__ __forceinline__ void sinh_cosh(double x, double& sh, double& ch) {
-  if (fabs(x) <= 1.0) {
+// Memristor current and conductance.  The current (g / b) sinh(b dV) = g dV p(x^2),
+// x = b dV, enters the KCL residual and is kept in FP64: for |x| < 3/4, p is the degree-6
+// Chebyshev-economised Taylor polynomial of sinh(x) / x (coefficients from
+// gen_sinh_poly.py; truncation error below 2e-18 relative), Horner in t = x^2 (6 FMAs);
+// outside that range the CUDA math library.  The range test reads the exponent bits (on
+// the integer pipe).  The conductance g cosh(x) only shapes the Newton matrix (the
+// Jacobian diagonal and a = mean(D)), so it is evaluated in FP32 (relative error below
+// 3e-7, which changes the inexact Newton steps but not the solution the FP64 residual
+// drives them to).
+__device__ __forceinline__ void device_current(const Grid& gr, double g, double dv,
+                                               double& cur_over_g, double& dg) {
+  const double x = gr.b * dv;
+  const uint32_t hi = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu;
+  if (hi < 0x3FE80000u) {                        // |x| < 0.75
     const double t = x * x;
-    double ps = 1.0 / 121645100408832000.0;                 // 1/19!
-    ps = fma(ps, t, 1.0 / 355687428096000.0);               // 1/17!
-    ps = fma(ps, t, 1.0 / 1307674368000.0);                 // 1/15!
-    ps = fma(ps, t, 1.0 / 6227020800.0);                    // 1/13!
-    ps = fma(ps, t, 1.0 / 39916800.0);                      // 1/11!
-    ps = fma(ps, t, 1.0 / 362880.0);                        // 1/9!
-    ps = fma(ps, t, 1.0 / 5040.0);                          // 1/7!
-    ps = fma(ps, t, 1.0 / 120.0);                           // 1/5!
-    ps = fma(ps, t, 1.0 / 6.0);                             // 1/3!
-    ps = fma(ps, t, 1.0);
-    sh = x * ps;
-    ch = f2d_bits(coshf(d2f_trunc(x)));
+    double ps = 1.62102664139390868e-10;         // t^6
+    ps = fma(ps, t, 2.50509370460377762e-08);    // t^5
+    ps = fma(ps, t, 2.75573237196537609e-06);    // t^4
+    ps = fma(ps, t, 1.98412698324150781e-04);    // t^3
+    ps = fma(ps, t, 8.33333333334163734e-03);    // t^2
+    ps = fma(ps, t, 1.66666666666666380e-01);    // t^1
+    ps = fma(ps, t, 1.0);                        // t^0
+    cur_over_g = dv * ps;
+    dg = f2d_bits(d2f_round(g) * coshf(d2f_round(x)));
   } else {
-    sh = sinh(x);
-    ch = cosh(x);
+    cur_over_g = sinh(x) * gr.inv_b;
+    dg = g * cosh(x);
   }
 }
 
@@ -102,18 +106,15 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
   if (j == 0) ft = fma(-gr.g_src, vin_i, ft);
   fb = fma(db, vb, -gr.gb * (bu + bd));
   const double dv = vt - vb;
-  double cur;
+  double cg;                                     // device current / g
   if (gr.b != 0.0) {
-    double sh, ch;
-    sinh_cosh(gr.b * dv, sh, ch);
-    cur = (g * gr.inv_b) * sh;
-    dg = g * ch;
+    device_current(gr, g, dv, cg, dg);
   } else {
-    cur = g * dv;
+    cg = dv;
     dg = g;
   }
-  ft += cur;
-  fb -= cur;
+  ft = fma(g, cg, ft);
+  fb = fma(-g, cg, fb);
 }
 
 __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl* ctl) {
@@ -167,6 +168,8 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
   double* Fb = Ft + mn;
   double* Db = D + (size_t)b * mn;
   const double* vinb = vin + (size_t)b * m;
+  // sum(D) stays in FP64: with uniform linear devices a = mean(D) must equal D to FP64
+  // rounding for the preconditioner to be exact (one GMRES iteration)
   double sf = 0.0, sd = 0.0;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
@@ -255,6 +258,8 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   double* Fb = Ft + mn;
   double* Db = D + (size_t)b * mn;
   const double* vinb = vin + (size_t)b * m;
+  // sum(D) stays in FP64: with uniform linear devices a = mean(D) must equal D to FP64
+  // rounding for the preconditioner to be exact (one GMRES iteration)
   double sf = 0.0, sd = 0.0;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
@@ -393,11 +398,8 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
   if (V == nullptr) return;
   __shared__ double red[kThreads / 32][KP];
   const int wv = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < KP; ++j) {
-    const double s = warp_sum(acc[j]);
-    if (l == 0) red[wv][j] = s;
-  }
+  const double tot = warp_sum_scatter<KP>(acc);
+  if (warp_scatter_writer<KP>(l)) red[wv][warp_scatter_index<KP>(l)] = tot;
   __syncthreads();
   if (threadIdx.x < nk && threadIdx.x < KP) {
     double s = 0.0;

@@ -651,10 +651,10 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
                            zero_state, h->F, h->D, h->part, nbR, B, h->ctl, cfg, h->cnt,
                            h->hflags_dev, s);
     count_launches(1);
-    // FP64 flops per cell: stencils 12, Taylor sinh/cosh 42, current/conductance 6,
-    // norms 5 (the zero state only the norms)
+    // FP64 flops per cell: stencils 8, sinh polynomial 16, current 4, norms 5 (the
+    // conductance cosh is FP32; the zero state only the norms)
     prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * (zero_state ? 32.0 : 48.0),
-             cells * (zero_state ? 5.0 : 65.0), s);
+             cells * (zero_state ? 5.0 : 33.0), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
     const int entering = n_active;

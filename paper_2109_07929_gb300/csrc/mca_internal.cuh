@@ -81,6 +81,53 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp sums of KP accumulators at once by recursive halving (reduce-scatter): at each of
+// the first log2(KP) butterfly levels a lane keeps half of its accumulators and sends the
+// other half to its partner, so the whole reduction takes KP - 1 + 5 - log2(KP) FP64
+// additions instead of 5 KP (FP64 additions are the scarce resource).  Returns, in every
+// lane, the warp total of accumulator warp_scatter_index<KP>(lane); acc is overwritten.
+// KP is a power of two <= 32.
+template <int KP>
+__device__ __forceinline__ double warp_sum_scatter(double (&acc)[KP]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int L = 0; L < 5; ++L) {
+    const int o = 16 >> L;
+    const int h = KP >> (L + 1);
+    if (h >= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < KP / 2; ++i) {
+        if (i < h) {
+          const double send = up ? acc[i] : acc[i + h];
+          const double keep = up ? acc[i + h] : acc[i];
+          acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      }
+    } else {
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+    }
+  }
+  return acc[0];
+}
+
+template <int KP>
+__device__ __forceinline__ int warp_scatter_index(int lane) {
+  int j = 0;
+#pragma unroll
+  for (int L = 0; L < 5; ++L) {
+    const int h = KP >> (L + 1);
+    if (h >= 1 && (lane & (16 >> L))) j += h;
+  }
+  return j;
+}
+
+// True in the one lane per accumulator that stores the result of warp_sum_scatter.
+template <int KP>
+__device__ __forceinline__ bool warp_scatter_writer(int lane) {
+  return (lane & (32 / KP - 1)) == 0;
+}
+
 // ---------------------------------------------------------------- kernels (launchers)
 // stencil / residual / Jacobian (k_stencil.cu)
 void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,

@@ -61,9 +61,9 @@ def test_eigenpairs(m, n):
 @pytest.mark.parametrize("vrange", [0.35, 2.0], ids=["series", "wide"])
 @pytest.mark.parametrize("m,n", SHAPES)
 def test_residual_and_jacobian_diagonal(m, n, vrange):
-    """|b dV| <= 1 uses the Taylor form of sinh, larger |b dV| the library function;
+    """|b dV| < 3/4 uses the economised polynomial for sinh, larger |b dV| the library function;
     both must give the residual to FP64 rounding.  D (cosh, the Jacobian diagonal) is
-    evaluated in FP32 for |b dV| <= 1: it only shapes the Newton matrix."""
+    evaluated in FP32: it only shapes the Newton matrix."""
     cb = mi.make_crossbar(m, n, 2, nvec=2)
     p = cb.params
     rng = np.random.default_rng(5)

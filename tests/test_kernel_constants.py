@@ -1,0 +1,79 @@
+"""Host-side checks of constants baked into the CUDA kernels (no GPU needed).
+
+The memristor current uses sinh(x) = x p(x^2) on |x| < 3/4 with a degree-6 polynomial p
+(k_stencil.cu).  Its coefficients are checked here against sinh itself in high precision,
+and against the generator script that derives them (Chebyshev economisation of the Taylor
+series), so that a mistyped digit or a wrong range cannot reach the residual unnoticed."""
+import re
+from fractions import Fraction
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+CSRC = ROOT / "paper_2109_07929_gb300" / "csrc"
+
+
+def _kernel_coefficients():
+    src = (CSRC / "k_stencil.cu").read_text()
+    body = src[src.index("device_current("):]
+    body = body[:body.index("cur_over_g = dv * ps;")]
+    vals = {}
+    for m in re.finditer(r"([0-9.]+e[-+][0-9]+|1\.0)\)?;\s*// t\^(\d)", body):
+        vals[int(m.group(2))] = float(m.group(1))
+    assert sorted(vals) == list(range(7)), vals
+    return [vals[k] for k in range(7)]
+
+
+def _range_limit():
+    src = (CSRC / "k_stencil.cu").read_text()
+    m = re.search(r"hi < 0x([0-9A-Fa-f]+)u\) \{\s*// \|x\| < ([0-9.]+)", src)
+    hi = int(m.group(1), 16)
+    return np.frombuffer(np.array([hi << 32], np.uint64).tobytes(), np.float64)[0], float(m.group(2))
+
+
+def test_range_test_matches_its_comment():
+    limit, stated = _range_limit()
+    assert limit == stated == 0.75
+
+
+def test_sinh_polynomial_accuracy_high_precision():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    c = [Fraction(v) for v in _kernel_coefficients()]
+    worst = 0.0
+    for x in np.linspace(0.0, 0.75, 2001)[1:]:
+        t = Fraction(float(x)) ** 2
+        p = sum(ck * t**k for k, ck in enumerate(c))            # exact in rationals
+        ref = mpmath.sinh(mpmath.mpf(float(x))) / mpmath.mpf(float(x))
+        err = abs((mpmath.mpf(p.numerator) / p.denominator - ref) / ref)
+        worst = max(worst, float(err))
+    # truncation < 2e-18 plus the rounding of the coefficients to FP64
+    assert worst < 3e-17, worst
+
+
+def test_sinh_polynomial_fp64_horner_within_two_ulp():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    c = _kernel_coefficients()
+    xs = np.concatenate([np.linspace(-0.7499, 0.7499, 3001), [1e-300, -1e-8, 0.5, 0.74999999]])
+    for x in xs:
+        t = x * x
+        ps = c[6]
+        for k in range(5, -1, -1):      # separate multiply and add: at least the rounding
+            ps = ps * t + c[k]            # of the kernel's FMAs
+        val = x * ps
+        ref = float(mpmath.sinh(mpmath.mpf(float(x))))
+        assert abs(val - ref) <= 2 * np.spacing(abs(ref)) + 1e-320, (x, val, ref)
+
+
+def test_generator_reproduces_kernel_coefficients():
+    pytest.importorskip("sympy")
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("gen_sinh_poly", CSRC / "gen_sinh_poly.py")
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    coef, bound = gen.coefficients()
+    assert bound < 2e-18
+    assert [float(v) for v in coef] == _kernel_coefficients()
