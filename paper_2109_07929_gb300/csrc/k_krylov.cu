@@ -177,12 +177,7 @@ k_update_norm(int phase, const double* w, size_t wstride, const double* __restri
   const double* Vb = V + (size_t)b * vstride;
   const size_t mn = n2 / 2;
   double acc[1] = {0.0};
-  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n2;
-       e += (size_t)nblk * kThreads) {
-    double x = wb[e];
-#pragma unroll
-    for (int j = 0; j < KP; ++j)
-      if (j < nk) x = fma(-hj[j], Vb[(size_t)j * n2 + e], x);
+  auto finish = [&](size_t e, double x) {
     ob[e] = x;
     if (xbf != nullptr) {
       const int l = (e >= mn) ? 1 : 0;
@@ -191,6 +186,30 @@ k_update_norm(int phase, const double* w, size_t wstride, const double* __restri
       xbf[(((size_t)b * 2 + l) * mp + i) * np + jj] = d2bf16_bits(x);
     }
     acc[0] = fma(x, x, acc[0]);
+  };
+  // four elements per trip with all their loads issued before the first store (out may
+  // alias w, so the compiler cannot move loads of the next trip above the stores)
+  const size_t st = (size_t)nblk * kThreads;
+  size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x;
+  for (; e + 3 * st < n2; e += 4 * st) {
+    double x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = wb[e + u * st];
+#pragma unroll
+    for (int j = 0; j < KP; ++j)
+      if (j < nk) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = fma(-hj[j], Vb[(size_t)j * n2 + e + u * st], x[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) finish(e + u * st, x[u]);
+  }
+  for (; e < n2; e += st) {
+    double x = wb[e];
+#pragma unroll
+    for (int j = 0; j < KP; ++j)
+      if (j < nk) x = fma(-hj[j], Vb[(size_t)j * n2 + e], x);
+    finish(e, x);
   }
   block_store_partials<1>(acc, 1, part, b, nblk);
   if (phase == UPD_PLAIN) return;
@@ -265,8 +284,20 @@ __global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z,
   __syncthreads();
   double* xb = x + (size_t)b * n2;
   const double* Zb = Z + (size_t)b * zstride;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n2;
-       e += (size_t)gridDim.x * blockDim.x) {
+  const size_t st = (size_t)gridDim.x * blockDim.x;
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + 3 * st < n2; e += 4 * st) {     // four independent elements per trip
+    double s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = xb[e + u * st];
+    for (int j = 0; j < kd; ++j) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] = fma(ys[j], Zb[(size_t)j * n2 + e + u * st], s[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xb[e + u * st] = s[u];
+  }
+  for (; e < n2; e += st) {
     double s = xb[e];
     for (int j = 0; j < kd; ++j) s = fma(ys[j], Zb[(size_t)j * n2 + e], s);
     xb[e] = s;
@@ -366,7 +397,7 @@ void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, Ve
                        int B, cudaStream_t s) {
   k_lsq<<<B, 32, 0, s>>>(ctl);
   int nb = (int)((n2 + kThreads - 1) / kThreads);
-  if (nb > 1216) nb = 1216;
+  if (nb > 608) nb = 608;
   k_update_x<<<dim3(nb, B), kThreads, 0, s>>>(x, Z, zstride, n2, ctl);
 }
 

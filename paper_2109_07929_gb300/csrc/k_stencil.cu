@@ -225,7 +225,7 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
     c.eta = eta;
     c.tol_abs = eta * fn;
     c.g[0] = fn;
-    c.s[0] = 1.0;
+    c.s[0] = -1.0 / fn;            // v_0 = -F / ||F|| from the stored residual
     c.orth = 0.0;
     c.reorth = 0;
     c.reorth_mask = 0u;
@@ -239,11 +239,15 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
 
 // Residual of the solver loop with the Newton control in the last block of each vector.
 // ZERO: the state is x = 0 (first Newton step from V = 0), where F = -Y and D = g.
+// F[b] is written at F + b*fstride: the solver points it at the first Krylov basis vector,
+// which GMRES keeps unnormalised (v_0 = -F / ||F||, the scale set by the Newton control),
+// and xbf (may be NULL) receives its BF16 copy for the tensor-core preconditioner.
 template <bool ZERO>
 __global__ void __launch_bounds__(kThreads)
 k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restrict__ map_of,
                   const double* __restrict__ vin,
-                  const double* __restrict__ x, double* __restrict__ F,
+                  const double* __restrict__ x, double* __restrict__ F, size_t fstride,
+                  __nv_bfloat16* __restrict__ xbf, int mp, int np,
                   double* __restrict__ D, double* __restrict__ part, int nblk, VecCtl* ctl,
                   SolverCfg cfg, unsigned int* cnt, int32_t* host_flags) {
   const int b = blockIdx.y;
@@ -254,8 +258,9 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   const double* gmap = gmaps + (map_of ? (size_t)map_of[b] * mn : (size_t)0);
   const double* Vt = x + (size_t)b * 2 * mn;
   const double* Vb = Vt + mn;
-  double* Ft = F + (size_t)b * 2 * mn;
+  double* Ft = F + (size_t)b * fstride;
   double* Fb = Ft + mn;
+  __nv_bfloat16* xt = xbf ? xbf + (size_t)b * 2 * mp * np : nullptr;
   double* Db = D + (size_t)b * mn;
   const double* vinb = vin + (size_t)b * m;
   // sum(D) stays in FP64: with uniform linear devices a = mean(D) must equal D to FP64
@@ -275,6 +280,10 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
+    if (xt != nullptr) {
+      xt[(size_t)i * np + j] = d2bf16_bits(ft);
+      xt[((size_t)mp + i) * np + j] = d2bf16_bits(fb);
+    }
     sf = fma(ft, ft, sf);
     sf = fma(fb, fb, sf);
     sd += dg;
@@ -469,16 +478,18 @@ void launch_residual(const Grid& gr, const double* gmap, const double* vin, cons
 
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
                             const double* vin, const double* x, bool zero_state, double* F,
-                            double* D, double* part, int nblk, int B, VecCtl* ctl,
-                            SolverCfg cfg, unsigned int* cnt, int32_t* host_flags,
-                            cudaStream_t s) {
+                            size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
+                            double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
+                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s) {
   dim3 grid(nblk, B);
   if (zero_state)
-    k_residual_newton<true><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, D, part,
-                                                      nblk, ctl, cfg, cnt, host_flags);
+    k_residual_newton<true><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, fstride,
+                                                      xbf, mp, np, D, part, nblk, ctl, cfg,
+                                                      cnt, host_flags);
   else
-    k_residual_newton<false><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, D, part,
-                                                       nblk, ctl, cfg, cnt, host_flags);
+    k_residual_newton<false><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, fstride,
+                                                       xbf, mp, np, D, part, nblk, ctl, cfg,
+                                                       cnt, host_flags);
 }
 
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,

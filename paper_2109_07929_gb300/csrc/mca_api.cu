@@ -647,13 +647,16 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
   for (int it = 0; it <= h->p.max_newton; ++it) {
     cudaEvent_t t0 = prof_begin(h, s);
     const bool zero_state = (it == 0) && !from_guess;
+    // F goes straight into the first Krylov basis vector (kept unnormalised) and its BF16
+    // copy, so no separate pass builds v_0
     launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
-                           zero_state, h->F, h->D, h->part, nbR, B, h->ctl, cfg, h->cnt,
-                           h->hflags_dev, s);
+                           zero_state, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np,
+                           h->D, h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s);
     count_launches(1);
     // FP64 flops per cell: stencils 8, sinh polynomial 16, current 4, norms 5 (the
     // conductance cosh is FP32; the zero state only the norms)
-    prof_end(h, t0, MCA_FAM_RESIDUAL, -1, cells * (zero_state ? 32.0 : 48.0),
+    prof_end(h, t0, MCA_FAM_RESIDUAL, -1,
+             cells * ((zero_state ? 32.0 : 48.0) + (tc ? 4.0 : 0.0)),
              cells * (zero_state ? 5.0 : 33.0), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -662,11 +665,6 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     for (int b = 0; b < B; ++b) n_active += reinterpret_cast<volatile int32_t*>(h->hflags)[b] ? 1 : 0;
     prof_flush(h, [&](int, bool) { return entering; });
     if (n_active == 0) break;
-    t0 = prof_begin(h, s);
-    launch_init_basis(h->F, -1.0, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->m,
-                      h->n, h->ctl, B, s);
-    count_launches(1);
-    prof_end(h, t0, MCA_FAM_SMALL, -1, 0.0, 0.0, s);
     MCA_TRY(gmres_cycle(h, h->D, B, s));
     t0 = prof_begin(h, s);
     launch_lsq_update(h->x, h->Z, zstride, h->n2, h->ctl, B, s);
@@ -952,8 +950,8 @@ static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
       probe.max_newton = 0;
       probe.newton_rtol = 0.0;
       launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
-                             false, h->F, h->D, h->part, nb, B, h->ctl, probe, h->cnt,
-                             nullptr, s);
+                             false, h->F, h->n2, nullptr, 0, 0, h->D, h->part, nb, B, h->ctl,
+                             probe, h->cnt, nullptr, s);
       count_launches(1);
       MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
                                    cudaMemcpyDeviceToHost, s));

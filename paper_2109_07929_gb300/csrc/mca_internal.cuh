@@ -140,11 +140,13 @@ void launch_residual(const Grid& gr, const double* gmap, const double* vin, cons
 // forcing term, start of the GMRES cycle).
 // gmaps: conductance maps of the crossbars sharing this shape (m*n each); map_of[b] picks
 // vector b's map (NULL: map 0 for all).
+// F[b] at F + b*fstride, with its BF16 copy in xbf (may be NULL); the Newton control
+// sets the scale -1/||F|| that turns the stored F into the first GMRES basis vector.
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
                             const double* vin, const double* x, bool zero_state, double* F,
-                            double* D, double* part, int nblk, int B, VecCtl* ctl,
-                            SolverCfg cfg, unsigned int* cnt, int32_t* host_flags,
-                            cudaStream_t s);
+                            size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
+                            double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
+                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s);
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
                        __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
                        int B, cudaStream_t s);
