@@ -323,6 +323,7 @@ def run_ours(args):
         "data": "synthetic", "config": workload_config(args, B),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
         "precond_tflops": precond_tflops, "kernel_breakdown": breakdown,
+        "gemm_tiles": gemm_tiles(solver),
         "newton_iters_per_solve": float(iters[:, 0].mean()),
         "gmres_iters_per_solve": float(iters[:, 1].mean()),
         "max_rel_residual": float(max(r for _, _, r in timed)),
@@ -442,6 +443,18 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
                         "log-uniform g x lognormal(0.1), BF16-split preconditioner, "
                         "CUDA graphs, autotuned tiles, device-resident inputs and outputs, "
                         "wall clock of the solves"}
+
+
+def gemm_tiles(solver):
+    """Tile configuration the autotuner picked for the four tensor-core transforms."""
+    names = ("X Q_r", "Q_c^T T1 + modes", "Y Q_r^T", "Q_c E")
+    out = {}
+    for name, (ws, bn, lp) in zip(names, solver.tile_config()):
+        if ws < 0:
+            return None
+        out[name] = {"kernel": "persistent" if ws else "tile-per-cta", "tile": f"128x{bn}",
+                     "layers_per_tile": lp}
+    return out
 
 
 # FP64 CUDA-core peak used for the FP64 form: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.

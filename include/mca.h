@@ -290,6 +290,12 @@ int mca_profile(mca_handle* h, int32_t enable);
 int mca_profile_read(mca_handle* h, int32_t family, int64_t* launches, double* ms,
                      double* bytes, double* flops);
 
+/* GEMM configuration of the four tensor-core transforms (after autotuning, if enabled):
+ * cfg[3 s + 0] = 1 persistent warp-specialised kernel, 0 one CTA per tile, -1 no
+ * tensor-core form; cfg[3 s + 1] = tile columns; cfg[3 s + 2] = layers per tile, for
+ * transform s = 0..3.  cfg: host, 12 int32.  Diagnostic only. */
+int mca_tile_config(const mca_handle* h, int32_t* cfg);
+
 /* ---- residual without device allocation ------------------------------------------- */
 
 /* Residual, Jacobian diagonal and their norms for callers that cannot allocate device

@@ -40,7 +40,7 @@ EXPORTED = (
     "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
     "mca_solve_many", "mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
     "mca_cnn_mse", "mca_cnn_adam", "mca_cnn_features", "mca_cnn_state", "mca_set_conductances",
-    "mca_wait_selftest",
+    "mca_wait_selftest", "mca_tile_config",
 )
 
 FAMILIES = ("residual", "spmv_dots", "reorth", "update_norm", "normalize", "small",
@@ -122,6 +122,8 @@ def load(build_if_missing=True):
     lib.mca_residual_noalloc.restype = ctypes.c_int
     lib.mca_solve_from.argtypes = [P, P, P, P, ctypes.c_int32, P, P, P, P, P]
     lib.mca_set_conductances.argtypes = [P, P]
+    lib.mca_tile_config.argtypes = [P, P]
+    lib.mca_tile_config.restype = ctypes.c_int
     lib.mca_wait_selftest.argtypes = [P, ctypes.c_int64]
     lib.mca_wait_selftest.restype = ctypes.c_int
     lib.mca_set_conductances.restype = ctypes.c_int
@@ -329,6 +331,12 @@ class Solver:
         """Pointer-level call of mca_solve (no allocation, no checks); returns the status."""
         return self.lib.mca_solve(self.h, vin_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr,
                                   _stream_ptr(stream))
+
+    def tile_config(self):
+        """[(persistent, tile columns, layers per tile)] of the four tensor-core transforms."""
+        cfg = (ctypes.c_int32 * 12)()
+        _check(self.lib.mca_tile_config(self.h, ctypes.addressof(cfg)))
+        return [tuple(cfg[3 * s:3 * s + 3]) for s in range(4)]
 
     def profile(self, enable=True):
         _check(self.lib.mca_profile(self.h, 1 if enable else 0))

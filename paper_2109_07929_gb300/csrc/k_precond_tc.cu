@@ -197,6 +197,21 @@ struct Layout {
   static constexpr int TMEM_COLS = (2 * BN < 32) ? 32 : 2 * BN;
 };
 
+// Instantiations of the persistent kernel (BN, SPLIT, EPI, LP).
+#define MCA_WS_LIST(X)                 \
+  X(128, false, EPI_BF16, 1)           \
+  X(256, false, EPI_BF16, 1)           \
+  X(64, false, EPI_MODES, 2)           \
+  X(128, false, EPI_MODES, 2)          \
+  X(64, false, EPI_MODES_SPLIT, 2)     \
+  X(128, false, EPI_MODES_SPLIT, 2)    \
+  X(128, true, EPI_SPLIT, 1)           \
+  X(256, true, EPI_SPLIT, 1)           \
+  X(128, false, EPI_F64, 1)            \
+  X(256, false, EPI_F64, 1)            \
+  X(128, true, EPI_F64, 1)             \
+  X(256, true, EPI_F64, 1)
+
 template <int BN, bool SPLIT, int EPI>
 __global__ void __launch_bounds__(kThreads, Layout<BN, SPLIT, EPI>::CTAS)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
@@ -397,6 +412,311 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Persistent, warp-specialised form of the same GEMMs.  One CTA per SM walks a static
+// round-robin list of output tiles; warp 0 streams A/B stages with TMA, warp 1 issues the
+// MMAs into one of two TMEM accumulators, and warps 2..9 drain the other accumulator (the
+// epilogue of tile i overlaps the main loop of tile i + 1; two warps per TMEM lane
+// quarter, each taking every other 32-column chunk).  A tile is 128 rows x BN
+// columns of LP layers: LP = 2 keeps both layers of a mode in one CTA (required by the
+// per-mode 2x2 epilogue), LP = 1 makes twice as many single-layer tiles (better balance
+// of the tiles over the SMs).  BF16 outputs are transposed through a 32 x 32 staging tile
+// per epilogue warp and leave in 16-byte chunks.
+constexpr int kWsThreads = 320;                 // 10 warps
+constexpr int kWsEpiWarps = 8;
+constexpr int kWsSmemMax = 227 * 1024;
+
+template <int BN, bool SPLIT, int EPI, int LP>
+struct WsLayout {
+  static constexpr int BKT = SPLIT ? BK_SPLIT : BK;
+  static constexpr int A_BYTES = BM * BKT * 2;
+  static constexpr int B_BYTES = BN * BKT * 2;
+  static constexpr int HALF = LP * A_BYTES + B_BYTES;
+  static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
+  static constexpr bool LO = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
+  static constexpr int NOUT = (EPI == EPI_F64) ? 0 : (LO ? 2 : 1) * LP;   // staged outputs
+  static constexpr int STG_WARP = NOUT * 32 * 32 * 2;                     // bytes per warp
+  static constexpr int STG_OFF_RAW = 0;
+  static constexpr int FIXED = kWsEpiWarps * STG_WARP + 512 + 1024;      // + barriers, align
+  static constexpr int STAGES_FIT = (kWsSmemMax - FIXED) / STAGE;
+  static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
+  static constexpr int STG_OFF = STAGES * STAGE;
+  static constexpr int BAR_OFF = STG_OFF + kWsEpiWarps * STG_WARP;
+  static constexpr int SMEM = BAR_OFF + 512 + 1024;
+  static constexpr int ACC_COLS = LP * BN;                                // one accumulator
+  static constexpr int TMEM_COLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
+  static_assert(STAGES >= 2, "not enough shared memory for two stages");
+  static_assert(2 * ACC_COLS <= 512, "two accumulators must fit in TMEM");
+  static_assert(SMEM <= kWsSmemMax, "shared memory plan too large");
+};
+
+template <int BN, bool SPLIT, int EPI, int LP>
+__global__ void __launch_bounds__(kWsThreads, 1)
+k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
+          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
+          GemmEpi ep, int B) {
+  using L = WsLayout<BN, SPLIT, EPI, LP>;
+  static_assert(LP == 2 || (EPI != EPI_MODES && EPI != EPI_MODES_SPLIT),
+                "the modes epilogue needs both layers in one tile");
+  constexpr int BKT = L::BKT;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + L::STAGES;
+  uint64_t* tfull = empty + L::STAGES;           // [2] accumulator ready
+  uint64_t* tempty = tfull + 2;                  // [2] accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // tiles: column tile fastest (neighbouring CTAs share their A rows in L2), then row
+  // tile, then layer (LP = 1), then vector
+  const int tr = ep.R / BM, tc = ep.C / BN;
+  const int per_vec = tr * tc * (LP == 1 ? 2 : 1);
+  const int ntiles = per_vec * B;
+  const int nkb = ep.K / BKT;
+  auto decode = [&](int t, int& b, int& layer, int& r0, int& c0) {
+    b = t / per_vec;
+    int u = t - b * per_vec;
+    layer = 0;
+    if (LP == 1) {
+      layer = u / (tr * tc);
+      u -= layer * tr * tc;
+    }
+    r0 = (u / tc) * BM;
+    c0 = (u % tc) * BN;
+  };
+  auto active = [&](int b) { return ep.ctl == nullptr || ep.ctl[b].gm_active; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < L::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kWsEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)L::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (one thread)
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int b, layer, r0, c0;
+        decode(t, b, layer, r0, c0);
+        if (!active(b)) continue;
+        const int row0 = (2 * b + layer) * ep.R + r0;     // first A row (layer 0 of LP = 2)
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % L::STAGES;
+          const uint32_t ph = (uint32_t)(it / L::STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u)) {
+            record_error(ep.err, MCA_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + s * L::STAGE;
+          mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
+          const int k0 = kb * BKT;
+#pragma unroll
+          for (int l = 0; l < LP; ++l)
+            tma_load_2d(st + l * L::A_BYTES, &tmA, k0, row0 + l * ep.R, &full[s]);
+          tma_load_2d(st + LP * L::A_BYTES, &tmB, k0, c0, &full[s]);
+          if (SPLIT) {
+            uint8_t* sl = st + L::HALF;
+#pragma unroll
+            for (int l = 0; l < LP; ++l)
+              tma_load_2d(sl + l * L::A_BYTES, &tmAl, k0, row0 + l * ep.R, &full[s]);
+            tma_load_2d(sl + LP * L::A_BYTES, &tmBl, k0, c0, &full[s]);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one thread)
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int it = 0, tl = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int b, layer, r0, c0;
+        decode(t, b, layer, r0, c0);
+        if (!active(b)) continue;
+        const int acc = tl & 1;
+        const uint32_t aph = (uint32_t)(tl >> 1) & 1u;
+        if (!mbar_wait(&tempty[acc], aph ^ 1u)) {
+          record_error(ep.err, MCA_ERR_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(acc * L::ACC_COLS);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % L::STAGES;
+          const uint32_t ph = (uint32_t)(it / L::STAGES) & 1u;
+          if (!mbar_wait(&full[s], ph)) {
+            record_error(ep.err, MCA_ERR_TIMEOUT);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint8_t* st = smem + s * L::STAGE;
+#pragma unroll
+          for (int kk = 0; kk < BKT / 16; ++kk) {
+            const int off = kk * 32;
+            const uint64_t bd = tile_desc<BKT>(st + LP * L::A_BYTES + off);
+            const uint32_t accf = (kb > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+            for (int l = 0; l < LP; ++l) {
+              const uint64_t ad = tile_desc<BKT>(st + l * L::A_BYTES + off);
+              umma(dacc + l * BN, ad, bd, idesc, accf);
+              if (SPLIT) {
+                const uint8_t* sl = st + L::HALF;
+                const uint64_t adl = tile_desc<BKT>(sl + l * L::A_BYTES + off);
+                const uint64_t bdl = tile_desc<BKT>(sl + LP * L::A_BYTES + off);
+                umma(dacc + l * BN, adl, bd, idesc, 1u);
+                umma(dacc + l * BN, ad, bdl, idesc, 1u);
+              }
+            }
+          }
+          umma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&tfull[acc]);
+        ++tl;
+      }
+    }
+  } else {
+    // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+    // the 32-column chunks cc with cc % 2 == (w - 2) / 4
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int rl = q * 32 + lane;                    // row inside the tile
+    __nv_bfloat16* stg =
+        reinterpret_cast<__nv_bfloat16*>(smem + L::STG_OFF + (warp - 2) * L::STG_WARP);
+    int tl = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int b, layer, r0, c0;
+      decode(t, b, layer, r0, c0);
+      if (!active(b)) continue;
+      const int acc = tl & 1;
+      const uint32_t aph = (uint32_t)(tl >> 1) & 1u;
+      const bool have = __all_sync(0xffffffffu, mbar_wait(&tfull[acc], aph) ? 1 : 0) != 0;
+      if (!have) {
+        if (lane == 0) record_error(ep.err, MCA_ERR_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      const int r = r0 + rl;
+      const bool r_ok = r < ep.R_valid;
+      const uint32_t lane_base =
+          tmem + (uint32_t)(acc * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
+      float a_mode = 0.f, mu_r = 0.f, sc = 1.f;
+      if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+        a_mode = (float)ep.ctl[b].a;
+        mu_r = r_ok ? ep.mu_f[r] : 0.f;
+        if (ep.kidx >= 0) sc = (float)ep.ctl[b].s[ep.kidx];
+      }
+#pragma unroll 1
+      for (int cc = half; cc < BN / 32; cc += 2) {
+        uint32_t v0[32], v1[32];
+        tmem_ld32(lane_base + cc * 32, v0);
+        if (LP == 2) tmem_ld32(lane_base + BN + cc * 32, v1);
+        if (EPI == EPI_F64) {
+          double* out = static_cast<double*>(ep.out);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = c0 + cc * 32 + j;
+            if (r_ok && c < ep.C_valid) {
+#pragma unroll
+              for (int l = 0; l < LP; ++l) {
+                const size_t o = (size_t)b * ep.o_bs + (size_t)(layer + l) * ep.o_ls +
+                                 (size_t)c * ep.o_ld + r;
+                out[o] = f2d_bits(__uint_as_float(l == 0 ? v0[j] : v1[j]));
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = c0 + cc * 32 + j;
+            float x0 = __uint_as_float(v0[j]);
+            float x1 = (LP == 2) ? __uint_as_float(v1[j]) : 0.f;
+            if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+              // [y_t; y_b] = (sc / det) [[nu + a, a], [a, mu + a]] [x_t; x_b]
+              float y0 = 0.f, y1 = 0.f;
+              if (r_ok && c < ep.C_valid) {
+                const float nu_c = ep.nu_f[c];
+                const float det = mu_r * nu_c + mu_r * a_mode + nu_c * a_mode;
+                // (approximate reciprocal: a few FP32 ulps, far below the BF16 outputs)
+                const float inv = __fdividef(sc, det);
+                y0 = ((nu_c + a_mode) * x0 + a_mode * x1) * inv;
+                y1 = (a_mode * x0 + (mu_r + a_mode) * x1) * inv;
+              }
+              x0 = y0;
+              x1 = y1;
+            }
+            // staging tile o: [32 columns][32 rows] of this warp
+#pragma unroll
+            for (int l = 0; l < LP; ++l) {
+              const float x = (l == 0) ? x0 : x1;
+              const __nv_bfloat16 hi = __float2bfloat16(x);
+              stg[(l * 32 + j) * 32 + lane] = hi;
+              if (L::LO)
+                stg[((LP + l) * 32 + j) * 32 + lane] = __float2bfloat16(x - __bfloat162float(hi));
+            }
+          }
+          __syncwarp();
+          // out: 32 columns x 64 bytes per staged output; 4 chunks of 16 bytes per column
+#pragma unroll
+          for (int o = 0; o < L::NOUT; ++o) {
+            const int l = o % LP;
+            __nv_bfloat16* out = static_cast<__nv_bfloat16*>((o < LP) ? ep.out : ep.out_lo);
+            const size_t base = (size_t)b * ep.o_bs + (size_t)(layer + l) * ep.o_ls + r0 + q * 32;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int id = lane + 32 * i;
+              const int col = id >> 2, part = id & 3;
+              const uint4 v = *reinterpret_cast<const uint4*>(&stg[(o * 32 + col) * 32 + part * 8]);
+              *reinterpret_cast<uint4*>(
+                  &out[base + (size_t)(c0 + cc * 32 + col) * ep.o_ld + part * 8]) = v;
+            }
+          }
+          __syncwarp();
+        }
+      }
+      // accumulator drained: the MMA warp may reuse it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                                      smem_u32(&tempty[acc]))
+                                  : "memory");
+      ++tl;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)L::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at,
 // with a limit of limit_ns, and records MCA_ERR_TIMEOUT when the wait gives up.
 __global__ void k_wait_selftest(unsigned long long limit_ns, int* err) {
@@ -444,6 +764,25 @@ cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtens
   }
   dim3 grid(ep.R / BM, ep.C / BN, B);
   kern<<<grid, kThreads, L::SMEM, s>>>(a, al, bm, bml, ep);
+  return cudaGetLastError();
+}
+
+int g_num_sms = 0;
+
+template <int BN, bool SPLIT, int EPI, int LP>
+cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
+                      const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
+  using L = WsLayout<BN, SPLIT, EPI, LP>;
+  if (ep.R % BM != 0 || ep.C % BN != 0 || ep.K % L::BKT != 0) return cudaErrorInvalidValue;
+  if (g_num_sms <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorInvalidValue;
+  }
+  const int ntiles = (ep.R / BM) * (ep.C / BN) * (LP == 1 ? 2 : 1) * B;
+  const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  k_gemm_ws<BN, SPLIT, EPI, LP><<<grid, kWsThreads, L::SMEM, s>>>(a, al, bm, bml, ep, B);
   return cudaGetLastError();
 }
 
@@ -503,6 +842,17 @@ cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtens
   return cudaErrorInvalidValue;
 }
 
+cudaError_t gemm_ws(int bn, int lp, bool split, int epi, const CUtensorMap& a,
+                    const CUtensorMap& al, const CUtensorMap& bm, const CUtensorMap& bml,
+                    const GemmEpi& ep, int B, cudaStream_t s) {
+#define MCA_WS_CASE(BN_, SPLIT_, EPI_, LP_)                                  \
+  if (bn == BN_ && split == SPLIT_ && epi == EPI_ && lp == LP_)              \
+    return launch_ws<BN_, SPLIT_, EPI_, LP_>(a, al, bm, bml, ep, B, s);
+  MCA_WS_LIST(MCA_WS_CASE)
+#undef MCA_WS_CASE
+  return cudaErrorInvalidValue;
+}
+
 // Set the dynamic shared-memory limit of every GEMM instantiation up front, so no
 // attribute call happens later inside a stream capture.
 cudaError_t configure_all() {
@@ -528,6 +878,15 @@ cudaError_t configure_all() {
   MCA_TC_CFG(128, true, EPI_F64)
   MCA_TC_CFG(64, true, EPI_F64)
 #undef MCA_TC_CFG
+#define MCA_WS_CFG(BN_, SPLIT_, EPI_, LP_)                                              \
+  {                                                                                     \
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN_, SPLIT_, EPI_, LP_>,             \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         WsLayout<BN_, SPLIT_, EPI_, LP_>::SMEM);       \
+    if (e != cudaSuccess) return e;                                                     \
+  }
+  MCA_WS_LIST(MCA_WS_CFG)
+#undef MCA_WS_CFG
   return cudaSuccess;
 }
 

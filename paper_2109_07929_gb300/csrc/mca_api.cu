@@ -95,8 +95,13 @@ struct mca_handle {
                 *El = nullptr;
   bool tc_ok = false;
   CUtensorMap mA1, mA2, mA3h, mA3l, mA4h, mA4l;           // A operands
-  CUtensorMap mB1[2], mB2[2], mB3h[2], mB3l[2], mB4h[2], mB4l[2];  // B operands, BN 128/64
+  // B operands for 128-, 64- and 256-column tiles
+  CUtensorMap mB1[3], mB2[3], mB3h[3], mB3l[3], mB4h[3], mB4l[3];
+  // GEMM form of each transform: ws = 1 persistent warp-specialised kernel (tiles of
+  // 128 x bn with lp layers), ws = 0 one CTA per 128 x bn two-layer tile
   int bn[4] = {128, 128, 128, 128};
+  int ws[4] = {0, 0, 0, 0};
+  int lp[4] = {2, 2, 2, 2};
   std::vector<void*> allocs;
   cudaEvent_t ev[MCA_KMAX + 1];
   bool ev_ok = false;
@@ -210,8 +215,8 @@ int setup_tc(mca_handle* h) {
   ok &= tc::make_map(&h->mA3l, h->Yl, B * 2 * mp, np, 128, kb);
   ok &= tc::make_map(&h->mA4h, h->Eh, B * 2 * np, mp, 128, kb);
   ok &= tc::make_map(&h->mA4l, h->El, B * 2 * np, mp, 128, kb);
-  const uint32_t bns[2] = {128, 64};
-  for (int q = 0; q < 2; ++q) {
+  const uint32_t bns[3] = {128, 64, 256};
+  for (int q = 0; q < 3; ++q) {
     ok &= tc::make_map(&h->mB1[q], h->QrT_bf, np, np, bns[q], 64);
     ok &= tc::make_map(&h->mB2[q], h->QcT_bf, mp, mp, bns[q], 64);
     ok &= tc::make_map(&h->mB3h[q], h->Qr_hi, np, np, bns[q], kb);
@@ -231,6 +236,11 @@ int setup_tc(mca_handle* h) {
   for (int s = 0; s < 4; ++s) {
     const long ctas128 = (long)(R[s] / 128) * (C[s] / 128) * h->Bmax;
     h->bn[s] = (ctas128 < sms) ? 64 : 128;
+    // persistent form by default: two-layer tiles for the modes transform, single-layer
+    // 128-column tiles for the others
+    h->ws[s] = 1;
+    h->lp[s] = (s == 1) ? 2 : 1;
+    if (s != 1) h->bn[s] = 128;
   }
   h->tc_ok = true;
   return MCA_OK;
@@ -342,8 +352,13 @@ int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, i
             const VecCtl* ctl, cudaStream_t s, int prof_k, int kidx = -1) {
   const int m = h->m, n = h->n;
   const size_t mn = h->mn, mp = h->mp, np = h->np;
-  auto q = [](int bn) { return bn == 128 ? 0 : 1; };
+  auto q = [](int bn) { return bn == 128 ? 0 : (bn == 64 ? 1 : 2); };
   const int bn = h->bn[step];
+  auto run = [&](bool sp_, int epi, const CUtensorMap& a, const CUtensorMap& al,
+                 const CUtensorMap& bm, const CUtensorMap& bml, const tc::GemmEpi& ep) {
+    return h->ws[step] ? tc::gemm_ws(bn, h->lp[step], sp_, epi, a, al, bm, bml, ep, B, s)
+                       : tc::gemm(bn, sp_, epi, a, al, bm, bml, ep, B, s);
+  };
   // executed MMA FLOPs per vector: 2 layers x 2 M N K, three products when split
   const double f_r = 4.0 * m * (double)n * n, f_c = 4.0 * n * (double)m * m;
   const double sp = split ? 3.0 : 1.0;
@@ -360,29 +375,28 @@ int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, i
     case 0:  // T1^T = (X Q_r)^T
       e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
       e.out = h->T1bf; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
-      MCA_CUDA_TRY(tc::gemm(bn, false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(bn)],
-                            h->mB1[q(bn)], e, B, s));
+      MCA_CUDA_TRY(run(false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(bn)], h->mB1[q(bn)], e));
       prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 8.0 * mn, f_r, s);
       break;
     case 1:  // Y_hat = modes^-1 (Q_c^T T1), stored [i'][k']
       e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
       e.out = h->Yh; e.out_lo = h->Yl; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
-      MCA_CUDA_TRY(tc::gemm(bn, false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2,
-                            h->mA2, h->mB2[q(bn)], h->mB2[q(bn)], e, B, s));
+      MCA_CUDA_TRY(run(false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2, h->mA2,
+                       h->mB2[q(bn)], h->mB2[q(bn)], e));
       prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, (split ? 12.0 : 8.0) * mn, f_c, s);
       break;
     case 2:  // E^T = (Y_hat Q_r^T)^T
       e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
       e.out = h->Eh; e.out_lo = h->El; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
-      MCA_CUDA_TRY(tc::gemm(bn, split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h, h->mA3l,
-                            h->mB3h[q(bn)], h->mB3l[q(bn)], e, B, s));
+      MCA_CUDA_TRY(run(split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h, h->mA3l,
+                       h->mB3h[q(bn)], h->mB3l[q(bn)], e));
       prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, (split ? 16.0 : 8.0) * mn, sp * f_r, s);
       break;
     default:  // Z = (E^T Q_c^T)^T, FP64 unpadded
       e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
       e.out = zout; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
-      MCA_CUDA_TRY(tc::gemm(bn, split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)],
-                            h->mB4l[q(bn)], e, B, s));
+      MCA_CUDA_TRY(run(split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)], h->mB4l[q(bn)],
+                       e));
       prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k, (split ? 8.0 : 4.0) * mn + 16.0 * mn,
                sp * f_c, s);
       break;
@@ -413,9 +427,19 @@ int autotune_tiles(mca_handle* h) {
   int rc = MCA_OK;
   for (int step = 0; step < 4 && rc == MCA_OK; ++step) {
     float best = 1e30f;
-    int best_bn = h->bn[step];
-    for (int bn : {128, 64}) {
+    int best_bn = h->bn[step], best_ws = h->ws[step], best_lp = h->lp[step];
+    const int Cs = (step == 0 || step == 2) ? h->np : h->mp;
+    // candidates (ws, bn, lp): the one-CTA-per-tile kernel with 128 / 64 columns, the
+    // persistent kernel with its instantiated tile shapes
+    const int cands[][3] = {{0, 128, 2}, {0, 64, 2}, {1, 128, 1}, {1, 256, 1},
+                            {1, 64, 2}, {1, 128, 2}};
+    for (const auto& cd : cands) {
+      const int ws = cd[0], bn = cd[1], lp = cd[2];
+      if (Cs % bn != 0) continue;
+      if (ws == 1 && ((step == 1) != (lp == 2))) continue;   // modes: 2 layers; others: 1
+      h->ws[step] = ws;
       h->bn[step] = bn;
+      h->lp[step] = lp;
       rc = tc_step(h, step, split, h->Z, zstride, B, h->ctl, 0, -1);
       if (rc != MCA_OK) break;
       cudaEventRecord(e0, 0);
@@ -431,9 +455,13 @@ int autotune_tiles(mca_handle* h) {
       if (ms < best) {
         best = ms;
         best_bn = bn;
+        best_ws = ws;
+        best_lp = lp;
       }
     }
     h->bn[step] = best_bn;
+    h->ws[step] = best_ws;
+    h->lp[step] = best_lp;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1197,6 +1225,16 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
 }
 
 int64_t mca_kernel_launches(void) { return g_launches.load(); }
+
+int mca_tile_config(const mca_handle* h, int32_t* cfg) {
+  if (!h || !cfg) return MCA_ERR_INVALID_ARG;
+  for (int s = 0; s < 4; ++s) {
+    cfg[3 * s + 0] = h->tc_ok ? h->ws[s] : -1;
+    cfg[3 * s + 1] = h->tc_ok ? h->bn[s] : 0;
+    cfg[3 * s + 2] = h->tc_ok ? (h->ws[s] ? h->lp[s] : 2) : 0;
+  }
+  return MCA_OK;
+}
 
 int mca_wait_selftest(mca_handle* h, int64_t limit_ns) {
   g_last_error.clear();

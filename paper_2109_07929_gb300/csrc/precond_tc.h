@@ -41,6 +41,11 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
 cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
+// Persistent warp-specialised form: one CTA per SM over tiles of 128 x bn with lp layers
+// (lp = 2 for the modes epilogues, which need both layers of a mode in one CTA).
+cudaError_t gemm_ws(int bn, int lp, bool split, int epi, const CUtensorMap& a,
+                    const CUtensorMap& al, const CUtensorMap& bm, const CUtensorMap& bml,
+                    const GemmEpi& ep, int B, cudaStream_t s);
 cudaError_t configure_all();
 cudaError_t wait_selftest(unsigned long long limit_ns, int* err, cudaStream_t s);
 void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
