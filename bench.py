@@ -45,7 +45,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=1024)
-    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--precision", default="bf16split", choices=["bf16split", "bf16", "fp64"])
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
