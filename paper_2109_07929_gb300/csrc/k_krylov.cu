@@ -355,8 +355,11 @@ void launch_sub(const double* a, const double* b, double* out, size_t n2, int B,
   k_sub<<<dim3(nb, B), kThreads, 0, s>>>(a, b, out, n2);
 }
 
-int vec_nblk(size_t n2) {
+int vec_nblk(size_t n2, int B) {
+  constexpr size_t kGridBlocks = 152 * 32;
   size_t nb = (n2 + kThreads - 1) / kThreads;
+  const size_t want = (kGridBlocks + B - 1) / (size_t)(B < 1 ? 1 : B);
+  if (nb > want) nb = want;
   if (nb > 608) nb = 608;
   return nb < 1 ? 1 : (int)nb;
 }

@@ -12,10 +12,30 @@
 // kernels keep FP64 instructions per cell low: diagonals are precomputed per position
 // class, and the device model uses a short economised polynomial for sinh and FP32 cosh
 // instead of the FP64 library functions.
+#include <cstring>
+
 #include "bits.cuh"
 #include "mca_internal.cuh"
 
 namespace mca {
+
+namespace {
+
+// sinh(x) / x ~ sum_k kSinhPoly[k] t^k, t = x^2, on |x| <= kSinhPolyX: the degree-6
+// Chebyshev-economised Taylor polynomial (coefficients from gen_sinh_poly.py; truncation
+// error below 2e-18 relative).
+constexpr double kSinhPolyX = 0.75;
+constexpr double kSinhPoly[7] = {
+  1.0,                          // t^0
+  1.66666666666666380e-01,      // t^1
+  8.33333333334163734e-03,      // t^2
+  1.98412698324150781e-04,      // t^3
+  2.75573237196537609e-06,      // t^4
+  2.50509370460377762e-08,      // t^5
+  1.62102664139390868e-10,      // t^6
+};
+
+}  // namespace
 
 Grid make_grid(const mca_params& p) {
   Grid g;
@@ -35,6 +55,17 @@ Grid make_grid(const mca_params& p) {
   g.db0 = (g.m == 1) ? g.g_bt + g.g_sense : g.g_bt + g.gb;
   g.dbm = 2.0 * g.gb;
   g.dbl = g.gb + g.g_sense;
+  // fold b into the polynomial: x = b dV, t = x^2 = b^2 dV^2
+  double b2k = 1.0;
+  for (int k = 0; k < 7; ++k) {
+    g.pc[k] = kSinhPoly[k] * b2k;
+    b2k *= p.b * p.b;
+  }
+  const double lim = (p.b != 0.0) ? kSinhPolyX / fabs(p.b) : 0.0;
+  unsigned long long bits;
+  memcpy(&bits, &lim, sizeof(bits));
+  g.dv_lim_bits = bits;
+  g.bf = (float)p.b;
   return g;
 }
 
@@ -58,33 +89,34 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
-// Memristor current and conductance.  The current (g / b) sinh(b dV) = g dV p(x^2),
-// x = b dV, enters the KCL residual and is kept in FP64: for |x| < 3/4, p is the degree-6
-// Chebyshev-economised Taylor polynomial of sinh(x) / x (coefficients from
-// gen_sinh_poly.py; truncation error below 2e-18 relative), Horner in t = x^2 (6 FMAs);
-// outside that range the CUDA math library.  The range test reads the exponent bits (on
-// the integer pipe).  The conductance g cosh(x) only shapes the Newton matrix (the
-// Jacobian diagonal and a = mean(D)), so it is evaluated in FP32 (relative error below
-// 3e-7, which changes the inexact Newton steps but not the solution the FP64 residual
-// drives them to).
+// Memristor current and conductance.  The current (g / b) sinh(b dV) = g dV P(dV^2) with
+// P(dV^2) = sinh(x) / x, x = b dV, enters the KCL residual and is kept in FP64: for
+// |x| < 3/4, P is the degree-6 economised polynomial above with b folded into its
+// coefficients (Horner, 6 FMAs); outside that range the CUDA math library.  The range
+// test compares bit patterns (on the integer pipe).  The conductance g cosh(x) only
+// shapes the Newton matrix (the Jacobian diagonal and a = mean(D)), so it is evaluated in
+// FP32 (relative error below 3e-7, which changes the inexact Newton steps but not the
+// solution the FP64 residual drives them to) and returned both as float and widened.
 __device__ __forceinline__ void device_current(const Grid& gr, double g, double dv,
-                                               double& cur_over_g, double& dg) {
-  const double x = gr.b * dv;
-  const uint32_t hi = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu;
-  if (hi < 0x3FE80000u) {                        // |x| < 0.75
-    const double t = x * x;
-    double ps = 1.62102664139390868e-10;         // t^6
-    ps = fma(ps, t, 2.50509370460377762e-08);    // t^5
-    ps = fma(ps, t, 2.75573237196537609e-06);    // t^4
-    ps = fma(ps, t, 1.98412698324150781e-04);    // t^3
-    ps = fma(ps, t, 8.33333333334163734e-03);    // t^2
-    ps = fma(ps, t, 1.66666666666666380e-01);    // t^1
-    ps = fma(ps, t, 1.0);                        // t^0
+                                               double& cur_over_g, double& dg, float& dgf) {
+  const unsigned long long ab = (unsigned long long)__double_as_longlong(dv) & 0x7FFFFFFFFFFFFFFFull;
+  if (ab < gr.dv_lim_bits) {
+    const double t = dv * dv;
+    double ps = gr.pc[6];
+    ps = fma(ps, t, gr.pc[5]);
+    ps = fma(ps, t, gr.pc[4]);
+    ps = fma(ps, t, gr.pc[3]);
+    ps = fma(ps, t, gr.pc[2]);
+    ps = fma(ps, t, gr.pc[1]);
+    ps = fma(ps, t, gr.pc[0]);
     cur_over_g = dv * ps;
-    dg = f2d_bits(d2f_round(g) * coshf(d2f_round(x)));
+    dgf = d2f_round(g) * coshf(d2f_round(dv) * gr.bf);
+    dg = f2d_bits(dgf);
   } else {
+    const double x = gr.b * dv;
     cur_over_g = sinh(x) * gr.inv_b;
     dg = g * cosh(x);
+    dgf = d2f_round(dg);
   }
 }
 
@@ -93,7 +125,7 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
                                               const double* __restrict__ Vt,
                                               const double* __restrict__ Vb, double g,
                                               double vin_i, double& ft, double& fb,
-                                              double& dg) {
+                                              double& dg, float& dgf) {
   const int m = gr.m, n = gr.n;
   const double vt = Vt[c], vb = Vb[c];
   const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
@@ -108,10 +140,11 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
   const double dv = vt - vb;
   double cg;                                     // device current / g
   if (gr.b != 0.0) {
-    device_current(gr, g, dv, cg, dg);
+    device_current(gr, g, dv, cg, dg, dgf);
   } else {
     cg = dv;
     dg = g;
+    dgf = 0.f;
   }
   ft = fma(g, cg, ft);
   fb = fma(-g, cg, fb);
@@ -168,21 +201,26 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
   double* Fb = Ft + mn;
   double* Db = D + (size_t)b * mn;
   const double* vinb = vin + (size_t)b * m;
-  // sum(D) stays in FP64: with uniform linear devices a = mean(D) must equal D to FP64
-  // rounding for the preconditioner to be exact (one GMRES iteration)
+  // sum(D): FP64 for linear devices, where a = mean(D) must equal a uniform D to FP64
+  // rounding for the preconditioner to be exact (one GMRES iteration); otherwise D itself
+  // is FP32 and so is its sum within a thread
+  const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
+  float sdf = 0.f;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int j = c - i * n;
     double ft, fb, dg;
-    cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg);
+    float dgf;
+    cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg, dgf);
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
     sf = fma(ft, ft, sf);
     sf = fma(fb, fb, sf);
-    sd += dg;
+    if (lin) sd += dg; else sdf += dgf;
   }
+  sd += f2d_bits(sdf);
   block_sum2(sf, sd);
   if (threadIdx.x == 0) {
     part[((size_t)b * 32 + 0) * nblk + blockIdx.x] = sf;
@@ -263,19 +301,23 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   __nv_bfloat16* xt = xbf ? xbf + (size_t)b * 2 * mp * np : nullptr;
   double* Db = D + (size_t)b * mn;
   const double* vinb = vin + (size_t)b * m;
-  // sum(D) stays in FP64: with uniform linear devices a = mean(D) must equal D to FP64
-  // rounding for the preconditioner to be exact (one GMRES iteration)
+  // sum(D): FP64 for linear devices, where a = mean(D) must equal a uniform D to FP64
+  // rounding for the preconditioner to be exact (one GMRES iteration); otherwise D itself
+  // is FP32 and so is its sum within a thread
+  const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
+  float sdf = 0.f;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int j = c - i * n;
     double ft, fb, dg;
+    float dgf = 0.f;
     if (ZERO) {
       ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
       fb = 0.0;
       dg = gmap[c];
     } else {
-      cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg);
+      cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg, dgf);
     }
     Ft[c] = ft;
     Fb[c] = fb;
@@ -286,8 +328,9 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     }
     sf = fma(ft, ft, sf);
     sf = fma(fb, fb, sf);
-    sd += dg;
+    if (ZERO || lin) sd += dg; else sdf += dgf;
   }
+  sd += f2d_bits(sdf);
   block_sum2(sf, sd);
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -460,9 +503,13 @@ __global__ void k_outputs(Grid gr, const double* __restrict__ vin, const double*
 
 }  // namespace
 
-int residual_nblk(int mn) {
+int residual_nblk(int mn, int B) {
+  constexpr int kGridBlocks = 152 * 32;
   int nb = (mn + kThreads - 1) / kThreads;
-  return nb < 608 ? (nb < 1 ? 1 : nb) : 608;
+  const int want = (kGridBlocks + B - 1) / (B < 1 ? 1 : B);
+  if (nb > want) nb = want;
+  if (nb > 608) nb = 608;
+  return nb < 1 ? 1 : nb;
 }
 
 void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,

@@ -553,8 +553,8 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
   const double cells = (double)h->mn;
   const size_t vstride = (size_t)(h->restart + 1) * n2;
   const size_t zstride = (size_t)h->restart * n2;
-  const int nbS = residual_nblk((int)h->mn);
-  const int nbV = vec_nblk(n2);
+  const int nbS = residual_nblk((int)h->mn, B);
+  const int nbV = vec_nblk(n2, B);
   const bool tc = is_tc(h->p.precision);
   const double* vk = h->V + (size_t)k * n2;
   double* zk = h->Z + (size_t)k * n2;
@@ -662,7 +662,7 @@ int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
 // from_guess: h->x already holds the initial states (otherwise Newton starts at x = 0).
 int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
   const SolverCfg cfg = make_cfg(h);
-  const int nbR = residual_nblk((int)h->mn);
+  const int nbR = residual_nblk((int)h->mn, B);
   const bool tc = is_tc(h->p.precision);
   const size_t vstride = (size_t)(h->restart + 1) * h->n2;
   const size_t zstride = (size_t)h->restart * h->n2;
@@ -970,7 +970,7 @@ static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
       // judge the guess: keep it only if its residual is finite and below ||F(0)|| = ||Y||
       MCA_CUDA_TRY(cudaMemcpyAsync(h->x, guess + (size_t)v0 * h->n2,
                                    (size_t)B * h->n2 * sizeof(double), cudaMemcpyDefault, s));
-      const int nb = residual_nblk((int)h->mn);
+      const int nb = residual_nblk((int)h->mn, B);
       launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
       count_launches(1);
       // residual of the guess (map-aware through the Newton kernel with max_newton = 0)
@@ -1176,8 +1176,8 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
   const size_t vstride = (size_t)(h->restart + 1) * n2;
   const size_t zstride = (size_t)h->restart * n2;
   const bool tc = is_tc(h->p.precision);
-  const int nbV = vec_nblk(n2);
-  const int nbS = residual_nblk((int)h->mn);
+  const int nbV = vec_nblk(n2, nvec);
+  const int nbS = residual_nblk((int)h->mn, nvec);
   const int cap = (max_iters > 0) ? max_iters : h->restart;
   MCA_TRY(load_ctl_a(h, a, nvec, s));
   MCA_CUDA_TRY(cudaMemsetAsync(dx, 0, (size_t)nvec * n2 * sizeof(double), s));

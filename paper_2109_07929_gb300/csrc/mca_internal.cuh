@@ -59,6 +59,12 @@ struct Grid {
   double g_bt, g_sense;     // bottom-column ends: termination (i = 0), sense (i = m-1)
   double b;                 // sinh nonlinearity (0 = linear device)
   double inv_b;             // 1 / b (0 when b = 0)
+  // sinh(b dV) / (b dV) = sum_k pc[k] (dV^2)^k for |dV| below the limit whose FP64 bit
+  // pattern (sign cleared) is dv_lim_bits: the polynomial of the memristor current with b
+  // folded into its coefficients
+  double pc[7];
+  unsigned long long dv_lim_bits;
+  float bf;                 // b in FP32 (for the FP32 conductance)
   // diagonals of the wire operators (eq. G with terminations): first / inside / last node
   double dt0, dtm, dtl;     // top row, along j
   double db0, dbm, dbl;     // bottom column, along i
@@ -158,9 +164,14 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
                       cudaStream_t s);
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,
                     double* kcl, int B, cudaStream_t s);
-int residual_nblk(int mn);
+// Blocks per vector of the grid-stride stencil / vector kernels for B vectors: about
+// kGridBlocks blocks in all (several waves of 256-thread blocks on 152 SMs, so the tail
+// is short) but never more than one element per thread or 608 blocks per vector; fewer
+// blocks per vector at large B leave each thread more elements, which shrinks the share
+// of the per-thread FP64 reduction work.
+int residual_nblk(int mn, int B = 1);
 // Krylov (k_krylov.cu)
-int vec_nblk(size_t n2);
+int vec_nblk(size_t n2, int B = 1);
 void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
                         const VecCtl* ctl, cudaStream_t s);
 // pass 2: w -= V h1, partial dots <V_j, w>; the last block reduces them into h2.

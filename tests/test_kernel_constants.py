@@ -1,7 +1,7 @@
 """Host-side checks of constants baked into the CUDA kernels (no GPU needed).
 
 The memristor current uses sinh(x) = x p(x^2) on |x| < 3/4 with a degree-6 polynomial p
-(k_stencil.cu).  Its coefficients are checked here against sinh itself in high precision,
+(k_stencil.cu, where b is folded into the coefficients at handle creation).  Its coefficients are checked here against sinh itself in high precision,
 and against the generator script that derives them (Chebyshev economisation of the Taylor
 series), so that a mistyped digit or a wrong range cannot reach the residual unnoticed."""
 import re
@@ -17,10 +17,10 @@ CSRC = ROOT / "paper_2109_07929_gb300" / "csrc"
 
 def _kernel_coefficients():
     src = (CSRC / "k_stencil.cu").read_text()
-    body = src[src.index("device_current("):]
-    body = body[:body.index("cur_over_g = dv * ps;")]
+    body = src[src.index("kSinhPoly[7] = {"):]
+    body = body[:body.index("};")]
     vals = {}
-    for m in re.finditer(r"([0-9.]+e[-+][0-9]+|1\.0)\)?;\s*// t\^(\d)", body):
+    for m in re.finditer(r"([0-9.]+e[-+][0-9]+|1\.0),\s*// t\^(\d)", body):
         vals[int(m.group(2))] = float(m.group(1))
     assert sorted(vals) == list(range(7)), vals
     return [vals[k] for k in range(7)]
@@ -28,14 +28,14 @@ def _kernel_coefficients():
 
 def _range_limit():
     src = (CSRC / "k_stencil.cu").read_text()
-    m = re.search(r"hi < 0x([0-9A-Fa-f]+)u\) \{\s*// \|x\| < ([0-9.]+)", src)
-    hi = int(m.group(1), 16)
-    return np.frombuffer(np.array([hi << 32], np.uint64).tobytes(), np.float64)[0], float(m.group(2))
+    m = re.search(r"kSinhPolyX = ([0-9.]+);", src)
+    return float(m.group(1))
 
 
-def test_range_test_matches_its_comment():
-    limit, stated = _range_limit()
-    assert limit == stated == 0.75
+def test_range_matches_the_generator():
+    pytest.importorskip("sympy")
+    gen = _generator()
+    assert _range_limit() == float(gen.X2) ** 0.5 == 0.75
 
 
 def test_sinh_polynomial_accuracy_high_precision():
@@ -68,12 +68,16 @@ def test_sinh_polynomial_fp64_horner_within_two_ulp():
         assert abs(val - ref) <= 2 * np.spacing(abs(ref)) + 1e-320, (x, val, ref)
 
 
-def test_generator_reproduces_kernel_coefficients():
-    pytest.importorskip("sympy")
+def _generator():
     import importlib.util
     spec = importlib.util.spec_from_file_location("gen_sinh_poly", CSRC / "gen_sinh_poly.py")
     gen = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(gen)
-    coef, bound = gen.coefficients()
+    return gen
+
+
+def test_generator_reproduces_kernel_coefficients():
+    pytest.importorskip("sympy")
+    coef, bound = _generator().coefficients()
     assert bound < 2e-18
     assert [float(v) for v in coef] == _kernel_coefficients()
