@@ -341,7 +341,31 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
     out[off + e] = a[off + e] - b[off + e];
 }
 
+__global__ void k_report(const VecCtl* __restrict__ ctl, const double* __restrict__ kcl,
+                         const int* __restrict__ err, HostReport* rep, int B) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const VecCtl& c = ctl[b];
+    HostReport r;
+    r.status = c.status;
+    r.newton_iters = c.newton_iters;
+    r.gmres_iters = c.gmres_iters;
+    r.k_done = c.k_done;
+    r.fnorm = c.fnorm;
+    r.ynorm = c.ynorm;
+    r.kcl = kcl ? kcl[b] : 0.0;
+    r.res_est = c.res_est;
+    rep[b] = r;
+  }
+  if (threadIdx.x == 0) rep[B].status = *err;
+  __threadfence_system();
+}
+
 }  // namespace
+
+void launch_report(const VecCtl* ctl, const double* kcl, const int* err, HostReport* rep,
+                   int B, cudaStream_t s) {
+  k_report<<<1, 128, 0, s>>>(ctl, kcl, err, rep, B);
+}
 
 void launch_gmres_init(const double* part_norm, int nblk, VecCtl* ctl, int B, double rtol,
                        int first, cudaStream_t s) {

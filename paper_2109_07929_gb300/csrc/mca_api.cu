@@ -86,6 +86,8 @@ struct mca_handle {
   VecCtl* ctl = nullptr;
   unsigned int* cnt = nullptr;    // per-vector block counters of the fused reductions
   int32_t* hflags = nullptr;      // pinned, mapped
+  HostReport* report = nullptr;   // pinned, mapped: Bmax + 1 entries
+  HostReport* report_dev = nullptr;
   int32_t* hflags_dev = nullptr;
   int* err = nullptr;
   double *T1_64 = nullptr, *Xh_64 = nullptr, *E_64 = nullptr;
@@ -108,6 +110,18 @@ struct mca_handle {
   // Work requested on the legacy default stream runs on this blocking stream instead
   // (same ordering with the legacy stream, and legal to capture into graphs).
   cudaStream_t own_stream = nullptr;
+  // Output copies of a pass run on copy_stream while the next pass computes: the state and
+  // output currents are double-buffered (x and iout point at the current pass' buffers).
+  cudaStream_t copy_stream = nullptr;
+  double* xbuf[2] = {nullptr, nullptr};
+  double* ioutbuf[2] = {nullptr, nullptr};
+  cudaEvent_t ev_solved = nullptr;
+  cudaEvent_t copy_done[2] = {nullptr, nullptr};
+  bool copy_pending[2] = {false, false};
+  // inputs of a pass are staged one pass ahead (before the previous pass' output copies
+  // are queued, so they never wait behind them on the copy engine)
+  double* vinbuf[2] = {nullptr, nullptr};
+  int* mapbuf[2] = {nullptr, nullptr};
   // statistics of the last solve pass (host copies)
   std::vector<VecCtl> ctl_host;
   // captured GMRES iterations, keyed by (iteration k, batch size B)
@@ -249,7 +263,9 @@ int setup_tc(mca_handle* h) {
 int alloc_workspace(mca_handle* h) {
   const size_t B = h->Bmax, n2 = h->n2, mn = h->mn;
   const size_t kv = h->restart + 1;
-  MCA_TRY(dalloc(h, &h->x, B * n2));
+  MCA_TRY(dalloc(h, &h->xbuf[0], B * n2));
+  MCA_TRY(dalloc(h, &h->xbuf[1], B * n2));
+  h->x = h->xbuf[0];
   MCA_TRY(dalloc(h, &h->F, B * n2));
   MCA_TRY(dalloc(h, &h->D, B * mn));
   MCA_TRY(dalloc(h, &h->V, B * kv * n2));
@@ -258,16 +274,23 @@ int alloc_workspace(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->part, B * 32 * MCA_NPART));
   MCA_TRY(dalloc(h, &h->h1, B * 32));
   MCA_TRY(dalloc(h, &h->h2, B * 32));
-  MCA_TRY(dalloc(h, &h->vin, B * h->m));
-  MCA_TRY(dalloc(h, &h->iout, B * h->n));
+  MCA_TRY(dalloc(h, &h->vinbuf[0], B * h->m));
+  MCA_TRY(dalloc(h, &h->vinbuf[1], B * h->m));
+  h->vin = h->vinbuf[0];
+  MCA_TRY(dalloc(h, &h->ioutbuf[0], B * h->n));
+  MCA_TRY(dalloc(h, &h->ioutbuf[1], B * h->n));
+  h->iout = h->ioutbuf[0];
   MCA_TRY(dalloc(h, &h->kcl, B));
   MCA_TRY(dalloc(h, &h->ctl, B));
   MCA_TRY(dalloc(h, &h->err, 1));
   MCA_TRY(dalloc(h, &h->cnt, B));
-  MCA_TRY(dalloc(h, &h->map_of, B));
+  MCA_TRY(dalloc(h, &h->mapbuf[0], B));
+  MCA_TRY(dalloc(h, &h->mapbuf[1], B));
+  h->map_of = h->mapbuf[0];
   h->fac_ld = std::max(h->m, h->n);
   MCA_TRY(dalloc(h, &h->fac, B * 4 * (size_t)h->fac_ld));
-  MCA_CUDA_TRY(cudaMemset(h->map_of, 0, B * sizeof(int)));
+  MCA_CUDA_TRY(cudaMemset(h->mapbuf[0], 0, B * sizeof(int)));
+  MCA_CUDA_TRY(cudaMemset(h->mapbuf[1], 0, B * sizeof(int)));
   h->map_host.assign(B, 0);
   MCA_CUDA_TRY(cudaMemset(h->err, 0, sizeof(int)));
   MCA_CUDA_TRY(cudaMemset(h->cnt, 0, B * sizeof(unsigned int)));
@@ -279,10 +302,16 @@ int alloc_workspace(mca_handle* h) {
   }
   MCA_CUDA_TRY(cudaHostAlloc(&h->hflags, 64 * sizeof(int32_t), cudaHostAllocMapped));
   MCA_CUDA_TRY(cudaHostGetDevicePointer(&h->hflags_dev, h->hflags, 0));
+  MCA_CUDA_TRY(cudaHostAlloc(&h->report, (B + 1) * sizeof(HostReport), cudaHostAllocMapped));
+  MCA_CUDA_TRY(cudaHostGetDevicePointer(&h->report_dev, h->report, 0));
   for (int k = 0; k <= MCA_KMAX; ++k)
     MCA_CUDA_TRY(cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming));
   h->ev_ok = true;
   MCA_CUDA_TRY(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamDefault));
+  MCA_CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  MCA_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_solved, cudaEventDisableTiming));
+  for (int q = 0; q < 2; ++q)
+    MCA_CUDA_TRY(cudaEventCreateWithFlags(&h->copy_done[q], cudaEventDisableTiming));
   h->ctl_host.resize(B);
   return MCA_OK;
 }
@@ -333,6 +362,35 @@ void prof_flush(mca_handle* h, F active) {
   }
   h->prof_pending.clear();
   h->prof_next = 0;
+}
+
+// Results of the pass' B vectors into h->ctl_host (status, iteration counts, norms) and,
+// if kcl_out is given, the KCL balances; returns the device error flag as a status.  Only
+// kernel work on s is waited for (no copy-engine transfer).
+int read_report(mca_handle* h, int B, const double* kcl_dev, double* kcl_out, cudaStream_t s) {
+  launch_report(h->ctl, kcl_dev, h->err, h->report_dev, B, s);
+  count_launches(1);
+  MCA_CUDA_TRY(cudaGetLastError());
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  const volatile HostReport* r = h->report;
+  for (int b = 0; b < B; ++b) {
+    VecCtl& c = h->ctl_host[b];
+    c.status = r[b].status;
+    c.newton_iters = r[b].newton_iters;
+    c.gmres_iters = r[b].gmres_iters;
+    c.k_done = r[b].k_done;
+    c.fnorm = r[b].fnorm;
+    c.ynorm = r[b].ynorm;
+    c.res_est = r[b].res_est;
+    if (kcl_out) kcl_out[b] = r[b].kcl;
+  }
+  const int e = r[B].status;
+  if (e != 0) {
+    cudaMemsetAsync(h->err, 0, sizeof(int), s);
+    set_error("a bounded device wait expired");
+    return e;
+  }
+  return MCA_OK;
 }
 
 int check_device_error(mca_handle* h) {
@@ -711,10 +769,7 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
   launch_outputs(h->gr, h->vin, h->x, h->iout, h->kcl, B, s);
   count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
-  MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
-                               cudaMemcpyDeviceToHost, s));
-  MCA_CUDA_TRY(cudaStreamSynchronize(s));
-  return check_device_error(h);
+  return MCA_OK;
 }
 
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
@@ -769,11 +824,16 @@ void mca_destroy(mca_handle* h) {
   cudaDeviceSynchronize();
   for (void* q : h->allocs) cudaFree(q);
   if (h->hflags) cudaFreeHost(h->hflags);
+  if (h->report) cudaFreeHost(h->report);
   if (h->ev_ok)
     for (int k = 0; k <= MCA_KMAX; ++k) cudaEventDestroy(h->ev[k]);
   for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second.first);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->ev_solved) cudaEventDestroy(h->ev_solved);
+  for (int q = 0; q < 2; ++q)
+    if (h->copy_done[q]) cudaEventDestroy(h->copy_done[q]);
   delete h;
 }
 
@@ -937,6 +997,10 @@ int mca_solve_from(mca_handle* h, const double* v_in, const double* guess,
   return solve_impl(h, v_in, guess, map_index, nvec, v_top, v_bot, i_out, stats, stream);
 }
 
+static int solve_passes(mca_handle* h, const double* v_in, const double* guess,
+                        const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
+                        double* i_out, mca_stats* stats, cudaStream_t s);
+
 static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
                       const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
                       double* i_out, mca_stats* stats, void* stream) {
@@ -954,17 +1018,53 @@ static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
     }
   }
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
-  const size_t m = h->m, n = h->n, mn = h->mn;
-  int worst = MCA_OK;
-  for (int v0 = 0; v0 < nvec; v0 += h->Bmax) {
-    const int B = std::min(h->Bmax, nvec - v0);
-    MCA_CUDA_TRY(cudaMemcpyAsync(h->vin, v_in + (size_t)v0 * m, (size_t)B * m * sizeof(double),
-                                 cudaMemcpyDefault, s));
-    if (h->n_maps > 1) {
-      for (int b = 0; b < B; ++b) h->map_host[b] = map_index ? map_index[v0 + b] : 0;
-      MCA_CUDA_TRY(cudaMemcpyAsync(h->map_of, h->map_host.data(), (size_t)B * sizeof(int),
-                                   cudaMemcpyHostToDevice, s));
+  int rc = solve_passes(h, v_in, guess, map_index, nvec, v_top, v_bot, i_out, stats, s);
+  // the outputs of every pass are in place when the call returns
+  for (int q = 0; q < 2; ++q) {
+    if (!h->copy_pending[q]) continue;
+    const cudaError_t e = cudaEventSynchronize(h->copy_done[q]);
+    h->copy_pending[q] = false;
+    if (e != cudaSuccess && (rc == MCA_OK || rc == MCA_ERR_NOT_CONVERGED ||
+                             rc == MCA_ERR_NONFINITE)) {
+      set_last_cuda_error(e, "output copy", __FILE__, __LINE__);
+      rc = MCA_ERR_CUDA;
     }
+  }
+  return rc;
+}
+
+// The passes of a solve call: batches of up to max_batch vectors.  Pass p works in state
+// buffer p % 2; its output copies go on the copy stream and overlap pass p + 1, which only
+// has to wait for the copies of pass p - 1 (same buffer) before it overwrites the state.
+// Inputs of the pass starting at vector v0 into staging buffer q (on s).
+static int stage_inputs(mca_handle* h, const double* v_in, const int32_t* map_index, int v0,
+                        int B, int q, cudaStream_t s) {
+  MCA_CUDA_TRY(cudaMemcpyAsync(h->vinbuf[q], v_in + (size_t)v0 * h->m,
+                               (size_t)B * h->m * sizeof(double), cudaMemcpyDefault, s));
+  if (h->n_maps > 1) {
+    for (int b = 0; b < B; ++b) h->map_host[b] = map_index ? map_index[v0 + b] : 0;
+    MCA_CUDA_TRY(cudaMemcpyAsync(h->mapbuf[q], h->map_host.data(), (size_t)B * sizeof(int),
+                                 cudaMemcpyHostToDevice, s));
+  }
+  return MCA_OK;
+}
+
+static int solve_passes(mca_handle* h, const double* v_in, const double* guess,
+                        const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
+                        double* i_out, mca_stats* stats, cudaStream_t s) {
+  const size_t m = h->m, n = h->n, mn = h->mn;
+  (void)m;
+  int worst = MCA_OK;
+  int pass = 0;
+  if (nvec > 0) MCA_TRY(stage_inputs(h, v_in, map_index, 0, std::min(h->Bmax, nvec), 0, s));
+  for (int v0 = 0; v0 < nvec; v0 += h->Bmax, ++pass) {
+    const int B = std::min(h->Bmax, nvec - v0);
+    const int q = pass & 1;
+    if (h->copy_pending[q]) MCA_CUDA_TRY(cudaStreamWaitEvent(s, h->copy_done[q], 0));
+    h->x = h->xbuf[q];
+    h->iout = h->ioutbuf[q];
+    h->vin = h->vinbuf[q];
+    h->map_of = h->mapbuf[q];
     std::vector<int> fell(B, 0);
     if (guess) {
       // judge the guess: keep it only if its residual is finite and below ||F(0)|| = ||Y||
@@ -981,9 +1081,7 @@ static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
                              false, h->F, h->n2, nullptr, 0, 0, h->D, h->part, nb, B, h->ctl,
                              probe, h->cnt, nullptr, s);
       count_launches(1);
-      MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)B * sizeof(VecCtl),
-                                   cudaMemcpyDeviceToHost, s));
-      MCA_CUDA_TRY(cudaStreamSynchronize(s));
+      MCA_TRY(read_report(h, B, nullptr, nullptr, s));
       for (int b = 0; b < B; ++b) {
         const VecCtl& c = h->ctl_host[b];
         const bool ok = std::isfinite(c.fnorm) && c.fnorm < c.ynorm;
@@ -995,17 +1093,28 @@ static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
     }
     int rc = solve_pass(h, B, s, guess != nullptr);
     if (rc != MCA_OK) return rc;
-    for (int b = 0; b < B; ++b) {
-      const double* xb = h->x + (size_t)b * h->n2;
-      MCA_TRY(copy_out(v_top ? v_top + (size_t)(v0 + b) * mn : nullptr, xb, mn * sizeof(double), s));
-      MCA_TRY(copy_out(v_bot ? v_bot + (size_t)(v0 + b) * mn : nullptr, xb + mn,
-                       mn * sizeof(double), s));
-    }
+    // the next pass' inputs, then this pass' output copies on the copy stream
+    const int v1 = v0 + h->Bmax;
+    if (v1 < nvec)
+      MCA_TRY(stage_inputs(h, v_in, map_index, v1, std::min(h->Bmax, nvec - v1), q ^ 1, s));
+    cudaStream_t cs = h->copy_stream;
+    MCA_CUDA_TRY(cudaEventRecord(h->ev_solved, s));
+    MCA_CUDA_TRY(cudaStreamWaitEvent(cs, h->ev_solved, 0));
+    // one strided copy per layer: state rows of 2 m n doubles into output rows of m n
+    if (v_top)
+      MCA_CUDA_TRY(cudaMemcpy2DAsync(v_top + (size_t)v0 * mn, mn * sizeof(double), h->x,
+                                     h->n2 * sizeof(double), mn * sizeof(double), B,
+                                     cudaMemcpyDefault, cs));
+    if (v_bot)
+      MCA_CUDA_TRY(cudaMemcpy2DAsync(v_bot + (size_t)v0 * mn, mn * sizeof(double), h->x + mn,
+                                     h->n2 * sizeof(double), mn * sizeof(double), B,
+                                     cudaMemcpyDefault, cs));
     MCA_TRY(copy_out(i_out ? i_out + (size_t)v0 * n : nullptr, h->iout,
-                     (size_t)B * n * sizeof(double), s));
+                     (size_t)B * n * sizeof(double), cs));
+    MCA_CUDA_TRY(cudaEventRecord(h->copy_done[q], cs));
+    h->copy_pending[q] = true;
     std::vector<double> kcl(B);
-    MCA_CUDA_TRY(cudaMemcpyAsync(kcl.data(), h->kcl, B * sizeof(double), cudaMemcpyDeviceToHost, s));
-    MCA_CUDA_TRY(cudaStreamSynchronize(s));
+    MCA_TRY(read_report(h, B, h->kcl, kcl.data(), s));
     for (int b = 0; b < B; ++b) {
       const VecCtl& c = h->ctl_host[b];
       if (c.status != MCA_OK && worst == MCA_OK) worst = c.status;

@@ -51,6 +51,17 @@ struct VecCtl {
   double s[MCA_KMAX + 1];
 };
 
+// Per-vector results of a solve pass, written by a kernel into mapped pinned host memory
+// so the host reads them without a copy (a small device-to-host copy would queue behind
+// the large output copies of the previous pass on the copy engine).
+struct HostReport {
+  int32_t status, newton_iters, gmres_iters, k_done;
+  double fnorm, ynorm, kcl, res_est;
+};
+// rep[b] for b < B from ctl[b] and kcl[b] (kcl may be NULL); rep[B].status = *err.
+void launch_report(const VecCtl* ctl, const double* kcl, const int* err, HostReport* rep,
+                   int B, cudaStream_t s);
+
 // Scalars of one crossbar needed by the stencil kernels.
 struct Grid {
   int m, n;                 // rows, cols

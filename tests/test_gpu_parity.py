@@ -294,6 +294,30 @@ def test_batch_matches_single_solves():
             assert _rel_err(vt[v], vt1[0]) < 1e-9 and _rel_err(vb[v], vb1[0]) < 1e-8
 
 
+def test_multi_pass_output_pipelining():
+    """A call with more vectors than max_batch runs in passes whose output copies overlap
+    the next pass (double-buffered state): 10 vectors in passes of 3 (one ragged) must give
+    the per-vector results, into host and into device buffers."""
+    cb = mi.make_crossbar(40, 36, 31, nvec=10)
+    p = cb.params
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=3,
+                            newton_rtol=1e-11), cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+        dvt = torch.empty(10, 40, 36, dtype=torch.float64, device=DEV)
+        dvb = torch.empty_like(dvt)
+        dio = torch.empty(10, 36, dtype=torch.float64, device=DEV)
+        s.solve(_t(cb.vin), dvt, dvb, dio)
+        singles = [s.solve(cb.vin[v:v + 1]) for v in range(10)]
+    for v in range(10):
+        assert st[v]["status"] == 0
+        assert _rel_err(vt[v], singles[v][0][0]) < 1e-9
+        assert _rel_err(vb[v], singles[v][1][0]) < 1e-8
+        np.testing.assert_allclose(io[v], singles[v][2][0], rtol=1e-8)
+    np.testing.assert_array_equal(dvt.cpu().numpy(), vt)
+    np.testing.assert_array_equal(dvb.cpu().numpy(), vb)
+    np.testing.assert_array_equal(dio.cpu().numpy(), io)
+
+
 def test_device_buffers_in_and_out():
     cb = mi.make_crossbar(20, 30, 5, nvec=2)
     p = cb.params
