@@ -272,8 +272,12 @@ __global__ void k_lsq(VecCtl* ctl) {
   }
 }
 
-// x <- x + sum_j y_j z_j over the finished cycle.
-__global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z,
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
+
+// x <- x + sum_j y_j z_j over the finished cycle (Z in FP64 or FP32).
+template <typename ZT>
+__global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z,
                            size_t zstride, size_t n2, const VecCtl* __restrict__ ctl) {
   const int b = blockIdx.y;
   const VecCtl& c = ctl[b];
@@ -283,7 +287,7 @@ __global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z,
   if (threadIdx.x < MCA_KMAX) ys[threadIdx.x] = (threadIdx.x < kd) ? c.y[threadIdx.x] : 0.0;
   __syncthreads();
   double* xb = x + (size_t)b * n2;
-  const double* Zb = Z + (size_t)b * zstride;
+  const ZT* Zb = Z + (size_t)b * zstride;
   const size_t st = (size_t)gridDim.x * blockDim.x;
   size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   for (; e + 3 * st < n2; e += 4 * st) {     // four independent elements per trip
@@ -292,14 +296,14 @@ __global__ void k_update_x(double* __restrict__ x, const double* __restrict__ Z,
     for (int u = 0; u < 4; ++u) s[u] = xb[e + u * st];
     for (int j = 0; j < kd; ++j) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) s[u] = fma(ys[j], Zb[(size_t)j * n2 + e + u * st], s[u]);
+      for (int u = 0; u < 4; ++u) s[u] = fma(ys[j], widen(Zb[(size_t)j * n2 + e + u * st]), s[u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) xb[e + u * st] = s[u];
   }
   for (; e < n2; e += st) {
     double s = xb[e];
-    for (int j = 0; j < kd; ++j) s = fma(ys[j], Zb[(size_t)j * n2 + e], s);
+    for (int j = 0; j < kd; ++j) s = fma(ys[j], widen(Zb[(size_t)j * n2 + e]), s);
     xb[e] = s;
   }
 }
@@ -420,12 +424,23 @@ void launch_update_norm(int phase, const double* w, size_t wstride, const double
                   nblk, ctl, cnt, h1, restart, host_flags, out, ostride, xbf, mp, np, m, n);
 }
 
-void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
-                       int B, cudaStream_t s) {
+template <typename ZT>
+void lsq_update(double* x, const ZT* Z, size_t zstride, size_t n2, VecCtl* ctl, int B,
+                cudaStream_t s) {
   k_lsq<<<B, 32, 0, s>>>(ctl);
   int nb = (int)((n2 + kThreads - 1) / kThreads);
   if (nb > 608) nb = 608;
-  k_update_x<<<dim3(nb, B), kThreads, 0, s>>>(x, Z, zstride, n2, ctl);
+  k_update_x<ZT><<<dim3(nb, B), kThreads, 0, s>>>(x, Z, zstride, n2, ctl);
+}
+
+void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
+                       int B, cudaStream_t s) {
+  lsq_update(x, Z, zstride, n2, ctl, B, s);
+}
+
+void launch_lsq_update(double* x, const float* Z, size_t zstride, size_t n2, VecCtl* ctl,
+                       int B, cudaStream_t s) {
+  lsq_update(x, Z, zstride, n2, ctl, B, s);
 }
 
 }  // namespace mca

@@ -185,7 +185,7 @@ struct Layout {
   static constexpr int B_BYTES = BN * BKT * 2;
   static constexpr int HALF = 2 * A_BYTES + B_BYTES;
   static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
-  static constexpr int STAGE_OUT = (EPI == EPI_F64) ? 0 :
+  static constexpr int STAGE_OUT = (EPI == EPI_F64 || EPI == EPI_F32) ? 0 :
       ((EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) ? 4 : 2) * BN * BM * 2;
   static constexpr int STAGES_MIN = (STAGE_OUT + STAGE - 1) / STAGE;
   static constexpr int STAGES_2 = STAGES_MIN > 2 ? STAGES_MIN : 2;
@@ -210,7 +210,11 @@ struct Layout {
   X(128, false, EPI_F64, 1)            \
   X(256, false, EPI_F64, 1)            \
   X(128, true, EPI_F64, 1)             \
-  X(256, true, EPI_F64, 1)
+  X(256, true, EPI_F64, 1)             \
+  X(128, false, EPI_F32, 1)            \
+  X(256, false, EPI_F32, 1)            \
+  X(128, true, EPI_F32, 1)             \
+  X(256, true, EPI_F32, 1)
 
 template <int BN, bool SPLIT, int EPI>
 __global__ void __launch_bounds__(kThreads, Layout<BN, SPLIT, EPI>::CTAS)
@@ -320,7 +324,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   // (the vote makes a timed-out wait uniform, so every thread meets the same barriers)
   const bool have = __syncthreads_and(mbar_wait(accum, 0) ? 1 : 0) != 0;
   if (!have && threadIdx.x == 0) record_error(ep.err, MCA_ERR_TIMEOUT);
-  constexpr bool kBf16Out = (EPI != EPI_F64);
+  constexpr bool kBf16Out = (EPI != EPI_F64 && EPI != EPI_F32);
   constexpr bool kLo = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
   constexpr int kOuts = kLo ? 4 : 2;            // [hi t, hi b, lo t, lo b]
   // BF16 outputs are staged transposed in the (now idle) pipeline buffers as
@@ -371,6 +375,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             double* out = static_cast<double*>(ep.out);
             out[o0] = f2d_bits(x0);
             out[o0 + ep.o_ls] = f2d_bits(x1);
+          }
+        } else if (EPI == EPI_F32) {
+          if (r_ok && c < ep.C_valid) {
+            const size_t o0 = (size_t)b * ep.o_bs + (size_t)c * ep.o_ld + r;
+            float* out = static_cast<float*>(ep.out);
+            out[o0] = x0;
+            out[o0 + ep.o_ls] = x1;
           }
         } else {
           const __nv_bfloat16 h0 = __float2bfloat16(x0);
@@ -434,7 +445,7 @@ struct WsLayout {
   static constexpr int HALF = LP * A_BYTES + B_BYTES;
   static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
   static constexpr bool LO = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
-  static constexpr int NOUT = (EPI == EPI_F64) ? 0 : (LO ? 2 : 1) * LP;   // staged outputs
+  static constexpr int NOUT = (EPI == EPI_F64 || EPI == EPI_F32) ? 0 : (LO ? 2 : 1) * LP;
   static constexpr int STG_WARP = NOUT * 32 * 32 * 2;                     // bytes per warp
   static constexpr int STG_OFF_RAW = 0;
   static constexpr int FIXED = kWsEpiWarps * STG_WARP + 512 + 1024;      // + barriers, align
@@ -635,8 +646,8 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         uint32_t v0[32], v1[32];
         tmem_ld32(lane_base + cc * 32, v0);
         if (LP == 2) tmem_ld32(lane_base + BN + cc * 32, v1);
-        if (EPI == EPI_F64) {
-          double* out = static_cast<double*>(ep.out);
+        if (EPI == EPI_F64 || EPI == EPI_F32) {
+          // unpadded FP64 or FP32 output: one full warp segment per column
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int c = c0 + cc * 32 + j;
@@ -645,7 +656,11 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
               for (int l = 0; l < LP; ++l) {
                 const size_t o = (size_t)b * ep.o_bs + (size_t)(layer + l) * ep.o_ls +
                                  (size_t)c * ep.o_ld + r;
-                out[o] = f2d_bits(__uint_as_float(l == 0 ? v0[j] : v1[j]));
+                const uint32_t v = (l == 0) ? v0[j] : v1[j];
+                if (EPI == EPI_F64)
+                  static_cast<double*>(ep.out)[o] = f2d_bits(__uint_as_float(v));
+                else
+                  static_cast<float*>(ep.out)[o] = __uint_as_float(v);
               }
             }
           }
@@ -838,6 +853,10 @@ cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtens
   MCA_TC_CASE(64, true, EPI_SPLIT)
   MCA_TC_CASE(128, true, EPI_F64)
   MCA_TC_CASE(64, true, EPI_F64)
+  MCA_TC_CASE(128, false, EPI_F32)
+  MCA_TC_CASE(64, false, EPI_F32)
+  MCA_TC_CASE(128, true, EPI_F32)
+  MCA_TC_CASE(64, true, EPI_F32)
 #undef MCA_TC_CASE
   return cudaErrorInvalidValue;
 }
@@ -877,6 +896,10 @@ cudaError_t configure_all() {
   MCA_TC_CFG(64, true, EPI_SPLIT)
   MCA_TC_CFG(128, true, EPI_F64)
   MCA_TC_CFG(64, true, EPI_F64)
+  MCA_TC_CFG(128, false, EPI_F32)
+  MCA_TC_CFG(64, false, EPI_F32)
+  MCA_TC_CFG(128, true, EPI_F32)
+  MCA_TC_CFG(64, true, EPI_F32)
 #undef MCA_TC_CFG
 #define MCA_WS_CFG(BN_, SPLIT_, EPI_, LP_)                                              \
   {                                                                                     \

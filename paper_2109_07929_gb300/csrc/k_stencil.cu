@@ -402,9 +402,13 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
 // K2 fused with the first classical Gram-Schmidt pass: w = J z for one cell (both
 // layers), then partial dots <V_j, w> for j < nk; the last block of each vector reduces
 // the partials into h.
-template <int KP>
+// z is FP64, or FP32 (the tensor-core preconditioner's accumulators, widened exactly).
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
+
+template <int KP, typename ZT>
 __global__ void __launch_bounds__(kThreads)
-k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
+k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
             size_t zstride, double* __restrict__ w, const double* __restrict__ V,
             size_t vstride, int nk, double* __restrict__ part, int nblk,
             const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h) {
@@ -412,8 +416,8 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
   if (ctl != nullptr && !ctl[b].gm_active) return;
   const int m = gr.m, n = gr.n, mn = m * n;
   const size_t n2 = 2 * (size_t)mn;
-  const double* zt = z + (size_t)b * zstride;
-  const double* zb = zt + mn;
+  const ZT* zt = z + (size_t)b * zstride;
+  const ZT* zb = zt + mn;
   const double* Db = D + (size_t)b * mn;
   double* wt = w + (size_t)b * n2;
   double* wb = wt + mn;
@@ -424,14 +428,14 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const double* __restrict__ z,
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int jj = c - i * n;
-    const double a = zt[c], bb = zb[c];
+    const double a = widen(zt[c]), bb = widen(zb[c]);
     const double cpl = Db[c] * (a - bb);
     const double dt = (jj == 0) ? gr.dt0 : ((jj == n - 1) ? gr.dtl : gr.dtm);
     const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
-    const double tl = (jj > 0) ? zt[c - 1] : 0.0;
-    const double tr = (jj < n - 1) ? zt[c + 1] : 0.0;
-    const double bu = (i > 0) ? zb[c - n] : 0.0;
-    const double bd = (i < m - 1) ? zb[c + n] : 0.0;
+    const double tl = (jj > 0) ? widen(zt[c - 1]) : 0.0;
+    const double tr = (jj < n - 1) ? widen(zt[c + 1]) : 0.0;
+    const double bu = (i > 0) ? widen(zb[c - n]) : 0.0;
+    const double bd = (i < m - 1) ? widen(zb[c + n]) : 0.0;
     const double ot = fma(dt, a, fma(-gr.gt, tl + tr, cpl));
     const double ob = fma(db, bb, fma(-gr.gb, bu + bd, -cpl));
     wt[c] = ot;
@@ -548,16 +552,16 @@ void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
   k_init_basis<<<dim3(nb, B), kThreads, 0, s>>>(F, sign, V0, vstride, xbf, mp, np, m, n, ctl);
 }
 
-void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t zstride,
-                      double* w, const double* V, size_t vstride, int nk, double* part,
-                      int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
-                      cudaStream_t s) {
+template <typename ZT>
+void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, double* w,
+               const double* V, size_t vstride, int nk, double* part, int nblk, int B,
+               const VecCtl* ctl, unsigned int* cnt, double* h, cudaStream_t s) {
   // z: the vector of batch entry 0, later entries zstride doubles apart; V: basis vector
   // 0 of batch entry 0 (nk vectors N2 apart, entries vstride apart), or NULL.
   dim3 grid(nblk, B);
-#define MCA_SPMV(KP_)                                                                    \
-  k_spmv_dots<KP_><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, \
-                                             nblk, ctl, cnt, h)
+#define MCA_SPMV(KP_)                                                                      \
+  k_spmv_dots<KP_, ZT><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, \
+                                                 nblk, ctl, cnt, h)
   if (nk <= 1) MCA_SPMV(1);
   else if (nk <= 2) MCA_SPMV(2);
   else if (nk <= 4) MCA_SPMV(4);
@@ -565,6 +569,20 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
   else if (nk <= 16) MCA_SPMV(16);
   else MCA_SPMV(32);
 #undef MCA_SPMV
+}
+
+void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t zstride,
+                      double* w, const double* V, size_t vstride, int nk, double* part,
+                      int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
+                      cudaStream_t s) {
+  spmv_dots(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h, s);
+}
+
+void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
+                      double* w, const double* V, size_t vstride, int nk, double* part,
+                      int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
+                      cudaStream_t s) {
+  spmv_dots(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h, s);
 }
 
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,

@@ -72,6 +72,7 @@ struct mca_handle {
   int n_maps = 1;
   double* g = nullptr;
   int* map_of = nullptr;               // device: map of each vector of the current pass
+  float* Z32 = nullptr;                // FP32 preconditioned vectors (tensor-core forms)
   std::vector<int> map_host;
   double *mu = nullptr, *nu = nullptr, *Qr = nullptr, *Qc = nullptr, *QrT = nullptr,
          *QcT = nullptr;
@@ -269,7 +270,12 @@ int alloc_workspace(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->F, B * n2));
   MCA_TRY(dalloc(h, &h->D, B * mn));
   MCA_TRY(dalloc(h, &h->V, B * kv * n2));
-  MCA_TRY(dalloc(h, &h->Z, B * h->restart * n2));
+  // preconditioned vectors: FP32 for the tensor-core forms (their FP32 accumulators,
+  // widened exactly where FP64 work reads them), FP64 otherwise
+  if (is_tc(h->p.precision))
+    MCA_TRY(dalloc(h, &h->Z32, B * h->restart * n2));
+  else
+    MCA_TRY(dalloc(h, &h->Z, B * h->restart * n2));
   MCA_TRY(dalloc(h, &h->W, B * n2));
   MCA_TRY(dalloc(h, &h->part, B * 32 * MCA_NPART));
   MCA_TRY(dalloc(h, &h->h1, B * 32));
@@ -406,8 +412,8 @@ int check_device_error(mca_handle* h) {
 
 // Tensor-core transform `step` (0..3) of the preconditioner for B vectors; the input of
 // step 0 is the BF16 copy in h->Xbf, the output of step 3 goes to zout (FP64).
-int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, int B,
-            const VecCtl* ctl, cudaStream_t s, int prof_k, int kidx = -1) {
+int tc_step(mca_handle* h, int step, bool split, void* zout, size_t zstride, int B,
+            const VecCtl* ctl, cudaStream_t s, int prof_k, int kidx = -1, bool z32 = false) {
   const int m = h->m, n = h->n;
   const size_t mn = h->mn, mp = h->mp, np = h->np;
   auto q = [](int bn) { return bn == 128 ? 0 : (bn == 64 ? 1 : 2); };
@@ -453,10 +459,10 @@ int tc_step(mca_handle* h, int step, bool split, double* zout, size_t zstride, i
     default:  // Z = (E^T Q_c^T)^T, FP64 unpadded
       e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
       e.out = zout; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
-      MCA_CUDA_TRY(run(split, tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)], h->mB4l[q(bn)],
-                       e));
-      prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k, (split ? 8.0 : 4.0) * mn + 16.0 * mn,
-               sp * f_c, s);
+      MCA_CUDA_TRY(run(split, z32 ? tc::EPI_F32 : tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)],
+                       h->mB4l[q(bn)], e));
+      prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k,
+               (split ? 8.0 : 4.0) * mn + (z32 ? 8.0 : 16.0) * mn, sp * f_c, s);
       break;
   }
   count_launches(1);
@@ -498,11 +504,11 @@ int autotune_tiles(mca_handle* h) {
       h->ws[step] = ws;
       h->bn[step] = bn;
       h->lp[step] = lp;
-      rc = tc_step(h, step, split, h->Z, zstride, B, h->ctl, 0, -1);
+      rc = tc_step(h, step, split, h->Z32, zstride, B, h->ctl, 0, -1, -1, true);
       if (rc != MCA_OK) break;
       cudaEventRecord(e0, 0);
       for (int r = 0; r < 3 && rc == MCA_OK; ++r)
-        rc = tc_step(h, step, split, h->Z, zstride, B, h->ctl, 0, -1);
+        rc = tc_step(h, step, split, h->Z32, zstride, B, h->ctl, 0, -1, -1, true);
       cudaEventRecord(e1, 0);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         rc = MCA_ERR_CUDA;
@@ -531,9 +537,12 @@ int autotune_tiles(mca_handle* h) {
 // z = P^-1 r for B vectors: r at rin + b*rstride, z at zout + b*zstride.  For the
 // tensor-core forms the BF16 copy of r must already be in h->Xbf.  kidx >= 0: r is the
 // unnormalised basis vector k, and z = P^-1 (ctl[b].s[kidx] r).
+// zout is double*, or float* when z32 (tensor-core forms only).
 int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstride,
-                  double* zout, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s,
-                  int prof_k = -1, const double* D = nullptr, int kidx = -1) {
+                  void* zout_v, size_t zstride, int B, const VecCtl* ctl, cudaStream_t s,
+                  int prof_k = -1, const double* D = nullptr, int kidx = -1,
+                  bool z32 = false) {
+  double* zout = static_cast<double*>(zout_v);
   if (precision == MCA_PREC_MHAT) {
     cudaEvent_t t0 = prof_begin(h, s);
     MCA_TRY(precond_mhat(h->gr, rin, rstride, zout, zstride, B, ctl, h->fac, h->fac_ld, kidx,
@@ -582,7 +591,7 @@ int precond_apply(mca_handle* h, int precision, const double* rin, size_t rstrid
   if (!h->tc_ok) return MCA_ERR_UNSUPPORTED;
   const bool split = (precision == MCA_PREC_BF16_SPLIT);
   for (int step = 0; step < 4; ++step)
-    MCA_TRY(tc_step(h, step, split, zout, zstride, B, ctl, s, prof_k, kidx));
+    MCA_TRY(tc_step(h, step, split, zout_v, zstride, B, ctl, s, prof_k, kidx, z32));
   return MCA_OK;
 }
 
@@ -615,15 +624,26 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
   const int nbV = vec_nblk(n2, B);
   const bool tc = is_tc(h->p.precision);
   const double* vk = h->V + (size_t)k * n2;
-  double* zk = h->Z + (size_t)k * n2;
   const double nk = k + 1;
+  cudaEvent_t t0 = nullptr;
   // (tensor-core forms read the BF16 copy of v_k written by the kernel that made v_k)
-  MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k));
-  cudaEvent_t t0 = prof_begin(h, s);
-  launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
-                   h->ctl, h->cnt, h->h1, s);
+  if (tc) {
+    float* zk = h->Z32 + (size_t)k * n2;
+    MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k,
+                          true));
+    t0 = prof_begin(h, s);
+    launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
+                     h->ctl, h->cnt, h->h1, s);
+  } else {
+    double* zk = h->Z + (size_t)k * n2;
+    MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k));
+    t0 = prof_begin(h, s);
+    launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
+                     h->ctl, h->cnt, h->h1, s);
+  }
   count_launches(1);
-  prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * (40.0 + 16.0 * nk), cells * (12.0 + 4.0 * nk), s);
+  prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * ((tc ? 32.0 : 40.0) + 16.0 * nk),
+           cells * (12.0 + 4.0 * nk), s);
   double* vnext = h->V + (size_t)(k + 1) * n2;
   __nv_bfloat16* xbf = tc ? h->Xbf : nullptr;
   t0 = prof_begin(h, s);
@@ -753,7 +773,10 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     if (n_active == 0) break;
     MCA_TRY(gmres_cycle(h, h->D, B, s));
     t0 = prof_begin(h, s);
-    launch_lsq_update(h->x, h->Z, zstride, h->n2, h->ctl, B, s);
+    if (tc)
+      launch_lsq_update(h->x, h->Z32, zstride, h->n2, h->ctl, B, s);
+    else
+      launch_lsq_update(h->x, h->Z, zstride, h->n2, h->ctl, B, s);
     count_launches(2);
     double kbar = 0.0;
     if (h->prof_on) {
@@ -762,7 +785,8 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
         if (h->ctl_host[b].k_done > 0) { kbar += h->ctl_host[b].k_done; ++c; }
       kbar = c ? kbar / c : 0.0;
     }
-    prof_end(h, t0, MCA_FAM_UPDATE_X, -1, cells * 16.0 * (2.0 + kbar), cells * 4.0 * kbar, s);
+    prof_end(h, t0, MCA_FAM_UPDATE_X, -1, cells * (32.0 + (tc ? 8.0 : 16.0) * kbar),
+             cells * 4.0 * kbar, s);
     prof_flush(h, [&](int, bool) { return n_active; });
     MCA_CUDA_TRY(cudaGetLastError());
   }
@@ -1306,7 +1330,10 @@ int mca_gmres_solve(mca_handle* h, const double* D, const double* a, const doubl
                       h->n, h->ctl, nvec, s);
     count_launches(3);
     MCA_TRY(gmres_cycle(h, D, nvec, s));
-    launch_lsq_update(dx, h->Z, zstride, n2, h->ctl, nvec, s);
+    if (tc)
+      launch_lsq_update(dx, h->Z32, zstride, n2, h->ctl, nvec, s);
+    else
+      launch_lsq_update(dx, h->Z, zstride, n2, h->ctl, nvec, s);
     count_launches(2);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl_host.data(), h->ctl, (size_t)nvec * sizeof(VecCtl),

@@ -173,6 +173,11 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
                       cudaStream_t s);
+// the same with z in FP32 (the tensor-core preconditioner's output, widened exactly)
+void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
+                      double* w, const double* V, size_t vstride, int nk, double* part,
+                      int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
+                      cudaStream_t s);
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,
                     double* kcl, int B, cudaStream_t s);
 // Blocks per vector of the grid-stride stencil / vector kernels for B vectors: about
@@ -207,6 +212,8 @@ void launch_update_norm(int phase, const double* w, size_t wstride, const double
                         int restart, int32_t* host_flags, double* out, size_t ostride,
                         __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s);
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
+                       int B, cudaStream_t s);
+void launch_lsq_update(double* x, const float* Z, size_t zstride, size_t n2, VecCtl* ctl,
                        int B, cudaStream_t s);
 // first = 1: remember beta = ||rhs|| and stop at rtol * beta; first = 0 (a restart): keep
 // the tolerance of the first cycle.

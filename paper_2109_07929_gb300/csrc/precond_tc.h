@@ -15,6 +15,7 @@ enum Epi {
   EPI_SPLIT = 2,        // out = bf16(acc), out_lo = bf16(acc - out)
   EPI_F64 = 3,          // out = (double)acc for r < R_valid, c < C_valid (unpadded)
   EPI_MODES_SPLIT = 4,  // EPI_MODES with a hi/lo pair
+  EPI_F32 = 5,          // out = acc (float) for r < R_valid, c < C_valid (unpadded)
 };
 
 // Output addressing: element (blk = 2b + layer, c, r) is written to
