@@ -169,6 +169,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[CW]) {
+  if constexpr (CW == 16) tmem_ld16(taddr, v); else tmem_ld32(taddr, v);
+}
+
 __device__ __forceinline__ void record_error(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
@@ -426,15 +442,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // ---------------------------------------------------------------------------------------
 // Persistent, warp-specialised form of the same GEMMs.  One CTA per SM walks a static
 // round-robin list of output tiles; warp 0 streams A/B stages with TMA, warp 1 issues the
-// MMAs into one of two TMEM accumulators, and warps 2..9 drain the other accumulator (the
-// epilogue of tile i overlaps the main loop of tile i + 1; two warps per TMEM lane
-// quarter, each taking every other 32-column chunk).  A tile is 128 rows x BN
+// MMAs into one of two TMEM accumulators, and the epilogue warps drain the other
+// accumulator (the epilogue of tile i overlaps the main loop of tile i + 1).  There are 8
+// epilogue warps (16 for the two-layer tiles, whose modes epilogue does the most work per
+// element): 2 or 4 per TMEM lane quarter, each taking every 2nd or 4th column chunk.  A tile is 128 rows x BN
 // columns of LP layers: LP = 2 keeps both layers of a mode in one CTA (required by the
 // per-mode 2x2 epilogue), LP = 1 makes twice as many single-layer tiles (better balance
-// of the tiles over the SMs).  BF16 outputs are transposed through a 32 x 32 staging tile
-// per epilogue warp and leave in 16-byte chunks.
-constexpr int kWsThreads = 320;                 // 10 warps
-constexpr int kWsEpiWarps = 8;
+// of the tiles over the SMs).  BF16 outputs are transposed through a small staging tile per
+// epilogue warp, one output at a time, and leave in 16-byte chunks.
 constexpr int kWsSmemMax = 227 * 1024;
 
 template <int BN, bool SPLIT, int EPI, int LP>
@@ -446,13 +461,15 @@ struct WsLayout {
   static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
   static constexpr bool LO = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
   static constexpr int NOUT = (EPI == EPI_F64 || EPI == EPI_F32) ? 0 : (LO ? 2 : 1) * LP;
-  static constexpr int STG_WARP = NOUT * 32 * 32 * 2;                     // bytes per warp
-  static constexpr int STG_OFF_RAW = 0;
-  static constexpr int FIXED = kWsEpiWarps * STG_WARP + 512 + 1024;      // + barriers, align
+  static constexpr int EW = (LP == 2) ? 16 : 8;                           // epilogue warps
+  static constexpr int THREADS = 64 + 32 * EW;
+  static constexpr int CW = (LP == 2) ? 16 : 32;            // columns per TMEM load/chunk
+  static constexpr int STG_WARP = NOUT > 0 ? CW * 32 * 2 : 0;             // bytes per warp
+  static constexpr int FIXED = EW * STG_WARP + 512 + 1024;                // + barriers, align
   static constexpr int STAGES_FIT = (kWsSmemMax - FIXED) / STAGE;
   static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
   static constexpr int STG_OFF = STAGES * STAGE;
-  static constexpr int BAR_OFF = STG_OFF + kWsEpiWarps * STG_WARP;
+  static constexpr int BAR_OFF = STG_OFF + EW * STG_WARP;
   static constexpr int SMEM = BAR_OFF + 512 + 1024;
   static constexpr int ACC_COLS = LP * BN;                                // one accumulator
   static constexpr int TMEM_COLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
@@ -462,7 +479,7 @@ struct WsLayout {
 };
 
 template <int BN, bool SPLIT, int EPI, int LP>
-__global__ void __launch_bounds__(kWsThreads, 1)
+__global__ void __launch_bounds__(WsLayout<BN, SPLIT, EPI, LP>::THREADS, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
           GemmEpi ep, int B) {
@@ -506,7 +523,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kWsEpiWarps);
+      mbar_init(&tempty[a], L::EW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -612,9 +629,11 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
   } else {
     // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 and
-    // the 32-column chunks cc with cc % 2 == (w - 2) / 4
+    // the CW-column chunks cc with cc % NG == (w - 2) / 4, NG = EW / 4
+    constexpr int NG = L::EW / 4;
+    constexpr int CW = L::CW;
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int grp = (warp - 2) >> 2;
     const int rl = q * 32 + lane;                    // row inside the tile
     __nv_bfloat16* stg =
         reinterpret_cast<__nv_bfloat16*>(smem + L::STG_OFF + (warp - 2) * L::STG_WARP);
@@ -635,22 +654,23 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const bool r_ok = r < ep.R_valid;
       const uint32_t lane_base =
           tmem + (uint32_t)(acc * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
-      float a_mode = 0.f, mu_r = 0.f, sc = 1.f;
+      float a_mode = 0.f, mu_a = 0.f, a2 = 0.f, sc = 1.f;
       if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
         a_mode = (float)ep.ctl[b].a;
-        mu_r = r_ok ? ep.mu_f[r] : 0.f;
+        mu_a = (r_ok ? ep.mu_f[r] : 0.f) + a_mode;
+        a2 = a_mode * a_mode;
         if (ep.kidx >= 0) sc = (float)ep.ctl[b].s[ep.kidx];
       }
 #pragma unroll 1
-      for (int cc = half; cc < BN / 32; cc += 2) {
-        uint32_t v0[32], v1[32];
-        tmem_ld32(lane_base + cc * 32, v0);
-        if (LP == 2) tmem_ld32(lane_base + BN + cc * 32, v1);
+      for (int cc = grp; cc < BN / CW; cc += NG) {
+        uint32_t v0[CW], v1[CW];
+        tmem_ld<CW>(lane_base + cc * CW, v0);
+        if (LP == 2) tmem_ld<CW>(lane_base + BN + cc * CW, v1);
         if (EPI == EPI_F64 || EPI == EPI_F32) {
           // unpadded FP64 or FP32 output: one full warp segment per column
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = c0 + cc * 32 + j;
+          for (int j = 0; j < CW; ++j) {
+            const int c = c0 + cc * CW + j;
             if (r_ok && c < ep.C_valid) {
 #pragma unroll
               for (int l = 0; l < LP; ++l) {
@@ -665,52 +685,53 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
           }
         } else {
+          if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+            // [y_t; y_b] = (sc / det) [[nu + a, a], [a, mu + a]] [x_t; x_b] in place,
+            // det = (mu + a)(nu + a) - a^2; the column eigenvalues come in with one
+            // coalesced load and a shuffle per column
+            const int cl = c0 + cc * CW + lane;
+            const float nu_l = (lane < CW && cl < ep.C_valid) ? ep.nu_f[cl] : 0.f;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = c0 + cc * 32 + j;
-            float x0 = __uint_as_float(v0[j]);
-            float x1 = (LP == 2) ? __uint_as_float(v1[j]) : 0.f;
-            if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
-              // [y_t; y_b] = (sc / det) [[nu + a, a], [a, mu + a]] [x_t; x_b]
+            for (int j = 0; j < CW; ++j) {
+              const int c = c0 + cc * CW + j;
+              const float nu_a = __shfl_sync(0xffffffffu, nu_l, j) + a_mode;
               float y0 = 0.f, y1 = 0.f;
               if (r_ok && c < ep.C_valid) {
-                const float nu_c = ep.nu_f[c];
-                const float det = mu_r * nu_c + mu_r * a_mode + nu_c * a_mode;
+                const float x0 = __uint_as_float(v0[j]), x1 = __uint_as_float(v1[j]);
                 // (approximate reciprocal: a few FP32 ulps, far below the BF16 outputs)
-                const float inv = __fdividef(sc, det);
-                y0 = ((nu_c + a_mode) * x0 + a_mode * x1) * inv;
-                y1 = (a_mode * x0 + (mu_r + a_mode) * x1) * inv;
+                const float inv = __fdividef(sc, fmaf(mu_a, nu_a, -a2));
+                y0 = fmaf(nu_a, x0, a_mode * x1) * inv;
+                y1 = fmaf(mu_a, x1, a_mode * x0) * inv;
               }
-              x0 = y0;
-              x1 = y1;
-            }
-            // staging tile o: [32 columns][32 rows] of this warp
-#pragma unroll
-            for (int l = 0; l < LP; ++l) {
-              const float x = (l == 0) ? x0 : x1;
-              const __nv_bfloat16 hi = __float2bfloat16(x);
-              stg[(l * 32 + j) * 32 + lane] = hi;
-              if (L::LO)
-                stg[((LP + l) * 32 + j) * 32 + lane] = __float2bfloat16(x - __bfloat162float(hi));
+              v0[j] = __float_as_uint(y0);
+              v1[j] = __float_as_uint(y1);
             }
           }
-          __syncwarp();
-          // out: 32 columns x 64 bytes per staged output; 4 chunks of 16 bytes per column
-#pragma unroll
+          // one output at a time through this warp's [CW columns][32 rows] staging tile,
+          // then 4 chunks of 16 bytes per column (64 bytes of rows)
+#pragma unroll 1
           for (int o = 0; o < L::NOUT; ++o) {
             const int l = o % LP;
-            __nv_bfloat16* out = static_cast<__nv_bfloat16*>((o < LP) ? ep.out : ep.out_lo);
+            const bool lo = o >= LP;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+              const float x = __uint_as_float((LP == 2 && l == 1) ? v1[j] : v0[j]);
+              const __nv_bfloat16 hi = __float2bfloat16(x);
+              stg[j * 32 + lane] = lo ? __float2bfloat16(x - __bfloat162float(hi)) : hi;
+            }
+            __syncwarp();
+            __nv_bfloat16* out = static_cast<__nv_bfloat16*>(lo ? ep.out_lo : ep.out);
             const size_t base = (size_t)b * ep.o_bs + (size_t)(layer + l) * ep.o_ls + r0 + q * 32;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < CW / 8; ++i) {
               const int id = lane + 32 * i;
               const int col = id >> 2, part = id & 3;
-              const uint4 v = *reinterpret_cast<const uint4*>(&stg[(o * 32 + col) * 32 + part * 8]);
+              const uint4 v = *reinterpret_cast<const uint4*>(&stg[col * 32 + part * 8]);
               *reinterpret_cast<uint4*>(
-                  &out[base + (size_t)(c0 + cc * 32 + col) * ep.o_ld + part * 8]) = v;
+                  &out[base + (size_t)(c0 + cc * CW + col) * ep.o_ld + part * 8]) = v;
             }
+            __syncwarp();
           }
-          __syncwarp();
         }
       }
       // accumulator drained: the MMA warp may reuse it
@@ -797,7 +818,7 @@ cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& al, const CUtenso
   }
   const int ntiles = (ep.R / BM) * (ep.C / BN) * (LP == 1 ? 2 : 1) * B;
   const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-  k_gemm_ws<BN, SPLIT, EPI, LP><<<grid, kWsThreads, L::SMEM, s>>>(a, al, bm, bml, ep, B);
+  k_gemm_ws<BN, SPLIT, EPI, LP><<<grid, L::THREADS, L::SMEM, s>>>(a, al, bm, bml, ep, B);
   return cudaGetLastError();
 }
 
