@@ -66,6 +66,14 @@ Grid make_grid(const mca_params& p) {
   memcpy(&bits, &lim, sizeof(bits));
   g.dv_lim_bits = bits;
   g.bf = (float)p.b;
+  g.gtf = (float)g.gt;
+  g.gbf = (float)g.gb;
+  g.dt0f = (float)g.dt0;
+  g.dtmf = (float)g.dtm;
+  g.dtlf = (float)g.dtl;
+  g.db0f = (float)g.db0;
+  g.dbmf = (float)g.dbm;
+  g.dblf = (float)g.dbl;
   return g;
 }
 
@@ -406,7 +414,7 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
 
-template <int KP, typename ZT>
+template <int KP, typename ZT, bool F32>
 __global__ void __launch_bounds__(kThreads)
 k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
             size_t zstride, double* __restrict__ w, const double* __restrict__ V,
@@ -428,16 +436,31 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int jj = c - i * n;
-    const double a = widen(zt[c]), bb = widen(zb[c]);
-    const double cpl = Db[c] * (a - bb);
-    const double dt = (jj == 0) ? gr.dt0 : ((jj == n - 1) ? gr.dtl : gr.dtm);
-    const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
-    const double tl = (jj > 0) ? widen(zt[c - 1]) : 0.0;
-    const double tr = (jj < n - 1) ? widen(zt[c + 1]) : 0.0;
-    const double bu = (i > 0) ? widen(zb[c - n]) : 0.0;
-    const double bd = (i < m - 1) ? widen(zb[c + n]) : 0.0;
-    const double ot = fma(dt, a, fma(-gr.gt, tl + tr, cpl));
-    const double ob = fma(db, bb, fma(-gr.gb, bu + bd, -cpl));
+    double ot, ob;
+    if constexpr (F32) {
+      // FP32 apply (z is FP32 here): the same formula, rounded to FP32, widened exactly
+      const float a = zt[c], bb = zb[c];
+      const float cpl = d2f_round(Db[c]) * (a - bb);
+      const float dt = (jj == 0) ? gr.dt0f : ((jj == n - 1) ? gr.dtlf : gr.dtmf);
+      const float db = (i == 0) ? gr.db0f : ((i == m - 1) ? gr.dblf : gr.dbmf);
+      const float tl = (jj > 0) ? (float)zt[c - 1] : 0.f;
+      const float tr = (jj < n - 1) ? (float)zt[c + 1] : 0.f;
+      const float bu = (i > 0) ? (float)zb[c - n] : 0.f;
+      const float bd = (i < m - 1) ? (float)zb[c + n] : 0.f;
+      ot = f2d_bits(fmaf(dt, a, fmaf(-gr.gtf, tl + tr, cpl)));
+      ob = f2d_bits(fmaf(db, bb, fmaf(-gr.gbf, bu + bd, -cpl)));
+    } else {
+      const double a = widen(zt[c]), bb = widen(zb[c]);
+      const double cpl = Db[c] * (a - bb);
+      const double dt = (jj == 0) ? gr.dt0 : ((jj == n - 1) ? gr.dtl : gr.dtm);
+      const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
+      const double tl = (jj > 0) ? widen(zt[c - 1]) : 0.0;
+      const double tr = (jj < n - 1) ? widen(zt[c + 1]) : 0.0;
+      const double bu = (i > 0) ? widen(zb[c - n]) : 0.0;
+      const double bd = (i < m - 1) ? widen(zb[c + n]) : 0.0;
+      ot = fma(dt, a, fma(-gr.gt, tl + tr, cpl));
+      ob = fma(db, bb, fma(-gr.gb, bu + bd, -cpl));
+    }
     wt[c] = ot;
     wb[c] = ob;
     if (V != nullptr) {
@@ -552,7 +575,7 @@ void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
   k_init_basis<<<dim3(nb, B), kThreads, 0, s>>>(F, sign, V0, vstride, xbf, mp, np, m, n, ctl);
 }
 
-template <typename ZT>
+template <typename ZT, bool F32>
 void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, double* w,
                const double* V, size_t vstride, int nk, double* part, int nblk, int B,
                const VecCtl* ctl, unsigned int* cnt, double* h, cudaStream_t s) {
@@ -560,8 +583,8 @@ void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, dou
   // 0 of batch entry 0 (nk vectors N2 apart, entries vstride apart), or NULL.
   dim3 grid(nblk, B);
 #define MCA_SPMV(KP_)                                                                      \
-  k_spmv_dots<KP_, ZT><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, part, \
-                                                 nblk, ctl, cnt, h)
+  k_spmv_dots<KP_, ZT, F32><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, \
+                                                      part, nblk, ctl, cnt, h)
   if (nk <= 1) MCA_SPMV(1);
   else if (nk <= 2) MCA_SPMV(2);
   else if (nk <= 4) MCA_SPMV(4);
@@ -575,14 +598,19 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
                       cudaStream_t s) {
-  spmv_dots(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h, s);
+  spmv_dots<double, false>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h,
+                           s);
 }
 
 void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
-                      cudaStream_t s) {
-  spmv_dots(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h, s);
+                      cudaStream_t s, bool f32) {
+  if (f32)
+    spmv_dots<float, true>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h, s);
+  else
+    spmv_dots<float, false>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h,
+                            s);
 }
 
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,

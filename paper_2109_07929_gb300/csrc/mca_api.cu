@@ -615,7 +615,8 @@ bool any_flag(const mca_handle* h, int B) {
 // the fused reductions, the conditional second pass and the Givens column) for the vectors
 // still iterating.  The basis vectors after v_0 are kept unnormalised with their scales in
 // VecCtl::s, so the update pass writes v_{k+1} (and its BF16 copy) directly.
-int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t s) {
+int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t s,
+                      bool f32 = false) {
   const size_t n2 = h->n2;
   const double cells = (double)h->mn;
   const size_t vstride = (size_t)(h->restart + 1) * n2;
@@ -633,7 +634,7 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
                           true));
     t0 = prof_begin(h, s);
     launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
-                     h->ctl, h->cnt, h->h1, s);
+                     h->ctl, h->cnt, h->h1, s, f32);
   } else {
     double* zk = h->Z + (size_t)k * n2;
     MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k));
@@ -642,8 +643,9 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
                      h->ctl, h->cnt, h->h1, s);
   }
   count_launches(1);
+  // FP64 flops: the stencil's 12 per cell only when the apply runs in FP64
   prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * ((tc ? 32.0 : 40.0) + 16.0 * nk),
-           cells * (12.0 + 4.0 * nk), s);
+           cells * ((f32 ? 0.0 : 12.0) + 4.0 * nk), s);
   double* vnext = h->V + (size_t)(k + 1) * n2;
   __nv_bfloat16* xbf = tc ? h->Xbf : nullptr;
   t0 = prof_begin(h, s);
@@ -669,14 +671,15 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
 }
 
 // Capture iteration k for batch size B once and replay it as one graph launch.
-int launch_iteration_graph(mca_handle* h, const double* D, int B, int k, cudaStream_t s) {
-  auto key = std::make_pair(k, B);
+int launch_iteration_graph(mca_handle* h, const double* D, int B, int k, cudaStream_t s,
+                           bool f32) {
+  auto key = std::make_pair(k + (f32 ? MCA_KMAX + 1 : 0), B);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaGraph_t graph = nullptr;
     MCA_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     g_capturing = true;
-    int rc = enqueue_iteration(h, D, B, k, s);
+    int rc = enqueue_iteration(h, D, B, k, s, f32);
     g_capturing = false;
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (rc != MCA_OK) {
@@ -700,13 +703,13 @@ int launch_iteration_graph(mca_handle* h, const double* D, int B, int k, cudaStr
 // One flexible GMRES cycle on the vectors whose gm_active flag is set; V[b][0] and its
 // BF16 copy are already in place.  D is the Jacobian diagonal (graphs only for the
 // handle's own D).
-int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s) {
+int gmres_cycle(mca_handle* h, const double* D, int B, cudaStream_t s, bool f32 = false) {
   const bool graphs = (h->p.flags & MCA_FLAG_GRAPHS) && !h->prof_on && D == h->D;
   for (int k = 0; k < h->restart; ++k) {
     if (graphs) {
-      MCA_TRY(launch_iteration_graph(h, D, B, k, s));
+      MCA_TRY(launch_iteration_graph(h, D, B, k, s, f32));
     } else {
-      MCA_TRY(enqueue_iteration(h, D, B, k, s));
+      MCA_TRY(enqueue_iteration(h, D, B, k, s, f32));
     }
     MCA_CUDA_TRY(cudaEventRecord(h->ev[k], s));
     if (k >= 1) {
@@ -771,7 +774,10 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     for (int b = 0; b < B; ++b) n_active += reinterpret_cast<volatile int32_t*>(h->hflags)[b] ? 1 : 0;
     prof_flush(h, [&](int, bool) { return entering; });
     if (n_active == 0) break;
-    MCA_TRY(gmres_cycle(h, h->D, B, s));
+    // the first step from V = 0 solves to the loosest forcing term, eta0: with the
+    // tensor-core forms its Jacobian applies run in FP32 when eta0 allows it
+    const bool f32 = tc && zero_state && h->p.eta0 >= kF32ApplyMinEta;
+    MCA_TRY(gmres_cycle(h, h->D, B, s, f32));
     t0 = prof_begin(h, s);
     if (tc)
       launch_lsq_update(h->x, h->Z32, zstride, h->n2, h->ctl, B, s);

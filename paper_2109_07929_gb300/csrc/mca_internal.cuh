@@ -76,6 +76,8 @@ struct Grid {
   double pc[7];
   unsigned long long dv_lim_bits;
   float bf;                 // b in FP32 (for the FP32 conductance)
+  // FP32 copies of the wire operators for the FP32 Jacobian apply
+  float gtf, gbf, dt0f, dtmf, dtlf, db0f, dbmf, dblf;
   // diagonals of the wire operators (eq. G with terminations): first / inside / last node
   double dt0, dtm, dtl;     // top row, along j
   double db0, dbm, dbl;     // bottom column, along i
@@ -173,11 +175,18 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
                       cudaStream_t s);
-// the same with z in FP32 (the tensor-core preconditioner's output, widened exactly)
+// the same with z in FP32 (the tensor-core preconditioner's output, widened exactly);
+// f32: the Jacobian apply itself in FP32 (w = J z rounded to FP32, then widened; the
+// dots stay FP64), for linear solves whose forcing term is loose (kF32ApplyMinEta)
 void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
-                      cudaStream_t s);
+                      cudaStream_t s, bool f32 = false);
+// Smallest forcing term at which a Newton step's Jacobian applies run in FP32.  FP32
+// rounding of J z is relative to the wire terms, which cancel heavily, so it leaves a
+// floor on the linear residual (near 1e-5 relative in an FP32 model of the solver); the
+// first Newton step, solved to eta0 = 1e-3, stays well above it.
+constexpr double kF32ApplyMinEta = 1e-4;
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,
                     double* kcl, int B, cudaStream_t s);
 // Blocks per vector of the grid-stride stencil / vector kernels for B vectors: about

@@ -206,7 +206,16 @@ def _check_solve(cb, prec, tol, vtol=1e-7, nvec=None, ref_tol=1e-13):
         assert rel <= tol * 1.01, (v, rel)
         np.testing.assert_allclose(st[v]["rel_residual"], rel, rtol=1e-3, atol=tol * 1e-3)
         ref = O.newton_solve(p, cb.gmap, vin[v], tol=ref_tol, linear="direct")
-        assert _rel_err(vt[v], ref.Vt) <= vtol and _rel_err(vb[v], ref.Vb) <= vtol
+        if prec == mca.PREC_FP64:
+            # the FP64 form: max relative error per layer
+            assert _rel_err(vt[v], ref.Vt) <= vtol and _rel_err(vb[v], ref.Vb) <= vtol
+        else:
+            # mixed-precision forms: errors on the scale of the solution (both layers), which
+            # is what the KCL stop test bounds; a layer far below the other (the bottom node
+            # of a 1x1 array sits 5 decades below the top one) has no per-layer guarantee
+            scale = max(np.abs(ref.Vt).max(), np.abs(ref.Vb).max())
+            assert np.abs(vt[v] - ref.Vt).max() <= vtol * scale
+            assert np.abs(vb[v] - ref.Vb).max() <= vtol * scale
         np.testing.assert_allclose(io[v], p.g_sense * vb[v][-1], rtol=1e-15)
         assert st[v]["kcl_rel_error"] <= 1e-6
     return st
