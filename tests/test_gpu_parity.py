@@ -290,6 +290,27 @@ def test_selective_reorthogonalisation_long_cycle():
     np.testing.assert_allclose(true_res, np.linalg.norm(rhs - J @ x_ref), rtol=1e-6)
 
 
+def test_fp32_first_step_apply_matches_fp64_apply():
+    """With eta0 >= 1e-4 the first Newton step runs its Jacobian applies in FP32; with a
+    tighter eta0 every apply is FP64.  Both must reach the requested KCL residual and the
+    same solution (to the stop test's scale), with the same number of Newton steps."""
+    cb = mi.make_crossbar(96, 80, 41, nvec=4, g_wire_bot=0.5)
+    p = cb.params
+    out = {}
+    for eta0 in (1e-3, 5e-5):
+        with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, newton_rtol=1e-10,
+                                eta0=eta0, max_batch=4), cb.gmap) as s:
+            out[eta0] = s.solve(cb.vin)
+    for v in range(4):
+        for eta0 in out:
+            st = out[eta0][3][v]
+            assert st["status"] == 0 and st["rel_residual"] <= 1e-10, (eta0, st)
+        scale = max(np.abs(out[5e-5][0][v]).max(), np.abs(out[5e-5][1][v]).max())
+        assert np.abs(out[1e-3][0][v] - out[5e-5][0][v]).max() <= 1e-7 * scale
+        assert np.abs(out[1e-3][1][v] - out[5e-5][1][v]).max() <= 1e-7 * scale
+        assert out[1e-3][3][v]["newton_iters"] <= out[5e-5][3][v]["newton_iters"] + 1
+
+
 def test_batch_matches_single_solves():
     cb = mi.make_crossbar(48, 40, 21, nvec=6)
     p = cb.params
