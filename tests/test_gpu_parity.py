@@ -348,6 +348,27 @@ def test_multi_pass_output_pipelining():
     np.testing.assert_array_equal(dio.cpu().numpy(), io)
 
 
+def test_multi_pass_warm_start_and_fallback():
+    """solve_from over several passes (7 vectors, passes of 3): exact solutions as guesses are
+    kept (no Newton work), garbage guesses fall back to V = 0, and every vector ends at the
+    plain solve's answer."""
+    cb = mi.make_crossbar(24, 28, 33, nvec=7)
+    p = cb.params
+    N = 24 * 28
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=3,
+                            newton_rtol=1e-11), cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+        guess = np.concatenate([vt.reshape(7, N), vb.reshape(7, N)], axis=1)
+        guess[1::2] = 1e3                                    # every other guess is garbage
+        vt2, vb2, io2, st2 = s.solve_from(cb.vin, _t(guess))
+    for v in range(7):
+        assert st2[v]["status"] == 0
+        assert st2[v]["fallback"] == (1 if v % 2 else 0), (v, st2[v])
+        if v % 2 == 0:
+            assert st2[v]["newton_iters"] == 0, st2[v]
+        assert _rel_err(vt2[v], vt[v]) < 1e-9 and _rel_err(vb2[v], vb[v]) < 1e-8
+
+
 def test_device_buffers_in_and_out():
     cb = mi.make_crossbar(20, 30, 5, nvec=2)
     p = cb.params
