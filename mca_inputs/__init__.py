@@ -37,6 +37,9 @@ class CrossbarParams:
     g_term_bot_top: float = 1e-3
     g_sense: float = 0.1
     b: float = 2.0
+    # device model: a2/a1 of the Yakopcic-form I-V curve (current scale for dV < 0 over the
+    # one for dV >= 0); 1 gives the symmetric sinh device
+    neg_ratio: float = 1.0
 
     def as_dict(self):
         return asdict(self)
@@ -64,8 +67,8 @@ def bimodal(rng, shape, p_on=0.1, g_on=1e-4, g_off=1e-6, sigma=0.1):
 
 
 def make_crossbar(rows, cols, seed, nvec=1, gdist="loguniform", sigma=0.0,
-                  vmax=0.3, **wiring) -> Crossbar:
-    """One crossbar: conductance map then ``nvec`` input vectors V_in ~ U[0, vmax]."""
+                  vmax=0.3, vmin=0.0, **wiring) -> Crossbar:
+    """One crossbar: conductance map then ``nvec`` input vectors V_in ~ U[vmin, vmax]."""
     rng = np.random.default_rng(seed)
     shape = (rows, cols)
     if gdist == "loguniform":
@@ -79,7 +82,7 @@ def make_crossbar(rows, cols, seed, nvec=1, gdist="loguniform", sigma=0.0,
         g = rng.uniform(0.0, 0.4, size=shape)
     else:
         raise ValueError(gdist)
-    vin = rng.uniform(0.0, vmax, size=(nvec, rows))
+    vin = rng.uniform(vmin, vmax, size=(nvec, rows))
     p = CrossbarParams(rows=rows, cols=cols, **wiring)
     return Crossbar(params=p, gmap=np.ascontiguousarray(g, dtype=np.float64),
                     vin=np.ascontiguousarray(vin, dtype=np.float64), seed=seed)

@@ -90,18 +90,33 @@ def source_vector(p, vin):
     return Yt, Yb
 
 
-def device_current(g, b, dv):
-    """Memristor current from top to bottom node, i = (g/b) sinh(b dv)."""
-    if b == 0.0:
-        return g * dv
-    return (g / b) * np.sinh(b * dv)
+def device_current(g, b, dv, neg_ratio=1.0):
+    """Memristor current from top to bottom node.  The experiments of Section 4 use the
+    Yakopcic model at fixed (programmed) internal states: a sinh of the voltage with one
+    amplitude for positive and another for negative bias.  With g the small-signal
+    conductance of the programmed state (a1 x b) and neg_ratio = a2 / a1:
+    i = (g/b) sinh(b dv) for dv >= 0 and neg_ratio (g/b) sinh(b dv) for dv < 0
+    (b = 0: the linear device g dv, scaled the same way)."""
+    dv = np.asarray(dv, dtype=np.float64)
+    i = g * dv if b == 0.0 else (g / b) * np.sinh(b * dv)
+    if neg_ratio != 1.0:
+        i = np.where(dv < 0.0, neg_ratio * i, i)
+    return i
 
 
-def device_conductance(g, b, dv):
-    """di/d(dv) = g cosh(b dv): the diagonal of the device blocks of eq. (J)."""
-    if b == 0.0:
-        return np.array(g, dtype=np.float64, copy=True)
-    return g * np.cosh(b * dv)
+def device_conductance(g, b, dv, neg_ratio=1.0):
+    """di/d(dv): g cosh(b dv), times neg_ratio where dv < 0 (the derivative on the side of
+    dv the device is on); the diagonal of the device blocks of eq. (J)."""
+    dv = np.asarray(dv, dtype=np.float64)
+    d = np.array(np.broadcast_to(g, dv.shape), dtype=np.float64, copy=True) if b == 0.0 \
+        else g * np.cosh(b * dv)
+    if neg_ratio != 1.0:
+        d = np.where(dv < 0.0, neg_ratio * d, d)
+    return d
+
+
+def _neg_ratio(p):
+    return getattr(p, "neg_ratio", 1.0)
 
 
 def residual(p, gmap, vin, Vt, Vb, ops=None):
@@ -109,7 +124,7 @@ def residual(p, gmap, vin, Vt, Vb, ops=None):
     V_t, V_b are flat row-major vectors of length m*n.  Returns (F_t, F_b)."""
     Gt, Gb = ops if ops is not None else layer_operators(p)
     Yt, Yb = source_vector(p, vin)
-    i = device_current(gmap.ravel(), p.b, Vt - Vb)
+    i = device_current(gmap.ravel(), p.b, Vt - Vb, _neg_ratio(p))
     Ft = Gt @ Vt + i - Yt
     Fb = Gb @ Vb - i - Yb
     return Ft, Fb
@@ -119,7 +134,7 @@ def jacobian(p, gmap, Vt, Vb, ops=None):
     """eq. (J): J = [[G_t, 0], [0, G_b]] + [[dI_t/dV_t, dI_t/dV_b], [-dI_b/dV_t,
     -dI_b/dV_b]] = [[G_t + D, -D], [-D, G_b + D]], D = diag(g cosh(b dV))."""
     Gt, Gb = ops if ops is not None else layer_operators(p)
-    D = sp.diags(device_conductance(gmap.ravel(), p.b, Vt - Vb))
+    D = sp.diags(device_conductance(gmap.ravel(), p.b, Vt - Vb, _neg_ratio(p)))
     return sp.bmat([[Gt + D, -D], [-D, Gb + D]], format="csr")
 
 
@@ -160,7 +175,7 @@ def precond_matrix(p, a1, a2, ops=None):
 def precond_scalars(p, gmap, Vt, Vb):
     """a1 = a2 = mean diagonal of the device conductance block (Section 3.1; the sign
     is taken so that both are the positive average device conductance)."""
-    a = float(np.mean(device_conductance(gmap.ravel(), p.b, Vt - Vb)))
+    a = float(np.mean(device_conductance(gmap.ravel(), p.b, Vt - Vb, _neg_ratio(p))))
     return a, a
 
 

@@ -50,6 +50,8 @@ def _netlist_residual(p, gmap, vin, Vt, Vb):
                 cur = gmap[i, j] * dv
             else:
                 cur = gmap[i, j] / p.b * np.sinh(p.b * dv)
+            if dv < 0:                                  # Yakopcic form: a2/a1 below zero
+                cur *= p.neg_ratio
             Ft[i, j] += cur
             Fb[i, j] -= cur
     return Ft.ravel(), Fb.ravel()
@@ -379,3 +381,100 @@ def test_pin_catches_wrong_precond_sign():
     # the literal sign reading of a1 (mean of dI_t/dV_b < 0) gives a different operator
     zt, zb = O.precond_apply_modes(eig, -a, -a, r[:12], r[12:], (3, 4))
     assert not np.allclose(np.concatenate([zt, zb]), z_ref, rtol=1e-6)
+
+
+# ---- Yakopcic-form device (asymmetric sinh, Section 4's device model) -------------------
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 3), (4, 5), (6, 6)])
+@pytest.mark.parametrize("b", [0.0, 2.0])
+def test_asymmetric_device_residual_matches_netlist(m, n, b):
+    rng = np.random.default_rng(17 + m * 10 + n)
+    p = _params(m, n, b=b, neg_ratio=0.35)
+    g = 10 ** rng.uniform(-6, -3, size=(m, n))
+    vin = rng.uniform(-0.3, 0.3, size=m)
+    Vt = rng.uniform(-0.3, 0.3, size=m * n)
+    Vb = rng.uniform(-0.2, 0.2, size=m * n)
+    Ft, Fb = O.residual(p, g, vin, Vt, Vb)
+    Rt, Rb = _netlist_residual(p, g, vin, Vt, Vb)
+    np.testing.assert_allclose(Ft, Rt, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(Fb, Rb, rtol=1e-12, atol=1e-15)
+
+
+def test_asymmetric_device_unit_ratio_is_the_sinh_device():
+    rng = np.random.default_rng(2)
+    g = 10 ** rng.uniform(-6, -4, size=50)
+    dv = rng.uniform(-0.5, 0.5, size=50)
+    np.testing.assert_array_equal(O.device_current(g, 2.0, dv, 1.0), g / 2.0 * np.sinh(2.0 * dv))
+    np.testing.assert_array_equal(O.device_conductance(g, 2.0, dv, 1.0), g * np.cosh(2.0 * dv))
+
+
+def test_asymmetric_device_jacobian_finite_difference():
+    """Away from dV = 0 (where the model has a kink when a2 != a1) J is the derivative."""
+    rng = np.random.default_rng(23)
+    m, n = 3, 4
+    p = _params(m, n, b=3.0, neg_ratio=0.4)
+    N = m * n
+    g = 10 ** rng.uniform(-4, -2, size=(m, n))
+    vin = rng.uniform(-0.3, 0.3, size=m)
+    Vb = rng.uniform(-0.2, 0.2, size=N)
+    dv = rng.uniform(0.01, 0.4, size=N) * rng.choice([-1.0, 1.0], size=N)
+    Vt = Vb + dv
+    J = O.jacobian(p, g, Vt, Vb).toarray()
+    h = 1e-6
+    Jfd = np.zeros_like(J)
+    x = np.concatenate([Vt, Vb])
+    for k in range(2 * N):
+        xp = x.copy(); xp[k] += h
+        xm = x.copy(); xm[k] -= h
+        Jfd[:, k] = (np.concatenate(O.residual(p, g, vin, xp[:N], xp[N:]))
+                     - np.concatenate(O.residual(p, g, vin, xm[:N], xm[N:]))) / (2 * h)
+    np.testing.assert_allclose(J, Jfd, rtol=1e-7, atol=1e-10)
+    assert (dv < 0).any() and (dv > 0).any()
+
+
+@pytest.mark.parametrize("vin0", [0.7, -0.7])
+def test_asymmetric_device_one_by_one_bisection(vin0):
+    """1x1 array under positive and negative drive: the scalar reduction of the bisection
+    pin with the Yakopcic-form current (a2/a1 = 0.3 on the negative side)."""
+    r_neg = 0.3
+    p = _params(1, 1, b=2.0, neg_ratio=r_neg)
+    g = np.array([[3e-2]])
+    vin = np.array([vin0])
+    gt_end = p.g_src + p.g_term_top_right
+    gb_end = p.g_term_bot_top + p.g_sense
+
+    def cur(u):
+        i = g[0, 0] / p.b * np.sinh(p.b * u)
+        return r_neg * i if u < 0 else i
+
+    def f(u):
+        return gt_end * (u + cur(u) / gb_end) + cur(u) - p.g_src * vin[0]
+
+    lo, hi = -1.0, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    u = 0.5 * (lo + hi)
+    vb = cur(u) / gb_end
+    r = O.newton_solve(p, g, vin, tol=1e-14, linear="direct")
+    assert r.status == "converged"
+    np.testing.assert_allclose(r.Vt[0, 0], u + vb, rtol=1e-12)
+    np.testing.assert_allclose(r.Vb[0, 0], vb, rtol=1e-11)
+    assert (u < 0) == (vin0 < 0)
+
+
+def test_asymmetric_device_newton_matches_dense_bruteforce():
+    rng = np.random.default_rng(29)
+    m, n = 3, 4
+    p = _params(m, n, neg_ratio=0.5)
+    g = 10 ** rng.uniform(-4, -2, size=(m, n))
+    vin = rng.uniform(-0.3, 0.3, size=m)
+    Vt_ref, Vb_ref = _dense_newton(p, g, vin, 1e-13)
+    for lin in ("direct", "pgmres"):
+        r = O.newton_solve(p, g, vin, tol=1e-13, linear=lin)
+        assert r.status == "converged", lin
+        np.testing.assert_allclose(r.Vt, Vt_ref, rtol=1e-7, atol=1e-12)
+        np.testing.assert_allclose(r.Vb, Vb_ref, rtol=1e-7, atol=1e-12)
