@@ -82,8 +82,21 @@ typedef struct mca_params {
   double eta0;               /* relative tolerance of the first linear solve             */
   double eta_max;            /* upper bound of later forcing terms                       */
   int32_t flags;             /* MCA_FLAG_* bit set                                       */
-  int32_t reserved;
+  int32_t device_model;      /* MCA_DEVICE_* (memristor I-V law)                         */
+  double neg_ratio;          /* MCA_DEVICE_YAKOPCIC: current amplitude for dV < 0 over the
+                                one for dV >= 0 (a2/a1, finite and > 0); else ignored    */
 } mca_params;
+
+/* ---- memristor I-V law (Section 2; Section 4 uses Yakopcic's model at programmed
+ * states).  g is each device's small-signal conductance (the conductance map), dV the
+ * top-minus-bottom node voltage:
+ *   MCA_DEVICE_SINH      i = (g/b) sinh(b dV)   (b = 0: i = g dV)
+ *   MCA_DEVICE_YAKOPCIC  the same for dV >= 0 and neg_ratio times it for dV < 0: the
+ *                        Yakopcic form a1 x sinh(b V) / a2 x sinh(b V) with the state x
+ *                        fixed, g = a1 x b and neg_ratio = a2 / a1.  The Jacobian uses the
+ *                        derivative on the side of dV the device is on. */
+#define MCA_DEVICE_SINH 0
+#define MCA_DEVICE_YAKOPCIC 1
 
 /* ---- flags --------------------------------------------------------------------------- */
 #define MCA_FLAG_GRAPHS 1      /* replay each GMRES iteration as a captured CUDA graph      */

@@ -24,6 +24,9 @@ PREC_NONE = 5
 FLAG_GRAPHS = 1
 FLAG_AUTOTUNE = 2
 
+DEVICE_SINH = 0
+DEVICE_YAKOPCIC = 1
+
 OK = 0
 ERR_INVALID_ARG = -1
 ERR_CUDA = -2
@@ -58,7 +61,8 @@ class Params(ctypes.Structure):
         ("max_newton", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("newton_rtol", ctypes.c_double), ("eta0", ctypes.c_double),
         ("eta_max", ctypes.c_double),
-        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("device_model", ctypes.c_int32),
+        ("neg_ratio", ctypes.c_double),
     ]
 
 

@@ -66,6 +66,9 @@ Grid make_grid(const mca_params& p) {
   memcpy(&bits, &lim, sizeof(bits));
   g.dv_lim_bits = bits;
   g.bf = (float)p.b;
+  g.rneg = (p.device_model == MCA_DEVICE_YAKOPCIC) ? p.neg_ratio : 1.0;
+  g.rnegf = (float)g.rneg;
+  g.yak = (g.rneg != 1.0) ? 1 : 0;
   g.gtf = (float)g.gt;
   g.gbf = (float)g.gb;
   g.dt0f = (float)g.dt0;
@@ -128,7 +131,21 @@ __device__ __forceinline__ void device_current(const Grid& gr, double g, double 
   }
 }
 
-// One cell of eq. (F) and the Jacobian diagonal; returns (F_t, F_b, D).
+// Yakopcic-form device: scale the current and the conductance of a device under negative
+// bias (sign read from the bit pattern, on the integer pipe).
+__device__ __forceinline__ void negative_bias(const Grid& gr, double dv, double& cur_over_g,
+                                              double& dg, float& dgf) {
+  const long long bits = __double_as_longlong(dv);
+  if (bits < 0 && bits != (long long)0x8000000000000000ull) {   // dV < 0, not -0
+    cur_over_g *= gr.rneg;
+    dg *= gr.rneg;
+    dgf *= gr.rnegf;
+  }
+}
+
+// One cell of eq. (F) and the Jacobian diagonal; returns (F_t, F_b, D).  YAK: the
+// Yakopcic-form device (a compile-time choice, so the sinh device pays nothing for it).
+template <bool YAK>
 __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
                                               const double* __restrict__ Vt,
                                               const double* __restrict__ Vb, double g,
@@ -154,6 +171,7 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
     dg = g;
     dgf = 0.f;
   }
+  if (YAK) negative_bias(gr, dv, cg, dg, dgf);
   ft = fma(g, cg, ft);
   fb = fma(-g, cg, fb);
 }
@@ -195,6 +213,7 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
 
 // K1: F = blockdiag(G_t, G_b) x + [i; -i] - [Y_t; 0] and D = g cosh(b dV) per cell, with
 // per-block partial sums of ||F||^2 and sum(D).
+template <bool YAK>
 __global__ void __launch_bounds__(kThreads)
 k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ vin,
            const double* __restrict__ x, double* __restrict__ F, double* __restrict__ D,
@@ -220,7 +239,7 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
     const int j = c - i * n;
     double ft, fb, dg;
     float dgf;
-    cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg, dgf);
+    cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg, dgf);
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
@@ -288,7 +307,7 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
 // F[b] is written at F + b*fstride: the solver points it at the first Krylov basis vector,
 // which GMRES keeps unnormalised (v_0 = -F / ||F||, the scale set by the Newton control),
 // and xbf (may be NULL) receives its BF16 copy for the tensor-core preconditioner.
-template <bool ZERO>
+template <bool ZERO, bool YAK>
 __global__ void __launch_bounds__(kThreads)
 k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restrict__ map_of,
                   const double* __restrict__ vin,
@@ -325,7 +344,8 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
       fb = 0.0;
       dg = gmap[c];
     } else {
-      cell_residual(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg, dgf);
+      cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
+                         dgf);
     }
     Ft[c] = ft;
     Fb[c] = fb;
@@ -547,7 +567,10 @@ void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
 void launch_residual(const Grid& gr, const double* gmap, const double* vin, const double* x,
                      double* F, double* D, double* part, int nblk, int B, const VecCtl* ctl,
                      cudaStream_t s) {
-  k_residual<<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
+  if (gr.yak)
+    k_residual<true><<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
+  else
+    k_residual<false><<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
 }
 
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
@@ -556,14 +579,18 @@ void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_
                             double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
                             unsigned int* cnt, int32_t* host_flags, cudaStream_t s) {
   dim3 grid(nblk, B);
+#define MCA_RESN(Z_, Y_)                                                                   \
+  k_residual_newton<Z_, Y_><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, fstride, \
+                                                      xbf, mp, np, D, part, nblk, ctl, cfg,  \
+                                                      cnt, host_flags)
+  // (the zero state has dV = 0 everywhere: no device is under negative bias)
   if (zero_state)
-    k_residual_newton<true><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, fstride,
-                                                      xbf, mp, np, D, part, nblk, ctl, cfg,
-                                                      cnt, host_flags);
+    MCA_RESN(true, false);
+  else if (gr.yak)
+    MCA_RESN(false, true);
   else
-    k_residual_newton<false><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, fstride,
-                                                       xbf, mp, np, D, part, nblk, ctl, cfg,
-                                                       cnt, host_flags);
+    MCA_RESN(false, false);
+#undef MCA_RESN
 }
 
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,

@@ -185,6 +185,14 @@ int validate(const mca_params* p) {
     set_error("b must be finite and >= 0");
     return MCA_ERR_INVALID_ARG;
   }
+  if (p->device_model != MCA_DEVICE_SINH && p->device_model != MCA_DEVICE_YAKOPCIC) {
+    set_error("unknown device_model");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (p->device_model == MCA_DEVICE_YAKOPCIC && !finite_pos(p->neg_ratio)) {
+    set_error("neg_ratio must be finite and > 0");
+    return MCA_ERR_INVALID_ARG;
+  }
   if (p->precision < MCA_PREC_FP64 || p->precision > MCA_PREC_NONE) {
     set_error("unknown precision");
     return MCA_ERR_INVALID_ARG;
@@ -822,6 +830,8 @@ void mca_default_params(mca_params* p) {
   p->g_term_bot_top = 1e-3;
   p->g_sense = 0.1;
   p->b = 2.0;
+  p->device_model = MCA_DEVICE_SINH;
+  p->neg_ratio = 1.0;
   p->precision = MCA_PREC_BF16_SPLIT;
   p->gmres_restart = 30;
   p->max_newton = 20;

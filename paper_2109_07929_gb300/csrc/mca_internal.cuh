@@ -76,6 +76,11 @@ struct Grid {
   double pc[7];
   unsigned long long dv_lim_bits;
   float bf;                 // b in FP32 (for the FP32 conductance)
+  // Yakopcic-form device: currents and conductances of devices with dV < 0 are scaled by
+  // rneg (yak = 0: the symmetric sinh device, rneg = 1)
+  int yak;
+  double rneg;
+  float rnegf;
   // FP32 copies of the wire operators for the FP32 Jacobian apply
   float gtf, gbf, dt0f, dtmf, dtlf, db0f, dbmf, dblf;
   // diagonals of the wire operators (eq. G with terminations): first / inside / last node

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts():
     # mca_params: 2 int32, 7 doubles, 4 int32, 3 doubles, 2 int32
-    assert ctypes.sizeof(mca.Params) == 8 + 7 * 8 + 4 * 4 + 3 * 8 + 8
+    assert ctypes.sizeof(mca.Params) == 8 + 7 * 8 + 4 * 4 + 3 * 8 + 8 + 8
     assert ctypes.sizeof(mca.Stats) == 4 * 4 + 2 * 8
 
 

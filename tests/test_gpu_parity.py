@@ -28,7 +28,8 @@ DEV = "cuda:0"
 def _params(p, **kw):
     base = dict(g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot, g_src=p.g_src,
                 g_term_top_right=p.g_term_top_right, g_term_bot_top=p.g_term_bot_top,
-                g_sense=p.g_sense, b=p.b)
+                g_sense=p.g_sense, b=p.b, neg_ratio=p.neg_ratio,
+                device_model=mca.DEVICE_YAKOPCIC if p.neg_ratio != 1.0 else mca.DEVICE_SINH)
     base.update(kw)
     return mca.default_params(p.rows, p.cols, **base)
 
@@ -85,6 +86,42 @@ def test_residual_and_jacobian_diagonal(m, n, vrange):
         np.testing.assert_allclose(D[v], Dr, rtol=3e-7)
         np.testing.assert_allclose(fn[v], np.linalg.norm(np.concatenate([Ft, Fb])), rtol=1e-12)
         np.testing.assert_allclose(dm[v], Dr.mean(), rtol=3e-7)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (33, 47), (130, 70)])
+def test_yakopcic_residual_and_jacobian_diagonal(m, n):
+    """Yakopcic-form devices (a2/a1 = 0.35) under both polarities: the residual to FP64
+    rounding and the Jacobian diagonal to the FP32 conductance tolerance."""
+    cb = mi.make_crossbar(m, n, 4, nvec=2, neg_ratio=0.35)
+    p = cb.params
+    rng = np.random.default_rng(8)
+    x = rng.uniform(-0.3, 0.3, size=(2, 2 * m * n))
+    with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=2), cb.gmap) as s:
+        F = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
+        D = torch.empty(2, m * n, dtype=torch.float64, device=DEV)
+        fn, dm = s.residual(_t(x), _t(cb.vin), F, D)
+        F = F.cpu().numpy()
+        D = D.cpu().numpy()
+    for v in range(2):
+        dv = x[v, :m * n] - x[v, m * n:]
+        assert (dv < 0).any() or m * n == 1
+        Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], x[v, :m * n], x[v, m * n:])
+        cur = np.abs(O.device_current(cb.gmap.ravel(), p.b, dv, p.neg_ratio)).max()
+        scale = 4 * max(p.g_wire_top, p.g_wire_bot) * np.abs(x[v]).max() + p.g_src * 0.3 + cur
+        np.testing.assert_allclose(F[v], np.concatenate([Ft, Fb]), rtol=0, atol=1e-14 * scale)
+        Dr = O.device_conductance(cb.gmap.ravel(), p.b, dv, p.neg_ratio)
+        np.testing.assert_allclose(D[v], Dr, rtol=3e-7)
+        np.testing.assert_allclose(dm[v], Dr.mean(), rtol=3e-7)
+
+
+@pytest.mark.parametrize("prec", [mca.PREC_FP64, mca.PREC_BF16_SPLIT], ids=["fp64", "bf16split"])
+@pytest.mark.parametrize("m,n", [(1, 1), (48, 40)])
+def test_yakopcic_solve_signed_inputs(m, n, prec):
+    """Newton on Yakopcic-form devices (a2/a1 = 0.5) with inputs of both signs, against
+    the oracle's direct-solve Newton."""
+    cb = mi.make_crossbar(m, n, 19, nvec=3, vmin=-0.3, neg_ratio=0.5)
+    assert (cb.vin < 0).any()
+    _check_solve(cb, prec, 1e-10)
 
 
 @pytest.mark.parametrize("m,n", SHAPES)
