@@ -46,7 +46,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--precision", default="bf16split", choices=["bf16split", "bf16", "fp64"])
+    ap.add_argument("--precision", default="bf16split",
+                    choices=["bf16split", "bf16", "fp64", "mhat"])
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -186,7 +187,7 @@ def run_ours(args):
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     prec = {"bf16split": mca.PREC_BF16_SPLIT, "bf16": mca.PREC_BF16,
-            "fp64": mca.PREC_FP64}[args.precision]
+            "fp64": mca.PREC_FP64, "mhat": mca.PREC_MHAT}[args.precision]
     B = args.batch
     W, K = args.warmup, args.steps
     m = n = args.size
@@ -292,7 +293,8 @@ def run_ours(args):
     fam = max(prof, key=lambda f: prof[f]["ms"])
     fp = prof[fam]
     gemm = fam.startswith("precond")
-    if gemm and prec != mca.PREC_FP64:
+    tc = prec in (mca.PREC_BF16, mca.PREC_BF16_SPLIT)
+    if gemm and tc:
         ach = fp["flops"] / (fp["ms"] / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s"}
@@ -320,13 +322,14 @@ def run_ours(args):
     # precond TFLOP/s in the dense eigenbasis count, 8 m n (m + n) per apply
     pc_ms = sum(prof[f]["ms"] for f in ("precond_1", "precond_2", "precond_3", "precond_4"))
     applies = prof["precond_1"]["flops"] / (4.0 * m * n * n) if prof["precond_1"]["flops"] else 0
-    precond_tflops = applies * 8.0 * m * n * (m + n) / (pc_ms / 1e3) / 1e12 if pc_ms else 0.0
+    precond_tflops = (applies * 8.0 * m * n * (m + n) / (pc_ms / 1e3) / 1e12
+                      if pc_ms and prec != mca.PREC_MHAT else None)
 
     iters = np.array([(a, b_) for a, b_, _ in timed])
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": 1000 * t / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+bf16" if prec != mca.PREC_FP64 else "f64",
+        "vs_baseline": None, "dtype": "f64+bf16" if prec in (mca.PREC_BF16, mca.PREC_BF16_SPLIT) else "f64",
         "data": "synthetic", "config": workload_config(args, B),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
         "precond_tflops": precond_tflops, "kernel_breakdown": breakdown,
