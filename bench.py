@@ -135,6 +135,22 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def job_time(t, pg):
+    """Elapsed time of the whole job: the maximum of the ranks' times (replicas run
+    independently; the slowest one ends the job).  No collective without a process group."""
+    if not pg:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64)
+    pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+    return float(tt[0])
+
+
+def replica_seed(rank):
+    """Each rank solves its own crossbar (no data is shared between ranks)."""
+    return 1000 + rank
+
+
 def oracle_solves(cb, count, start=0):
     """Time `count` oracle solves (Newton + preconditioned GMRES, FP64, NumPy/SciPy)."""
     from oracle import mca_oracle as O
@@ -191,7 +207,7 @@ def run_ours(args):
     B = args.batch
     W, K = args.warmup, args.steps
     m = n = args.size
-    cb = mi.config_large(args.size, 1000 + rank, nvec=(W + max(K, 2 * E2E_PASSES)) * B)
+    cb = mi.config_large(args.size, replica_seed(rank), nvec=(W + max(K, 2 * E2E_PASSES)) * B)
     p = cb.params
     params = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
                                 g_src=p.g_src, g_term_top_right=p.g_term_top_right,
@@ -237,11 +253,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = mca.kernel_launches() - launches0
     clocks = sampler.stop()
-    t = ev0.elapsed_time(ev1) / 1000.0
+    t = job_time(ev0.elapsed_time(ev1) / 1000.0, pg)
     if pg:
-        tt = torch.tensor([t], dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t = float(tt[0])
         pg.barrier()
     value = world * K * B / t
 
@@ -273,11 +286,7 @@ def run_ours(args):
         step_host(W + i * P)
     e1.record(stream)
     torch.cuda.synchronize()
-    te = e0.elapsed_time(e1) / 1000.0
-    if pg:
-        tt = torch.tensor([te], dtype=torch.float64)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        te = float(tt[0])
+    te = job_time(e0.elapsed_time(e1) / 1000.0, pg)
     e2e = {"value": world * ke * P * B / te, "unit": "solves/s",
            "h2d_bytes_per_step": P * B * m * 8,
            "d2h_bytes_per_step": P * B * (2 * m * n + n) * 8 + P * B * mca.ctypes.sizeof(mca.Stats),
