@@ -136,8 +136,11 @@ int mca_create(const mca_params* p, const double* g_map, mca_handle** out);
  *   v_bot : nvec*m*n bottom-layer node voltages out, or NULL.
  *   i_out : nvec*n sensed column currents g_sense * V_b[m-1, j] out, or NULL.
  *   stats : nvec entries out, or NULL.
- *   stream: cudaStream_t to run on (NULL = legacy default stream).  The call returns
- *           after the results are written.
+ *   stream: cudaStream_t to run on (NULL = the handle's own stream, ordered with the
+ *           legacy default stream).  The call returns after the results are written.
+ * More than max_batch vectors run as passes of max_batch; the output copies of a pass run
+ * on an internal stream while the next pass computes (the handle double-buffers its state),
+ * so a call over several batches hides most of the device-to-host traffic.
  * Returns MCA_OK when every vector met newton_rtol, else the first failing status
  * (MCA_ERR_NOT_CONVERGED / MCA_ERR_NONFINITE; outputs are still written), or
  * MCA_ERR_INVALID_ARG / MCA_ERR_CUDA / MCA_ERR_TIMEOUT. */
