@@ -342,6 +342,10 @@ def run_ours(args):
         "data": "synthetic", "config": workload_config(args, B),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
         "precond_tflops": precond_tflops, "kernel_breakdown": breakdown,
+        # summed device time of the timed kernels per step (profile pass) over the timed
+        # step: what is left is host-side gaps (Newton checks, graph launches)
+        "kernel_ms_per_step": total_ms / min(K, 4),
+        "gpu_busy_frac": (total_ms / min(K, 4)) / (1000 * t / K),
         "gemm_tiles": gemm_tiles(solver),
         "newton_iters_per_solve": float(iters[:, 0].mean()),
         "gmres_iters_per_solve": float(iters[:, 1].mean()),
