@@ -48,6 +48,10 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--precision", default="bf16split",
                     choices=["bf16split", "bf16", "fp64", "mhat"])
+    ap.add_argument("--device", default="sinh", choices=["sinh", "yakopcic"],
+                    help="memristor I-V law; yakopcic: a2/a1 = --neg-ratio below zero, "
+                         "inputs of both signs")
+    ap.add_argument("--neg-ratio", type=float, default=0.5)
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -162,9 +166,11 @@ def oracle_solves(cb, count, start=0):
 
 
 def workload_config(args, batch):
+    dev = ("sinh devices b=2, V_in~U[0,0.3] V" if getattr(args, "device", "sinh") == "sinh" else
+           f"Yakopcic-form devices b=2 a2/a1={args.neg_ratio:g}, V_in~U[-0.3,0.3] V")
     return {
         "workload": f"{args.size}x{args.size} MCA, log-uniform g in [1e-6,1e-4] S, wires "
-                    "1 S top / 0.5 S bottom, sinh devices b=2, V_in~U[0,0.3] V, "
+                    f"1 S top / 0.5 S bottom, {dev}, "
                     f"Newton to {TOL:g} rel. KCL residual, FGMRES(30)",
         "rows": args.size, "cols": args.size, "batch_per_step": batch,
         "precision": args.precision, "newton_rtol": TOL,
@@ -172,11 +178,20 @@ def workload_config(args, batch):
     }
 
 
+def make_workload(args, seed, nvec):
+    """The timed crossbar: sinh devices with V_in >= 0, or Yakopcic-form devices
+    (a2/a1 = --neg-ratio) with inputs of both signs."""
+    if getattr(args, "device", "sinh") == "sinh":
+        return mi.config_large(args.size, seed, nvec=nvec)
+    return mi.make_crossbar(args.size, args.size, seed, nvec=nvec, g_wire_bot=0.5,
+                            vmin=-0.3, neg_ratio=args.neg_ratio)
+
+
 def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
-    cb = mi.config_large(args.size, 0, nvec=args.warmup + args.steps)
+    cb = make_workload(args, 0, args.warmup + args.steps)
     oracle_solves(cb, args.warmup)
     t = oracle_solves(cb, args.steps, start=args.warmup)
     value = args.steps / t
@@ -207,12 +222,15 @@ def run_ours(args):
     B = args.batch
     W, K = args.warmup, args.steps
     m = n = args.size
-    cb = mi.config_large(args.size, replica_seed(rank), nvec=(W + max(K, 2 * E2E_PASSES)) * B)
+    cb = make_workload(args, replica_seed(rank), (W + max(K, 2 * E2E_PASSES)) * B)
     p = cb.params
     params = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
                                 g_src=p.g_src, g_term_top_right=p.g_term_top_right,
                                 g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
-                                precision=prec, newton_rtol=TOL, max_batch=B)
+                                precision=prec, newton_rtol=TOL, max_batch=B,
+                                device_model=(mca.DEVICE_SINH if args.device == "sinh"
+                                              else mca.DEVICE_YAKOPCIC),
+                                neg_ratio=p.neg_ratio)
     solver = mca.Solver(params, cb.gmap)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -359,7 +377,8 @@ def run_ours(args):
         p64 = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
                                  g_src=p.g_src, g_term_top_right=p.g_term_top_right,
                                  g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
-                                 precision=mca.PREC_FP64, newton_rtol=TOL, max_batch=1)
+                                 precision=mca.PREC_FP64, newton_rtol=TOL, max_batch=1,
+                                 device_model=params.device_model, neg_ratio=p.neg_ratio)
         with mca.Solver(p64, cb.gmap) as s64:
             vt1 = torch.empty(1, m, n, dtype=torch.float64, device=dev)
             vb1 = torch.empty_like(vt1)
