@@ -254,6 +254,26 @@ int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nve
 int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* w,
                        int32_t nvec, void* stream);
 
+/* The same apply with z in FP32, as the solver takes it from the tensor-core
+ * preconditioner (eq. (J); Section 3.1 for the operator).  mode picks the arithmetic:
+ *   MCA_APPLY_PAIR : FP32 pairs, the solver's form for the BF16 and BF16_SPLIT
+ *                    preconditioners: z and the neighbours enter error-free FP32 products
+ *                    with the wire conductances and D (each split into two FP32 halves)
+ *                    and error-free FP32 sums; the low parts are summed in FP32 and the
+ *                    result is rounded once to FP64.  Error within about 2^-45 of the
+ *                    sum of |diag z|, |g_wire (z_left + z_right)|, |D (z_t - z_b)|.
+ *   MCA_APPLY_F64  : FP64 arithmetic on z widened exactly (error within about 2^-51).
+ *   MCA_APPLY_F32  : FP32 arithmetic, w rounded to FP32 (the solver's first Newton step
+ *                    when eta0 >= 1e-4).
+ *   D : device, nvec * m*n (FP64);  z : device, nvec * 2*m*n (FP32);  w : device out,
+ *   nvec * 2*m*n (FP64).  Returns MCA_ERR_INVALID_ARG for a null pointer, nvec outside
+ *   1..max_batch or an unknown mode. */
+#define MCA_APPLY_PAIR 0
+#define MCA_APPLY_F64 1
+#define MCA_APPLY_F32 2
+int mca_jacobian_apply_f32(mca_handle* h, const double* D, const float* z, double* w,
+                           int32_t nvec, int32_t mode, void* stream);
+
 /* Preconditioner apply z = P^-1 r (eqs. (P), (block), (M)) with a1 = a2 = a[v] per
  * vector, in the given MCA_PREC_* precision (FP64, BF16, BF16_SPLIT or MHAT; the
  * tensor-core forms need a handle created with one of them).

@@ -27,6 +27,10 @@ FLAG_AUTOTUNE = 2
 DEVICE_SINH = 0
 DEVICE_YAKOPCIC = 1
 
+APPLY_PAIR = 0
+APPLY_F64 = 1
+APPLY_F32 = 2
+
 OK = 0
 ERR_INVALID_ARG = -1
 ERR_CUDA = -2
@@ -38,7 +42,8 @@ ERR_UNSUPPORTED = -7
 
 EXPORTED = (
     "mca_default_params", "mca_create", "mca_solve", "mca_destroy", "mca_strerror",
-    "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_precond_apply",
+    "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_jacobian_apply_f32",
+    "mca_precond_apply",
     "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
     "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
     "mca_solve_many", "mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
@@ -115,6 +120,7 @@ def load(build_if_missing=True):
     lib.mca_last_error_message.restype = ctypes.c_char_p
     lib.mca_residual.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P]
     lib.mca_jacobian_apply.argtypes = [P, P, P, P, ctypes.c_int32, P]
+    lib.mca_jacobian_apply_f32.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
     lib.mca_precond_apply.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
     lib.mca_eigenpairs.argtypes = [P, P, P, P, P]
     lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double,
@@ -144,7 +150,7 @@ def load(build_if_missing=True):
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
     for name in ("mca_create", "mca_create_multi", "mca_solve_multi", "mca_solve_many",
-                 "mca_solve", "mca_residual", "mca_jacobian_apply",
+                 "mca_solve", "mca_residual", "mca_jacobian_apply", "mca_jacobian_apply_f32",
                  "mca_precond_apply", "mca_eigenpairs", "mca_gmres_solve", "mca_profile",
                  "mca_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
@@ -368,6 +374,12 @@ class Solver:
     def jacobian_apply(self, D, z, w, stream=None):
         _check(self.lib.mca_jacobian_apply(self.h, _ptr(D), _ptr(z), _ptr(w), z.shape[0],
                                            _stream_ptr(stream)))
+
+    def jacobian_apply_f32(self, D, z, w, mode=None, stream=None):
+        """w = J z with FP32 z; mode APPLY_PAIR (the solver's form), APPLY_F64 or APPLY_F32."""
+        _check(self.lib.mca_jacobian_apply_f32(self.h, _ptr(D), _ptr(z), _ptr(w), z.shape[0],
+                                               APPLY_PAIR if mode is None else mode,
+                                               _stream_ptr(stream)))
 
     def precond_apply(self, a, r, z, precision=None, stream=None):
         a = np.ascontiguousarray(a, np.float64)

@@ -16,6 +16,7 @@
 
 #include "bits.cuh"
 #include "mca_internal.cuh"
+#include "twofloat.cuh"
 
 namespace mca {
 
@@ -34,6 +35,9 @@ constexpr double kSinhPoly[7] = {
   2.50509370460377762e-08,      // t^5
   1.62102664139390868e-10,      // t^6
 };
+
+// x - (double)(float)x rounded to FP32: the low half of x as an FP32 pair
+float low_part(double x) { return (float)(x - (double)(float)x); }
 
 }  // namespace
 
@@ -57,8 +61,11 @@ Grid make_grid(const mca_params& p) {
   g.dbl = g.gb + g.g_sense;
   // fold b into the polynomial: x = b dV, t = x^2 = b^2 dV^2
   double b2k = 1.0;
+  g.tail32 = 1;
   for (int k = 0; k < 7; ++k) {
     g.pc[k] = kSinhPoly[k] * b2k;
+    g.pcf[k] = (float)g.pc[k];
+    if (k >= 3 && !(g.pc[k] >= 1e-30 && g.pc[k] <= 1e30)) g.tail32 = 0;
     b2k *= p.b * p.b;
   }
   const double lim = (p.b != 0.0) ? kSinhPolyX / fabs(p.b) : 0.0;
@@ -77,6 +84,14 @@ Grid make_grid(const mca_params& p) {
   g.db0f = (float)g.db0;
   g.dbmf = (float)g.dbm;
   g.dblf = (float)g.dbl;
+  g.gtl = low_part(g.gt);
+  g.gbl = low_part(g.gb);
+  g.dt0l = low_part(g.dt0);
+  g.dtml = low_part(g.dtm);
+  g.dtll = low_part(g.dtl);
+  g.db0l = low_part(g.db0);
+  g.dbml = low_part(g.dbm);
+  g.dbll = low_part(g.dbl);
   return g;
 }
 
@@ -101,10 +116,14 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 }
 
 // Memristor current and conductance.  The current (g / b) sinh(b dV) = g dV P(dV^2) with
-// P(dV^2) = sinh(x) / x, x = b dV, enters the KCL residual and is kept in FP64: for
-// |x| < 3/4, P is the degree-6 economised polynomial above with b folded into its
-// coefficients (Horner, 6 FMAs); outside that range the CUDA math library.  The range
-// test compares bit patterns (on the integer pipe).  The conductance g cosh(x) only
+// P(dV^2) = sinh(x) / x, x = b dV, enters the KCL residual and is kept to FP64 accuracy:
+// for |x| < 3/4, P is the degree-6 economised polynomial above with b folded into its
+// coefficients, evaluated by Horner's rule in FP64 for the terms up to t^2 and, when
+// tail32, in FP32 for the tail t^3 (pc3 + pc4 t + pc5 t^2 + pc6 t^3): that tail is at
+// most x^6 / 5040 < 3.5e-5 of P, so its FP32 rounding (a few 2^-24) moves P by less than
+// 1e-11 relative, while it takes three FMAs off the FP64 pipe.  Outside |x| < 3/4 the
+// CUDA math library.  The range test compares bit patterns (on the integer pipe).
+// The conductance g cosh(x) only
 // shapes the Newton matrix (the Jacobian diagonal and a = mean(D)), so it is evaluated in
 // FP32 (relative error below 3e-7, which changes the inexact Newton steps but not the
 // solution the FP64 residual drives them to) and returned both as float and widened.
@@ -113,15 +132,25 @@ __device__ __forceinline__ void device_current(const Grid& gr, double g, double 
   const unsigned long long ab = (unsigned long long)__double_as_longlong(dv) & 0x7FFFFFFFFFFFFFFFull;
   if (ab < gr.dv_lim_bits) {
     const double t = dv * dv;
-    double ps = gr.pc[6];
-    ps = fma(ps, t, gr.pc[5]);
-    ps = fma(ps, t, gr.pc[4]);
-    ps = fma(ps, t, gr.pc[3]);
-    ps = fma(ps, t, gr.pc[2]);
+    const float dvf = d2f_round(dv);
+    double ps;
+    if (gr.tail32) {
+      const float tf = dvf * dvf;
+      float r = fmaf(gr.pcf[6], tf, gr.pcf[5]);
+      r = fmaf(r, tf, gr.pcf[4]);
+      r = fmaf(r, tf, gr.pcf[3]);
+      ps = fma(f2d_bits(r), t, gr.pc[2]);
+    } else {
+      ps = gr.pc[6];
+      ps = fma(ps, t, gr.pc[5]);
+      ps = fma(ps, t, gr.pc[4]);
+      ps = fma(ps, t, gr.pc[3]);
+      ps = fma(ps, t, gr.pc[2]);
+    }
     ps = fma(ps, t, gr.pc[1]);
     ps = fma(ps, t, gr.pc[0]);
     cur_over_g = dv * ps;
-    dgf = d2f_round(g) * coshf(d2f_round(dv) * gr.bf);
+    dgf = d2f_round(g) * coshf(dvf * gr.bf);
     dg = f2d_bits(dgf);
   } else {
     const double x = gr.b * dv;
@@ -434,7 +463,42 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
 
-template <int KP, typename ZT, bool F32>
+// One cell of w = J z in FP32 pairs (ApplyMode kApplyPair).  The FP32 inputs a = z_t,
+// bb = z_b and the neighbours enter error-free products with the FP32 halves of the wire
+// constants and of D, and error-free sums; the low parts (each within 2^-24 of its term)
+// are added in FP32 and the pair is rounded once to FP64.  D (a - bb) is shared by the
+// two layers.  FP64 work: splitting D and the two final additions.
+__device__ __forceinline__ void apply_pair(float a, float bb, float tl, float tr, float bu,
+                                           float bd, double Dd, float dth, float dtl,
+                                           float dbh, float dbl, const Grid& gr, double& ot,
+                                           double& ob) {
+  const float dh = d2f_round(Dd);
+  const float dl = d2f_round(Dd - f2d_bits(dh));
+  float ed, e3;
+  const float d = two_sum(a, -bb, ed);
+  const float p3 = two_prod(dh, d, e3);
+  const float t3 = fmaf(dl, d, fmaf(dh, ed, e3));           // D (a - bb) = p3 + t3
+  // top: dt a - gt (tl + tr) + D (a - bb)
+  float es, e1, e2, eu, ev;
+  const float st = two_sum(tl, tr, es);
+  const float p1 = two_prod(dth, a, e1);
+  const float p2 = two_prod(gr.gtf, st, e2);
+  const float u = two_sum(p1, -p2, eu);
+  const float v = two_sum(u, p3, ev);
+  const float lt = (fmaf(dtl, a, e1) - fmaf(gr.gtl, st, fmaf(gr.gtf, es, e2))) + (t3 + (eu + ev));
+  // bottom: db bb - gb (bu + bd) - D (a - bb)
+  float fs, f1, f2, fu, fv;
+  const float sb = two_sum(bu, bd, fs);
+  const float q1 = two_prod(dbh, bb, f1);
+  const float q2 = two_prod(gr.gbf, sb, f2);
+  const float ub = two_sum(q1, -q2, fu);
+  const float vb = two_sum(ub, -p3, fv);
+  const float lb = (fmaf(dbl, bb, f1) - fmaf(gr.gbl, sb, fmaf(gr.gbf, fs, f2))) + ((fu + fv) - t3);
+  ot = f2d_bits(v) + f2d_bits(lt);
+  ob = f2d_bits(vb) + f2d_bits(lb);
+}
+
+template <int KP, typename ZT, int AM>
 __global__ void __launch_bounds__(kThreads)
 k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
             size_t zstride, double* __restrict__ w, const double* __restrict__ V,
@@ -457,7 +521,14 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
     const int i = c / n;
     const int jj = c - i * n;
     double ot, ob;
-    if constexpr (F32) {
+    if constexpr (AM == kApplyPair) {
+      const bool f = (jj == 0), l = (jj == n - 1), u = (i == 0), dn = (i == m - 1);
+      apply_pair(zt[c], zb[c], f ? 0.f : (float)zt[c - 1], l ? 0.f : (float)zt[c + 1],
+                 u ? 0.f : (float)zb[c - n], dn ? 0.f : (float)zb[c + n], Db[c],
+                 f ? gr.dt0f : (l ? gr.dtlf : gr.dtmf), f ? gr.dt0l : (l ? gr.dtll : gr.dtml),
+                 u ? gr.db0f : (dn ? gr.dblf : gr.dbmf), u ? gr.db0l : (dn ? gr.dbll : gr.dbml),
+                 gr, ot, ob);
+    } else if constexpr (AM == kApplyF32) {
       // FP32 apply (z is FP32 here): the same formula, rounded to FP32, widened exactly
       const float a = zt[c], bb = zb[c];
       const float cpl = d2f_round(Db[c]) * (a - bb);
@@ -602,7 +673,7 @@ void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
   k_init_basis<<<dim3(nb, B), kThreads, 0, s>>>(F, sign, V0, vstride, xbf, mp, np, m, n, ctl);
 }
 
-template <typename ZT, bool F32>
+template <typename ZT, int AM>
 void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, double* w,
                const double* V, size_t vstride, int nk, double* part, int nblk, int B,
                const VecCtl* ctl, unsigned int* cnt, double* h, cudaStream_t s) {
@@ -610,7 +681,7 @@ void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, dou
   // 0 of batch entry 0 (nk vectors N2 apart, entries vstride apart), or NULL.
   dim3 grid(nblk, B);
 #define MCA_SPMV(KP_)                                                                      \
-  k_spmv_dots<KP_, ZT, F32><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, \
+  k_spmv_dots<KP_, ZT, AM><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, \
                                                       part, nblk, ctl, cnt, h)
   if (nk <= 1) MCA_SPMV(1);
   else if (nk <= 2) MCA_SPMV(2);
@@ -625,19 +696,23 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
                       cudaStream_t s) {
-  spmv_dots<double, false>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h,
+  spmv_dots<double, kApplyF64>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h,
                            s);
 }
 
 void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
-                      cudaStream_t s, bool f32) {
-  if (f32)
-    spmv_dots<float, true>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h, s);
+                      cudaStream_t s, int apply) {
+  if (apply == kApplyF32)
+    spmv_dots<float, kApplyF32>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt,
+                                h, s);
+  else if (apply == kApplyF64)
+    spmv_dots<float, kApplyF64>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt,
+                                h, s);
   else
-    spmv_dots<float, false>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt, h,
-                            s);
+    spmv_dots<float, kApplyPair>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt,
+                                 h, s);
 }
 
 void launch_outputs(const Grid& gr, const double* vin, const double* x, double* i_out,

@@ -642,7 +642,7 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
                           true));
     t0 = prof_begin(h, s);
     launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
-                     h->ctl, h->cnt, h->h1, s, f32);
+                     h->ctl, h->cnt, h->h1, s, f32 ? kApplyF32 : kApplyPair);
   } else {
     double* zk = h->Z + (size_t)k * n2;
     MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k));
@@ -651,9 +651,10 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
                      h->ctl, h->cnt, h->h1, s);
   }
   count_launches(1);
-  // FP64 flops: the stencil's 12 per cell only when the apply runs in FP64
+  // FP64 flops per cell: the stencil's 12 when the apply runs in FP64 (FP64 z), 3 in the
+  // FP32-pair apply (splitting D, forming the two results), none in the FP32 apply
   prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * ((tc ? 32.0 : 40.0) + 16.0 * nk),
-           cells * ((f32 ? 0.0 : 12.0) + 4.0 * nk), s);
+           cells * ((tc ? (f32 ? 0.0 : 3.0) : 12.0) + 4.0 * nk), s);
   double* vnext = h->V + (size_t)(k + 1) * n2;
   __nv_bfloat16* xbf = tc ? h->Xbf : nullptr;
   t0 = prof_begin(h, s);
@@ -1253,6 +1254,31 @@ int mca_jacobian_apply(mca_handle* h, const double* D, const double* z, double* 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_spmv_dots(h->gr, D, z, h->n2, w, nullptr, 0, 0, h->part, residual_nblk((int)h->mn),
                    nvec, nullptr, nullptr, nullptr, s);
+  count_launches(1);
+  MCA_CUDA_TRY(cudaGetLastError());
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  return MCA_OK;
+}
+
+int mca_jacobian_apply_f32(mca_handle* h, const double* D, const float* z, double* w,
+                           int32_t nvec, int32_t mode, void* stream) {
+  g_last_error.clear();
+  if (!h || !D || !z || !w || nvec < 1 || nvec > h->Bmax) {
+    set_error("bad arguments (nvec must be in 1..max_batch)");
+    return MCA_ERR_INVALID_ARG;
+  }
+  int apply;
+  switch (mode) {
+    case MCA_APPLY_PAIR: apply = kApplyPair; break;
+    case MCA_APPLY_F64: apply = kApplyF64; break;
+    case MCA_APPLY_F32: apply = kApplyF32; break;
+    default:
+      set_error("mode must be MCA_APPLY_PAIR, MCA_APPLY_F64 or MCA_APPLY_F32");
+      return MCA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  launch_spmv_dots(h->gr, D, z, h->n2, w, nullptr, 0, 0, h->part, residual_nblk((int)h->mn),
+                   nvec, nullptr, nullptr, nullptr, s, apply);
   count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
   MCA_CUDA_TRY(cudaStreamSynchronize(s));

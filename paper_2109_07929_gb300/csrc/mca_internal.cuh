@@ -75,14 +75,21 @@ struct Grid {
   // folded into its coefficients
   double pc[7];
   unsigned long long dv_lim_bits;
+  // the tail pc[3] + pc[4] t + pc[5] t^2 + pc[6] t^3 in FP32 (pcf) when tail32: at most
+  // 3.5e-5 of the polynomial, so FP32 rounding there costs below 1e-11 relative; tail32
+  // is off when a folded coefficient leaves [1e-30, 1e30] (b outside about [0.02, 4000])
+  float pcf[7];
+  int tail32;
   float bf;                 // b in FP32 (for the FP32 conductance)
   // Yakopcic-form device: currents and conductances of devices with dV < 0 are scaled by
   // rneg (yak = 0: the symmetric sinh device, rneg = 1)
   int yak;
   double rneg;
   float rnegf;
-  // FP32 copies of the wire operators for the FP32 Jacobian apply
+  // FP32 copies of the wire operators for the FP32 Jacobian apply (each rounded to
+  // nearest), and the FP32 remainders x - (double)xf for the pair apply
   float gtf, gbf, dt0f, dtmf, dtlf, db0f, dbmf, dblf;
+  float gtl, gbl, dt0l, dtml, dtll, db0l, dbml, dbll;
   // diagonals of the wire operators (eq. G with terminations): first / inside / last node
   double dt0, dtm, dtl;     // top row, along j
   double db0, dbm, dbl;     // bottom column, along i
@@ -180,13 +187,20 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
                       cudaStream_t s);
-// the same with z in FP32 (the tensor-core preconditioner's output, widened exactly);
-// f32: the Jacobian apply itself in FP32 (w = J z rounded to FP32, then widened; the
-// dots stay FP64), for linear solves whose forcing term is loose (kF32ApplyMinEta)
+// The same with z in FP32 (the tensor-core preconditioner's output).  apply picks the
+// arithmetic of w = J z; the dots stay FP64 in every mode:
+//   kApplyPair: FP32 pairs (error-free products and sums of the FP32 z with the wire
+//     constants and D split into FP32 pairs), rounded once to FP64; the error stays
+//     within about 2^-45 of the size of the terms, against 2^-51 for kApplyF64, and the FP64
+//     pipe only splits D and forms the two results (3 operations per cell instead of 8);
+//   kApplyF64: FP64 on z widened exactly;
+//   kApplyF32: plain FP32 (w rounded to FP32, then widened), for linear solves whose
+//     forcing term is loose (kF32ApplyMinEta).
+enum ApplyMode { kApplyF64 = 0, kApplyF32 = 1, kApplyPair = 2 };
 void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
-                      cudaStream_t s, bool f32 = false);
+                      cudaStream_t s, int apply);
 // Smallest forcing term at which a Newton step's Jacobian applies run in FP32.  FP32
 // rounding of J z is relative to the wire terms, which cancel heavily, so it leaves a
 // floor on the linear residual (near 1e-5 relative in an FP32 model of the solver); the

@@ -13,6 +13,7 @@ Tolerances:
 """
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import mca_inputs as mi
 from oracle import mca_oracle as O
@@ -88,6 +89,33 @@ def test_residual_and_jacobian_diagonal(m, n, vrange):
         np.testing.assert_allclose(dm[v], Dr.mean(), rtol=3e-7)
 
 
+@pytest.mark.parametrize("b", [0.01, 5000.0])
+def test_residual_outside_fp32_tail_range(b):
+    """b = 0.01 and b = 5000 put the polynomial's folded tail coefficients outside the FP32
+    range the kernel allows, so the whole polynomial runs in FP64; both branches of
+    |b dV| < 3/4 are hit.  Same bar as above."""
+    m, n = 40, 37
+    cb = mi.make_crossbar(m, n, 21, nvec=2, b=b)
+    p = cb.params
+    rng = np.random.default_rng(22)
+    x = rng.uniform(-0.3 / b, 1.2 / b, size=(2, 2 * m * n))
+    with mca.Solver(_params(p, precision=mca.PREC_FP64, max_batch=2), cb.gmap) as s:
+        F = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
+        D = torch.empty(2, m * n, dtype=torch.float64, device=DEV)
+        s.residual(_t(x), _t(cb.vin), F, D)
+        F = F.cpu().numpy()
+        D = D.cpu().numpy()
+    for v in range(2):
+        dv = x[v, :m * n] - x[v, m * n:]
+        assert (np.abs(b * dv) < 0.75).any() and (np.abs(b * dv) > 0.75).any()
+        Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], x[v, :m * n], x[v, m * n:])
+        cur = np.abs(cb.gmap.ravel() / p.b * np.sinh(p.b * dv)).max()
+        scale = 4 * max(p.g_wire_top, p.g_wire_bot) * np.abs(x[v]).max() + p.g_src * 0.3 + cur
+        np.testing.assert_allclose(F[v], np.concatenate([Ft, Fb]), rtol=0, atol=1e-14 * scale)
+        Dr = O.device_conductance(cb.gmap.ravel(), p.b, dv)
+        np.testing.assert_allclose(D[v], Dr, rtol=3e-7)
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (33, 47), (130, 70)])
 def test_yakopcic_residual_and_jacobian_diagonal(m, n):
     """Yakopcic-form devices (a2/a1 = 0.35) under both polarities: the residual to FP64
@@ -141,6 +169,74 @@ def test_jacobian_apply(m, n):
     for v in range(2):
         ref = J @ z[v]
         np.testing.assert_allclose(w[v], ref, rtol=0, atol=1e-14 * 8 * np.abs(z[v]).max())
+
+
+@pytest.mark.parametrize("wires", ["unit", "odd"])
+@pytest.mark.parametrize("m,n", SHAPES + [(256, 256)])
+def test_jacobian_apply_fp32_z(m, n, wires):
+    """w = J z with FP32 z in the three arithmetics of the solver, against the definition,
+    each row's error relative to the size of its terms (|J| |z|): the FP32-pair form within
+    2^-44 (a few roundings of its low parts, each 2^-48 of the terms; an exact-arithmetic
+    model of these inputs peaks at 2^-45.9), the FP64 form within 2^-50 (five FP64
+    roundings), the FP32 form within 2^-20 (eight FP32 roundings, constants included).  "odd" wire and
+    termination conductances are not FP32 numbers, so their low halves are exercised; half
+    of the D values are FP32 numbers (as from the FP32 conductance) and half are not.  The
+    second vector is smooth (neighbours nearly equal), where the wire terms cancel to a few
+    parts in 1e4 of their size."""
+    kw = {} if wires == "unit" else dict(g_wire_top=0.7, g_wire_bot=0.3, g_src=1.3,
+                                         g_term_top_right=1e-3 / 3, g_term_bot_top=1e-3 / 7,
+                                         g_sense=1.1)
+    cb = mi.make_crossbar(m, n, 9, **kw)
+    p = cb.params
+    rng = np.random.default_rng(12)
+    xt = rng.uniform(0, 0.3, size=m * n)
+    xb = rng.uniform(0, 0.1, size=m * n)
+    Dr = O.device_conductance(cb.gmap.ravel(), p.b, xt - xb)
+    Dr[::2] = Dr[::2].astype(np.float32).astype(np.float64)
+    Gt, Gb = O.layer_operators(p)
+    Dm = sp.diags(Dr)
+    J = sp.bmat([[Gt + Dm, -Dm], [-Dm, Gb + Dm]], format="csr")
+    z = np.empty((2, 2 * m * n), dtype=np.float32)
+    z[0] = rng.standard_normal(2 * m * n)
+    ii, jj = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    smooth = np.sin(0.01 * ii + 0.013 * jj).ravel()
+    z[1] = np.concatenate([smooth, 0.5 * smooth]) * (1 + 1e-4 * rng.standard_normal(2 * m * n))
+    z64 = z.astype(np.float64)
+    # per-row size of the terms of J z: |diag z_i| + sum |offdiag z_j|
+    Jabs = np.abs(J)
+    out = {}
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, max_batch=2), cb.gmap) as s:
+        Dd = _t(np.stack([Dr, Dr]))
+        zd = torch.as_tensor(z, device=DEV)
+        for mode in (mca.APPLY_PAIR, mca.APPLY_F64, mca.APPLY_F32):
+            w = torch.empty(2, 2 * m * n, dtype=torch.float64, device=DEV)
+            s.jacobian_apply_f32(Dd, zd, w, mode=mode)
+            out[mode] = w.cpu().numpy()
+    for v in range(2):
+        ref = J @ z64[v]
+        size = Jabs @ np.abs(z64[v])
+        for mode, bound in ((mca.APPLY_PAIR, 2.0 ** -44), (mca.APPLY_F64, 2.0 ** -50),
+                            (mca.APPLY_F32, 2.0 ** -20)):
+            err = np.abs(out[mode][v] - ref)
+            assert (err <= bound * size).all(), (mode, v, (err / np.maximum(size, 1e-300)).max())
+    # the cancellation case separates the forms: relative to the result itself, the
+    # FP32 form is far off where the pair form is not
+    ref = J @ z64[1]
+    if m * n > 1:
+        rel = lambda w: np.linalg.norm(w - ref) / np.linalg.norm(ref)  # noqa: E731
+        assert rel(out[mca.APPLY_PAIR][1]) < 1e-11
+        assert rel(out[mca.APPLY_F32][1]) > 100 * rel(out[mca.APPLY_PAIR][1])
+
+
+def test_jacobian_apply_fp32_z_rejects_bad_mode():
+    cb = mi.make_crossbar(8, 8, 1)
+    with mca.Solver(_params(cb.params, precision=mca.PREC_BF16_SPLIT, max_batch=1),
+                    cb.gmap) as s:
+        D = _t(np.ones((1, 64)))
+        z = torch.zeros(1, 128, dtype=torch.float32, device=DEV)
+        w = torch.empty(1, 128, dtype=torch.float64, device=DEV)
+        with pytest.raises(RuntimeError):
+            s.jacobian_apply_f32(D, z, w, mode=7)
 
 
 @pytest.mark.parametrize("m,n", SHAPES + [(256, 256)])
