@@ -42,7 +42,8 @@ ERR_UNSUPPORTED = -7
 
 EXPORTED = (
     "mca_default_params", "mca_create", "mca_solve", "mca_destroy", "mca_strerror",
-    "mca_last_error_message", "mca_residual", "mca_jacobian_apply", "mca_jacobian_apply_f32",
+    "mca_last_error_message", "mca_residual", "mca_residual_pair", "mca_jacobian_apply",
+    "mca_jacobian_apply_f32",
     "mca_precond_apply",
     "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
     "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
@@ -121,6 +122,7 @@ def load(build_if_missing=True):
     lib.mca_residual.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P]
     lib.mca_jacobian_apply.argtypes = [P, P, P, P, ctypes.c_int32, P]
     lib.mca_jacobian_apply_f32.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
+    lib.mca_residual_pair.argtypes = [P, P, P, ctypes.c_int32, P, P, P, P, P, P]
     lib.mca_precond_apply.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P]
     lib.mca_eigenpairs.argtypes = [P, P, P, P, P]
     lib.mca_gmres_solve.argtypes = [P, P, P, P, P, ctypes.c_int32, ctypes.c_double,
@@ -150,7 +152,8 @@ def load(build_if_missing=True):
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
     for name in ("mca_create", "mca_create_multi", "mca_solve_multi", "mca_solve_many",
-                 "mca_solve", "mca_residual", "mca_jacobian_apply", "mca_jacobian_apply_f32",
+                 "mca_solve", "mca_residual", "mca_residual_pair", "mca_jacobian_apply",
+                 "mca_jacobian_apply_f32",
                  "mca_precond_apply", "mca_eigenpairs", "mca_gmres_solve", "mca_profile",
                  "mca_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
@@ -370,6 +373,16 @@ class Solver:
         _check(self.lib.mca_residual(self.h, _ptr(x), _ptr(vin), nvec, _ptr(F), _ptr(D),
                                      _ptr(fn), _ptr(dm), _stream_ptr(stream)))
         return fn, dm
+
+    def residual_pair(self, x, vin, F, D, stream=None):
+        """The FP32-pair residual; returns (||F||, mean(D), error bound on ||F||)."""
+        nvec = x.shape[0]
+        fn = np.zeros(nvec)
+        dm = np.zeros(nvec)
+        fe = np.zeros(nvec)
+        _check(self.lib.mca_residual_pair(self.h, _ptr(x), _ptr(vin), nvec, _ptr(F), _ptr(D),
+                                          _ptr(fn), _ptr(dm), _ptr(fe), _stream_ptr(stream)))
+        return fn, dm, fe
 
     def jacobian_apply(self, D, z, w, stream=None):
         _check(self.lib.mca_jacobian_apply(self.h, _ptr(D), _ptr(z), _ptr(w), z.shape[0],

@@ -12,6 +12,7 @@
 // kernels keep FP64 instructions per cell low: diagonals are precomputed per position
 // class, and the device model uses a short economised polynomial for sinh and FP32 cosh
 // instead of the FP64 library functions.
+#include <cmath>
 #include <cstring>
 
 #include "bits.cuh"
@@ -71,10 +72,16 @@ Grid make_grid(const mca_params& p) {
   const double lim = (p.b != 0.0) ? kSinhPolyX / fabs(p.b) : 0.0;
   unsigned long long bits;
   memcpy(&bits, &lim, sizeof(bits));
-  g.dv_lim_bits = bits;
+  g.dv_lim_hi = (uint32_t)(bits >> 32);
   g.bf = (float)p.b;
+  g.pc1l = low_part(g.pc[1]);
+  g.pc2l = low_part(g.pc[2]);
+  g.dv_limf = (float)lim;
+  g.gsrcf = (float)g.g_src;
+  g.gsrcl = low_part(g.g_src);
   g.rneg = (p.device_model == MCA_DEVICE_YAKOPCIC) ? p.neg_ratio : 1.0;
   g.rnegf = (float)g.rneg;
+  g.rnegl = low_part(g.rneg);
   g.yak = (g.rneg != 1.0) ? 1 : 0;
   g.gtf = (float)g.gt;
   g.gbf = (float)g.gb;
@@ -115,6 +122,25 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
+// Block-wide sum of three values; result valid in thread 0.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double sa[kThreads / 32], sb[kThreads / 32], sc[kThreads / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; sc[w] = c; }
+  __syncthreads();
+  if (w == 0) {
+    a = (l < kThreads / 32) ? sa[l] : 0.0;
+    b = (l < kThreads / 32) ? sb[l] : 0.0;
+    c = (l < kThreads / 32) ? sc[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+  }
+}
+
 // Memristor current and conductance.  The current (g / b) sinh(b dV) = g dV P(dV^2) with
 // P(dV^2) = sinh(x) / x, x = b dV, enters the KCL residual and is kept to FP64 accuracy:
 // for |x| < 3/4, P is the degree-6 economised polynomial above with b folded into its
@@ -129,8 +155,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 // solution the FP64 residual drives them to) and returned both as float and widened.
 __device__ __forceinline__ void device_current(const Grid& gr, double g, double dv,
                                                double& cur_over_g, double& dg, float& dgf) {
-  const unsigned long long ab = (unsigned long long)__double_as_longlong(dv) & 0x7FFFFFFFFFFFFFFFull;
-  if (ab < gr.dv_lim_bits) {
+  // (the high words suffice: both branches are accurate near the limit)
+  if (((uint32_t)__double2hiint(dv) & 0x7FFFFFFFu) < gr.dv_lim_hi) {
     const double t = dv * dv;
     const float dvf = d2f_round(dv);
     double ps;
@@ -164,8 +190,8 @@ __device__ __forceinline__ void device_current(const Grid& gr, double g, double 
 // bias (sign read from the bit pattern, on the integer pipe).
 __device__ __forceinline__ void negative_bias(const Grid& gr, double dv, double& cur_over_g,
                                               double& dg, float& dgf) {
-  const long long bits = __double_as_longlong(dv);
-  if (bits < 0 && bits != (long long)0x8000000000000000ull) {   // dV < 0, not -0
+  const uint32_t hi = (uint32_t)__double2hiint(dv), lo = (uint32_t)__double2loint(dv);
+  if ((hi >> 31) && ((hi & 0x7FFFFFFFu) | lo)) {   // dV < 0, not -0
     cur_over_g *= gr.rneg;
     dg *= gr.rneg;
     dgf *= gr.rnegf;
@@ -205,6 +231,132 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
   fb = fma(-g, cg, fb);
 }
 
+// ---- the residual in FP32 pairs ------------------------------------------------------
+//
+// The same cell as cell_residual with every FP64 operand split into an FP32 pair
+// (d2f_round / d2f_low, integer pipe) and every product and sum formed error-free
+// (two_prod, two_sum); the low parts are summed in FP32 and each result is rounded once to
+// FP64.  Besides F and D the cell returns the size of its terms (|wire diagonal x| +
+// |wire coupling sum| + |current| + |source|, per layer), from which the Newton control
+// bounds the error of ||F||: kPairErrScale times the 2-norm of those sizes.  The exact
+// difference is a few 2^-48 of the sizes (the split of each voltage is good to 2^-48, and
+// every low part is within 2^-24 of a term that is within 2^-24 of a size); the scale
+// leaves a factor of 16 over 2^-44.
+//
+// FP64 work per cell: the two final additions (the norm then takes two FMAs); the device
+// current's polynomial runs in pairs up to t^2 and in FP32 beyond (tail32 is required).
+
+struct F2 {
+  float h, l;   // unevaluated sum h + l
+};
+
+constexpr double kPairErrScale = 1.0 / (double)(1ull << 40);
+
+__device__ __forceinline__ F2 split2(double x) { return F2{d2f_round(x), d2f_low(x)}; }
+
+// a * b for a pair a and an FP32 pair b, as a pair (not renormalised)
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+  float e;
+  const float p = two_prod(a.h, b.h, e);
+  return F2{p, fmaf(a.h, b.l, fmaf(a.l, b.h, e))};
+}
+
+// current / g of one device, (1 / b) sinh(b dV) for dV = d + dl, as a pair; for
+// |b dV| < 3/4: dV P(dV^2) with P - 1 = t (pc1 + t (pc2 + t r)), r the FP32 tail
+__device__ __forceinline__ F2 current_pair(const Grid& gr, float d, float dl) {
+  if (fabsf(d) < gr.dv_limf) {
+    float et;
+    const float t = two_prod(d, d, et);
+    const float tl = fmaf(2.f * d, dl, et);                 // dV^2 = t + tl
+    float r = fmaf(gr.pcf[6], t, gr.pcf[5]);
+    r = fmaf(r, t, gr.pcf[4]);
+    r = fmaf(r, t, gr.pcf[3]);
+    float ea, eb, ec, ed;
+    const float a = two_prod(t, r, ea);
+    const float q2 = two_sum(gr.pcf[2], a, eb);
+    const float q2l = (gr.pc2l + fmaf(tl, r, ea)) + eb;      // pc2 + t r
+    const float bq = two_prod(t, q2, ec);
+    const float bql = fmaf(t, q2l, fmaf(tl, q2, ec));
+    const float q1 = two_sum(gr.pcf[1], bq, ed);
+    const float q1l = (gr.pc1l + bql) + ed;                  // pc1 + t q2
+    const F2 pm1 = mul2(F2{t, tl}, F2{q1, q1l});             // P - 1
+    const F2 c = mul2(F2{d, dl}, pm1);                       // dV (P - 1)
+    float eg;
+    const float h = two_sum(d, c.h, eg);
+    return F2{h, dl + (c.l + eg)};
+  }
+  const double x = gr.b * (f2d_bits(d) + f2d_bits(dl));
+  return split2(sinh(x) * gr.inv_b);
+}
+
+template <bool YAK>
+__device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j, int c,
+                                                   const double* __restrict__ Vt,
+                                                   const double* __restrict__ Vb, double g64,
+                                                   double vin_i, double& ft, double& fb,
+                                                   double& dg, float& dgf, float& size2) {
+  const int m = gr.m, n = gr.n;
+  const F2 z0{0.f, 0.f};
+  const F2 vt = split2(Vt[c]), vb = split2(Vb[c]);
+  const F2 tl = (j > 0) ? split2(Vt[c - 1]) : z0;
+  const F2 tr = (j < n - 1) ? split2(Vt[c + 1]) : z0;
+  const F2 bu = (i > 0) ? split2(Vb[c - n]) : z0;
+  const F2 bd = (i < m - 1) ? split2(Vb[c + n]) : z0;
+  const bool jf = (j == 0), jl = (j == n - 1), iu = (i == 0), il = (i == m - 1);
+  const F2 dt{jf ? gr.dt0f : (jl ? gr.dtlf : gr.dtmf), jf ? gr.dt0l : (jl ? gr.dtll : gr.dtml)};
+  const F2 db{iu ? gr.db0f : (il ? gr.dblf : gr.dbmf), iu ? gr.db0l : (il ? gr.dbll : gr.dbml)};
+  // device voltage dV = d + dl and current g * cg
+  float ed;
+  const float d = two_sum(vt.h, -vb.h, ed);
+  const float dl = ed + (vt.l - vb.l);
+  F2 cg = current_pair(gr, d, dl);
+  const bool big = !(fabsf(d) < gr.dv_limf);
+  if (big) {
+    const double dgd = g64 * cosh(gr.b * (f2d_bits(d) + f2d_bits(dl)));
+    dg = dgd;
+    dgf = d2f_round(dgd);
+  } else {
+    dgf = d2f_round(g64) * coshf(d * gr.bf);
+  }
+  if (YAK && (d < 0.f || (d == 0.f && dl < 0.f))) {     // dV < 0
+    cg = mul2(cg, F2{gr.rnegf, gr.rnegl});
+    dgf *= gr.rnegf;
+    if (big) dg *= gr.rneg;
+  }
+  if (!big) dg = f2d_bits(dgf);
+  const F2 cur = mul2(split2(g64), cg);
+  // top: dt vt - gt (tl + tr) + cur [- g_src vin]
+  const F2 a1 = mul2(vt, dt);
+  float es;
+  const float st = two_sum(tl.h, tr.h, es);
+  const F2 a2 = mul2(F2{st, es + (tl.l + tr.l)}, F2{gr.gtf, gr.gtl});
+  float eu, ev;
+  const float u = two_sum(a1.h, -a2.h, eu);
+  float v = two_sum(u, cur.h, ev);
+  float lt = (a1.l - a2.l) + (cur.l + (eu + ev));
+  float szt = fabsf(a1.h) + fabsf(a2.h) + fabsf(cur.h);
+  if (jf) {
+    const F2 a3 = mul2(split2(vin_i), F2{gr.gsrcf, gr.gsrcl});
+    float ew;
+    v = two_sum(v, -a3.h, ew);
+    lt += ew - a3.l;
+    szt += fabsf(a3.h);
+  }
+  // bottom: db vb - gb (bu + bd) - cur
+  const F2 b1 = mul2(vb, db);
+  float fs;
+  const float sb = two_sum(bu.h, bd.h, fs);
+  const F2 b2 = mul2(F2{sb, fs + (bu.l + bd.l)}, F2{gr.gbf, gr.gbl});
+  float fu, fv;
+  const float ub = two_sum(b1.h, -b2.h, fu);
+  const float wb = two_sum(ub, -cur.h, fv);
+  const float lb = (b1.l - b2.l) + ((fu + fv) - cur.l);
+  const float szb = fabsf(b1.h) + fabsf(b2.h) + fabsf(cur.h);
+  ft = f2d_bits(v) + f2d_bits(lt);
+  fb = f2d_bits(wb) + f2d_bits(lb);
+  size2 = fmaf(szt, szt, fmaf(szb, szb, size2));
+}
+
 __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl* ctl) {
   const int b = blockIdx.x;
   double s = 0.0;
@@ -227,6 +379,7 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
     c.gmres_iters = 0;
     c.gm_active = 0;
     c.k_done = 0;
+    c.need_fp64 = 0;
     if (!isfinite(yn)) {
       c.status = MCA_ERR_NONFINITE;
       c.newton_active = 0;
@@ -241,8 +394,9 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
 }
 
 // K1: F = blockdiag(G_t, G_b) x + [i; -i] - [Y_t; 0] and D = g cosh(b dV) per cell, with
-// per-block partial sums of ||F||^2 and sum(D).
-template <bool YAK>
+// per-block partial sums of ||F||^2 and sum(D) (PAIR: the FP32-pair cell, and a third
+// partial sum, of the squared term sizes).
+template <bool YAK, bool PAIR>
 __global__ void __launch_bounds__(kThreads)
 k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ vin,
            const double* __restrict__ x, double* __restrict__ F, double* __restrict__ D,
@@ -262,13 +416,18 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
   // is FP32 and so is its sum within a thread
   const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
-  float sdf = 0.f;
+  float sdf = 0.f, ss = 0.f;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int j = c - i * n;
     double ft, fb, dg;
     float dgf;
-    cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg, dgf);
+    if constexpr (PAIR)
+      cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
+                              dg, dgf, ss);
+    else
+      cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
+                         dgf);
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
@@ -277,10 +436,12 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
     if (lin) sd += dg; else sdf += dgf;
   }
   sd += f2d_bits(sdf);
-  block_sum2(sf, sd);
+  double sz = f2d_bits(ss);
+  block_sum3(sf, sd, sz);
   if (threadIdx.x == 0) {
     part[((size_t)b * 32 + 0) * nblk + blockIdx.x] = sf;
     part[((size_t)b * 32 + 1) * nblk + blockIdx.x] = sd;
+    if (PAIR) part[((size_t)b * 32 + 2) * nblk + blockIdx.x] = sz;
   }
 }
 
@@ -288,10 +449,22 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
 // convergence test, forcing term of the next linear solve (first: eta0; then
 // Eisenstat-Walker 0.9 (|F_k|/|F_k-1|)^2 capped by eta_max, and never tighter than needed
 // to reach the target), GMRES cycle start.  Runs in one thread.
+// err >= 0 (the FP32-pair residual): ||F|| is known to within err; when the target
+// newton_rtol ||Y|| lies within that band of it, nothing is decided or changed here: the
+// vector is flagged (need_fp64, host flag 2) for the FP64 residual to decide.
 __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const SolverCfg& cfg,
-                               int32_t* host_flag) {
+                               int32_t* host_flag, double err = -1.0) {
   const double fn = sqrt(sf);
   const double a = sd / (double)mn;
+  if (err >= 0.0 && isfinite(fn) && isfinite(a) &&
+      fabs(fn - cfg.newton_rtol * c.ynorm) <= err) {
+    c.need_fp64 = 1;
+    c.gm_active = 0;
+    if (host_flag) *host_flag = 2;
+    __threadfence_system();
+    return;
+  }
+  c.need_fp64 = 0;
   c.fnorm_prev = c.fnorm;
   c.fnorm = fn;
   c.a = a;
@@ -333,19 +506,21 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
 
 // Residual of the solver loop with the Newton control in the last block of each vector.
 // ZERO: the state is x = 0 (first Newton step from V = 0), where F = -Y and D = g.
+// PAIR: the FP32-pair cell, whose ||F|| comes with an error bound (see newton_control).
+// confirm: only vectors flagged need_fp64 by a PAIR launch run (the FP64 decision).
 // F[b] is written at F + b*fstride: the solver points it at the first Krylov basis vector,
 // which GMRES keeps unnormalised (v_0 = -F / ||F||, the scale set by the Newton control),
 // and xbf (may be NULL) receives its BF16 copy for the tensor-core preconditioner.
-template <bool ZERO, bool YAK>
-__global__ void __launch_bounds__(kThreads)
+template <bool ZERO, bool YAK, bool PAIR>
+__global__ void __launch_bounds__(kThreads, 4)
 k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restrict__ map_of,
                   const double* __restrict__ vin,
                   const double* __restrict__ x, double* __restrict__ F, size_t fstride,
                   __nv_bfloat16* __restrict__ xbf, int mp, int np,
                   double* __restrict__ D, double* __restrict__ part, int nblk, VecCtl* ctl,
-                  SolverCfg cfg, unsigned int* cnt, int32_t* host_flags) {
+                  SolverCfg cfg, unsigned int* cnt, int32_t* host_flags, int confirm) {
   const int b = blockIdx.y;
-  if (!ctl[b].newton_active) return;
+  if (confirm ? !ctl[b].need_fp64 : !ctl[b].newton_active) return;
   const int m = gr.m, n = gr.n;
   const int mn = m * n;
   // conductance map of this vector's crossbar (several crossbars of one shape share a batch)
@@ -362,7 +537,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   // is FP32 and so is its sum within a thread
   const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
-  float sdf = 0.f;
+  float sdf = 0.f, ss = 0.f;
   for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
     const int i = c / n;
     const int j = c - i * n;
@@ -372,6 +547,9 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
       ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
       fb = 0.0;
       dg = gmap[c];
+    } else if (PAIR) {
+      cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
+                              dg, dgf, ss);
     } else {
       cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
                          dgf);
@@ -388,21 +566,28 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     if (ZERO || lin) sd += dg; else sdf += dgf;
   }
   sd += f2d_bits(sdf);
-  block_sum2(sf, sd);
+  double sz = f2d_bits(ss);
+  if (PAIR)
+    block_sum3(sf, sd, sz);
+  else
+    block_sum2(sf, sd);
   __shared__ bool last;
   if (threadIdx.x == 0) {
     part[((size_t)b * 32 + 0) * nblk + blockIdx.x] = sf;
     part[((size_t)b * 32 + 1) * nblk + blockIdx.x] = sd;
+    if (PAIR) part[((size_t)b * 32 + 2) * nblk + blockIdx.x] = sz;
     __threadfence();
     last = (atomicAdd(&cnt[b], 1u) == (unsigned)nblk - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // fixed-order sum over blocks: warp 0 -> ||F||^2, warp 1 -> sum(D)
+  // fixed-order sum over blocks: warp 0 -> ||F||^2, warp 1 -> sum(D), warp 2 -> the
+  // squared term sizes (PAIR)
+  constexpr int kRows = PAIR ? 3 : 2;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __shared__ double tot[2];
-  if (w < 2) {
+  __shared__ double tot[3];
+  if (w < kRows) {
     double s = 0.0;
     for (int t = l; t < nblk; t += 32) s += __ldcg(&part[((size_t)b * 32 + w) * nblk + t]);
     s = warp_sum(s);
@@ -411,7 +596,8 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   __syncthreads();
   if (threadIdx.x == 0) {
     cnt[b] = 0;
-    newton_control(ctl[b], tot[0], tot[1], mn, cfg, host_flags ? &host_flags[b] : nullptr);
+    newton_control(ctl[b], tot[0], tot[1], mn, cfg, host_flags ? &host_flags[b] : nullptr,
+                   PAIR ? kPairErrScale * sqrt(tot[2]) : -1.0);
   }
 }
 
@@ -637,30 +823,39 @@ void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
 
 void launch_residual(const Grid& gr, const double* gmap, const double* vin, const double* x,
                      double* F, double* D, double* part, int nblk, int B, const VecCtl* ctl,
-                     cudaStream_t s) {
-  if (gr.yak)
-    k_residual<true><<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
-  else
-    k_residual<false><<<dim3(nblk, B), kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl);
+                     cudaStream_t s, bool pair) {
+  const dim3 grid(nblk, B);
+#define MCA_RES(Y_, P_) \
+  k_residual<Y_, P_><<<grid, kThreads, 0, s>>>(gr, gmap, vin, x, F, D, part, nblk, ctl)
+  if (gr.yak) {
+    if (pair) MCA_RES(true, true); else MCA_RES(true, false);
+  } else {
+    if (pair) MCA_RES(false, true); else MCA_RES(false, false);
+  }
+#undef MCA_RES
 }
+
+double pair_err_bound(double size2_sum) { return kPairErrScale * std::sqrt(size2_sum); }
 
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
                             const double* vin, const double* x, bool zero_state, double* F,
                             size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
                             double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
-                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s) {
+                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s, bool pair,
+                            bool confirm) {
   dim3 grid(nblk, B);
-#define MCA_RESN(Z_, Y_)                                                                   \
-  k_residual_newton<Z_, Y_><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F, fstride, \
-                                                      xbf, mp, np, D, part, nblk, ctl, cfg,  \
-                                                      cnt, host_flags)
+#define MCA_RESN(Z_, Y_, P_)                                                                \
+  k_residual_newton<Z_, Y_, P_><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F,      \
+                                                          fstride, xbf, mp, np, D, part,     \
+                                                          nblk, ctl, cfg, cnt, host_flags,   \
+                                                          confirm ? 1 : 0)
   // (the zero state has dV = 0 everywhere: no device is under negative bias)
   if (zero_state)
-    MCA_RESN(true, false);
+    MCA_RESN(true, false, false);
   else if (gr.yak)
-    MCA_RESN(false, true);
+    if (pair) MCA_RESN(false, true, true); else MCA_RESN(false, true, false);
   else
-    MCA_RESN(false, false);
+    if (pair) MCA_RESN(false, false, true); else MCA_RESN(false, false, false);
 #undef MCA_RESN
 }
 

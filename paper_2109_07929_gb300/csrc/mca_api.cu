@@ -767,21 +767,39 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     const bool zero_state = (it == 0) && !from_guess;
     // F goes straight into the first Krylov basis vector (kept unnormalised) and its BF16
     // copy, so no separate pass builds v_0
+    // with the tensor-core forms, states after the first take the residual in FP32 pairs;
+    // a vector whose ||F|| it leaves undecided against the target gets the FP64 residual
+    const bool pair = tc && !zero_state && h->gr.tail32;
     launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
                            zero_state, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np,
-                           h->D, h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s);
+                           h->D, h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s, pair);
     count_launches(1);
     // FP64 flops per cell: stencils 8, sinh polynomial 16, current 4, norms 5 (the
-    // conductance cosh is FP32; the zero state only the norms)
+    // conductance cosh is FP32; the zero state only the norms); the pair form: its two
+    // final additions and the norms
     prof_end(h, t0, MCA_FAM_RESIDUAL, -1,
              cells * ((zero_state ? 32.0 : 48.0) + (tc ? 4.0 : 0.0)),
-             cells * (zero_state ? 5.0 : 33.0), s);
+             cells * (zero_state ? 5.0 : (pair ? 6.0 : 33.0)), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
     const int entering = n_active;
+    volatile int32_t* hf = reinterpret_cast<volatile int32_t*>(h->hflags);
+    int undecided = 0;
+    for (int b = 0; b < B; ++b) undecided += (hf[b] == 2) ? 1 : 0;
+    if (undecided > 0) {
+      t0 = prof_begin(h, s);
+      launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
+                             false, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np, h->D,
+                             h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s, false,
+                             true);
+      count_launches(1);
+      prof_end(h, t0, MCA_FAM_RESIDUAL, -2, cells * (48.0 + 4.0), cells * 33.0, s);
+      MCA_CUDA_TRY(cudaGetLastError());
+      MCA_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     n_active = 0;
-    for (int b = 0; b < B; ++b) n_active += reinterpret_cast<volatile int32_t*>(h->hflags)[b] ? 1 : 0;
-    prof_flush(h, [&](int, bool) { return entering; });
+    for (int b = 0; b < B; ++b) n_active += hf[b] ? 1 : 0;
+    prof_flush(h, [&](int k, bool) { return k == -2 ? undecided : entering; });
     if (n_active == 0) break;
     // the first step from V = 0 solves to the loosest forcing term, eta0: with the
     // tensor-core forms its Jacobian applies run in FP32 when eta0 allows it
@@ -1240,6 +1258,37 @@ int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nve
   for (int b = 0; b < nvec; ++b) {
     if (fnorm) fnorm[b] = std::sqrt(hh[(size_t)b * 32]);
     if (dmean) dmean[b] = hh[(size_t)b * 32 + 1] / (double)h->mn;
+  }
+  return MCA_OK;
+}
+
+int mca_residual_pair(mca_handle* h, const double* x, const double* v_in, int32_t nvec,
+                      double* F, double* D, double* fnorm, double* dmean, double* ferr,
+                      void* stream) {
+  g_last_error.clear();
+  if (!h || !x || !v_in || !F || !D || nvec < 1 || nvec > h->Bmax) {
+    set_error("bad arguments (nvec must be in 1..max_batch)");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (!h->gr.tail32) {
+    set_error("the FP32-pair residual needs b in about [0.02, 4000] (FP32 polynomial tail)");
+    return MCA_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = residual_nblk((int)h->mn);
+  launch_residual(h->gr, h->g, v_in, x, F, D, h->part, nb, nvec, nullptr, s, true);
+  count_launches(1);
+  launch_reduce_dots(h->part, nb, 3, h->h1, nvec, nullptr, s);
+  count_launches(1);
+  MCA_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hh((size_t)nvec * 32);
+  MCA_CUDA_TRY(cudaMemcpyAsync(hh.data(), h->h1, hh.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int b = 0; b < nvec; ++b) {
+    if (fnorm) fnorm[b] = std::sqrt(hh[(size_t)b * 32]);
+    if (dmean) dmean[b] = hh[(size_t)b * 32 + 1] / (double)h->mn;
+    if (ferr) ferr[b] = pair_err_bound(hh[(size_t)b * 32 + 2]);
   }
   return MCA_OK;
 }

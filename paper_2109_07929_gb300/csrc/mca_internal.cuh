@@ -38,6 +38,8 @@ struct VecCtl {
   int32_t k_done;      // columns finished in this cycle
   int32_t reorth;      // the current iteration needs the second Gram-Schmidt pass
   uint32_t reorth_mask;  // bit k: iteration k of this cycle took the second pass
+  int32_t need_fp64;   // the FP32-pair residual could not decide convergence
+  int32_t pad_;
   double orth;         // running estimate of the basis' loss of orthogonality
   double orth1;        // estimate for the new vector after the first pass (when reorth)
   double wn2;          // its squared norm after the first pass (when reorth)
@@ -70,16 +72,19 @@ struct Grid {
   double g_bt, g_sense;     // bottom-column ends: termination (i = 0), sense (i = m-1)
   double b;                 // sinh nonlinearity (0 = linear device)
   double inv_b;             // 1 / b (0 when b = 0)
-  // sinh(b dV) / (b dV) = sum_k pc[k] (dV^2)^k for |dV| below the limit whose FP64 bit
-  // pattern (sign cleared) is dv_lim_bits: the polynomial of the memristor current with b
+  // sinh(b dV) / (b dV) = sum_k pc[k] (dV^2)^k for |dV| below the limit whose FP64 high
+  // word (sign cleared) is dv_lim_hi: the polynomial of the memristor current with b
   // folded into its coefficients
   double pc[7];
-  unsigned long long dv_lim_bits;
+  uint32_t dv_lim_hi;
   // the tail pc[3] + pc[4] t + pc[5] t^2 + pc[6] t^3 in FP32 (pcf) when tail32: at most
   // 3.5e-5 of the polynomial, so FP32 rounding there costs below 1e-11 relative; tail32
   // is off when a folded coefficient leaves [1e-30, 1e30] (b outside about [0.02, 4000])
   float pcf[7];
   int tail32;
+  // for the FP32-pair residual: low halves of pc[1], pc[2] (pcf holds the high halves),
+  // the polynomial's range in FP32, the source conductance and rneg as FP32 pairs
+  float pc1l, pc2l, dv_limf, gsrcf, gsrcl, rnegl;
   float bf;                 // b in FP32 (for the FP32 conductance)
   // Yakopcic-form device: currents and conductances of devices with dV < 0 are scaled by
   // rneg (yak = 0: the symmetric sinh device, rneg = 1)
@@ -163,9 +168,13 @@ __device__ __forceinline__ bool warp_scatter_writer(int lane) {
 // stencil / residual / Jacobian (k_stencil.cu)
 void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
                           cudaStream_t s);
+// pair: the residual in FP32 pairs (requires gr.tail32), which also leaves the squared
+// term sizes' partial sums in part row 2; pair_err_bound turns their total into the bound
+// on the error of ||F||
 void launch_residual(const Grid& gr, const double* gmap, const double* vin, const double* x,
                      double* F, double* D, double* part, int nblk, int B, const VecCtl* ctl,
-                     cudaStream_t s);
+                     cudaStream_t s, bool pair = false);
+double pair_err_bound(double size2_sum);
 // Residual of the solver loop: zero_state skips the device model at x = 0 (F = -Y,
 // D = g); the last block of each vector runs the Newton control (convergence test,
 // forcing term, start of the GMRES cycle).
@@ -173,11 +182,15 @@ void launch_residual(const Grid& gr, const double* gmap, const double* vin, cons
 // vector b's map (NULL: map 0 for all).
 // F[b] at F + b*fstride, with its BF16 copy in xbf (may be NULL); the Newton control
 // sets the scale -1/||F|| that turns the stored F into the first GMRES basis vector.
+// pair (not with zero_state; requires gr.tail32): the FP32-pair residual, whose Newton
+// control leaves a vector undecided (host flag 2, need_fp64) when the target lies within
+// its error bound of ||F||; confirm: the FP64 residual for exactly those vectors.
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
                             const double* vin, const double* x, bool zero_state, double* F,
                             size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
                             double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
-                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s);
+                            unsigned int* cnt, int32_t* host_flags, cudaStream_t s,
+                            bool pair = false, bool confirm = false);
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
                        __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
                        int B, cudaStream_t s);
