@@ -252,7 +252,37 @@ struct F2 {
 
 constexpr double kPairErrScale = 1.0 / (double)(1ull << 40);
 
-__device__ __forceinline__ F2 split2(double x) { return F2{d2f_round(x), d2f_low(x)}; }
+// x as an FP32 pair (d2f_round(x), d2f_low(x)); one range test selects the common case
+// 2^-74 <= |x| < 2^128, where both halves come from the two 32-bit words directly.
+__device__ __forceinline__ F2 split2(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t ex = (hi >> 20) & 0x7FFu;
+  if (ex - 949u <= 201u) {
+    const uint32_t lo2 = lo + (1u << 28);                       // round at mantissa bit 29
+    const uint32_t hi2 = hi + (lo2 < lo ? 1u : 0u);
+    const uint32_t hb = ((((hi2 & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo2 >> 29)) |
+                        (hi & 0x80000000u);                      // exponent rebiased by 896
+    const int32_t dl = (int32_t)(lo - (lo2 & 0xE0000000u));      // x - hi in ulps of x
+    const float mag = u29_to_float((uint32_t)(dl < 0 ? -dl : dl)) *
+                      __int_as_float((int)(ex - 948u) << 23);
+    const uint32_t sg = (hi & 0x80000000u) ^ (dl < 0 ? 0x80000000u : 0u);
+    return F2{__uint_as_float(hb), __uint_as_float(__float_as_uint(mag) ^ sg)};
+  }
+  return F2{d2f_round(x), d2f_low(x)};
+}
+
+// BF16 (round to nearest even) of a float; Inf / NaN kept
+__device__ __forceinline__ __nv_bfloat16 f2bf16_bits(float x) {
+  const uint32_t f = __float_as_uint(x);
+  uint32_t r;
+  if ((f & 0x7F800000u) == 0x7F800000u)
+    r = (f >> 16) | ((f & 0xFFFFu) ? 0x40u : 0u);
+  else
+    r = (f + 0x7FFFu + ((f >> 16) & 1u)) >> 16;
+  __nv_bfloat16_raw raw;
+  raw.x = (unsigned short)r;
+  return __nv_bfloat16(raw);
+}
 
 // a * b for a pair a and an FP32 pair b, as a pair (not renormalised)
 __device__ __forceinline__ F2 mul2(F2 a, F2 b) {
@@ -294,7 +324,8 @@ __device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j,
                                                    const double* __restrict__ Vt,
                                                    const double* __restrict__ Vb, double g64,
                                                    double vin_i, double& ft, double& fb,
-                                                   double& dg, float& dgf, float& size2) {
+                                                   double& dg, float& dgf, float& size2,
+                                                   float& ft32, float& fb32) {
   const int m = gr.m, n = gr.n;
   const F2 z0{0.f, 0.f};
   const F2 vt = split2(Vt[c]), vb = split2(Vb[c]);
@@ -354,6 +385,8 @@ __device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j,
   const float szb = fabsf(b1.h) + fabsf(b2.h) + fabsf(cur.h);
   ft = f2d_bits(v) + f2d_bits(lt);
   fb = f2d_bits(wb) + f2d_bits(lb);
+  ft32 = v + lt;
+  fb32 = wb + lb;
   size2 = fmaf(szt, szt, fmaf(szb, szb, size2));
 }
 
@@ -422,9 +455,10 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
     const int j = c - i * n;
     double ft, fb, dg;
     float dgf;
+    float f32a, f32b;
     if constexpr (PAIR)
       cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
-                              dg, dgf, ss);
+                              dg, dgf, ss, f32a, f32b);
     else
       cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
                          dgf);
@@ -538,18 +572,22 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
   float sdf = 0.f, ss = 0.f;
-  for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
-    const int i = c / n;
-    const int j = c - i * n;
+  // grid-stride walk over the cells with (i, j) advanced incrementally (no division per
+  // cell); the BF16 copy sits in the padded [layer][mp][np] layout at row offset i * np
+  const int S = nblk * kThreads;
+  const int Si = S / n, Sj = S - Si * n;
+  int c = blockIdx.x * kThreads + threadIdx.x;
+  int i = c / n, j = c - (c / n) * n;
+  for (; c < mn; c += S) {
     double ft, fb, dg;
-    float dgf = 0.f;
+    float dgf = 0.f, ft32, fb32;
     if (ZERO) {
       ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
       fb = 0.0;
       dg = gmap[c];
     } else if (PAIR) {
       cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
-                              dg, dgf, ss);
+                              dg, dgf, ss, ft32, fb32);
     } else {
       cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
                          dgf);
@@ -558,12 +596,24 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     Fb[c] = fb;
     Db[c] = dg;
     if (xt != nullptr) {
-      xt[(size_t)i * np + j] = d2bf16_bits(ft);
-      xt[((size_t)mp + i) * np + j] = d2bf16_bits(fb);
+      const int o = i * np + j;
+      if (PAIR) {
+        xt[o] = f2bf16_bits(ft32);
+        xt[o + mp * np] = f2bf16_bits(fb32);
+      } else {
+        xt[o] = d2bf16_bits(ft);
+        xt[o + mp * np] = d2bf16_bits(fb);
+      }
     }
     sf = fma(ft, ft, sf);
     sf = fma(fb, fb, sf);
     if (ZERO || lin) sd += dg; else sdf += dgf;
+    j += Sj;
+    i += Si;
+    if (j >= n) {
+      j -= n;
+      ++i;
+    }
   }
   sd += f2d_bits(sdf);
   double sz = f2d_bits(ss);
