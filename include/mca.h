@@ -249,15 +249,16 @@ const char* mca_last_error_message(void);
 int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nvec,
                  double* F, double* D, double* fnorm, double* dmean, void* stream);
 
-/* The same residual in FP32 pairs, the form the solver uses for the states after the
- * first with the BF16 and BF16_SPLIT preconditioners (eq. (F), eq. (J)).  Each FP64
+/* The same residual in FP32 pairs, the form the solver uses, with the BF16 and BF16_SPLIT
+ * preconditioners, for states far from convergence (eq. (F), eq. (J)).  Each FP64
  * voltage is split into two FP32 halves, products and sums are formed error-free in FP32
  * and each F entry is rounded once to FP64; D is the FP32 conductance as in mca_residual.
  *   ferr : host out, nvec bounds on | ||F computed|| - ||F exact|| | (may be NULL):
  *          2^-40 times the 2-norm of the per-entry term sizes (|wire diagonal x| +
- *          |wire couplings| + |device current| + |source current|).  The solver's Newton
- *          control accepts or rejects convergence from this residual only when the target
- *          lies outside ||F|| +- ferr, and otherwise decides with the FP64 residual.
+ *          |wire couplings| + |device current| + |source current|).  The solver uses
+ *          this residual only for iterates whose ||F|| - ferr stays more than 10 times
+ *          above the target (there it is the right-hand side of the next inexact Newton
+ *          step); every convergence decision is made on the FP64 residual.
  * Other arguments as mca_residual.  Returns MCA_ERR_UNSUPPORTED when b lies outside about
  * [0.02, 4000] (the device polynomial's tail leaves the FP32 range). */
 int mca_residual_pair(mca_handle* h, const double* x, const double* v_in, int32_t nvec,

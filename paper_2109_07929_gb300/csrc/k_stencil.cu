@@ -233,7 +233,9 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
 
 // ---- the residual in FP32 pairs ------------------------------------------------------
 //
-// The same cell as cell_residual with every FP64 operand split into an FP32 pair
+// For Newton iterates far from convergence, whose residual only becomes the right-hand side
+// of the next inexact linear solve (every convergence decision is made on the FP64
+// residual).  The same cell as cell_residual with every FP64 operand split into an FP32 pair
 // (d2f_round / d2f_low, integer pipe) and every product and sum formed error-free
 // (two_prod, two_sum); the low parts are summed in FP32 and each result is rounded once to
 // FP64.  Besides F and D the cell returns the size of its terms (|wire diagonal x| +
@@ -251,6 +253,8 @@ struct F2 {
 };
 
 constexpr double kPairErrScale = 1.0 / (double)(1ull << 40);
+// the pair residual is used only for iterates more than this factor above the target
+constexpr double kPairMinRatio = 10.0;
 
 // x as an FP32 pair (d2f_round(x), d2f_low(x)); one range test selects the common case
 // 2^-74 <= |x| < 2^128, where both halves come from the two 32-bit words directly.
@@ -413,6 +417,7 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
     c.gm_active = 0;
     c.k_done = 0;
     c.need_fp64 = 0;
+    c.res_est = INFINITY;          // no linear solve yet
     if (!isfinite(yn)) {
       c.status = MCA_ERR_NONFINITE;
       c.newton_active = 0;
@@ -483,15 +488,18 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
 // convergence test, forcing term of the next linear solve (first: eta0; then
 // Eisenstat-Walker 0.9 (|F_k|/|F_k-1|)^2 capped by eta_max, and never tighter than needed
 // to reach the target), GMRES cycle start.  Runs in one thread.
-// err >= 0 (the FP32-pair residual): ||F|| is known to within err; when the target
-// newton_rtol ||Y|| lies within that band of it, nothing is decided or changed here: the
-// vector is flagged (need_fp64, host flag 2) for the FP64 residual to decide.
+// err >= 0 (the FP32-pair residual): ||F|| is known to within err.  The pair residual
+// only serves iterates that are certainly more than kPairMinRatio times the target
+// newton_rtol ||Y|| away from convergence (there it is the right-hand side of the next
+// inexact Newton step); for any other vector nothing is decided or changed here: it is
+// flagged (need_fp64, host flag 2) for the FP64 residual, which makes every convergence
+// decision.
 __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const SolverCfg& cfg,
                                int32_t* host_flag, double err = -1.0) {
   const double fn = sqrt(sf);
   const double a = sd / (double)mn;
   if (err >= 0.0 && isfinite(fn) && isfinite(a) &&
-      fabs(fn - cfg.newton_rtol * c.ynorm) <= err) {
+      fn - err <= kPairMinRatio * cfg.newton_rtol * c.ynorm) {
     c.need_fp64 = 1;
     c.gm_active = 0;
     if (host_flag) *host_flag = 2;
@@ -540,7 +548,8 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
 
 // Residual of the solver loop with the Newton control in the last block of each vector.
 // ZERO: the state is x = 0 (first Newton step from V = 0), where F = -Y and D = g.
-// PAIR: the FP32-pair cell, whose ||F|| comes with an error bound (see newton_control).
+// PAIR: the FP32-pair cell for vectors far from convergence, whose ||F|| comes with an
+// error bound (see newton_control), the FP64 cell for the others.
 // confirm: only vectors flagged need_fp64 by a PAIR launch run (the FP64 decision).
 // F[b] is written at F + b*fstride: the solver points it at the first Krylov basis vector,
 // which GMRES keeps unnormalised (v_0 = -F / ||F||, the scale set by the Newton control),
@@ -555,6 +564,10 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
                   SolverCfg cfg, unsigned int* cnt, int32_t* host_flags, int confirm) {
   const int b = blockIdx.y;
   if (confirm ? !ctl[b].need_fp64 : !ctl[b].newton_active) return;
+  // PAIR: a vector whose last linear solve ended within kPairMinRatio of the target (its
+  // new residual may decide convergence) takes the FP64 cell right away
+  const bool use_pair =
+      PAIR && !(ctl[b].res_est <= kPairMinRatio * cfg.newton_rtol * ctl[b].ynorm);
   const int m = gr.m, n = gr.n;
   const int mn = m * n;
   // conductance map of this vector's crossbar (several crossbars of one shape share a batch)
@@ -585,7 +598,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
       ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
       fb = 0.0;
       dg = gmap[c];
-    } else if (PAIR) {
+    } else if (PAIR && use_pair) {
       cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
                               dg, dgf, ss, ft32, fb32);
     } else {
@@ -597,7 +610,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     Db[c] = dg;
     if (xt != nullptr) {
       const int o = i * np + j;
-      if (PAIR) {
+      if (PAIR && use_pair) {
         xt[o] = f2bf16_bits(ft32);
         xt[o + mp * np] = f2bf16_bits(fb32);
       } else {
@@ -647,7 +660,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   if (threadIdx.x == 0) {
     cnt[b] = 0;
     newton_control(ctl[b], tot[0], tot[1], mn, cfg, host_flags ? &host_flags[b] : nullptr,
-                   PAIR ? kPairErrScale * sqrt(tot[2]) : -1.0);
+                   use_pair ? kPairErrScale * sqrt(tot[2]) : -1.0);
   }
 }
 

@@ -767,8 +767,9 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     const bool zero_state = (it == 0) && !from_guess;
     // F goes straight into the first Krylov basis vector (kept unnormalised) and its BF16
     // copy, so no separate pass builds v_0
-    // with the tensor-core forms, states after the first take the residual in FP32 pairs;
-    // a vector whose ||F|| it leaves undecided against the target gets the FP64 residual
+    // with the tensor-core forms, states after the first whose last linear solve ended far
+    // above the target take the residual in FP32 pairs; a vector whose pair ||F|| is not
+    // certainly far above the target gets the FP64 residual, which decides convergence
     const bool pair = tc && !zero_state && h->gr.tail32;
     launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
                            zero_state, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np,

@@ -182,9 +182,11 @@ double pair_err_bound(double size2_sum);
 // vector b's map (NULL: map 0 for all).
 // F[b] at F + b*fstride, with its BF16 copy in xbf (may be NULL); the Newton control
 // sets the scale -1/||F|| that turns the stored F into the first GMRES basis vector.
-// pair (not with zero_state; requires gr.tail32): the FP32-pair residual, whose Newton
-// control leaves a vector undecided (host flag 2, need_fp64) when the target lies within
-// its error bound of ||F||; confirm: the FP64 residual for exactly those vectors.
+// pair (not with zero_state; requires gr.tail32): the FP32-pair residual for vectors whose
+// last linear solve ended more than 10 times above the target; its Newton control accepts
+// ||F|| only when, within its error bound, it is still more than 10 times above the target,
+// and otherwise leaves the vector undecided (host flag 2, need_fp64); confirm: the FP64
+// residual for exactly those vectors.
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
                             const double* vin, const double* x, bool zero_state, double* F,
                             size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
