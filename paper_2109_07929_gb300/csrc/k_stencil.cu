@@ -417,6 +417,8 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
     c.gm_active = 0;
     c.k_done = 0;
     c.need_fp64 = 0;
+    c.d64 = 1;
+    c.d64_next = 0;
     c.res_est = INFINITY;          // no linear solve yet
     if (!isfinite(yn)) {
       c.status = MCA_ERR_NONFINITE;
@@ -500,6 +502,7 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
   const double a = sd / (double)mn;
   if (err >= 0.0 && isfinite(fn) && isfinite(a) &&
       fn - err <= kPairMinRatio * cfg.newton_rtol * c.ynorm) {
+    c.d64_next = 0;                // the FP64 residual rewrites D
     c.need_fp64 = 1;
     c.gm_active = 0;
     if (host_flag) *host_flag = 2;
@@ -507,6 +510,8 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
     return;
   }
   c.need_fp64 = 0;
+  c.d64 = c.d64_next;
+  c.d64_next = 0;
   c.fnorm_prev = c.fnorm;
   c.fnorm = fn;
   c.a = a;
@@ -585,6 +590,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
   float sdf = 0.f, ss = 0.f;
+  bool dnot32 = false;
   // grid-stride walk over the cells with (i, j) advanced incrementally (no division per
   // cell); the BF16 copy sits in the padded [layer][mp][np] layout at row offset i * np
   const int S = nblk * kThreads;
@@ -608,6 +614,13 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
+    {
+      // D is an FP32 number when its low 29 mantissa bits are clear and its exponent is
+      // in the FP32 normal range (or D = 0)
+      const uint32_t dh = (uint32_t)__double2hiint(dg), dlw = (uint32_t)__double2loint(dg);
+      const uint32_t de = (dh >> 20) & 0x7FFu;
+      dnot32 |= ((dlw & 0x1FFFFFFFu) != 0u) || (de - 897u > 253u && ((dh & 0x7FFFFFFFu) | dlw));
+    }
     if (xt != nullptr) {
       const int o = i * np + j;
       if (PAIR && use_pair) {
@@ -630,6 +643,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   }
   sd += f2d_bits(sdf);
   double sz = f2d_bits(ss);
+  if (__syncthreads_or(dnot32) && threadIdx.x == 0) atomicOr(&ctl[b].d64_next, 1);
   if (PAIR)
     block_sum3(sf, sd, sz);
   else
@@ -720,9 +734,9 @@ __device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
 __device__ __forceinline__ void apply_pair(float a, float bb, float tl, float tr, float bu,
                                            float bd, double Dd, float dth, float dtl,
                                            float dbh, float dbl, const Grid& gr, double& ot,
-                                           double& ob) {
+                                           double& ob, bool dsplit) {
   const float dh = d2f_round(Dd);
-  const float dl = d2f_round(Dd - f2d_bits(dh));
+  const float dl = dsplit ? d2f_round(Dd - f2d_bits(dh)) : 0.f;
   float ed, e3;
   const float d = two_sum(a, -bb, ed);
   const float p3 = two_prod(dh, d, e3);
@@ -755,6 +769,8 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
             const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h) {
   const int b = blockIdx.y;
   if (ctl != nullptr && !ctl[b].gm_active) return;
+  // the pair apply skips the split of D when every entry is an FP32 number
+  const bool dsplit = (ctl == nullptr) || ctl[b].d64;
   const int m = gr.m, n = gr.n, mn = m * n;
   const size_t n2 = 2 * (size_t)mn;
   const ZT* zt = z + (size_t)b * zstride;
@@ -776,7 +792,7 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
                  u ? 0.f : (float)zb[c - n], dn ? 0.f : (float)zb[c + n], Db[c],
                  f ? gr.dt0f : (l ? gr.dtlf : gr.dtmf), f ? gr.dt0l : (l ? gr.dtll : gr.dtml),
                  u ? gr.db0f : (dn ? gr.dblf : gr.dbmf), u ? gr.db0l : (dn ? gr.dbll : gr.dbml),
-                 gr, ot, ob);
+                 gr, ot, ob, dsplit);
     } else if constexpr (AM == kApplyF32) {
       // FP32 apply (z is FP32 here): the same formula, rounded to FP32, widened exactly
       const float a = zt[c], bb = zb[c];

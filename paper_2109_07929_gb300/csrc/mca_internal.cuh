@@ -39,6 +39,8 @@ struct VecCtl {
   int32_t reorth;      // the current iteration needs the second Gram-Schmidt pass
   uint32_t reorth_mask;  // bit k: iteration k of this cycle took the second pass
   int32_t need_fp64;   // the FP32-pair residual could not decide convergence
+  int32_t d64;         // some entry of D is not an FP32 number (the pair apply splits D)
+  int32_t d64_next;    // the same, gathered by the blocks of the running residual launch
   int32_t pad_;
   double orth;         // running estimate of the basis' loss of orthogonality
   double orth1;        // estimate for the new vector after the first pass (when reorth)

@@ -423,10 +423,7 @@ def _check_solve(cb, prec, tol, vtol=1e-7, nvec=None, ref_tol=1e-13):
         Yt, _ = O.source_vector(p, vin[v])
         rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
         assert rel <= tol * 1.01, (v, rel)
-        # the tensor-core forms may take the final ||F|| from the FP32-pair residual, whose
-        # error is a few 2^-46 of the term sizes (the FP64 form: FP64 rounding)
-        atol = tol * (1e-3 if prec == mca.PREC_FP64 else 1e-2)
-        np.testing.assert_allclose(st[v]["rel_residual"], rel, rtol=1e-3, atol=atol)
+        np.testing.assert_allclose(st[v]["rel_residual"], rel, rtol=1e-3, atol=tol * 1e-3)
         ref = O.newton_solve(p, cb.gmap, vin[v], tol=ref_tol, linear="direct")
         if prec == mca.PREC_FP64:
             # the FP64 form: max relative error per layer
