@@ -140,8 +140,8 @@ k_reorth_dots(const double* __restrict__ u, const double* __restrict__ V, size_t
   for (int j = 0; j < KP; ++j) acc[j] = 0.0;
   const double* ub = u + (size_t)b * vstride;
   const double* Vb = V + (size_t)b * vstride;
-  for (size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x; e < n2;
-       e += (size_t)nblk * kThreads) {
+  const int N2 = (int)n2;
+  for (int e = blockIdx.x * kThreads + threadIdx.x; e < N2; e += nblk * kThreads) {
     const double x = ub[e];
 #pragma unroll
     for (int j = 0; j < KP; ++j)
@@ -288,22 +288,26 @@ __global__ void k_update_x(double* __restrict__ x, const ZT* __restrict__ Z,
   __syncthreads();
   double* xb = x + (size_t)b * n2;
   const ZT* Zb = Z + (size_t)b * zstride;
-  const size_t st = (size_t)gridDim.x * blockDim.x;
-  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  for (; e + 3 * st < n2; e += 4 * st) {     // four independent elements per trip
+  // 32-bit element indices (n2 < 2^31), as in k_update_norm
+  const int N2 = (int)n2;
+  const int st = gridDim.x * blockDim.x;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * st < N2; e += 4 * st) {     // four independent elements per trip
     double s[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) s[u] = xb[e + u * st];
-    for (int j = 0; j < kd; ++j) {
+    const ZT* zj = Zb;
+    for (int j = 0; j < kd; ++j, zj += n2) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) s[u] = fma(ys[j], widen(Zb[(size_t)j * n2 + e + u * st]), s[u]);
+      for (int u = 0; u < 4; ++u) s[u] = fma(ys[j], widen(zj[e + u * st]), s[u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) xb[e + u * st] = s[u];
   }
-  for (; e < n2; e += st) {
+  for (; e < N2; e += st) {
     double s = xb[e];
-    for (int j = 0; j < kd; ++j) s = fma(ys[j], widen(Zb[(size_t)j * n2 + e]), s);
+    const ZT* zj = Zb;
+    for (int j = 0; j < kd; ++j, zj += n2) s = fma(ys[j], widen(zj[e]), s);
     xb[e] = s;
   }
 }

@@ -488,6 +488,7 @@ int autotune_tiles(mca_handle* h) {
     c.a = 2e-5;
     c.gm_active = 1;
     c.newton_active = 1;
+    c.d64 = 1;
   }
   MCA_CUDA_TRY(cudaMemcpy(h->ctl, h->ctl_host.data(), (size_t)B * sizeof(VecCtl),
                           cudaMemcpyHostToDevice));
@@ -1346,6 +1347,7 @@ static int load_ctl_a(mca_handle* h, const double* a, int nvec, cudaStream_t s) 
     c.a = a[b];
     c.gm_active = 1;
     c.newton_active = 1;
+    c.d64 = 1;                     // D is the caller's: split it in the pair apply
   }
   MCA_CUDA_TRY(cudaMemcpyAsync(h->ctl, h->ctl_host.data(), (size_t)nvec * sizeof(VecCtl),
                                cudaMemcpyHostToDevice, s));
