@@ -260,7 +260,7 @@ int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nve
  *          above the target (there it is the right-hand side of the next inexact Newton
  *          step); every convergence decision is made on the FP64 residual.
  * Other arguments as mca_residual.  Returns MCA_ERR_UNSUPPORTED when b lies outside about
- * [0.02, 4000] (the device polynomial's tail leaves the FP32 range). */
+ * [0.021, 2000] (the device polynomial's tail leaves the FP32 range). */
 int mca_residual_pair(mca_handle* h, const double* x, const double* v_in, int32_t nvec,
                       double* F, double* D, double* fnorm, double* dmean, double* ferr,
                       void* stream);

@@ -1273,7 +1273,7 @@ int mca_residual_pair(mca_handle* h, const double* x, const double* v_in, int32_
     return MCA_ERR_INVALID_ARG;
   }
   if (!h->gr.tail32) {
-    set_error("the FP32-pair residual needs b in about [0.02, 4000] (FP32 polynomial tail)");
+    set_error("the FP32-pair residual needs b in about [0.021, 2000] (FP32 polynomial tail)");
     return MCA_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -81,7 +81,7 @@ struct Grid {
   uint32_t dv_lim_hi;
   // the tail pc[3] + pc[4] t + pc[5] t^2 + pc[6] t^3 in FP32 (pcf) when tail32: at most
   // 3.5e-5 of the polynomial, so FP32 rounding there costs below 1e-11 relative; tail32
-  // is off when a folded coefficient leaves [1e-30, 1e30] (b outside about [0.02, 4000])
+  // is off when a folded coefficient leaves [1e-30, 1e30] (b outside about [0.021, 2000])
   float pcf[7];
   int tail32;
   // for the FP32-pair residual: low halves of pc[1], pc[2] (pcf holds the high halves),

@@ -68,6 +68,37 @@ def test_sinh_polynomial_fp64_horner_within_two_ulp():
         assert abs(val - ref) <= 2 * np.spacing(abs(ref)) + 1e-320, (x, val, ref)
 
 
+@pytest.mark.parametrize("b", [2.0, 0.025, 7.5, 2000.0])
+def test_fp32_tail_of_the_polynomial(b):
+    """The kernels evaluate the tail t^3 (c3 + c4 t + c5 t^2 + c6 t^3) of the folded
+    polynomial in FP32 (coefficients pc_k = c_k b^2k rounded to FP32, t from dV rounded to
+    FP32) and the rest in FP64.  That tail is at most x^6/5040 of P, so the current must stay
+    within 1e-11 relative (plus FP64 rounding) of (1/b) sinh(b dV) over |b dV| < 3/4."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    c = _kernel_coefficients()
+    pc = [c[k] * b ** (2 * k) for k in range(7)]
+    assert all(1e-30 <= pc[k] <= 1e30 for k in range(3, 7))   # the kernels' FP32-tail range
+    pcf = [np.float32(v) for v in pc]
+    worst = 0.0
+    for x in np.concatenate([np.linspace(-0.7499, 0.7499, 1501), [1e-12, 0.3, -0.6]]):
+        dv = x / b
+        t = dv * dv
+        dvf = np.float32(dv)
+        tf = np.float32(dvf * dvf)
+        r = np.float32(np.float64(pcf[6]) * tf + pcf[5])
+        r = np.float32(np.float64(r) * tf + pcf[4])
+        r = np.float32(np.float64(r) * tf + pcf[3])
+        ps = float(r) * t + pc[2]
+        ps = ps * t + pc[1]
+        ps = ps * t + pc[0]
+        val = dv * ps
+        ref = float(mpmath.sinh(mpmath.mpf(b) * mpmath.mpf(dv)) / mpmath.mpf(b))
+        err = abs(val - ref) - 4 * np.spacing(abs(ref))
+        worst = max(worst, err / abs(ref))
+    assert worst < 1e-11, worst
+
+
 def _generator():
     import importlib.util
     spec = importlib.util.spec_from_file_location("gen_sinh_poly", CSRC / "gen_sinh_poly.py")
