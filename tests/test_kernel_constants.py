@@ -94,6 +94,9 @@ def test_fp32_tail_of_the_polynomial(b):
         ps = ps * t + pc[0]
         val = dv * ps
         ref = float(mpmath.sinh(mpmath.mpf(b) * mpmath.mpf(dv)) / mpmath.mpf(b))
+        if ref == 0.0:
+            assert val == 0.0
+            continue
         err = abs(val - ref) - 4 * np.spacing(abs(ref))
         worst = max(worst, err / abs(ref))
     assert worst < 1e-11, worst
