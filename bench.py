@@ -3,13 +3,15 @@
 
 Workload: the 1024 x 1024 memristor crossbar (2.1M unknowns), log-uniform device
 conductances in [1e-6, 1e-4] S, top wires 1 S, bottom wires 0.5 S, 10 ohm drivers and
-sense, 1 kohm terminations, sinh devices (b = 2), V_in ~ U[0, 0.3] V.  One step solves a
-batch of input vectors to a relative KCL residual ||F||/||Y|| <= 1e-8 with Newton +
+sense, 1 kohm terminations, sinh devices (b = 2), V_in ~ U[0, 0.3] V.  One step solves
+--handles handles of --batch input vectors each, concurrently (mca_solve_many, one host
+thread and stream per handle), to a relative KCL residual ||F||/||Y|| <= 1e-8 with Newton +
 flexible GMRES(30) preconditioned by the Kronecker/block preconditioner (tensor-core BF16
 transforms, split back transforms); value = solves per second.
 
 The JSON line also carries: the end-to-end figure through the C ABI with host buffers,
-the roofline of the dominant kernel family (CUDA events on the solve stream), the same
+the roofline of the dominant kernel family (CUDA events on the solve stream, in a pass of
+one handle alone), the same
 workload in the plain FP64 GPU form, the preconditioner TFLOP/s (dense eigenbasis count
 8 m n (m + n) per apply), and the CPU oracle on the host cores.
 
@@ -45,7 +47,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=1024)
-    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=64, help="vectors per handle pass (<= 64)")
+    ap.add_argument("--handles", type=int, default=2,
+                    help="handles solved concurrently per step (mca_solve_many, one host "
+                         "thread and stream each)")
     ap.add_argument("--precision", default="bf16split",
                     choices=["bf16split", "bf16", "fp64", "mhat"])
     ap.add_argument("--device", default="sinh", choices=["sinh", "yakopcic"],
@@ -220,9 +225,11 @@ def run_ours(args):
     prec = {"bf16split": mca.PREC_BF16_SPLIT, "bf16": mca.PREC_BF16,
             "fp64": mca.PREC_FP64, "mhat": mca.PREC_MHAT}[args.precision]
     B = args.batch
+    H = max(1, args.handles)
+    S = H * B                       # solves per step
     W, K = args.warmup, args.steps
     m = n = args.size
-    cb = make_workload(args, replica_seed(rank), (W + max(K, 2 * E2E_PASSES)) * B)
+    cb = make_workload(args, replica_seed(rank), (W + max(K, 2 * E2E_PASSES)) * S)
     p = cb.params
     params = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
                                 g_src=p.g_src, g_term_top_right=p.g_term_top_right,
@@ -231,17 +238,20 @@ def run_ours(args):
                                 device_model=(mca.DEVICE_SINH if args.device == "sinh"
                                               else mca.DEVICE_YAKOPCIC),
                                 neg_ratio=p.neg_ratio)
-    solver = mca.Solver(params, cb.gmap)
+    solvers = [mca.Solver(params, cb.gmap) for _ in range(H)]
+    solver = solvers[0]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     vin = torch.as_tensor(cb.vin, device=dev)
-    vt = torch.empty(B, m, n, dtype=torch.float64, device=dev)
-    vb = torch.empty_like(vt)
-    io = torch.empty(B, n, dtype=torch.float64, device=dev)
+    outs = [(torch.empty(B, m, n, dtype=torch.float64, device=dev),
+             torch.empty(B, m, n, dtype=torch.float64, device=dev),
+             torch.empty(B, n, dtype=torch.float64, device=dev)) for _ in range(H)]
+    vt, vb, io = outs[0]
     stats = (mca.Stats * B)()
     sp = mca.ctypes.cast(stats, mca.ctypes.c_void_p)
 
-    def step(i, check):
+    def step1(i, check):
+        # one handle, B vectors, on the bench stream
         rc = solver.solve_raw(vin[i * B:(i + 1) * B].data_ptr(), B, vt.data_ptr(), vb.data_ptr(),
                               io.data_ptr(), sp, stream)
         if rc != 0:
@@ -250,6 +260,19 @@ def run_ours(args):
             for s in stats:
                 assert s.status == 0 and s.rel_residual <= TOL, (s.status, s.rel_residual)
                 check.append((s.newton_iters, s.gmres_iters, s.rel_residual))
+
+    def step(i, check):
+        # one step: H handles of B vectors each, solved concurrently (mca_solve_many returns
+        # when all are done)
+        if H == 1:
+            return step1(i, check)
+        vins = [vin[i * S + h * B:i * S + (h + 1) * B] for h in range(H)]
+        res = mca.solve_many(solvers, vins, n_threads=H, outs=outs)
+        for r in res:
+            for s in r[3]:
+                assert s["status"] == 0 and s["rel_residual"] <= TOL, s
+                if check is not None:
+                    check.append((s["newton_iters"], s["gmres_iters"], s["rel_residual"]))
 
     warm = []
     for i in range(W):
@@ -274,25 +297,33 @@ def run_ours(args):
     t = job_time(ev0.elapsed_time(ev1) / 1000.0, pg)
     if pg:
         pg.barrier()
-    value = world * K * B / t
+    value = world * K * S / t
 
     # ---- end to end through the C ABI with host buffers (pinned), copies included.  One
-    # call takes E2E_PASSES batches of B vectors: the library runs them as passes of B and
+    # call gives each handle P passes of B vectors: the library runs them as passes of B and
     # overlaps each pass' device->host output copies with the next pass' kernels.
-    P = E2E_PASSES
+    P = max(2, min(E2E_PASSES, E2E_SOLVES // S))
     vin_h = torch.as_tensor(cb.vin).pin_memory()
-    vt_h = torch.empty(P * B, m, n, dtype=torch.float64).pin_memory()
-    vb_h = torch.empty_like(vt_h).pin_memory()
-    io_h = torch.empty(P * B, n, dtype=torch.float64).pin_memory()
+    outs_h = [(torch.empty(P * B, m, n, dtype=torch.float64).pin_memory(),
+               torch.empty(P * B, m, n, dtype=torch.float64).pin_memory(),
+               torch.empty(P * B, n, dtype=torch.float64).pin_memory()) for _ in range(H)]
 
     stats_e = (mca.Stats * (P * B))()
     sp_e = mca.ctypes.cast(stats_e, mca.ctypes.c_void_p)
 
     def step_host(i):
-        rc = solver.solve_raw(vin_h[i * B:(i + P) * B].data_ptr(), P * B, vt_h.data_ptr(),
-                              vb_h.data_ptr(), io_h.data_ptr(), sp_e, stream)
-        if rc != 0:
-            raise RuntimeError(f"solve failed with status {rc}")
+        base = i * S
+        if H == 1:
+            vt_h, vb_h, io_h = outs_h[0]
+            rc = solver.solve_raw(vin_h[base:base + P * B].data_ptr(), P * B, vt_h.data_ptr(),
+                                  vb_h.data_ptr(), io_h.data_ptr(), sp_e, stream)
+            if rc != 0:
+                raise RuntimeError(f"solve failed with status {rc}")
+            return
+        vins = [vin_h[base + h * P * B:base + (h + 1) * P * B] for h in range(H)]
+        for r in mca.solve_many(solvers, vins, n_threads=H, outs=outs_h):
+            for st_ in r[3]:
+                assert st_["status"] == 0 and st_["rel_residual"] <= TOL, st_
 
     step_host(0)
     torch.cuda.synchronize()
@@ -305,15 +336,17 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     te = job_time(e0.elapsed_time(e1) / 1000.0, pg)
-    e2e = {"value": world * ke * P * B / te, "unit": "solves/s",
-           "h2d_bytes_per_step": P * B * m * 8,
-           "d2h_bytes_per_step": P * B * (2 * m * n + n) * 8 + P * B * mca.ctypes.sizeof(mca.Stats),
-           "solves_per_call": P * B, "calls": ke}
+    e2e = {"value": world * ke * P * S / te, "unit": "solves/s",
+           "h2d_bytes_per_step": P * S * m * 8,
+           "d2h_bytes_per_step": P * S * (2 * m * n + n) * 8 + P * S * mca.ctypes.sizeof(mca.Stats),
+           "solves_per_call": P * S, "calls": ke}
 
-    # ---- per-family kernel timing (CUDA events on the solve stream, separate pass)
+    # ---- per-family kernel timing (CUDA events on the solve stream, separate pass of one
+    # handle alone: the concurrent handles' kernels overlap, which per-launch events cannot
+    # apportion)
     solver.profile(True)
     for i in range(W, W + min(K, 4)):
-        step(i, None)
+        step1(i, None)
     prof = solver.profile_read()
     solver.profile(False)
     peaks, peak_src = load_peaks()
@@ -357,20 +390,23 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": 1000 * t / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+bf16" if prec in (mca.PREC_BF16, mca.PREC_BF16_SPLIT) else "f64",
-        "data": "synthetic", "config": workload_config(args, B),
+        "data": "synthetic",
+        "config": dict(workload_config(args, S), handles=H, batch_per_handle=B,
+                       profile_pass="kernel_breakdown and roofline: one handle alone"),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
         "precond_tflops": precond_tflops, "kernel_breakdown": breakdown,
         # summed device time of the timed kernels per step (profile pass) over the timed
         # step: what is left is host-side gaps (Newton checks, graph launches)
-        "kernel_ms_per_step": total_ms / min(K, 4),
-        "gpu_busy_frac": (total_ms / min(K, 4)) / (1000 * t / K),
+        "kernel_ms_per_step": total_ms / min(K, 4) * H,
+        "gpu_busy_frac": (total_ms / min(K, 4) * H) / (1000 * t / K),
         "gemm_tiles": gemm_tiles(solver),
         "newton_iters_per_solve": float(iters[:, 0].mean()),
         "gmres_iters_per_solve": float(iters[:, 1].mean()),
         "max_rel_residual": float(max(r for _, _, r in timed)),
     }
-    solver.close()
-    del vt, vb, io
+    for s_ in solvers:
+        s_.close()
+    del vt, vb, io, outs, outs_h
 
     # ---- the same workload in the plain FP64 GPU form (one vector)
     if not args.no_fp64_form and prec != mca.PREC_FP64:
@@ -506,6 +542,7 @@ def gemm_tiles(solver):
 
 # Batches per end-to-end call (see the e2e block in run_bench).
 E2E_PASSES = 8
+E2E_SOLVES = 256     # solves per end-to-end call
 
 
 # FP64 CUDA-core peak used for the FP64 form: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
