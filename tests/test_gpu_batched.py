@@ -111,3 +111,36 @@ def test_statistical_characterisation_sample():
     finally:
         for s in solvers:
             s.close()
+
+
+def test_concurrent_handles_device_buffers():
+    """The bench's pattern: two handles of one crossbar solved concurrently from two host
+    threads with device-resident inputs and outputs (graph capture in both threads at once).
+    Each handle's results equal a later solve of the same vectors on its own, and the oracle
+    recomputes the KCL residual of some of them."""
+    cb = mi.make_crossbar(256, 256, 21, nvec=32)
+    p = cb.params
+    prm = _params(p, precision=mca.PREC_BF16_SPLIT, max_batch=16, newton_rtol=1e-8)
+    hs = [mca.Solver(prm, cb.gmap) for _ in range(2)]
+    try:
+        dev = "cuda:0"
+        vin = torch.as_tensor(cb.vin, device=dev)
+        outs = [(torch.empty(16, 256, 256, dtype=torch.float64, device=dev),
+                 torch.empty(16, 256, 256, dtype=torch.float64, device=dev),
+                 torch.empty(16, 256, dtype=torch.float64, device=dev)) for _ in range(2)]
+        res = mca.solve_many(hs, [vin[:16], vin[16:]], n_threads=2, outs=outs)
+        for k in range(2):
+            assert all(x["status"] == 0 for x in res[k][3])
+            vt1, vb1, io1, _ = hs[k].solve(cb.vin[16 * k:16 * (k + 1)])
+            assert _rel(outs[k][0].cpu().numpy(), vt1) < 1e-12
+            assert _rel(outs[k][2].cpu().numpy(), io1) < 1e-12
+        for v in (0, 17, 31):
+            k, j = divmod(v, 16)
+            vt = outs[k][0][j].cpu().numpy().ravel()
+            vb = outs[k][1][j].cpu().numpy().ravel()
+            Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], vt, vb)
+            Yt, _ = O.source_vector(p, cb.vin[v])
+            assert np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt) <= 1e-8 * 1.01
+    finally:
+        for h in hs:
+            h.close()
