@@ -19,6 +19,7 @@
 //
 // All device-side waits are bounded by a wall-clock limit; on expiry the CTA records
 // MCA_ERR_TIMEOUT in a device flag, frees its TMEM and returns.
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -803,38 +804,42 @@ cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtens
   return cudaGetLastError();
 }
 
-int g_num_sms = 0;
+// set on first use; atomic because handles may be used from several host threads
+std::atomic<int> g_num_sms{0};
 
 template <int BN, bool SPLIT, int EPI, int LP>
 cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
                       const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
   using L = WsLayout<BN, SPLIT, EPI, LP>;
   if (ep.R % BM != 0 || ep.C % BN != 0 || ep.K % L::BKT != 0) return cudaErrorInvalidValue;
-  if (g_num_sms <= 0) {
+  int nsm = g_num_sms.load(std::memory_order_relaxed);
+  if (nsm <= 0) {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm <= 0)
       return cudaErrorInvalidValue;
+    g_num_sms.store(nsm, std::memory_order_relaxed);
   }
   const int ntiles = (ep.R / BM) * (ep.C / BN) * (LP == 1 ? 2 : 1) * B;
-  const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  const int grid = ntiles < nsm ? ntiles : nsm;
   k_gemm_ws<BN, SPLIT, EPI, LP><<<grid, L::THREADS, L::SMEM, s>>>(a, al, bm, bml, ep, B);
   return cudaGetLastError();
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 }  // namespace
 
 bool encode_available() {
-  if (g_encode) return true;
+  if (g_encode.load()) return true;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                        &q) != cudaSuccess ||
       q != cudaDriverEntryPointSuccess || fn == nullptr)
     return false;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  g_encode.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn));
   return true;
 }
 
@@ -848,7 +853,7 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
   cuuint64_t gstride[1] = {cols * 2};
   cuuint32_t box[2] = {box_k, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
+  CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
                         gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         box_k == (uint32_t)BK ? CU_TENSOR_MAP_SWIZZLE_128B
                                               : CU_TENSOR_MAP_SWIZZLE_64B,
@@ -896,8 +901,6 @@ cudaError_t gemm_ws(int bn, int lp, bool split, int epi, const CUtensorMap& a,
 // Set the dynamic shared-memory limit of every GEMM instantiation up front, so no
 // attribute call happens later inside a stream capture.
 cudaError_t configure_all() {
-  const CUtensorMap* none = nullptr;
-  (void)none;
 #define MCA_TC_CFG(BN_, SPLIT_, EPI_)                                                   \
   {                                                                                     \
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN_, SPLIT_, EPI_>,                  \
