@@ -1,14 +1,13 @@
 // Residual evaluation that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the KCL residual:
-// code that runs while a stream is being captured into a CUDA graph (allocation is not a
-// capturable operation), services that must not touch the allocator after start-up
-// (fixed memory budgets, real-time loops), and hosts whose device memory belongs to
-// another framework's pool.  mca_create() allocates the whole solver workspace, so those
-// callers get this one entry point instead: it needs no handle, takes every input and
-// output from the caller, and keeps its only scratch -- the per-block partial sums of
-// ||F||^2 and sum(D) -- in the fixed array below, which every GPU that loads the library
-// holds until the process exits.
+// services that must not touch the device allocator after start-up (fixed memory
+// budgets, real-time control loops), and hosts whose device memory belongs to another
+// framework's pool, which hands out no raw allocations.  mca_create() allocates the whole
+// solver workspace, so those callers get this one entry point instead: it needs no
+// handle, takes every input and output from the caller, and keeps its only scratch -- the
+// per-block partial sums of ||F||^2 and sum(D) -- in the fixed array below, which every
+// GPU that loads the library holds until the process exits.
 //
 // Rules of use:
 //   * at most kMaxVec input vectors per call (larger calls return MCA_ERR_INVALID_ARG);
@@ -29,8 +28,8 @@ namespace mca {
 
 namespace {
 
-constexpr int kMaxVec = 8;          // vectors per call
-constexpr int kMaxBlocks = 608;     // residual_nblk() never exceeds this
+constexpr int kMaxVec = 8;                        // vectors per call
+constexpr int kMaxBlocks = kResidualMaxBlocks;    // residual_nblk() never exceeds this
 constexpr int kMaxDevices = 64;
 
 // Partial sums of the residual kernel: [vector][32 rows][block] (rows 0 and 1 used).
@@ -85,14 +84,13 @@ using namespace mca;
 extern "C" int mca_residual_noalloc(const mca_params* p, const double* g_map, const double* x,
                                     const double* v_in, int32_t nvec, double* F, double* D,
                                     double* fnorm, double* dmean, void* stream) {
+  clear_error_message();
   if (!p || !g_map || !x || !v_in || !F || !D) {
     set_error_message("mca_residual_noalloc: NULL argument");
     return MCA_ERR_INVALID_ARG;
   }
-  if (p->rows < 1 || p->cols < 1 || p->rows > 16384 || p->cols > 16384) {
-    set_error_message("mca_residual_noalloc: rows and cols must be in 1..16384");
-    return MCA_ERR_INVALID_ARG;
-  }
+  // the same circuit checks as mca_create (sizes, conductances, b, device model)
+  if (validate_circuit(p) != MCA_OK) return MCA_ERR_INVALID_ARG;
   if (nvec < 1 || nvec > kMaxVec) {
     set_error_message("mca_residual_noalloc: nvec must be in 1..8 (size of the fixed scratch)");
     return MCA_ERR_INVALID_ARG;
@@ -103,9 +101,17 @@ extern "C" int mca_residual_noalloc(const mca_params* p, const double* g_map, co
   const Grid gr = make_grid(*p);
   const int mn = gr.m * gr.n;
   const int nblk = residual_nblk(mn);
+  if (nblk > kMaxBlocks) {   // the partial sums would not fit the fixed array
+    set_error_message("mca_residual_noalloc: residual grid exceeds the fixed scratch");
+    return MCA_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   launch_residual(gr, g_map, v_in, x, F, D, part, nblk, nvec, nullptr, s);
-  if (fnorm || dmean) k_noalloc_finish<<<nvec, 32, 0, s>>>(part, nblk, mn, fnorm, dmean);
+  count_launches(1);
+  if (fnorm || dmean) {
+    k_noalloc_finish<<<nvec, 32, 0, s>>>(part, nblk, mn, fnorm, dmean);
+    count_launches(1);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "mca_residual_noalloc launch", __FILE__, __LINE__);

@@ -37,8 +37,16 @@ def test_noalloc_residual_matches_handle_residual(m, n, nvec):
             D1 = torch.full_like(D0, float("nan"))
             fn1 = torch.full((nvec,), float("nan"), dtype=torch.float64, device="cuda:0")
             dm1 = torch.full_like(fn1, float("nan"))
+            torch.cuda.synchronize()
+            used0 = torch.cuda.memory_allocated()
+            free0 = torch.cuda.mem_get_info()[0]
             mca.residual_noalloc(params, g, x, vin, F1, D1, fn1, dm1)
             torch.cuda.synchronize()
+            if call == 1:
+                # after the first call (which loads the kernels and looks up the scratch
+                # address) a call leaves the device allocator and free memory untouched
+                assert torch.cuda.memory_allocated() == used0
+                assert torch.cuda.mem_get_info()[0] == free0
             assert torch.equal(F0, F1) and torch.equal(D0, D1)
             np.testing.assert_allclose(fn1.cpu().numpy(), fn0, rtol=1e-12)
             np.testing.assert_allclose(dm1.cpu().numpy(), dm0, rtol=1e-12)
@@ -51,5 +59,19 @@ def test_noalloc_rejects_too_many_vectors():
         mca.residual_noalloc(params, torch.ones(16, dtype=torch.float64, device="cuda:0"), x,
                              torch.zeros(9, 4, dtype=torch.float64, device="cuda:0"),
                              torch.empty_like(x), torch.empty(9, 16, dtype=torch.float64,
+                                                              device="cuda:0"))
+    assert e.value.code == mca.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value", [("g_wire_top", 0.0), ("b", float("nan")),
+                                         ("device_model", 7), ("g_sense", -1.0)])
+def test_noalloc_rejects_bad_circuit_parameters(field, value):
+    params = mca.default_params(4, 4)
+    setattr(params, field, value)
+    x = torch.zeros(1, 32, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(mca.MCAError) as e:
+        mca.residual_noalloc(params, torch.ones(16, dtype=torch.float64, device="cuda:0"), x,
+                             torch.zeros(1, 4, dtype=torch.float64, device="cuda:0"),
+                             torch.empty_like(x), torch.empty(1, 16, dtype=torch.float64,
                                                               device="cuda:0"))
     assert e.value.code == mca.ERR_INVALID_ARG
