@@ -105,6 +105,30 @@ def config_large(n, seed, nvec=1):
     return make_crossbar(n, n, seed, nvec=nvec, g_wire_bot=0.5)
 
 
+@dataclass
+class CrossbarSet:
+    """Several crossbars of one shape and wiring with their input vectors interleaved:
+    vector v belongs to crossbar map_index[v]."""
+    params: CrossbarParams
+    gmaps: np.ndarray       # (k, m, n)
+    vin: np.ndarray         # (nvec, m)
+    map_index: np.ndarray   # (nvec,) int32
+    seeds: tuple
+
+
+def config_large_set(n, seeds=(0, 1, 2, 3), nvec=4):
+    """The n x n workload over several crossbars (seeds 0-3 by default): crossbar k is
+    config_large(n, seeds[k]); vector v is crossbar v % k's own vector v // k."""
+    k = len(seeds)
+    per = (nvec + k - 1) // k
+    cbs = [config_large(n, s, nvec=per) for s in seeds]
+    idx = np.arange(nvec)
+    vin = np.stack([cbs[v % k].vin[v // k] for v in idx])
+    return CrossbarSet(params=cbs[0].params, gmaps=np.stack([c.gmap for c in cbs]),
+                       vin=np.ascontiguousarray(vin), map_index=(idx % k).astype(np.int32),
+                       seeds=tuple(seeds))
+
+
 BATCH_SIZES = (64, 128, 256, 512)
 
 

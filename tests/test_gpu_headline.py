@@ -1,0 +1,101 @@
+"""Parity of the exact configuration the throughput figure is measured on.
+
+1024 x 1024 crossbars (seeds 0-3 in one multi-map handle, input vectors interleaved over
+them; log-uniform g, wires 1 S top / 0.5 S bottom, sinh devices b = 2), BF16-split
+tensor-core preconditioner, Newton to 1e-8 relative KCL residual, two handles of 64 input
+vectors each solved concurrently through mca_solve_many with device-resident buffers,
+default flags (CUDA graphs and the tile autotuner).  The checks:
+
+* the autotuner picked the persistent warp-specialised kernel with 128 x 256 tiles for
+  transforms 1, 3 and 4 (the kernels the throughput figure runs);
+* the CPU oracle recomputes the FP64 KCL residual ||F||/||Y|| (eq. (F), Section 2) of a
+  sample of the 128 returned solutions from both handles, and the Kirchhoff balance;
+* at a 1e-12 solve in the same configuration, one vector's node voltages match the
+  oracle's Newton + preconditioned GMRES solution to 1e-7 on the scale of the solution.
+"""
+import numpy as np
+import pytest
+
+import mca_inputs as mi
+from oracle import mca_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2109_07929_gb300 as mca  # noqa: E402
+
+M = N = 1024
+B = 64          # vectors per handle
+H = 2           # handles solved concurrently
+SAMPLE = (0, 13, 63, 64, 90, 127)   # vectors whose residual the oracle recomputes
+
+
+def _params(p, tol):
+    return mca.default_params(M, N, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
+                              g_src=p.g_src, g_term_top_right=p.g_term_top_right,
+                              g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
+                              precision=mca.PREC_BF16_SPLIT, newton_rtol=tol, max_batch=B)
+
+
+def _solve_two_handles(ws, tol):
+    dev = "cuda:0"
+    solvers = [mca.Solver(_params(ws.params, tol), ws.gmaps) for _ in range(H)]
+    try:
+        tiles = [s.tile_config() for s in solvers]
+        vin = torch.as_tensor(ws.vin, device=dev)
+        outs = [(torch.empty(B, M, N, dtype=torch.float64, device=dev),
+                 torch.empty(B, M, N, dtype=torch.float64, device=dev),
+                 torch.empty(B, N, dtype=torch.float64, device=dev)) for _ in range(H)]
+        res = mca.solve_many(solvers, [vin[h * B:(h + 1) * B] for h in range(H)],
+                             map_indices=[ws.map_index[h * B:(h + 1) * B] for h in range(H)],
+                             n_threads=H, outs=outs)
+        torch.cuda.synchronize()
+        stats = [st for r in res for st in r[3]]
+        return tiles, outs, stats
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def _vec(outs, v):
+    h, j = divmod(v, B)
+    return (outs[h][0][j].cpu().numpy(), outs[h][1][j].cpu().numpy(),
+            outs[h][2][j].cpu().numpy())
+
+
+def test_headline_configuration_against_oracle():
+    ws = mi.config_large_set(M, seeds=(0, 1, 2, 3), nvec=H * B)
+    p = ws.params
+    tiles, outs, stats = _solve_two_handles(ws, 1e-8)
+    for cfg in tiles:
+        # (persistent, tile columns, layers per tile) of transforms 1..4
+        for s in (0, 2, 3):
+            assert cfg[s] == (1, 256, 1), cfg
+        assert cfg[1][0] == 1, cfg
+    assert len(stats) == H * B
+    for st in stats:
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-8, st
+    for v in SAMPLE:
+        vt, vb, io = _vec(outs, v)
+        g = ws.gmaps[ws.map_index[v]]
+        Ft, Fb = O.residual(p, g, ws.vin[v], vt.ravel(), vb.ravel())
+        Yt, _ = O.source_vector(p, ws.vin[v])
+        rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
+        assert rel <= 1e-8 * 1.01, (v, rel)
+        np.testing.assert_allclose(stats[v]["rel_residual"], rel, rtol=1e-3, atol=1e-11)
+        np.testing.assert_allclose(io, p.g_sense * vb[-1], rtol=1e-15)
+        i_in = O.outputs(p, ws.vin[v], vt, vb)["i_in"].sum()
+        assert abs(O.kcl_balance(p, ws.vin[v], vt, vb)) <= 1e-6 * i_in
+    del outs
+    torch.cuda.empty_cache()
+
+    # the same configuration solved tight: voltages against the oracle's solution
+    _, outs, stats = _solve_two_handles(ws, 1e-12)
+    for st in stats:
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-12, st
+    v = 77
+    vt, vb, _ = _vec(outs, v)
+    ref = O.newton_solve(p, ws.gmaps[ws.map_index[v]], ws.vin[v], tol=1e-12, linear="pgmres")
+    scale = max(np.abs(ref.Vt).max(), np.abs(ref.Vb).max())
+    assert np.abs(vt - ref.Vt).max() <= 1e-7 * scale
+    assert np.abs(vb - ref.Vb).max() <= 1e-7 * scale

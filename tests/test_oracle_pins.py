@@ -267,6 +267,37 @@ def test_mhat_apply_and_condition():
     assert ok and diagM > 20 * a2
 
 
+def _dense_schur(p, a1, a2):
+    """eq. (M) formed densely as the Schur complement C - D B^-1 A of P (eq. P)."""
+    Gt, Gb = O.layer_operators(p)
+    N = p.rows * p.cols
+    I = np.eye(N)
+    return -a2 * I - (Gb.toarray() + a2 * I) @ np.linalg.inv(-a1 * I) @ (Gt.toarray() + a1 * I)
+
+
+@pytest.mark.parametrize("a", [2e-5, 0.3, 0.5, 1.0, 3.0])
+def test_mhat_condition_against_dense_schur_diagonal(a):
+    """eqs. (diagM), (condition): diag(M) at an interior node is read off the dense
+    Schur complement, and the condition 20 a2 < diag(M) + a2 is decided on it.  With
+    equal wires the function's diag(M) is that entry; with unequal wires it is the entry
+    of the array whose wires are both the weaker one, which bounds every interior entry of
+    the actual M from below.  The a values straddle the point where the condition fails."""
+    m, n = 5, 6
+    interior = [i * n + j for i in range(1, m - 1) for j in range(1, n - 1)]
+    for gt, gb in ((1.0, 1.0), (1.0, 0.5), (0.4, 2.0)):
+        p = _params(m, n, g_wire_top=gt, g_wire_bot=gb)
+        ok, diagM = O.mhat_condition(p, a, a)
+        gw = min(gt, gb)
+        M_weak = _dense_schur(_params(m, n, g_wire_top=gw, g_wire_bot=gw), a, a)
+        d_weak = np.diag(M_weak)[interior]
+        np.testing.assert_allclose(d_weak, diagM, rtol=1e-12)
+        assert ok == bool(20 * a < d_weak[0] + a)
+        d_true = np.diag(_dense_schur(p, a, a))[interior]
+        assert diagM <= d_true.min() * (1 + 1e-12)
+        if gt == gb:
+            np.testing.assert_allclose(d_true, diagM, rtol=1e-12)
+
+
 def test_kcl_conservation_and_outputs():
     cb = mi.config_small(0)
     p = cb.params
