@@ -55,9 +55,11 @@ extern "C" {
 #define MCA_PREC_FP64 0        /* all four eigenbasis transforms in FP64 (CUDA cores)     */
 #define MCA_PREC_BF16 1        /* all four transforms on tcgen05 tensor cores, BF16 in,
                                   FP32 accumulate                                        */
-#define MCA_PREC_BF16_SPLIT 2  /* forward transforms BF16; back transforms with hi+lo
-                                  BF16 splitting of both operands (3 tensor-core
-                                  products, FP32 accumulate)                             */
+#define MCA_PREC_BF16_SPLIT 2  /* forward transforms BF16; back transforms with the
+                                  eigenvectors split as hi+lo BF16 pairs: transform 3
+                                  Y_hat (hi) x Q_r (hi+lo), 2 tensor-core products;
+                                  transform 4 E (hi+lo) x Q_c (hi+lo), 3 products
+                                  (hi*hi + lo*hi + hi*lo); FP32 accumulate               */
 #define MCA_PREC_MHAT 3        /* the paper's own evaluation: eq. (block) with the
                                   approximate Schur complement M_hat of eq. (Mhat), applied
                                   by tridiagonal solves (eq. 2matrix4), FP64              */
@@ -338,7 +340,7 @@ int mca_profile(mca_handle* h, int32_t enable);
 /* Totals of one family since the last enable: launches that did work, their summed
  * device time in ms, and their algorithmic DRAM bytes and FLOPs (counting only the
  * vectors still iterating in each launch; the tensor-core transforms count the MMA
- * FLOPs they execute, 3 products per split transform).  Any output may be NULL. */
+ * FLOPs they execute: 2 products in split transform 3, 3 in split transform 4).  Any output may be NULL. */
 int mca_profile_read(mca_handle* h, int32_t family, int64_t* launches, double* ms,
                      double* bytes, double* flops);
 
@@ -351,10 +353,11 @@ int mca_tile_config(const mca_handle* h, int32_t* cfg);
 /* ---- residual without device allocation ------------------------------------------- */
 
 /* Residual, Jacobian diagonal and their norms for callers that cannot allocate device
- * memory: code running inside CUDA graph stream capture (allocation cannot be captured),
- * services that forbid allocator calls after start-up, and hosts whose device memory is
- * owned by another framework's pool.  The paper has no counterpart; this is a usage
- * variant of mca_residual() that needs no handle and makes no cudaMalloc/cudaFree.
+ * memory: services that forbid allocator calls after start-up (fixed memory budgets,
+ * real-time loops), and hosts whose device memory is owned by another framework's pool.
+ * The paper has no counterpart; this is a usage variant of mca_residual() that needs no
+ * handle and makes no cudaMalloc/cudaFree.  Parameters are checked as in mca_create()
+ * (circuit part only: sizes, conductances, b, device model).
  *   p      : circuit parameters (rows, cols, wire/termination conductances, b).
  *   g_map  : device, m*n memristor conductances.
  *   x      : device, nvec * 2*m*n states [V_t ; V_b].

@@ -345,6 +345,13 @@ class Solver:
         return self.lib.mca_solve(self.h, vin_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr,
                                   _stream_ptr(stream))
 
+    def solve_multi_raw(self, vin_ptr, map_ptr, nvec, vt_ptr, vb_ptr, io_ptr, stats_ptr=None,
+                        stream=None):
+        """Pointer-level call of mca_solve_multi (map_ptr: host int32 map indices or None);
+        returns the status."""
+        return self.lib.mca_solve_multi(self.h, vin_ptr, map_ptr, nvec, vt_ptr, vb_ptr, io_ptr,
+                                        stats_ptr, _stream_ptr(stream))
+
     def tile_config(self):
         """[(persistent, tile columns, layers per tile)] of the four tensor-core transforms."""
         cfg = (ctypes.c_int32 * 12)()

@@ -13,9 +13,13 @@
 // the MMA descriptors expect, and every epilogue writes its tile transposed, which makes
 // the TMEM lane = output row mapping store coalesced.
 //
-// Precision: the back transforms (3, 4) multiply the large amplified low modes of Y_hat;
-// with MCA_PREC_BF16_SPLIT both of their operands are split as hi + lo BF16 pairs and
-// the three products hi*hi + hi*lo + lo*hi accumulate in the same FP32 tile.
+// Precision: the back transforms (3, 4) multiply the large amplified low modes of Y_hat.
+// With MCA_PREC_BF16_SPLIT the eigenvector operands of both are split as hi + lo BF16
+// pairs, so the rounding of Q does not leak the amplified low modes into the high ones.
+// Transform 3's data operand Y_hat stays one BF16 word (its rounding changes each mode by
+// 2^-9 of itself: two products, A*hi + A*lo), while transform 4's data operand E (modes
+// along rows only) is split as well: three products hi*hi + lo*hi + hi*lo in one FP32
+// tile.
 //
 // All device-side waits are bounded by a wall-clock limit; on expiry the CTA records
 // MCA_ERR_TIMEOUT in a device flag, frees its TMEM and returns.
@@ -195,15 +199,16 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 // to ~200 KB of stages.  A staged BF16 epilogue reuses the stage buffers (2 or 4 output
 // tiles of 128 x BN), which sets the floor on their size.  Split GEMMs use 32-wide K
 // tiles (64-byte swizzle) to make their stages small enough to pair up.
-template <int BN, bool SPLIT, int EPI>
+template <int BN, int SPLIT, int EPI>
 struct Layout {
   static constexpr int BKT = SPLIT ? BK_SPLIT : BK;
   static constexpr int A_BYTES = BM * BKT * 2;
   static constexpr int B_BYTES = BN * BKT * 2;
-  static constexpr int HALF = 2 * A_BYTES + B_BYTES;
-  static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
+  static constexpr int HALF = 2 * A_BYTES + B_BYTES;       // hi words: 2 layers of A, B
+  static constexpr int STAGE = SPLIT == SPLIT_AB ? 2 * HALF :
+                               (SPLIT == SPLIT_B ? HALF + B_BYTES : HALF);
   static constexpr int STAGE_OUT = (EPI == EPI_F64 || EPI == EPI_F32) ? 0 :
-      ((EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT) ? 4 : 2) * BN * BM * 2;
+      (EPI == EPI_SPLIT ? 4 : 2) * BN * BM * 2;
   static constexpr int STAGES_MIN = (STAGE_OUT + STAGE - 1) / STAGE;
   static constexpr int STAGES_2 = STAGES_MIN > 2 ? STAGES_MIN : 2;
   static constexpr int CTAS = (STAGES_2 * STAGE <= 110 * 1024) ? 2 : 1;
@@ -216,24 +221,39 @@ struct Layout {
 
 // Instantiations of the persistent kernel (BN, SPLIT, EPI, LP).
 #define MCA_WS_LIST(X)                 \
-  X(128, false, EPI_BF16, 1)           \
-  X(256, false, EPI_BF16, 1)           \
-  X(64, false, EPI_MODES, 2)           \
-  X(128, false, EPI_MODES, 2)          \
-  X(64, false, EPI_MODES_SPLIT, 2)     \
-  X(128, false, EPI_MODES_SPLIT, 2)    \
-  X(128, true, EPI_SPLIT, 1)           \
-  X(256, true, EPI_SPLIT, 1)           \
-  X(128, false, EPI_F64, 1)            \
-  X(256, false, EPI_F64, 1)            \
-  X(128, true, EPI_F64, 1)             \
-  X(256, true, EPI_F64, 1)             \
-  X(128, false, EPI_F32, 1)            \
-  X(256, false, EPI_F32, 1)            \
-  X(128, true, EPI_F32, 1)             \
-  X(256, true, EPI_F32, 1)
+  X(128, SPLIT_NONE, EPI_BF16, 1)      \
+  X(256, SPLIT_NONE, EPI_BF16, 1)      \
+  X(64, SPLIT_NONE, EPI_MODES, 2)      \
+  X(128, SPLIT_NONE, EPI_MODES, 2)     \
+  X(128, SPLIT_B, EPI_SPLIT, 1)        \
+  X(256, SPLIT_B, EPI_SPLIT, 1)        \
+  X(128, SPLIT_NONE, EPI_F64, 1)       \
+  X(256, SPLIT_NONE, EPI_F64, 1)       \
+  X(128, SPLIT_AB, EPI_F64, 1)         \
+  X(256, SPLIT_AB, EPI_F64, 1)         \
+  X(128, SPLIT_NONE, EPI_F32, 1)       \
+  X(256, SPLIT_NONE, EPI_F32, 1)       \
+  X(128, SPLIT_AB, EPI_F32, 1)         \
+  X(256, SPLIT_AB, EPI_F32, 1)
 
-template <int BN, bool SPLIT, int EPI>
+// Instantiations of the one-CTA-per-tile kernel (BN, SPLIT, EPI).
+#define MCA_TC_LIST(X)                 \
+  X(128, SPLIT_NONE, EPI_BF16)         \
+  X(64, SPLIT_NONE, EPI_BF16)          \
+  X(128, SPLIT_NONE, EPI_MODES)        \
+  X(64, SPLIT_NONE, EPI_MODES)         \
+  X(128, SPLIT_NONE, EPI_F64)          \
+  X(64, SPLIT_NONE, EPI_F64)           \
+  X(128, SPLIT_B, EPI_SPLIT)           \
+  X(64, SPLIT_B, EPI_SPLIT)            \
+  X(128, SPLIT_AB, EPI_F64)            \
+  X(64, SPLIT_AB, EPI_F64)             \
+  X(128, SPLIT_NONE, EPI_F32)          \
+  X(64, SPLIT_NONE, EPI_F32)           \
+  X(128, SPLIT_AB, EPI_F32)            \
+  X(64, SPLIT_AB, EPI_F32)
+
+template <int BN, int SPLIT, int EPI>
 __global__ void __launch_bounds__(kThreads, Layout<BN, SPLIT, EPI>::CTAS)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
@@ -290,11 +310,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       tma_load_2d(st, &tmA, k0, blk0 * ep.R + r0, &full[s]);
       tma_load_2d(st + L::A_BYTES, &tmA, k0, blk1 * ep.R + r0, &full[s]);
       tma_load_2d(st + 2 * L::A_BYTES, &tmB, k0, c0, &full[s]);
-      if (SPLIT) {
+      if (SPLIT == SPLIT_AB) {
         uint8_t* sl = st + L::HALF;
         tma_load_2d(sl, &tmAl, k0, blk0 * ep.R + r0, &full[s]);
         tma_load_2d(sl + L::A_BYTES, &tmAl, k0, blk1 * ep.R + r0, &full[s]);
         tma_load_2d(sl + 2 * L::A_BYTES, &tmBl, k0, c0, &full[s]);
+      } else if (SPLIT == SPLIT_B) {
+        tma_load_2d(st + L::HALF, &tmBl, k0, c0, &full[s]);
       }
     }
   } else if (threadIdx.x == 32) {
@@ -320,7 +342,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
         umma(tmem, a0, bd, idesc, acc);
         umma(tmem + BN, a1, bd, idesc, acc);
-        if (SPLIT) {
+        if (SPLIT == SPLIT_AB) {
           const uint8_t* sl = st + L::HALF;
           const uint64_t a0l = tile_desc<BKT>(sl + off);
           const uint64_t a1l = tile_desc<BKT>(sl + L::A_BYTES + off);
@@ -328,6 +350,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           umma(tmem, a0l, bd, idesc, 1u);
           umma(tmem, a0, bdl, idesc, 1u);
           umma(tmem + BN, a1l, bd, idesc, 1u);
+          umma(tmem + BN, a1, bdl, idesc, 1u);
+        } else if (SPLIT == SPLIT_B) {
+          const uint64_t bdl = tile_desc<BKT>(st + L::HALF + off);
+          umma(tmem, a0, bdl, idesc, 1u);
           umma(tmem + BN, a1, bdl, idesc, 1u);
         }
       }
@@ -342,7 +368,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const bool have = __syncthreads_and(mbar_wait(accum, 0) ? 1 : 0) != 0;
   if (!have && threadIdx.x == 0) record_error(ep.err, MCA_ERR_TIMEOUT);
   constexpr bool kBf16Out = (EPI != EPI_F64 && EPI != EPI_F32);
-  constexpr bool kLo = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
+  constexpr bool kLo = (EPI == EPI_SPLIT);
   constexpr int kOuts = kLo ? 4 : 2;            // [hi t, hi b, lo t, lo b]
   // BF16 outputs are staged transposed in the (now idle) pipeline buffers as
   // stage[o][c][r] and leave in 16-byte chunks along r; FP64 outputs go straight out
@@ -357,7 +383,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     float a_mode = 0.f, mu_r = 0.f;
     const bool r_ok = r < ep.R_valid;
     float sc = 1.f;          // scale of the unnormalised input basis vector
-    if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+    if (EPI == EPI_MODES) {
       a_mode = (float)ep.ctl[b].a;
       mu_r = r_ok ? ep.mu_f[r] : 0.f;
       if (ep.kidx >= 0) sc = (float)ep.ctl[b].s[ep.kidx];
@@ -373,7 +399,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const int c = c0 + cl;
         float x0 = __uint_as_float(v0[q]);
         float x1 = __uint_as_float(v1[q]);
-        if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+        if (EPI == EPI_MODES) {
           // [y_t; y_b] = (1/det) [[nu + a, a], [a, mu + a]] [x_t; x_b]
           float y0 = 0.f, y1 = 0.f;
           if (r_ok && c < ep.C_valid) {
@@ -453,14 +479,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // epilogue warp, one output at a time, and leave in 16-byte chunks.
 constexpr int kWsSmemMax = 227 * 1024;
 
-template <int BN, bool SPLIT, int EPI, int LP>
+template <int BN, int SPLIT, int EPI, int LP>
 struct WsLayout {
   static constexpr int BKT = SPLIT ? BK_SPLIT : BK;
   static constexpr int A_BYTES = BM * BKT * 2;
   static constexpr int B_BYTES = BN * BKT * 2;
-  static constexpr int HALF = LP * A_BYTES + B_BYTES;
-  static constexpr int STAGE = SPLIT ? 2 * HALF : HALF;
-  static constexpr bool LO = (EPI == EPI_SPLIT || EPI == EPI_MODES_SPLIT);
+  static constexpr int HALF = LP * A_BYTES + B_BYTES;      // hi words: LP layers of A, B
+  static constexpr int STAGE = SPLIT == SPLIT_AB ? 2 * HALF :
+                               (SPLIT == SPLIT_B ? HALF + B_BYTES : HALF);
+  static constexpr bool LO = (EPI == EPI_SPLIT);
   static constexpr int NOUT = (EPI == EPI_F64 || EPI == EPI_F32) ? 0 : (LO ? 2 : 1) * LP;
   static constexpr int EW = (LP == 2) ? 16 : 8;                           // epilogue warps
   static constexpr int THREADS = 64 + 32 * EW;
@@ -479,14 +506,13 @@ struct WsLayout {
   static_assert(SMEM <= kWsSmemMax, "shared memory plan too large");
 };
 
-template <int BN, bool SPLIT, int EPI, int LP>
+template <int BN, int SPLIT, int EPI, int LP>
 __global__ void __launch_bounds__(WsLayout<BN, SPLIT, EPI, LP>::THREADS, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
           GemmEpi ep, int B) {
   using L = WsLayout<BN, SPLIT, EPI, LP>;
-  static_assert(LP == 2 || (EPI != EPI_MODES && EPI != EPI_MODES_SPLIT),
-                "the modes epilogue needs both layers in one tile");
+  static_assert(LP == 2 || EPI != EPI_MODES, "the modes epilogue needs both layers in one tile");
   constexpr int BKT = L::BKT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -565,12 +591,14 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           for (int l = 0; l < LP; ++l)
             tma_load_2d(st + l * L::A_BYTES, &tmA, k0, row0 + l * ep.R, &full[s]);
           tma_load_2d(st + LP * L::A_BYTES, &tmB, k0, c0, &full[s]);
-          if (SPLIT) {
+          if (SPLIT == SPLIT_AB) {
             uint8_t* sl = st + L::HALF;
 #pragma unroll
             for (int l = 0; l < LP; ++l)
               tma_load_2d(sl + l * L::A_BYTES, &tmAl, k0, row0 + l * ep.R, &full[s]);
             tma_load_2d(sl + LP * L::A_BYTES, &tmBl, k0, c0, &full[s]);
+          } else if (SPLIT == SPLIT_B) {
+            tma_load_2d(st + L::HALF, &tmBl, k0, c0, &full[s]);
           }
         }
       }
@@ -612,12 +640,14 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             for (int l = 0; l < LP; ++l) {
               const uint64_t ad = tile_desc<BKT>(st + l * L::A_BYTES + off);
               umma(dacc + l * BN, ad, bd, idesc, accf);
-              if (SPLIT) {
+              if (SPLIT == SPLIT_AB) {
                 const uint8_t* sl = st + L::HALF;
                 const uint64_t adl = tile_desc<BKT>(sl + l * L::A_BYTES + off);
                 const uint64_t bdl = tile_desc<BKT>(sl + LP * L::A_BYTES + off);
                 umma(dacc + l * BN, adl, bd, idesc, 1u);
                 umma(dacc + l * BN, ad, bdl, idesc, 1u);
+              } else if (SPLIT == SPLIT_B) {
+                umma(dacc + l * BN, ad, tile_desc<BKT>(st + L::HALF + off), idesc, 1u);
               }
             }
           }
@@ -656,7 +686,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const uint32_t lane_base =
           tmem + (uint32_t)(acc * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
       float a_mode = 0.f, mu_a = 0.f, a2 = 0.f, sc = 1.f;
-      if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+      if (EPI == EPI_MODES) {
         a_mode = (float)ep.ctl[b].a;
         mu_a = (r_ok ? ep.mu_f[r] : 0.f) + a_mode;
         a2 = a_mode * a_mode;
@@ -686,7 +716,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
           }
         } else {
-          if (EPI == EPI_MODES || EPI == EPI_MODES_SPLIT) {
+          if (EPI == EPI_MODES) {
             // [y_t; y_b] = (sc / det) [[nu + a, a], [a, mu + a]] [x_t; x_b] in place,
             // det = (mu + a)(nu + a) - a^2; the column eigenvalues come in with one
             // coalesced load and a shuffle per column
@@ -787,7 +817,7 @@ __global__ void k_cast_pad(const double* __restrict__ x, size_t xstride,
   }
 }
 
-template <int BN, bool SPLIT, int EPI>
+template <int BN, int SPLIT, int EPI>
 cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
                        const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
   using L = Layout<BN, SPLIT, EPI>;
@@ -804,22 +834,25 @@ cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtens
   return cudaGetLastError();
 }
 
-// set on first use; atomic because handles may be used from several host threads
-std::atomic<int> g_num_sms{0};
+// SM count per device ordinal, set on first use there; atomic because handles may be
+// used from several host threads
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_num_sms[kMaxDevices] = {};
 
-template <int BN, bool SPLIT, int EPI, int LP>
+template <int BN, int SPLIT, int EPI, int LP>
 cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
                       const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
   using L = WsLayout<BN, SPLIT, EPI, LP>;
   if (ep.R % BM != 0 || ep.C % BN != 0 || ep.K % L::BKT != 0) return cudaErrorInvalidValue;
-  int nsm = g_num_sms.load(std::memory_order_relaxed);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return cudaErrorInvalidValue;
+  int nsm = g_num_sms[dev].load(std::memory_order_relaxed);
   if (nsm <= 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         nsm <= 0)
       return cudaErrorInvalidValue;
-    g_num_sms.store(nsm, std::memory_order_relaxed);
+    g_num_sms[dev].store(nsm, std::memory_order_relaxed);
   }
   const int ntiles = (ep.R / BM) * (ep.C / BN) * (LP == 1 ? 2 : 1) * B;
   const int grid = ntiles < nsm ? ntiles : nsm;
@@ -861,33 +894,18 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
   return r == CUDA_SUCCESS;
 }
 
-cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
+cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s) {
 #define MCA_TC_CASE(BN_, SPLIT_, EPI_)                                       \
   if (bn == BN_ && split == SPLIT_ && epi == EPI_)                           \
     return launch_one<BN_, SPLIT_, EPI_>(a, al, bm, bml, ep, B, s);
-  MCA_TC_CASE(128, false, EPI_BF16)
-  MCA_TC_CASE(64, false, EPI_BF16)
-  MCA_TC_CASE(128, false, EPI_MODES)
-  MCA_TC_CASE(64, false, EPI_MODES)
-  MCA_TC_CASE(128, false, EPI_MODES_SPLIT)
-  MCA_TC_CASE(64, false, EPI_MODES_SPLIT)
-  MCA_TC_CASE(128, false, EPI_F64)
-  MCA_TC_CASE(64, false, EPI_F64)
-  MCA_TC_CASE(128, true, EPI_SPLIT)
-  MCA_TC_CASE(64, true, EPI_SPLIT)
-  MCA_TC_CASE(128, true, EPI_F64)
-  MCA_TC_CASE(64, true, EPI_F64)
-  MCA_TC_CASE(128, false, EPI_F32)
-  MCA_TC_CASE(64, false, EPI_F32)
-  MCA_TC_CASE(128, true, EPI_F32)
-  MCA_TC_CASE(64, true, EPI_F32)
+  MCA_TC_LIST(MCA_TC_CASE)
 #undef MCA_TC_CASE
   return cudaErrorInvalidValue;
 }
 
-cudaError_t gemm_ws(int bn, int lp, bool split, int epi, const CUtensorMap& a,
+cudaError_t gemm_ws(int bn, int lp, int split, int epi, const CUtensorMap& a,
                     const CUtensorMap& al, const CUtensorMap& bm, const CUtensorMap& bml,
                     const GemmEpi& ep, int B, cudaStream_t s) {
 #define MCA_WS_CASE(BN_, SPLIT_, EPI_, LP_)                                  \
@@ -908,22 +926,7 @@ cudaError_t configure_all() {
                                          Layout<BN_, SPLIT_, EPI_>::SMEM);              \
     if (e != cudaSuccess) return e;                                                     \
   }
-  MCA_TC_CFG(128, false, EPI_BF16)
-  MCA_TC_CFG(64, false, EPI_BF16)
-  MCA_TC_CFG(128, false, EPI_MODES)
-  MCA_TC_CFG(64, false, EPI_MODES)
-  MCA_TC_CFG(128, false, EPI_MODES_SPLIT)
-  MCA_TC_CFG(64, false, EPI_MODES_SPLIT)
-  MCA_TC_CFG(128, false, EPI_F64)
-  MCA_TC_CFG(64, false, EPI_F64)
-  MCA_TC_CFG(128, true, EPI_SPLIT)
-  MCA_TC_CFG(64, true, EPI_SPLIT)
-  MCA_TC_CFG(128, true, EPI_F64)
-  MCA_TC_CFG(64, true, EPI_F64)
-  MCA_TC_CFG(128, false, EPI_F32)
-  MCA_TC_CFG(64, false, EPI_F32)
-  MCA_TC_CFG(128, true, EPI_F32)
-  MCA_TC_CFG(64, true, EPI_F32)
+  MCA_TC_LIST(MCA_TC_CFG)
 #undef MCA_TC_CFG
 #define MCA_WS_CFG(BN_, SPLIT_, EPI_, LP_)                                              \
   {                                                                                     \

@@ -141,120 +141,11 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
-// Memristor current and conductance.  The current (g / b) sinh(b dV) = g dV P(dV^2) with
-// P(dV^2) = sinh(x) / x, x = b dV, enters the KCL residual and is kept to FP64 accuracy:
-// for |x| < 3/4, P is the degree-6 economised polynomial above with b folded into its
-// coefficients, evaluated by Horner's rule in FP64 for the terms up to t^2 and, when
-// tail32, in FP32 for the tail t^3 (pc3 + pc4 t + pc5 t^2 + pc6 t^3): that tail is at
-// most x^6 / 5040 < 3.5e-5 of P, so its FP32 rounding (a few 2^-24) moves P by less than
-// 1e-11 relative, while it takes three FMAs off the FP64 pipe.  Outside |x| < 3/4 the
-// CUDA math library.  The range test compares bit patterns (on the integer pipe).
-// The conductance g cosh(x) only
-// shapes the Newton matrix (the Jacobian diagonal and a = mean(D)), so it is evaluated in
-// FP32 (relative error below 3e-7, which changes the inexact Newton steps but not the
-// solution the FP64 residual drives them to) and returned both as float and widened.
-__device__ __forceinline__ void device_current(const Grid& gr, double g, double dv,
-                                               double& cur_over_g, double& dg, float& dgf) {
-  // (the high words suffice: both branches are accurate near the limit)
-  if (((uint32_t)__double2hiint(dv) & 0x7FFFFFFFu) < gr.dv_lim_hi) {
-    const double t = dv * dv;
-    const float dvf = d2f_round(dv);
-    double ps;
-    if (gr.tail32) {
-      const float tf = dvf * dvf;
-      float r = fmaf(gr.pcf[6], tf, gr.pcf[5]);
-      r = fmaf(r, tf, gr.pcf[4]);
-      r = fmaf(r, tf, gr.pcf[3]);
-      ps = fma(f2d_bits(r), t, gr.pc[2]);
-    } else {
-      ps = gr.pc[6];
-      ps = fma(ps, t, gr.pc[5]);
-      ps = fma(ps, t, gr.pc[4]);
-      ps = fma(ps, t, gr.pc[3]);
-      ps = fma(ps, t, gr.pc[2]);
-    }
-    ps = fma(ps, t, gr.pc[1]);
-    ps = fma(ps, t, gr.pc[0]);
-    cur_over_g = dv * ps;
-    dgf = d2f_round(g) * coshf(dvf * gr.bf);
-    dg = f2d_bits(dgf);
-  } else {
-    const double x = gr.b * dv;
-    cur_over_g = sinh(x) * gr.inv_b;
-    dg = g * cosh(x);
-    dgf = d2f_round(dg);
-  }
-}
-
-// Yakopcic-form device: scale the current and the conductance of a device under negative
-// bias (sign read from the bit pattern, on the integer pipe).
-__device__ __forceinline__ void negative_bias(const Grid& gr, double dv, double& cur_over_g,
-                                              double& dg, float& dgf) {
-  const uint32_t hi = (uint32_t)__double2hiint(dv), lo = (uint32_t)__double2loint(dv);
-  if ((hi >> 31) && ((hi & 0x7FFFFFFFu) | lo)) {   // dV < 0, not -0
-    cur_over_g *= gr.rneg;
-    dg *= gr.rneg;
-    dgf *= gr.rnegf;
-  }
-}
-
-// One cell of eq. (F) and the Jacobian diagonal; returns (F_t, F_b, D).  YAK: the
-// Yakopcic-form device (a compile-time choice, so the sinh device pays nothing for it).
-template <bool YAK>
-__device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
-                                              const double* __restrict__ Vt,
-                                              const double* __restrict__ Vb, double g,
-                                              double vin_i, double& ft, double& fb,
-                                              double& dg, float& dgf) {
-  const int m = gr.m, n = gr.n;
-  const double vt = Vt[c], vb = Vb[c];
-  const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
-  const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
-  const double tl = (j > 0) ? Vt[c - 1] : 0.0;
-  const double tr = (j < n - 1) ? Vt[c + 1] : 0.0;
-  const double bu = (i > 0) ? Vb[c - n] : 0.0;
-  const double bd = (i < m - 1) ? Vb[c + n] : 0.0;
-  ft = fma(dt, vt, -gr.gt * (tl + tr));
-  if (j == 0) ft = fma(-gr.g_src, vin_i, ft);
-  fb = fma(db, vb, -gr.gb * (bu + bd));
-  const double dv = vt - vb;
-  double cg;                                     // device current / g
-  if (gr.b != 0.0) {
-    device_current(gr, g, dv, cg, dg, dgf);
-  } else {
-    cg = dv;
-    dg = g;
-    dgf = 0.f;
-  }
-  if (YAK) negative_bias(gr, dv, cg, dg, dgf);
-  ft = fma(g, cg, ft);
-  fb = fma(-g, cg, fb);
-}
-
-// ---- the residual in FP32 pairs ------------------------------------------------------
-//
-// For Newton iterates far from convergence, whose residual only becomes the right-hand side
-// of the next inexact linear solve (every convergence decision is made on the FP64
-// residual).  The same cell as cell_residual with every FP64 operand split into an FP32 pair
-// (d2f_round / d2f_low, integer pipe) and every product and sum formed error-free
-// (two_prod, two_sum); the low parts are summed in FP32 and each result is rounded once to
-// FP64.  Besides F and D the cell returns the size of its terms (|wire diagonal x| +
-// |wire coupling sum| + |current| + |source|, per layer), from which the Newton control
-// bounds the error of ||F||: kPairErrScale times the 2-norm of those sizes.  The exact
-// difference is a few 2^-48 of the sizes (the split of each voltage is good to 2^-48, and
-// every low part is within 2^-24 of a term that is within 2^-24 of a size); the scale
-// leaves a factor of 16 over 2^-44.
-//
-// FP64 work per cell: the two final additions (the norm then takes two FMAs); the device
-// current's polynomial runs in pairs up to t^2 and in FP32 beyond (tail32 is required).
+// ---- FP32 pairs: a value held as the unevaluated sum h + l of two floats -------------
 
 struct F2 {
   float h, l;   // unevaluated sum h + l
 };
-
-constexpr double kPairErrScale = 1.0 / (double)(1ull << 40);
-// the pair residual is used only for iterates more than this factor above the target
-constexpr double kPairMinRatio = 10.0;
 
 // x as an FP32 pair (d2f_round(x), d2f_low(x)); one range test selects the common case
 // 2^-74 <= |x| < 2^128, where both halves come from the two 32-bit words directly.
@@ -275,6 +166,147 @@ __device__ __forceinline__ F2 split2(double x) {
   return F2{d2f_round(x), d2f_low(x)};
 }
 
+// a * b for a pair a and an FP32 pair b, as a pair (not renormalised)
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+  float e;
+  const float p = two_prod(a.h, b.h, e);
+  return F2{p, fmaf(a.h, b.l, fmaf(a.l, b.h, e))};
+}
+
+// P(dV^2) - 1 = t (pc1 + t (pc2 + t r)), t = dV^2, for dV = d + dl as an FP32 pair, with the
+// polynomial's tail r = pc3 + pc4 t + pc5 t^2 + pc6 t^3 in FP32 (at most x^6 / 5040 < 3.5e-5
+// of P for x = b dV, |x| < 3/4): error-free FP32 products and sums (two_prod, two_sum), the
+// low parts added in FP32.  The result carries the FP32 tail's relative error (below
+// 3e-11 of P - 1) and a few 2^-44 from the pair arithmetic.
+__device__ __forceinline__ F2 poly_m1_pair(const Grid& gr, float d, float dl) {
+  float et;
+  const float t = two_prod(d, d, et);
+  const float tl = fmaf(2.f * d, dl, et);                   // dV^2 = t + tl
+  float r = fmaf(gr.pcf[6], t, gr.pcf[5]);
+  r = fmaf(r, t, gr.pcf[4]);
+  r = fmaf(r, t, gr.pcf[3]);
+  float ea, eb, ec, ed;
+  const float a = two_prod(t, r, ea);
+  const float q2 = two_sum(gr.pcf[2], a, eb);
+  const float q2l = (gr.pc2l + fmaf(tl, r, ea)) + eb;        // pc2 + t r
+  const float bq = two_prod(t, q2, ec);
+  const float bql = fmaf(t, q2l, fmaf(tl, q2, ec));
+  const float q1 = two_sum(gr.pcf[1], bq, ed);
+  const float q1l = (gr.pc1l + bql) + ed;                    // pc1 + t q2
+  return mul2(F2{t, tl}, F2{q1, q1l});                       // P - 1
+}
+
+// Memristor current and conductance for the FP64 residual.  The current
+// (g / b) sinh(b dV) = g dV P(dV^2) with P(dV^2) = sinh(x) / x, x = b dV, enters the KCL
+// residual at FP64 accuracy: for |x| < 3/4 (range test on the high word, integer pipe),
+// P - 1 comes from the FP32-pair polynomial above (b folded into its coefficients), is
+// rounded once to FP64, and cur = fma(g dV, P - 1, g dV): three FP64 instructions where a
+// Horner evaluation in FP64 takes seven.  Outside that range the CUDA math library.  The
+// conductance g cosh(x) only shapes the Newton matrix (the Jacobian diagonal and
+// a = mean(D)), so it is evaluated in FP32 (relative error below 3e-7, which changes the
+// inexact Newton steps but not the solution the FP64 residual drives them to) and returned
+// both as float and widened.
+__device__ __forceinline__ void device_current(const Grid& gr, double g, double dv,
+                                               double& cur, double& dg, float& dgf) {
+  if (((uint32_t)__double2hiint(dv) & 0x7FFFFFFFu) < gr.dv_lim_hi && gr.tail32) {
+    const F2 d = split2(dv);
+    const F2 q = poly_m1_pair(gr, d.h, d.l);
+    const double gd = g * dv;
+    cur = fma(gd, f2d_bits(q.h) + f2d_bits(q.l), gd);
+    dgf = d2f_round(g) * coshf(d.h * gr.bf);
+    dg = f2d_bits(dgf);
+  } else if (((uint32_t)__double2hiint(dv) & 0x7FFFFFFFu) < gr.dv_lim_hi) {
+    // b outside the FP32 tail's range: Horner in FP64
+    const double t = dv * dv;
+    double ps = gr.pc[6];
+    ps = fma(ps, t, gr.pc[5]);
+    ps = fma(ps, t, gr.pc[4]);
+    ps = fma(ps, t, gr.pc[3]);
+    ps = fma(ps, t, gr.pc[2]);
+    ps = fma(ps, t, gr.pc[1]);
+    ps = fma(ps, t, gr.pc[0]);
+    cur = g * (dv * ps);
+    dgf = d2f_round(g) * coshf(d2f_round(dv) * gr.bf);
+    dg = f2d_bits(dgf);
+  } else {
+    const double x = gr.b * dv;
+    cur = g * (sinh(x) * gr.inv_b);
+    dg = g * cosh(x);
+    dgf = d2f_round(dg);
+  }
+}
+
+// Yakopcic-form device: scale the current and the conductance of a device under negative
+// bias (sign read from the bit pattern, on the integer pipe).
+__device__ __forceinline__ void negative_bias(const Grid& gr, double dv, double& cur,
+                                              double& dg, float& dgf) {
+  const uint32_t hi = (uint32_t)__double2hiint(dv), lo = (uint32_t)__double2loint(dv);
+  if ((hi >> 31) && ((hi & 0x7FFFFFFFu) | lo)) {   // dV < 0, not -0
+    cur *= gr.rneg;
+    dg *= gr.rneg;
+    dgf *= gr.rnegf;
+  }
+}
+
+// One cell of eq. (F) and the Jacobian diagonal; returns (F_t, F_b, D).  YAK: the
+// Yakopcic-form device (a compile-time choice, so the sinh device pays nothing for it).
+// FP64 instructions: the device voltage 1, the current 3 (device_current), and per layer
+// the neighbour sum and two FMAs that add the wire diagonal term and the coupling term to
+// the current (10 in all; the source term adds one on the first column).
+template <bool YAK>
+__device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
+                                              const double* __restrict__ Vt,
+                                              const double* __restrict__ Vb, double g,
+                                              double vin_i, double& ft, double& fb,
+                                              double& dg, float& dgf) {
+  const int m = gr.m, n = gr.n;
+  const double vt = Vt[c], vb = Vb[c];
+  const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
+  const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
+  const double tl = (j > 0) ? Vt[c - 1] : 0.0;
+  const double tr = (j < n - 1) ? Vt[c + 1] : 0.0;
+  const double bu = (i > 0) ? Vb[c - n] : 0.0;
+  const double bd = (i < m - 1) ? Vb[c + n] : 0.0;
+  const double dv = vt - vb;
+  double cur;                                    // device current, top to bottom
+  if (gr.b != 0.0) {
+    device_current(gr, g, dv, cur, dg, dgf);
+  } else {
+    cur = g * dv;
+    dg = g;
+    dgf = 0.f;
+  }
+  if (YAK) negative_bias(gr, dv, cur, dg, dgf);
+  ft = fma(-gr.gt, tl + tr, fma(dt, vt, cur));
+  if (j == 0) ft = fma(-gr.g_src, vin_i, ft);
+  fb = fma(-gr.gb, bu + bd, fma(db, vb, -cur));
+}
+
+// ---- the residual in FP32 pairs ------------------------------------------------------
+//
+// For Newton iterates far from convergence, whose residual only becomes the right-hand side
+// of the next inexact linear solve (every convergence decision is made on the FP64
+// residual).  The same cell as cell_residual with every FP64 operand split into an FP32 pair
+// (d2f_round / d2f_low, integer pipe) and every product and sum formed error-free
+// (two_prod, two_sum); the low parts are summed in FP32 and each result is rounded once to
+// FP64.  Besides F and D the cell returns the size of its terms (|wire diagonal x| +
+// |wire coupling sum| + |current| + |source|, per layer), from which the Newton control
+// bounds the error of ||F||: kPairErrScale times the 2-norm of those sizes.  The exact
+// difference is a few 2^-48 of the sizes (the split of each voltage is good to 2^-48, and
+// every low part is within 2^-24 of a term that is within 2^-24 of a size); the scale
+// leaves a factor of 16 over 2^-44.
+//
+// FP64 work per cell: the two final additions (the norm then takes two FMAs); the device
+// current's polynomial runs in pairs up to t^2 and in FP32 beyond (tail32 is required).
+
+constexpr double kPairErrScale = 1.0 / (double)(1ull << 40);
+// smallest convergence threshold newton_rtol ||Y|| for which the FP64 residual's ||F||^2 is
+// summed in FP32: entries that matter against it are above 1e-13 / sqrt(2 m n), whose
+// squares are normal FP32 numbers for any size this library takes
+constexpr double kNorm32Min = 1e-13;
+// the pair residual is used only for iterates more than this factor above the target
+constexpr double kPairMinRatio = 10.0;
+
 // BF16 (round to nearest even) of a float; Inf / NaN kept
 __device__ __forceinline__ __nv_bfloat16 f2bf16_bits(float x) {
   const uint32_t f = __float_as_uint(x);
@@ -288,32 +320,11 @@ __device__ __forceinline__ __nv_bfloat16 f2bf16_bits(float x) {
   return __nv_bfloat16(raw);
 }
 
-// a * b for a pair a and an FP32 pair b, as a pair (not renormalised)
-__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
-  float e;
-  const float p = two_prod(a.h, b.h, e);
-  return F2{p, fmaf(a.h, b.l, fmaf(a.l, b.h, e))};
-}
-
 // current / g of one device, (1 / b) sinh(b dV) for dV = d + dl, as a pair; for
 // |b dV| < 3/4: dV P(dV^2) with P - 1 = t (pc1 + t (pc2 + t r)), r the FP32 tail
 __device__ __forceinline__ F2 current_pair(const Grid& gr, float d, float dl) {
   if (fabsf(d) < gr.dv_limf) {
-    float et;
-    const float t = two_prod(d, d, et);
-    const float tl = fmaf(2.f * d, dl, et);                 // dV^2 = t + tl
-    float r = fmaf(gr.pcf[6], t, gr.pcf[5]);
-    r = fmaf(r, t, gr.pcf[4]);
-    r = fmaf(r, t, gr.pcf[3]);
-    float ea, eb, ec, ed;
-    const float a = two_prod(t, r, ea);
-    const float q2 = two_sum(gr.pcf[2], a, eb);
-    const float q2l = (gr.pc2l + fmaf(tl, r, ea)) + eb;      // pc2 + t r
-    const float bq = two_prod(t, q2, ec);
-    const float bql = fmaf(t, q2l, fmaf(tl, q2, ec));
-    const float q1 = two_sum(gr.pcf[1], bq, ed);
-    const float q1l = (gr.pc1l + bql) + ed;                  // pc1 + t q2
-    const F2 pm1 = mul2(F2{t, tl}, F2{q1, q1l});             // P - 1
+    const F2 pm1 = poly_m1_pair(gr, d, dl);                  // P - 1
     const F2 c = mul2(F2{d, dl}, pm1);                       // dV (P - 1)
     float eg;
     const float h = two_sum(d, c.h, eg);
@@ -588,8 +599,14 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   // rounding for the preconditioner to be exact (one GMRES iteration); otherwise D itself
   // is FP32 and so is its sum within a thread
   const bool lin = (gr.b == 0.0);
+  // ||F||^2 of the FP64 cell: the squares of the FP32-rounded entries summed in FP32 with
+  // compensation (TwoSum), within about 1e-7 relative, when the convergence threshold
+  // newton_rtol ||Y|| exceeds kNorm32Min: every entry that can matter for the test is
+  // then far inside the FP32 range.  Otherwise FP64 FMAs.  The zero state needs no sum:
+  // F(0) = -Y, so ||F|| = ||Y||.
+  const bool norm32 = cfg.newton_rtol * ctl[b].ynorm > kNorm32Min;
   double sf = 0.0, sd = 0.0;
-  float sdf = 0.f, ss = 0.f;
+  float sdf = 0.f, ss = 0.f, sfh = 0.f, sfl = 0.f;
   bool dnot32 = false;
   // grid-stride walk over the cells with (i, j) advanced incrementally (no division per
   // cell); the BF16 copy sits in the padded [layer][mp][np] layout at row offset i * np
@@ -604,6 +621,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
       ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
       fb = 0.0;
       dg = gmap[c];
+      dgf = d2f_round(dg);
     } else if (PAIR && use_pair) {
       cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
                               dg, dgf, ss, ft32, fb32);
@@ -631,9 +649,18 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
         xt[o + mp * np] = d2bf16_bits(fb);
       }
     }
-    sf = fma(ft, ft, sf);
-    sf = fma(fb, fb, sf);
-    if (ZERO || lin) sd += dg; else sdf += dgf;
+    if (!ZERO) {
+      if ((PAIR && use_pair) || !norm32) {
+        sf = fma(ft, ft, sf);
+        sf = fma(fb, fb, sf);
+      } else {
+        const float a = d2f_round(ft), bb = d2f_round(fb);
+        float e;
+        sfh = two_sum(sfh, fmaf(a, a, bb * bb), e);
+        sfl += e;
+      }
+    }
+    if (lin) sd += dg; else sdf += dgf;
     j += Sj;
     i += Si;
     if (j >= n) {
@@ -642,6 +669,7 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
     }
   }
   sd += f2d_bits(sdf);
+  sf += f2d_bits(sfh) + f2d_bits(sfl);
   double sz = f2d_bits(ss);
   if (__syncthreads_or(dnot32) && threadIdx.x == 0) atomicOr(&ctl[b].d64_next, 1);
   if (PAIR)
@@ -673,7 +701,8 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   __syncthreads();
   if (threadIdx.x == 0) {
     cnt[b] = 0;
-    newton_control(ctl[b], tot[0], tot[1], mn, cfg, host_flags ? &host_flags[b] : nullptr,
+    const double f2 = ZERO ? ctl[b].ynorm * ctl[b].ynorm : tot[0];
+    newton_control(ctl[b], f2, tot[1], mn, cfg, host_flags ? &host_flags[b] : nullptr,
                    use_pair ? kPairErrScale * sqrt(tot[2]) : -1.0);
   }
 }
@@ -891,7 +920,7 @@ int residual_nblk(int mn, int B) {
   int nb = (mn + kThreads - 1) / kThreads;
   const int want = (kGridBlocks + B - 1) / (B < 1 ? 1 : B);
   if (nb > want) nb = want;
-  if (nb > 608) nb = 608;
+  if (nb > kResidualMaxBlocks) nb = kResidualMaxBlocks;
   return nb < 1 ? 1 : nb;
 }
 

@@ -50,6 +50,7 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 
 static void set_error(const char* msg) { g_last_error = msg; }
 void set_error_message(const char* msg) { g_last_error = msg; }
+void clear_error_message() { g_last_error.clear(); }
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -94,10 +95,10 @@ struct mca_handle {
   double *T1_64 = nullptr, *Xh_64 = nullptr, *E_64 = nullptr;
   double* fac = nullptr;          // tridiagonal factors of the paper-literal M_hat
   int fac_ld = 0;
-  __nv_bfloat16 *Xbf = nullptr, *T1bf = nullptr, *Yh = nullptr, *Yl = nullptr, *Eh = nullptr,
+  __nv_bfloat16 *Xbf = nullptr, *T1bf = nullptr, *Yh = nullptr, *Eh = nullptr,
                 *El = nullptr;
   bool tc_ok = false;
-  CUtensorMap mA1, mA2, mA3h, mA3l, mA4h, mA4l;           // A operands
+  CUtensorMap mA1, mA2, mA3, mA4h, mA4l;                 // A operands
   // B operands for 128-, 64- and 256-column tiles
   CUtensorMap mB1[3], mB2[3], mB3h[3], mB3l[3], mB4h[3], mB4l[3];
   // GEMM form of each transform: ws = 1 persistent warp-specialised kernel (tiles of
@@ -169,8 +170,13 @@ int dalloc(mca_handle* h, T** p, size_t count) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-int validate(const mca_params* p) {
-  if (!p) return MCA_ERR_INVALID_ARG;
+}  // namespace
+
+int mca::validate_circuit(const mca_params* p) {
+  if (!p) {
+    set_error("NULL parameters");
+    return MCA_ERR_INVALID_ARG;
+  }
   if (p->rows < 1 || p->cols < 1 || p->rows > 16384 || p->cols > 16384) {
     set_error("rows/cols must be in 1..16384");
     return MCA_ERR_INVALID_ARG;
@@ -193,6 +199,14 @@ int validate(const mca_params* p) {
     set_error("neg_ratio must be finite and > 0");
     return MCA_ERR_INVALID_ARG;
   }
+  return MCA_OK;
+}
+
+namespace {
+
+int validate(const mca_params* p) {
+  const int rc = validate_circuit(p);
+  if (rc != MCA_OK) return rc;
   if (p->precision < MCA_PREC_FP64 || p->precision > MCA_PREC_NONE) {
     set_error("unknown precision");
     return MCA_ERR_INVALID_ARG;
@@ -223,19 +237,18 @@ int setup_tc(mca_handle* h) {
   MCA_TRY(dalloc(h, &h->Xbf, B * 2 * mp * np));
   MCA_TRY(dalloc(h, &h->T1bf, B * 2 * np * mp));
   MCA_TRY(dalloc(h, &h->Yh, B * 2 * mp * np));
-  MCA_TRY(dalloc(h, &h->Yl, B * 2 * mp * np));
   MCA_TRY(dalloc(h, &h->Eh, B * 2 * np * mp));
   MCA_TRY(dalloc(h, &h->El, B * 2 * np * mp));
   MCA_CUDA_TRY(cudaMemset(h->Xbf, 0, B * 2 * mp * np * sizeof(__nv_bfloat16)));
   bool ok = true;
-  // K tiles: 64 wide for the single-product transforms, 32 wide for the split
-  // back transforms, which also hold both operands in hi/lo pairs (split precision)
+  // K tiles: 64 wide for the single-word transforms, 32 wide for the split back
+  // transforms (split precision: transform 3 holds Q_r as a hi/lo pair, transform 4 both
+  // of its operands)
   const bool split = h->p.precision == MCA_PREC_BF16_SPLIT;
   const uint32_t kb = split ? 32u : 64u;
   ok &= tc::make_map(&h->mA1, h->Xbf, B * 2 * mp, np, 128, 64);
   ok &= tc::make_map(&h->mA2, h->T1bf, B * 2 * np, mp, 128, 64);
-  ok &= tc::make_map(&h->mA3h, h->Yh, B * 2 * mp, np, 128, kb);
-  ok &= tc::make_map(&h->mA3l, h->Yl, B * 2 * mp, np, 128, kb);
+  ok &= tc::make_map(&h->mA3, h->Yh, B * 2 * mp, np, 128, kb);
   ok &= tc::make_map(&h->mA4h, h->Eh, B * 2 * np, mp, 128, kb);
   ok &= tc::make_map(&h->mA4l, h->El, B * 2 * np, mp, 128, kb);
   const uint32_t bns[3] = {128, 64, 256};
@@ -426,14 +439,16 @@ int tc_step(mca_handle* h, int step, bool split, void* zout, size_t zstride, int
   const size_t mn = h->mn, mp = h->mp, np = h->np;
   auto q = [](int bn) { return bn == 128 ? 0 : (bn == 64 ? 1 : 2); };
   const int bn = h->bn[step];
-  auto run = [&](bool sp_, int epi, const CUtensorMap& a, const CUtensorMap& al,
+  auto run = [&](int sp_, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const tc::GemmEpi& ep) {
     return h->ws[step] ? tc::gemm_ws(bn, h->lp[step], sp_, epi, a, al, bm, bml, ep, B, s)
                        : tc::gemm(bn, sp_, epi, a, al, bm, bml, ep, B, s);
   };
-  // executed MMA FLOPs per vector: 2 layers x 2 M N K, three products when split
+  // executed MMA FLOPs per vector: 2 layers x 2 M N K; when split, two products in
+  // transform 3 (Q_r as hi + lo) and three in transform 4 (E and Q_c as hi + lo)
   const double f_r = 4.0 * m * (double)n * n, f_c = 4.0 * n * (double)m * m;
-  const double sp = split ? 3.0 : 1.0;
+  const int sp3 = split ? tc::SPLIT_B : tc::SPLIT_NONE;
+  const int sp4 = split ? tc::SPLIT_AB : tc::SPLIT_NONE;
   tc::GemmEpi e{};
   e.ctl = ctl;
   e.kidx = kidx;
@@ -447,30 +462,32 @@ int tc_step(mca_handle* h, int step, bool split, void* zout, size_t zstride, int
     case 0:  // T1^T = (X Q_r)^T
       e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
       e.out = h->T1bf; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
-      MCA_CUDA_TRY(run(false, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(bn)], h->mB1[q(bn)], e));
+      MCA_CUDA_TRY(run(tc::SPLIT_NONE, tc::EPI_BF16, h->mA1, h->mA1, h->mB1[q(bn)],
+                       h->mB1[q(bn)], e));
       prof_end(h, t0, MCA_FAM_PRECOND_1, prof_k, 8.0 * mn, f_r, s);
       break;
-    case 1:  // Y_hat = modes^-1 (Q_c^T T1), stored [i'][k']
+    case 1:  // Y_hat = modes^-1 (Q_c^T T1), stored [i'][k'] (one BF16 word)
       e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
-      e.out = h->Yh; e.out_lo = h->Yl; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
-      MCA_CUDA_TRY(run(false, split ? tc::EPI_MODES_SPLIT : tc::EPI_MODES, h->mA2, h->mA2,
-                       h->mB2[q(bn)], h->mB2[q(bn)], e));
-      prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, (split ? 12.0 : 8.0) * mn, f_c, s);
+      e.out = h->Yh; e.o_bs = 2 * mp * np; e.o_ls = mp * np; e.o_ld = np;
+      MCA_CUDA_TRY(run(tc::SPLIT_NONE, tc::EPI_MODES, h->mA2, h->mA2, h->mB2[q(bn)],
+                       h->mB2[q(bn)], e));
+      prof_end(h, t0, MCA_FAM_PRECOND_2, prof_k, 8.0 * mn, f_c, s);
       break;
     case 2:  // E^T = (Y_hat Q_r^T)^T
       e.R = h->mp; e.K = h->np; e.C = h->np; e.R_valid = m; e.C_valid = n;
       e.out = h->Eh; e.out_lo = h->El; e.o_bs = 2 * np * mp; e.o_ls = np * mp; e.o_ld = mp;
-      MCA_CUDA_TRY(run(split, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3h, h->mA3l,
+      MCA_CUDA_TRY(run(sp3, split ? tc::EPI_SPLIT : tc::EPI_BF16, h->mA3, h->mA3,
                        h->mB3h[q(bn)], h->mB3l[q(bn)], e));
-      prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, (split ? 16.0 : 8.0) * mn, sp * f_r, s);
+      prof_end(h, t0, MCA_FAM_PRECOND_3, prof_k, (split ? 12.0 : 8.0) * mn,
+               (split ? 2.0 : 1.0) * f_r, s);
       break;
     default:  // Z = (E^T Q_c^T)^T, FP64 unpadded
       e.R = h->np; e.K = h->mp; e.C = h->mp; e.R_valid = n; e.C_valid = m;
       e.out = zout; e.o_bs = zstride; e.o_ls = mn; e.o_ld = n;
-      MCA_CUDA_TRY(run(split, z32 ? tc::EPI_F32 : tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)],
+      MCA_CUDA_TRY(run(sp4, z32 ? tc::EPI_F32 : tc::EPI_F64, h->mA4h, h->mA4l, h->mB4h[q(bn)],
                        h->mB4l[q(bn)], e));
       prof_end(h, t0, MCA_FAM_PRECOND_4, prof_k,
-               (split ? 8.0 : 4.0) * mn + (z32 ? 8.0 : 16.0) * mn, sp * f_c, s);
+               (split ? 8.0 : 4.0) * mn + (z32 ? 8.0 : 16.0) * mn, (split ? 3.0 : 1.0) * f_c, s);
       break;
   }
   count_launches(1);

@@ -231,6 +231,8 @@ void launch_outputs(const Grid& gr, const double* vin, const double* x, double* 
 // blocks per vector at large B leave each thread more elements, which shrinks the share
 // of the per-thread FP64 reduction work.
 int residual_nblk(int mn, int B = 1);
+// Upper bound of residual_nblk() for every mn and B (sizes the partial-sum buffers).
+constexpr int kResidualMaxBlocks = 608;
 // Krylov (k_krylov.cu)
 int vec_nblk(size_t n2, int B = 1);
 void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
@@ -312,5 +314,9 @@ void launch_modes_2x2_f64(double* Xh, const double* mu, const double* nu, int m,
 namespace mca {
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 void set_error_message(const char* msg);
+void clear_error_message();
 void count_launches(int n);
+// Checks of the circuit part of mca_params (sizes, conductances, b, device model); sets
+// the error message and returns MCA_ERR_INVALID_ARG on the first failure.
+int validate_circuit(const mca_params* p);
 }

@@ -14,9 +14,13 @@ enum Epi {
   EPI_MODES = 1,        // out = bf16(per-mode 2x2 inverse of eq. P applied to (acc_t, acc_b))
   EPI_SPLIT = 2,        // out = bf16(acc), out_lo = bf16(acc - out)
   EPI_F64 = 3,          // out = (double)acc for r < R_valid, c < C_valid (unpadded)
-  EPI_MODES_SPLIT = 4,  // EPI_MODES with a hi/lo pair
   EPI_F32 = 5,          // out = acc (float) for r < R_valid, c < C_valid (unpadded)
 };
+
+// Operand words of a GEMM: one BF16 word each (SPLIT_NONE); A and B both hi + lo, three
+// products hi*hi + lo*hi + hi*lo (SPLIT_AB); only B hi + lo, two products A*hi + A*lo
+// (SPLIT_B).
+enum Split { SPLIT_NONE = 0, SPLIT_AB = 1, SPLIT_B = 2 };
 
 // Output addressing: element (blk = 2b + layer, c, r) is written to
 //   out[b*o_bs + layer*o_ls + c*o_ld + r].
@@ -36,15 +40,15 @@ struct GemmEpi {
 };
 
 bool encode_available();
-// box_k: 64 (single-product GEMMs) or 32 (split GEMMs)
+// box_k: 64 (single-word GEMMs) or 32 (split GEMMs)
 bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
               uint32_t box_rows, uint32_t box_k);
-cudaError_t gemm(int bn, bool split, int epi, const CUtensorMap& a, const CUtensorMap& al,
+cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
 // Persistent warp-specialised form: one CTA per SM over tiles of 128 x bn with lp layers
 // (lp = 2 for the modes epilogues, which need both layers of a mode in one CTA).
-cudaError_t gemm_ws(int bn, int lp, bool split, int epi, const CUtensorMap& a,
+cudaError_t gemm_ws(int bn, int lp, int split, int epi, const CUtensorMap& a,
                     const CUtensorMap& al, const CUtensorMap& bm, const CUtensorMap& bml,
                     const GemmEpi& ep, int B, cudaStream_t s);
 cudaError_t configure_all();
