@@ -11,11 +11,15 @@ transforms, split back transforms); value = solves per second.
 
 The JSON line also carries: the end-to-end figure through the C ABI with host buffers,
 the roofline of the dominant kernel family (CUDA events on the solve stream, in a pass of
-one handle alone), the same
-workload in the plain FP64 GPU form, the preconditioner TFLOP/s (dense eigenbasis count
-8 m n (m + n) per apply), and the CPU oracle on the host cores.
+one handle alone), the same workload in the two all-FP64 GPU forms (the exact eigenbasis
+preconditioner with FP64 transforms, and the paper's M_hat applied by tridiagonal solves)
+at the same batching, the 2048 x 2048 crossbar with an oracle-recomputed residual, the
+preconditioner TFLOP/s (dense eigenbasis count 8 m n (m + n) per apply), the batched
+statistical-characterisation workload, and the CPU oracle on the host cores (the 1024^2
+workload, plus the 32^2 and 256^2 configurations single-threaded and on all cores).
 
 --impl reference times the CPU oracle itself on the same workload (the reference arm).
+--profile-precond applies the preconditioner alone (for ncu captures of its GEMMs).
 """
 from __future__ import annotations
 
@@ -60,6 +64,14 @@ def parse_args():
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-2048", action="store_true", help="skip the 2048^2 leg")
+    ap.add_argument("--restart", type=int, default=30, help="GMRES restart length")
+    ap.add_argument("--profile-precond", type=int, default=0, metavar="REPS",
+                    help="only apply the preconditioner REPS times to --batch random vectors "
+                         "of a --size^2 handle (between cudaProfilerStart/Stop)")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="(internal) time the oracle on the 32^2 and 256^2 configurations "
+                         "and print one JSON line; bench.py runs it in child processes")
     ap.add_argument("--table1", action="store_true",
                     help="GPU version of the paper's Table 1 (GMRES steps per preconditioner)")
     return ap.parse_args()
@@ -155,18 +167,22 @@ def job_time(t, pg):
     return float(tt[0])
 
 
-def replica_seed(rank):
-    """Each rank solves its own crossbar (no data is shared between ranks)."""
-    return 1000 + rank
+def replica_seeds(rank):
+    """Each rank solves its own crossbars (no data is shared between ranks): rank r takes
+    the four crossbars of seeds 4r .. 4r + 3 (rank 0: seeds 0-3, the 1024^2 workload's)."""
+    return tuple(range(4 * rank, 4 * rank + 4))
 
 
-def oracle_solves(cb, count, start=0):
-    """Time `count` oracle solves (Newton + preconditioned GMRES, FP64, NumPy/SciPy)."""
+def oracle_solves(ws, count, start=0, tol=TOL):
+    """Time `count` oracle solves (Newton + preconditioned GMRES, FP64, NumPy/SciPy) of
+    the workload's vectors start, start + 1, ... (each on its own crossbar's map)."""
     from oracle import mca_oracle as O
     t0 = time.perf_counter()
     for v in range(start, start + count):
-        r = O.newton_solve(cb.params, cb.gmap, cb.vin[v % len(cb.vin)], tol=TOL, linear="pgmres")
-        assert r.rel_residual <= TOL
+        v %= len(ws.vin)
+        r = O.newton_solve(ws.params, ws.gmaps[ws.map_index[v]], ws.vin[v], tol=tol,
+                           linear="pgmres")
+        assert r.rel_residual <= tol
     return time.perf_counter() - t0
 
 
@@ -174,31 +190,35 @@ def workload_config(args, batch):
     dev = ("sinh devices b=2, V_in~U[0,0.3] V" if getattr(args, "device", "sinh") == "sinh" else
            f"Yakopcic-form devices b=2 a2/a1={args.neg_ratio:g}, V_in~U[-0.3,0.3] V")
     return {
-        "workload": f"{args.size}x{args.size} MCA, log-uniform g in [1e-6,1e-4] S, wires "
+        "workload": f"{args.size}x{args.size} MCA, log-uniform g in [1e-6,1e-4] S "
+                    f"(crossbar seeds 0-3, vectors interleaved over them), wires "
                     f"1 S top / 0.5 S bottom, {dev}, "
-                    f"Newton to {TOL:g} rel. KCL residual, FGMRES(30)",
+                    f"Newton to {TOL:g} rel. KCL residual, FGMRES({args.restart})",
         "rows": args.size, "cols": args.size, "batch_per_step": batch,
         "precision": args.precision, "newton_rtol": TOL,
         "cache": "inputs larger than L2: the Krylov basis of one solve is ~1 GB",
     }
 
 
-def make_workload(args, seed, nvec):
-    """The timed crossbar: sinh devices with V_in >= 0, or Yakopcic-form devices
-    (a2/a1 = --neg-ratio) with inputs of both signs."""
+def make_workload(args, rank, nvec):
+    """The timed crossbars: four log-uniform crossbars with sinh devices and V_in >= 0
+    (seeds 4r .. 4r + 3), or one Yakopcic-form crossbar (a2/a1 = --neg-ratio) with inputs
+    of both signs."""
     if getattr(args, "device", "sinh") == "sinh":
-        return mi.config_large(args.size, seed, nvec=nvec)
-    return mi.make_crossbar(args.size, args.size, seed, nvec=nvec, g_wire_bot=0.5,
-                            vmin=-0.3, neg_ratio=args.neg_ratio)
+        return mi.config_large_set(args.size, seeds=replica_seeds(rank), nvec=nvec)
+    cb = mi.make_crossbar(args.size, args.size, replica_seeds(rank)[0], nvec=nvec,
+                          g_wire_bot=0.5, vmin=-0.3, neg_ratio=args.neg_ratio)
+    return mi.CrossbarSet(params=cb.params, gmaps=cb.gmap[None], vin=cb.vin,
+                          map_index=np.zeros(nvec, np.int32), seeds=(cb.seed,))
 
 
 def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return
-    cb = make_workload(args, 0, args.warmup + args.steps)
-    oracle_solves(cb, args.warmup)
-    t = oracle_solves(cb, args.steps, start=args.warmup)
+    ws = make_workload(args, 0, args.warmup + args.steps)
+    oracle_solves(ws, args.warmup)
+    t = oracle_solves(ws, args.steps, start=args.warmup)
     value = args.steps / t
     cores = os.cpu_count()
     line = {
@@ -208,12 +228,193 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args, 1),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} oracle solves of the {args.size}^2 crossbar, "
+                         "sample": f"{args.steps} oracle solves of the {args.size}^2 crossbars, "
                                    "one input vector each"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def params_for(mca, p, prec, B, restart=30, tol=TOL, device_model=None):
+    """Library parameters of a workload's wiring at one precision and batch."""
+    return mca.default_params(p.rows, p.cols, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
+                              g_src=p.g_src, g_term_top_right=p.g_term_top_right,
+                              g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
+                              precision=prec, newton_rtol=tol, max_batch=B,
+                              gmres_restart=restart,
+                              device_model=(mca.DEVICE_SINH if device_model is None
+                                            else device_model),
+                              neg_ratio=p.neg_ratio)
+
+
+def solve_step(mca, solvers, vin_d, map_d, first, outs, check=None):
+    """One step: handle h solves vectors first + h*B .. first + (h+1)*B (each with its
+    crossbar's map), all handles concurrently through mca_solve_many (which returns when
+    every handle is done).  Every solve must reach the tolerance."""
+    B = outs[0][0].shape[0]
+    nv = vin_d.shape[0]
+    vins, maps = [], []
+    for h in range(len(solvers)):
+        a = (first + h * B) % nv
+        if a + B <= nv:             # a view: no copy inside a timed step
+            vins.append(vin_d[a:a + B])
+            maps.append(map_d[a:a + B])
+        else:
+            idx = [(a + j) % nv for j in range(B)]
+            vins.append(vin_d[idx])
+            maps.append(map_d[idx])
+    res = mca.solve_many(solvers, vins, map_indices=maps, n_threads=len(solvers), outs=outs)
+    for r in res:
+        for st in r[3]:
+            assert st["status"] == 0 and st["rel_residual"] <= TOL, st
+            if check is not None:
+                check.append((st["newton_iters"], st["gmres_iters"], st["rel_residual"]))
+    return res
+
+
+def time_form(mca, torch, ws, prec, H, B, steps, first, restart=30, device_model=None,
+              grab=None):
+    """Solves/s of the workload in another preconditioner form: H handles of B vectors,
+    one untimed step, then `steps` timed steps (CUDA events around the synchronous
+    mca_solve_many calls), device-resident inputs and outputs.  grab = j also returns the
+    node voltages of vector j of the last step's first handle (host) and its index."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    params = params_for(mca, ws.params, prec, B, restart, device_model=device_model)
+    solvers = [mca.Solver(params, ws.gmaps) for _ in range(H)]
+    try:
+        m, n = ws.params.rows, ws.params.cols
+        vin_d = torch.as_tensor(ws.vin, device=dev)
+        outs = [(torch.empty(B, m, n, dtype=torch.float64, device=dev),
+                 torch.empty(B, m, n, dtype=torch.float64, device=dev),
+                 torch.empty(B, n, dtype=torch.float64, device=dev)) for _ in range(H)]
+        solve_step(mca, solvers, vin_d, ws.map_index, first, outs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        chk = []
+        e0.record()
+        for i in range(steps):
+            solve_step(mca, solvers, vin_d, ws.map_index, first + (i + 1) * H * B, outs, chk)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        it = np.array([(a, b_) for a, b_, _ in chk])
+        got = None
+        if grab is not None:
+            v = (first + steps * H * B + grab) % vin_d.shape[0]
+            got = (v, outs[0][0][grab].cpu().numpy(), outs[0][1][grab].cpu().numpy())
+        return got, {"value": steps * H * B / t, "unit": "solves/s", "handles": H,
+                "batch_per_handle": B, "solves": steps * H * B,
+                "newton_iters_per_solve": float(it[:, 0].mean()),
+                "gmres_iters_per_solve": float(it[:, 1].mean()),
+                "max_rel_residual": float(max(r for _, _, r in chk))}
+    finally:
+        for s_ in solvers:
+            s_.close()
+        torch.cuda.empty_cache()
+
+
+def run_2048(mca, torch, args, rank, B=16, steps=3):
+    """The 2048 x 2048 crossbars (8.4M unknowns) in the headline's precision: one handle of
+    B vectors over the four crossbars, and the oracle's FP64 KCL residual of one of the
+    returned solutions."""
+    from oracle import mca_oracle as O
+    ws = mi.config_large_set(2048, seeds=replica_seeds(rank), nvec=(steps + 1) * B)
+    (v, vt, vb), r = time_form(mca, torch, ws, mca.PREC_BF16_SPLIT, 1, B, steps, 0,
+                               args.restart, grab=B - 1)
+    # one solution of the last timed pass recomputed by the oracle
+    g = ws.gmaps[ws.map_index[v]]
+    Ft, Fb = O.residual(ws.params, g, ws.vin[v], vt.ravel(), vb.ravel())
+    Yt, _ = O.source_vector(ws.params, ws.vin[v])
+    rel = float(np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt))
+    assert rel <= TOL * 1.01, rel
+    r["oracle_rel_residual"] = rel
+    r["oracle_checked_vector"] = int(v)
+    r["workload"] = ("2048x2048 MCA, crossbar seeds 0-3, same wiring, devices and precision "
+                     "as the headline")
+    return r
+
+
+def oracle_configs():
+    """Oracle timings on the two small configurations, in this process' BLAS threading:
+    32^2 (seed 0, Newton to 1e-10) with the banded direct solve and with preconditioned
+    GMRES, each repeated for about a second; 256^2 bimodal (seeds 0-7, one vector each,
+    Newton to 1e-8) with preconditioned GMRES on every seed and the banded solve on seed 0
+    (about 10 s per solve: the LAPACK band LU of a 131k x 131k matrix of bandwidth 512)."""
+    from oracle import mca_oracle as O
+    out = {}
+
+    def rate(fn, min_s=1.0):
+        k, t = 0, 0.0
+        while t < min_s or k == 0:
+            a = time.perf_counter()
+            fn()
+            t += time.perf_counter() - a
+            k += 1
+        return {"value": k / t, "unit": "solves/s", "solves": k, "seconds": t}
+
+    c1 = mi.config_small(0)
+    for lin in ("banded", "pgmres"):
+        out[f"c1_32_{lin}"] = rate(lambda: O.newton_solve(c1.params, c1.gmap, c1.vin[0],
+                                                          tol=1e-10, linear=lin))
+    c2 = [mi.config_bimodal(sd) for sd in range(8)]
+    a = time.perf_counter()
+    for cb in c2:
+        r = O.newton_solve(cb.params, cb.gmap, cb.vin[0], tol=TOL, linear="pgmres")
+        assert r.rel_residual <= TOL
+    t = time.perf_counter() - a
+    out["c2_256_pgmres"] = {"value": 8 / t, "unit": "solves/s", "solves": 8, "seconds": t,
+                            "seeds": "0-7"}
+    a = time.perf_counter()
+    r = O.newton_solve(c2[0].params, c2[0].gmap, c2[0].vin[0], tol=TOL, linear="banded")
+    t = time.perf_counter() - a
+    assert r.rel_residual <= TOL
+    out["c2_256_banded"] = {"value": 1 / t, "unit": "solves/s", "solves": 1, "seconds": t,
+                            "seeds": "0"}
+    return out
+
+
+def oracle_configs_in_children():
+    """oracle_configs() in two child processes: BLAS limited to one thread, and BLAS on
+    every core (the children import no CUDA)."""
+    res = {}
+    for name, threads in (("single_thread", 1), ("all_cores", os.cpu_count())):
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-configs"],
+                           env=env, capture_output=True, text=True, timeout=600)
+        if r.returncode != 0:
+            res[name] = {"error": r.stderr[-300:]}
+            continue
+        res[name] = dict(json.loads(r.stdout.strip().splitlines()[-1]), threads=threads)
+    return res
+
+
+def run_profile_precond(args):
+    """Apply the preconditioner alone, for ncu captures of its GEMMs: a --size^2 handle
+    with max_batch --batch and restart --restart (the tile autotuner runs at create), then
+    --profile-precond applies to --batch random vectors between cudaProfilerStart/Stop."""
+    import torch
+    import paper_2109_07929_gb300 as mca
+    prec = {"bf16split": mca.PREC_BF16_SPLIT, "bf16": mca.PREC_BF16}[args.precision]
+    ws = mi.config_large_set(args.size, nvec=args.batch)
+    B, m, n = args.batch, args.size, args.size
+    with mca.Solver(params_for(mca, ws.params, prec, B, args.restart), ws.gmaps) as s:
+        r = torch.as_tensor(np.random.default_rng(0).standard_normal((B, 2 * m * n)),
+                            device="cuda")
+        z = torch.empty_like(r)
+        a = np.full(B, 2e-5)
+        s.precond_apply(a, r, z)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        for _ in range(args.profile_precond):
+            s.precond_apply(a, r, z)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profile_precond": args.profile_precond, "batch": B, "size": m,
+                          "tiles": gemm_tiles(s)}), flush=True)
 
 
 def run_ours(args):
@@ -229,50 +430,23 @@ def run_ours(args):
     S = H * B                       # solves per step
     W, K = args.warmup, args.steps
     m = n = args.size
-    cb = make_workload(args, replica_seed(rank), (W + max(K, 2 * E2E_PASSES)) * S)
-    p = cb.params
-    params = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
-                                g_src=p.g_src, g_term_top_right=p.g_term_top_right,
-                                g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
-                                precision=prec, newton_rtol=TOL, max_batch=B,
-                                device_model=(mca.DEVICE_SINH if args.device == "sinh"
-                                              else mca.DEVICE_YAKOPCIC),
-                                neg_ratio=p.neg_ratio)
-    solvers = [mca.Solver(params, cb.gmap) for _ in range(H)]
+    ws = make_workload(args, rank, (W + max(K, 2 * E2E_PASSES)) * S)
+    p = ws.params
+    params = params_for(mca, p, prec, B, args.restart,
+                        device_model=(mca.DEVICE_SINH if args.device == "sinh"
+                                      else mca.DEVICE_YAKOPCIC))
+    solvers = [mca.Solver(params, ws.gmaps) for _ in range(H)]
     solver = solvers[0]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    vin = torch.as_tensor(cb.vin, device=dev)
+    vin = torch.as_tensor(ws.vin, device=dev)
     outs = [(torch.empty(B, m, n, dtype=torch.float64, device=dev),
              torch.empty(B, m, n, dtype=torch.float64, device=dev),
              torch.empty(B, n, dtype=torch.float64, device=dev)) for _ in range(H)]
-    vt, vb, io = outs[0]
-    stats = (mca.Stats * B)()
-    sp = mca.ctypes.cast(stats, mca.ctypes.c_void_p)
-
-    def step1(i, check):
-        # one handle, B vectors, on the bench stream
-        rc = solver.solve_raw(vin[i * B:(i + 1) * B].data_ptr(), B, vt.data_ptr(), vb.data_ptr(),
-                              io.data_ptr(), sp, stream)
-        if rc != 0:
-            raise RuntimeError(f"solve failed with status {rc}")
-        if check is not None:
-            for s in stats:
-                assert s.status == 0 and s.rel_residual <= TOL, (s.status, s.rel_residual)
-                check.append((s.newton_iters, s.gmres_iters, s.rel_residual))
 
     def step(i, check):
-        # one step: H handles of B vectors each, solved concurrently (mca_solve_many returns
-        # when all are done)
-        if H == 1:
-            return step1(i, check)
-        vins = [vin[i * S + h * B:i * S + (h + 1) * B] for h in range(H)]
-        res = mca.solve_many(solvers, vins, n_threads=H, outs=outs)
-        for r in res:
-            for s in r[3]:
-                assert s["status"] == 0 and s["rel_residual"] <= TOL, s
-                if check is not None:
-                    check.append((s["newton_iters"], s["gmres_iters"], s["rel_residual"]))
+        # one step: H handles of B vectors each, solved concurrently
+        solve_step(mca, solvers, vin, ws.map_index, i * S, outs, check)
 
     warm = []
     for i in range(W):
@@ -303,25 +477,16 @@ def run_ours(args):
     # call gives each handle P passes of B vectors: the library runs them as passes of B and
     # overlaps each pass' device->host output copies with the next pass' kernels.
     P = max(2, min(E2E_PASSES, E2E_SOLVES // S))
-    vin_h = torch.as_tensor(cb.vin).pin_memory()
+    vin_h = torch.as_tensor(ws.vin).pin_memory()
     outs_h = [(torch.empty(P * B, m, n, dtype=torch.float64).pin_memory(),
                torch.empty(P * B, m, n, dtype=torch.float64).pin_memory(),
                torch.empty(P * B, n, dtype=torch.float64).pin_memory()) for _ in range(H)]
 
-    stats_e = (mca.Stats * (P * B))()
-    sp_e = mca.ctypes.cast(stats_e, mca.ctypes.c_void_p)
-
     def step_host(i):
         base = i * S
-        if H == 1:
-            vt_h, vb_h, io_h = outs_h[0]
-            rc = solver.solve_raw(vin_h[base:base + P * B].data_ptr(), P * B, vt_h.data_ptr(),
-                                  vb_h.data_ptr(), io_h.data_ptr(), sp_e, stream)
-            if rc != 0:
-                raise RuntimeError(f"solve failed with status {rc}")
-            return
         vins = [vin_h[base + h * P * B:base + (h + 1) * P * B] for h in range(H)]
-        for r in mca.solve_many(solvers, vins, n_threads=H, outs=outs_h):
+        maps = [ws.map_index[base + h * P * B:base + (h + 1) * P * B] for h in range(H)]
+        for r in mca.solve_many(solvers, vins, map_indices=maps, n_threads=H, outs=outs_h):
             for st_ in r[3]:
                 assert st_["status"] == 0 and st_["rel_residual"] <= TOL, st_
 
@@ -337,16 +502,23 @@ def run_ours(args):
     torch.cuda.synchronize()
     te = job_time(e0.elapsed_time(e1) / 1000.0, pg)
     e2e = {"value": world * ke * P * S / te, "unit": "solves/s",
-           "h2d_bytes_per_step": P * S * m * 8,
+           "h2d_bytes_per_step": P * S * (m * 8 + 4),
            "d2h_bytes_per_step": P * S * (2 * m * n + n) * 8 + P * S * mca.ctypes.sizeof(mca.Stats),
            "solves_per_call": P * S, "calls": ke}
 
     # ---- per-family kernel timing (CUDA events on the solve stream, separate pass of one
     # handle alone: the concurrent handles' kernels overlap, which per-launch events cannot
     # apportion)
+    st1 = (mca.Stats * B)()
+    sp1 = mca.ctypes.cast(st1, mca.ctypes.c_void_p)
+    vt, vb, io = outs[0]
     solver.profile(True)
     for i in range(W, W + min(K, 4)):
-        step1(i, None)
+        mi_ = np.ascontiguousarray(ws.map_index[i * S:i * S + B])
+        rc = solver.solve_multi_raw(vin[i * S:i * S + B].data_ptr(), mi_.ctypes.data, B,
+                                    vt.data_ptr(), vb.data_ptr(), io.data_ptr(), sp1, stream)
+        if rc != 0:
+            raise RuntimeError(f"solve failed with status {rc}")
     prof = solver.profile_read()
     solver.profile(False)
     peaks, peak_src = load_peaks()
@@ -384,6 +556,11 @@ def run_ours(args):
     applies = prof["precond_1"]["flops"] / (4.0 * m * n * n) if prof["precond_1"]["flops"] else 0
     precond_tflops = (applies * 8.0 * m * n * (m + n) / (pc_ms / 1e3) / 1e12
                       if pc_ms and prec != mca.PREC_MHAT else None)
+    precond_frac = None
+    if precond_tflops:
+        precond_frac = {"of_sustained": precond_tflops / peaks.get("bf16_tflops_sustained", 1700.0),
+                        "of_burst": precond_tflops / peaks.get("bf16_tflops", 1900.0),
+                        "peak_source": peak_src}
 
     iters = np.array([(a, b_) for a, b_, _ in timed])
     out = {
@@ -394,7 +571,8 @@ def run_ours(args):
         "config": dict(workload_config(args, S), handles=H, batch_per_handle=B,
                        profile_pass="kernel_breakdown and roofline: one handle alone"),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-        "precond_tflops": precond_tflops, "kernel_breakdown": breakdown,
+        "precond_tflops": precond_tflops, "precond_frac": precond_frac,
+        "kernel_breakdown": breakdown,
         # summed device time of the timed kernels per step (profile pass) over the timed
         # step: what is left is host-side gaps (Newton checks, graph launches)
         "kernel_ms_per_step": total_ms / min(K, 4) * H,
@@ -407,36 +585,28 @@ def run_ours(args):
     for s_ in solvers:
         s_.close()
     del vt, vb, io, outs, outs_h
+    torch.cuda.empty_cache()
 
-    # ---- the same workload in the plain FP64 GPU form (one vector)
-    if not args.no_fp64_form and prec != mca.PREC_FP64:
-        p64 = mca.default_params(m, n, g_wire_top=p.g_wire_top, g_wire_bot=p.g_wire_bot,
-                                 g_src=p.g_src, g_term_top_right=p.g_term_top_right,
-                                 g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
-                                 precision=mca.PREC_FP64, newton_rtol=TOL, max_batch=1,
-                                 device_model=params.device_model, neg_ratio=p.neg_ratio)
-        with mca.Solver(p64, cb.gmap) as s64:
-            vt1 = torch.empty(1, m, n, dtype=torch.float64, device=dev)
-            vb1 = torch.empty_like(vt1)
-            io1 = torch.empty(1, n, dtype=torch.float64, device=dev)
-            st1 = (mca.Stats * 1)()
-            sp1 = mca.ctypes.cast(st1, mca.ctypes.c_void_p)
-            s64.solve_raw(vin[0:1].data_ptr(), 1, vt1.data_ptr(), vb1.data_ptr(), io1.data_ptr(),
-                          sp1, stream)
-            a = torch.cuda.Event(enable_timing=True)
-            b_ = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            nf = 2
-            for i in range(nf):
-                rc = s64.solve_raw(vin[1 + i:2 + i].data_ptr(), 1, vt1.data_ptr(), vb1.data_ptr(),
-                                   io1.data_ptr(), sp1, stream)
-                assert rc == 0 and st1[0].rel_residual <= TOL
-            b_.record(stream)
-            torch.cuda.synchronize()
-            t64 = a.elapsed_time(b_) / 1000.0
-            out["fp64_form"] = {"value": nf / t64, "unit": "solves/s",
-                                "gmres_iters_per_solve": st1[0].gmres_iters,
-                                "speedup_of_mixed": value / (world * nf / t64)}
+    # ---- the same workload in the all-FP64 GPU forms, at the headline's batching where it
+    # is affordable: the exact eigenbasis preconditioner with FP64 transforms (CUDA-core
+    # FP64 GEMMs; one handle of B vectors) and the paper's M_hat (eq. (block) with
+    # tridiagonal solves; H handles of B vectors, as the headline)
+    if not args.no_fp64_form and prec not in (mca.PREC_FP64, mca.PREC_MHAT):
+        _, f64 = time_form(mca, torch, ws, mca.PREC_FP64, 1, B, 1, 0, args.restart,
+                           params.device_model)
+        _, mh = time_form(mca, torch, ws, mca.PREC_MHAT, H, B, 2, 0, args.restart,
+                          params.device_model)
+        out["fp64_form"] = f64
+        out["mhat_form"] = mh
+        best = max(f64["value"], mh["value"])
+        out["speedup_of_mixed"] = {
+            "value": value / best, "against": "mhat_form" if mh["value"] >= f64["value"]
+            else "fp64_form",
+            "note": "device solves/s of the headline over the faster all-FP64 GPU form"}
+
+    # ---- 2048 x 2048 crossbars, with an oracle-recomputed residual
+    if not args.no_2048 and args.size == 1024 and prec == mca.PREC_BF16_SPLIT:
+        out["size_2048"] = run_2048(mca, torch, args, rank)
 
     # ---- the batched statistical-characterisation workload (secondary figure)
     if not args.no_batched and args.size == 1024:
@@ -447,13 +617,14 @@ def run_ours(args):
         # a bounded sample: whole oracle solves until about 10 s of CPU work (at most 25)
         ncpu, tcpu = 0, 0.0
         while ncpu < 25 and (ncpu == 0 or tcpu < 10.0):
-            tcpu += oracle_solves(cb, 1, start=ncpu)
+            tcpu += oracle_solves(ws, 1, start=ncpu)
             ncpu += 1
         out["cpu_baseline"] = {"value": ncpu / tcpu, "unit": "solves/s", "cores": os.cpu_count(),
                                "kind": "oracle",
                                "sample": f"{ncpu} oracle solves (Newton + FP64 preconditioned "
-                                         f"GMRES, NumPy/SciPy) of the {m}^2 crossbar, vectors "
-                                         f"0-{ncpu - 1}, {tcpu:.1f} s"}
+                                         f"GMRES, NumPy/SciPy) of the {m}^2 workload, vectors "
+                                         f"0-{ncpu - 1} (crossbars 0-3), {tcpu:.1f} s",
+                               "configs": oracle_configs_in_children()}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if pg:
@@ -472,18 +643,12 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
     for k, cb in enumerate(cbs):
         groups.setdefault((cb.params.rows, cb.params.cols), []).append(k)
 
-    def params_for(p, B):
-        return mca.default_params(p.rows, p.cols, g_wire_top=p.g_wire_top,
-                                  g_wire_bot=p.g_wire_bot, g_src=p.g_src,
-                                  g_term_top_right=p.g_term_top_right,
-                                  g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b,
-                                  newton_rtol=TOL, max_batch=B, gmres_restart=16)
-
     solvers, vins, maps = [], [], []
     for (m, n), ks in sorted(groups.items()):
         p = cbs[ks[0]].params
         B = min(64, len(ks) * nvec)   # one pass per shape group where it fits
-        solvers.append(mca.Solver(params_for(p, B), np.stack([cbs[k].gmap for k in ks])))
+        solvers.append(mca.Solver(params_for(mca, p, mca.PREC_BF16_SPLIT, B, restart=16),
+                                  np.stack([cbs[k].gmap for k in ks])))
         vins.append(np.concatenate([cbs[k].vin for k in ks]))
         maps.append(np.repeat(np.arange(len(ks)), nvec))
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -507,7 +672,8 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
     tb = 0.0
     for k in sample:
         cb = cbs[k]
-        with mca.Solver(params_for(cb.params, nvec), cb.gmap) as s1:
+        with mca.Solver(params_for(mca, cb.params, mca.PREC_BF16_SPLIT, nvec, restart=16),
+                        cb.gmap) as s1:
             vin_d = torch.as_tensor(cb.vin, device=dev)
             vt = torch.empty(nvec, s1.m, s1.n, dtype=torch.float64, device=dev)
             vb = torch.empty_like(vt)
@@ -613,8 +779,14 @@ def run_table1(args):
 
 def main():
     args = parse_args()
+    if args.oracle_configs:
+        print(json.dumps(oracle_configs()), flush=True)
+        return
     if args.table1:
         run_table1(args)
+        return
+    if args.profile_precond:
+        run_profile_precond(args)
         return
     if args.impl == "reference":
         run_reference(args)
