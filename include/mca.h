@@ -180,55 +180,97 @@ int mca_solve_many(mca_handle* const* hs, int32_t nh, const double* const* v_in,
 int mca_set_conductances(mca_handle* h, const double* g_maps);
 
 /* Newton from a caller's initial guess instead of V = 0 (warm start).
- *   guess : device, nvec * 2*m*n states [V_t ; V_b] (e.g. from the CNN below).
- * A guess is rejected (stats.fallback = 1) when its residual is not finite or not
- * smaller than the residual of V = 0 (||F(guess)|| >= ||Y||); that vector then starts
- * from V = 0, whose first Newton step is the linear-circuit solve.  The Newton solve is
- * the judge of the guess: the returned voltages meet newton_rtol either way.  Other
- * arguments as in mca_solve_multi. */
+ *   guess    : device, nvec * 2*m*n states [V_t ; V_b] (e.g. V_lin + the CNN's correction).
+ *   fallback : device, nvec * 2*m*n states, or NULL for V = 0.
+ * The residual of the guess and of the fallback state are evaluated; a guess is rejected
+ * (stats.fallback = 1) when its residual is not finite or not smaller than the
+ * fallback's (||F(guess)|| >= ||F(fallback)||, with ||F(0)|| = ||Y|| for NULL), and that
+ * vector starts from the fallback state instead.  The Newton solve is the judge of the
+ * guess: the returned voltages meet newton_rtol either way, and stats.newton_iters counts
+ * the steps taken from the starting state.  Other arguments as in mca_solve_multi. */
 int mca_solve_from(mca_handle* h, const double* v_in, const double* guess,
-                   const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
-                   double* i_out, mca_stats* stats, void* stream);
+                   const double* fallback, const int32_t* map_index, int32_t nvec,
+                   double* v_top, double* v_bot, double* i_out, mca_stats* stats, void* stream);
 
-/* ---- learned warm start: kernels of the CNN (not part of the paper) ---------------
- * Activations are NCHW FP32 device arrays; weights [cout][cin][3][3] are BF16 (uint16_t
- * bit patterns) with FP32 accumulation; every layer is a 3x3 convolution with dilation d
- * and zero padding d (output size = input size), then bias and act (0 none, 1 leaky ReLU
- * with slope 0.1).  cin, cout <= 64.  All calls only enqueue work on the stream. */
-int mca_cnn_conv_forward(const float* x, int32_t n, int32_t cin, int32_t h, int32_t w,
-                         const uint16_t* wt, const float* bias, int32_t cout, int32_t dilation,
-                         int32_t act, float* y, void* stream);
+/* ---- learned warm start: the network's kernels (not part of the paper) -------------
+ * The network maps a crossbar's conductances, its input vector and the state V_lin after
+ * the first Newton step to the correction V* - V_lin.  Activations and gradients are NHWC
+ * BF16 device tensors with 32 channels ([n][y][x][c], uint16_t bit patterns, channels
+ * beyond a layer's count zero); FP32 master weights w[cout][cin][K][K] live with the
+ * optimiser and mca_cnn_prep_weights turns them into the BF16 operand tiles.  A layer is
+ * a K x K convolution (K odd, <= 15) with dilation d and zero padding d (K - 1) / 2
+ * (output size = input size), bias and act (0 none, 1 leaky ReLU with slope 0.1).  The
+ * convolutions run on the tcgen05 tensor cores (BF16 operands, FP32 accumulation).  All
+ * calls only enqueue work on the stream; the caller owns every buffer.  Returns
+ * MCA_ERR_INVALID_ARG for bad sizes or NULL buffers. */
 
-/* Backward of one layer from gy = dL/dy: gz_scratch (n*cout*h*w floats) receives dL/dz,
- * gx (may be NULL) dL/dx, gw (cout*cin*9) and gb (cout) the parameter gradients;
- * part holds nchunk*(cout*cin*9 + cout) floats of per-chunk partial sums (the pixel
- * reduction is split into nchunk chunks and summed in a fixed order). */
-int mca_cnn_conv_backward(const float* x, const float* y, const float* gy, int32_t n,
-                          int32_t cin, int32_t h, int32_t w, const uint16_t* wt, int32_t cout,
-                          int32_t dilation, int32_t act, float* gz_scratch, float* gx,
-                          float* gw, float* gb, float* part, int32_t nchunk, void* stream);
+/* Convolution as an implicit GEMM over 128-pixel row tiles.
+ *   x       : NHWC32, n x h x w pixels.
+ *   wt      : BF16 tiles [K*K][cout_mma][32] (forward) or [K*K][32][32] (backward data),
+ *             from mca_cnn_prep_weights.
+ *   cout_mma: 16 or 32 (32 for backward); cout <= cout_mma channels are written.
+ *   backward = 0: out = act(conv(x) + bias) (bias may be NULL);
+ *   backward = 1: x is the output gradient dL/dz of a layer, wt its backward tile, and
+ *             out = dL/dx, times act'(y_prev) when act = 1 (y_prev: NHWC32 output of the
+ *             layer below, i.e. the layer's input), the gradient dL/dz of that layer.
+ *   out     : NHWC32 BF16 output (may be NULL); out32: [n][h][w][cout] FP32 (may be NULL). */
+int mca_cnn_conv(const uint16_t* x, int32_t n, int32_t h, int32_t w, const uint16_t* wt,
+                 int32_t ksize, int32_t dilation, int32_t cout_mma, int32_t cout,
+                 const float* bias, int32_t act, int32_t backward, const uint16_t* y_prev,
+                 uint16_t* out, float* out32, void* stream);
 
-/* Mean squared error over count values; gpred (may be NULL) receives 2 (pred - t)/count,
- * part holds 256 floats, loss (device, 1 float) the mean. */
-int mca_cnn_mse(const float* pred, const float* target, int64_t count, float* gpred,
-                float* part, float* loss, void* stream);
+/* Floats of scratch mca_cnn_conv_wgrad needs for n x h x w pixels and K x K kernels
+ * (-1 for bad sizes). */
+int64_t mca_cnn_wgrad_scratch(int32_t n, int32_t h, int32_t w, int32_t ksize);
 
-/* One Adam step (bias-corrected, step >= 1) on FP32 master weights w; w_bf16 (may be
- * NULL) receives the BF16 copy used by the convolutions. */
-int mca_cnn_adam(float* w, uint16_t* w_bf16, const float* g, float* m1, float* m2, int64_t count,
-                 float lr, float beta1, float beta2, float eps, int32_t step, void* stream);
+/* Parameter gradients of a layer from its input x and output gradient gz (both NHWC32):
+ * gw[cout][cin][K][K] = sum_p gz[p][co] x[p + d (ky - r, kx - r)][ci] (FP32, written), and
+ * gb[cout] = sum_p gz[p][co] (may be NULL).  scratch: mca_cnn_wgrad_scratch floats. */
+int mca_cnn_conv_wgrad(const uint16_t* x, const uint16_t* gz, int32_t n, int32_t h, int32_t w,
+                       int32_t ksize, int32_t dilation, int32_t cin, int32_t cout,
+                       float* scratch, float* gw, float* gb, void* stream);
 
-/* Network input for nvec vectors of one crossbar: x[v] = [log10(g) + 5, V_in[v][i]/vscale
- * broadcast along row i] and, with nchan = 4, the node position [j/(n-1), i/(m-1)];
- * nchan x m x n FP32 each (gmap, vin device FP64). */
-int mca_cnn_features(const double* gmap, const double* vin, int32_t nvec, int32_t m, int32_t n,
-                     float vscale, int32_t nchan, float* x, void* stream);
+/* BF16 operand tiles of one layer from its FP32 master weights w[cout][cin][K][K]:
+ * wf[K*K][cout_mma][32] = w[co][ci][t] (forward; may be NULL) and wb[K*K][32][32] =
+ * w[co][ci][K*K - 1 - t] at [t][ci][co] (backward data: flipped taps; may be NULL). */
+int mca_cnn_prep_weights(const float* w, int32_t cout, int32_t cin, int32_t ksize,
+                         int32_t cout_mma, uint16_t* wf, uint16_t* wb, void* stream);
 
-/* Convert between the network's 2-channel output y = [V_t/vscale, V_b*bscale/vscale] and
- * FP64 solver states x = [V_t ; V_b]: to_state = 1 writes x from y, to_state = 0 writes
- * y_out from x (training targets). */
-int mca_cnn_state(const float* y, double* x, int32_t nvec, int32_t m, int32_t n, float vscale,
-                  float bscale, int32_t to_state, float* y_out, void* stream);
+/* Network input x (NHWC32, nvec x m x n) of nvec vectors: channel 0 = log10(g) + 5,
+ * 1 = V_in[i] / vscale along row i, 2 = V_lin,t / vscale, 3 = V_lin,b * bscale / vscale.
+ *   g_maps: device FP64 maps (m*n each); map_index: device int32 per vector (NULL: map 0);
+ *   v_in: device nvec * m; vlin_t, vlin_b: device nvec * m*n voltages of each layer (the
+ *   layout of mca_solve's v_top and v_bot). */
+int mca_cnn_features(const double* g_maps, const int32_t* map_index, const double* v_in,
+                     const double* vlin_t, const double* vlin_b, int32_t nvec, int32_t m,
+                     int32_t n, float vscale, float bscale, uint16_t* x, void* stream);
+
+/* Training target target[v][node][2] = (V* - V_lin) * (dscale_t, dscale_b) (FP32), from
+ * the two layers of V* and of V_lin (nvec * m*n each). */
+int mca_cnn_target(const double* vstar_t, const double* vstar_b, const double* vlin_t,
+                   const double* vlin_b, int32_t nvec, int32_t m, int32_t n, float dscale_t,
+                   float dscale_b, float* target, void* stream);
+
+/* Warm-start state guess = V_lin + pred / (dscale_t, dscale_b) as FP64 states [V_t ; V_b]
+ * (nvec * 2*m*n) from the network's FP32 output pred[v][node][2]; pred = NULL writes V_lin
+ * itself (the fallback state of mca_solve_from). */
+int mca_cnn_guess(const float* pred, const double* vlin_t, const double* vlin_b, int32_t nvec,
+                  int32_t m, int32_t n, float dscale_t, float dscale_b, double* guess,
+                  void* stream);
+
+/* Mean squared error of pred against target over npix pixels x 2 channels (loss: device,
+ * 1 float; part: 256 floats) and its gradient gz = 2 (pred - target) / (2 npix) as NHWC32
+ * BF16 (may be NULL). */
+int mca_cnn_loss(const float* pred, const float* target, int64_t npix, uint16_t* gz,
+                 float* part, float* loss, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on FP32 master weights w. */
+int mca_cnn_adam(float* w, const float* g, float* m1, float* m2, int64_t count, float lr,
+                 float beta1, float beta2, float eps, int32_t step, void* stream);
+
+/* Synchronise the stream and report whether a bounded wait of a network kernel expired
+ * since the last check (MCA_ERR_TIMEOUT, flag cleared) or MCA_OK. */
+int mca_cnn_check(void* stream);
 
 /* Release the handle and its device memory.  NULL is ignored. */
 void mca_destroy(mca_handle* h);

@@ -47,8 +47,9 @@ EXPORTED = (
     "mca_precond_apply",
     "mca_eigenpairs", "mca_gmres_solve", "mca_profile", "mca_profile_read",
     "mca_kernel_launches", "mca_residual_noalloc", "mca_create_multi", "mca_solve_multi",
-    "mca_solve_many", "mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
-    "mca_cnn_mse", "mca_cnn_adam", "mca_cnn_features", "mca_cnn_state", "mca_set_conductances",
+    "mca_solve_many", "mca_solve_from", "mca_cnn_conv", "mca_cnn_wgrad_scratch",
+    "mca_cnn_conv_wgrad", "mca_cnn_prep_weights", "mca_cnn_features", "mca_cnn_target",
+    "mca_cnn_guess", "mca_cnn_loss", "mca_cnn_adam", "mca_cnn_check", "mca_set_conductances",
     "mca_wait_selftest", "mca_tile_config",
 )
 
@@ -132,7 +133,7 @@ def load(build_if_missing=True):
     lib.mca_residual_noalloc.argtypes = [ctypes.POINTER(Params), P, P, P, ctypes.c_int32, P, P,
                                          P, P, P]
     lib.mca_residual_noalloc.restype = ctypes.c_int
-    lib.mca_solve_from.argtypes = [P, P, P, P, ctypes.c_int32, P, P, P, P, P]
+    lib.mca_solve_from.argtypes = [P, P, P, P, P, ctypes.c_int32, P, P, P, P, P]
     lib.mca_set_conductances.argtypes = [P, P]
     lib.mca_tile_config.argtypes = [P, P]
     lib.mca_tile_config.restype = ctypes.c_int
@@ -140,14 +141,20 @@ def load(build_if_missing=True):
     lib.mca_wait_selftest.restype = ctypes.c_int
     lib.mca_set_conductances.restype = ctypes.c_int
     I, F = ctypes.c_int32, ctypes.c_float
-    lib.mca_cnn_conv_forward.argtypes = [P, I, I, I, I, P, P, I, I, I, P, P]
-    lib.mca_cnn_conv_backward.argtypes = [P, P, P, I, I, I, I, P, I, I, I, P, P, P, P, P, I, P]
-    lib.mca_cnn_mse.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
-    lib.mca_cnn_adam.argtypes = [P, P, P, P, P, ctypes.c_int64, F, F, F, F, I, P]
-    lib.mca_cnn_features.argtypes = [P, P, I, I, I, F, I, P, P]
-    lib.mca_cnn_state.argtypes = [P, P, I, I, I, F, F, I, P, P]
-    for name in ("mca_solve_from", "mca_cnn_conv_forward", "mca_cnn_conv_backward",
-                 "mca_cnn_mse", "mca_cnn_adam", "mca_cnn_features", "mca_cnn_state"):
+    lib.mca_cnn_conv.argtypes = [P, I, I, I, P, I, I, I, I, P, I, I, P, P, P, P]
+    lib.mca_cnn_wgrad_scratch.argtypes = [I, I, I, I]
+    lib.mca_cnn_wgrad_scratch.restype = ctypes.c_int64
+    lib.mca_cnn_conv_wgrad.argtypes = [P, P, I, I, I, I, I, I, I, P, P, P, P]
+    lib.mca_cnn_prep_weights.argtypes = [P, I, I, I, I, P, P, P]
+    lib.mca_cnn_features.argtypes = [P, P, P, P, P, I, I, I, F, F, P, P]
+    lib.mca_cnn_target.argtypes = [P, P, P, P, I, I, I, F, F, P, P]
+    lib.mca_cnn_guess.argtypes = [P, P, P, I, I, I, F, F, P, P]
+    lib.mca_cnn_loss.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
+    lib.mca_cnn_adam.argtypes = [P, P, P, P, ctypes.c_int64, F, F, F, F, I, P]
+    lib.mca_cnn_check.argtypes = [P]
+    for name in ("mca_solve_from", "mca_cnn_conv", "mca_cnn_conv_wgrad", "mca_cnn_prep_weights",
+                 "mca_cnn_features", "mca_cnn_target", "mca_cnn_guess", "mca_cnn_loss",
+                 "mca_cnn_adam", "mca_cnn_check"):
         getattr(lib, name).restype = ctypes.c_int
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
@@ -317,9 +324,10 @@ class Solver:
         _check(self.lib.mca_set_conductances(self.h, _ptr(g)))
 
     def solve_from(self, vin, guess, v_top=None, v_bot=None, i_out=None, stream=None,
-                   map_index=None, allow_not_converged=False):
+                   map_index=None, allow_not_converged=False, fallback=None):
         """Newton from a device guess (nvec, 2*m*n) FP64 with the fallback rule of
-        mca_solve_from; returns (v_top, v_bot, i_out, stats)."""
+        mca_solve_from (fallback: device states of the same shape, or None for V = 0);
+        returns (v_top, v_bot, i_out, stats)."""
         nvec = vin.shape[0]
         mi = None if map_index is None else np.ascontiguousarray(map_index, np.int32)
         if isinstance(vin, np.ndarray):
@@ -331,7 +339,8 @@ class Solver:
         if i_out is None:
             i_out = np.empty((nvec, self.n))
         st = (Stats * nvec)()
-        rc = self.lib.mca_solve_from(self.h, _ptr(vin), _ptr(guess), _ptr(mi), nvec, _ptr(v_top),
+        rc = self.lib.mca_solve_from(self.h, _ptr(vin), _ptr(guess), _ptr(fallback), _ptr(mi),
+                                     nvec, _ptr(v_top),
                                      _ptr(v_bot), _ptr(i_out), ctypes.cast(st, ctypes.c_void_p),
                                      _stream_ptr(stream))
         _check(rc, (ERR_NOT_CONVERGED, ERR_NONFINITE) if allow_not_converged else ())

@@ -1,21 +1,24 @@
 """Learned warm start for the crossbar solve (a throughput pattern on top of the paper's
 method, not part of it).
 
-A six-layer dilated CNN maps a crossbar's conductance map and input vector (plus the
-node position) to a guess of both layers' node voltages.  It is trained on solves the
-method itself produces, and the guess only seeds Newton: ``Solver.solve_from`` rejects
-a guess whose KCL residual is not below that of V = 0 (then the linear-circuit start is
-used) and always iterates to the requested tolerance, so the network can save work but
-never change the answer.
+The first Newton step from V = 0 is the linear-circuit solve; what is left after it is
+the nonlinear correction V* - V_lin.  A six-layer convolutional network (11 x 11 kernels,
+32 channels, dilations 1 .. 32, about 0.52M parameters, BF16 weights with FP32
+accumulation) maps a crossbar's conductance map, its input vector and V_lin to that
+correction.  It is trained on solves the method itself produces, and its guess
+V_lin + correction only seeds Newton: ``Solver.solve_from`` keeps the guess only when its
+KCL residual is below that of V_lin (otherwise Newton continues from V_lin) and always
+iterates to the requested tolerance, so the network can save work but never change the
+answer.
 
-Every arithmetic step runs in the library's kernels (convolutions forward and backward,
-leaky ReLU, MSE, Adam, feature and state conversion); PyTorch only provides device
-buffers.  Run ``python -m paper_2109_07929_gb300.cnn --help`` to train and evaluate.
+Every arithmetic step runs in the library's kernels (tensor-core convolutions forward,
+backward and weight gradient, loss, Adam, the BF16 operand tiles, features, targets and
+guesses); PyTorch only provides device buffers.  Run ``python -m paper_2109_07929_gb300.cnn
+--help`` to train and evaluate.
 """
 from __future__ import annotations
 
 import argparse
-import ctypes
 import json
 import os
 import struct
@@ -23,17 +26,24 @@ import time
 
 import numpy as np
 
-from . import (PREC_BF16_SPLIT, Solver, _check, _ptr, _stream_ptr, default_params, load)
+from . import (PREC_BF16_SPLIT, Solver, _check, _ptr, _stream_ptr, default_params, load,
+               residual_noalloc)
 
-# (cin, cout, dilation, leaky-ReLU) per layer: 6 layers, 32 channels, receptive field 127
+# (cin, cout, dilation, leaky-ReLU) per layer; 11 x 11 kernels: receptive field 631 nodes
 LAYERS = ((4, 32, 1, 1), (32, 32, 2, 1), (32, 32, 4, 1), (32, 32, 8, 1), (32, 32, 16, 1),
           (32, 2, 32, 0))
+KSIZE = 11
+C = 32            # channels of the NHWC activation tensors (padded)
 VSCALE = 0.3      # volts: V_in ~ U[0, 0.3]
 BSCALE = 4.0      # bottom-layer voltages are ~4x smaller than the top layer's
-NCHAN = 4         # log g, V_in, column position, row position
+DSCALE = 2000.0   # 1/V: the correction V* - V_lin is a few 1e-4 V
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
-                       "warmstart_cnn.bin")
-_MAGIC = b"MCACNN01"
+                       "warmstart_cnn11.bin")
+_MAGIC = b"MCACNN02"
+
+
+def _cout_mma(cout):
+    return 16 if cout <= 16 else 32
 
 
 class WarmStartCNN:
@@ -43,101 +53,131 @@ class WarmStartCNN:
         self.lib = load()
         self.dev = torch.device(device)
         rng = np.random.default_rng(seed)
-        self.w, self.b = [], []
+        T = KSIZE * KSIZE
+        self.w, self.b, self.wf, self.wb = [], [], [], []
         for cin, cout, d, act in LAYERS:
-            std = np.sqrt(2.0 / (cin * 9)) if act else 1e-2
-            self.w.append(torch.as_tensor(rng.standard_normal((cout, cin, 3, 3)) * std,
+            std = np.sqrt(2.0 / (cin * T)) if act else 1e-3
+            self.w.append(torch.as_tensor(rng.standard_normal((cout, cin, KSIZE, KSIZE)) * std,
                                           dtype=torch.float32, device=self.dev))
             self.b.append(torch.zeros(cout, dtype=torch.float32, device=self.dev))
-        self._sync_bf16()
+            self.wf.append(torch.empty(T, _cout_mma(cout), C, dtype=torch.int16, device=self.dev))
+            self.wb.append(torch.empty(T, C, C, dtype=torch.int16, device=self.dev))
         self.mw = [torch.zeros_like(w) for w in self.w]
         self.vw = [torch.zeros_like(w) for w in self.w]
         self.mb = [torch.zeros_like(b) for b in self.b]
         self.vb = [torch.zeros_like(b) for b in self.b]
         self.step = 0
+        self._scratch = {}
+        for li in range(len(LAYERS)):
+            self.prep(li)
 
     def n_params(self):
         return int(sum(w.numel() + b.numel() for w, b in zip(self.w, self.b)))
 
-    def _sync_bf16(self):
-        torch = self.torch
-        self.wb = [w.to(torch.bfloat16).view(torch.int16).contiguous() for w in self.w]
+    def prep(self, li, stream=None):
+        """BF16 operand tiles of layer li from its FP32 master weights (library kernel)."""
+        cin, cout, d, act = LAYERS[li]
+        _check(self.lib.mca_cnn_prep_weights(_ptr(self.w[li]), cout, cin, KSIZE, _cout_mma(cout),
+                                             _ptr(self.wf[li]), _ptr(self.wb[li]),
+                                             _stream_ptr(stream)))
+
+    def _nhwc(self, N, H, W):
+        return self.torch.empty(N, H, W, C, dtype=self.torch.int16, device=self.dev)
 
     # ---- forward / backward through the library kernels -------------------------------
     def forward(self, x, N, H, W, stream=None):
+        """x: NHWC32 BF16 input (N, H, W, 32).  Returns the hidden activations (NHWC32 BF16,
+        the input first) and the FP32 prediction (N, H, W, 2)."""
         torch = self.torch
         acts = [x]
-        for (cin, cout, d, act), wb, b in zip(LAYERS, self.wb, self.b):
-            y = torch.empty(N, cout, H, W, dtype=torch.float32, device=self.dev)
-            _check(self.lib.mca_cnn_conv_forward(_ptr(acts[-1]), N, cin, H, W, _ptr(wb), _ptr(b),
-                                                 cout, d, act, _ptr(y), _stream_ptr(stream)))
-            acts.append(y)
-        return acts
+        pred = None
+        for li, (cin, cout, d, act) in enumerate(LAYERS):
+            last = li == len(LAYERS) - 1
+            out = None if last else self._nhwc(N, H, W)
+            out32 = torch.empty(N, H, W, cout, dtype=torch.float32, device=self.dev) if last else None
+            _check(self.lib.mca_cnn_conv(_ptr(acts[-1]), N, H, W, _ptr(self.wf[li]), KSIZE, d,
+                                         _cout_mma(cout), cout, _ptr(self.b[li]), act, 0, None,
+                                         _ptr(out), _ptr(out32), _stream_ptr(stream)))
+            if last:
+                pred = out32
+            else:
+                acts.append(out)
+        return acts, pred
 
-    def train_step(self, x, target, N, H, W, lr, stream=None, nchunk=64):
+    def train_step(self, x, target, N, H, W, lr, stream=None):
         torch = self.torch
-        acts = self.forward(x, N, H, W, stream)
-        pred = acts[-1]
-        g = torch.empty_like(pred)
+        acts, pred = self.forward(x, N, H, W, stream)
+        gz = self._nhwc(N, H, W)
         part = torch.empty(256, dtype=torch.float32, device=self.dev)
         loss = torch.empty(1, dtype=torch.float32, device=self.dev)
-        _check(self.lib.mca_cnn_mse(_ptr(pred), _ptr(target), pred.numel(), _ptr(g), _ptr(part),
-                                    _ptr(loss), _stream_ptr(stream)))
+        _check(self.lib.mca_cnn_loss(_ptr(pred), _ptr(target), N * H * W, _ptr(gz), _ptr(part),
+                                     _ptr(loss), _stream_ptr(stream)))
+        key = (N, H, W)
+        if key not in self._scratch:
+            nf = int(self.lib.mca_cnn_wgrad_scratch(N, H, W, KSIZE))
+            self._scratch[key] = torch.empty(nf, dtype=torch.float32, device=self.dev)
+        scratch = self._scratch[key]
         self.step += 1
         for li in range(len(LAYERS) - 1, -1, -1):
             cin, cout, d, act = LAYERS[li]
-            gz = torch.empty_like(acts[li + 1])
-            gx = torch.empty_like(acts[li]) if li > 0 else None
             gw = torch.empty_like(self.w[li])
             gb = torch.empty_like(self.b[li])
-            pbuf = torch.empty(nchunk * (cout * cin * 9 + cout), dtype=torch.float32,
-                               device=self.dev)
-            _check(self.lib.mca_cnn_conv_backward(
-                _ptr(acts[li]), _ptr(acts[li + 1]), _ptr(g), N, cin, H, W, _ptr(self.wb[li]),
-                cout, d, act, _ptr(gz), _ptr(gx), _ptr(gw), _ptr(gb), _ptr(pbuf), nchunk,
-                _stream_ptr(stream)))
-            for p, gp, m1, m2, pb in ((self.w[li], gw, self.mw[li], self.vw[li], self.wb[li]),
-                                      (self.b[li], gb, self.mb[li], self.vb[li], None)):
-                _check(self.lib.mca_cnn_adam(_ptr(p), _ptr(pb), _ptr(gp), _ptr(m1), _ptr(m2),
-                                             p.numel(), lr, 0.9, 0.999, 1e-8, self.step,
-                                             _stream_ptr(stream)))
-            g = gx
+            _check(self.lib.mca_cnn_conv_wgrad(_ptr(acts[li]), _ptr(gz), N, H, W, KSIZE, d, cin,
+                                               cout, _ptr(scratch), _ptr(gw), _ptr(gb),
+                                               _stream_ptr(stream)))
+            gprev = None
+            if li > 0:
+                # dL/dz of the layer below: the transposed convolution of gz times the leaky
+                # ReLU derivative at that layer's output (this layer's input)
+                gprev = self._nhwc(N, H, W)
+                _check(self.lib.mca_cnn_conv(_ptr(gz), N, H, W, _ptr(self.wb[li]), KSIZE, d, C,
+                                             cin, None, LAYERS[li - 1][3], 1, _ptr(acts[li]),
+                                             _ptr(gprev), None, _stream_ptr(stream)))
+            for p, g, m1, m2 in ((self.w[li], gw, self.mw[li], self.vw[li]),
+                                 (self.b[li], gb, self.mb[li], self.vb[li])):
+                _check(self.lib.mca_cnn_adam(_ptr(p), _ptr(g), _ptr(m1), _ptr(m2), p.numel(), lr,
+                                             0.9, 0.999, 1e-8, self.step, _stream_ptr(stream)))
+            self.prep(li, stream)
+            gz = gprev
         return loss
 
-    # ---- guesses ------------------------------------------------------------------------
-    def features(self, gmap_dev, vin_dev, m, n, stream=None):
-        torch = self.torch
+    # ---- inputs, targets, guesses -----------------------------------------------------
+    def features(self, gmaps_dev, map_dev, vin_dev, vlt, vlb, m, n, stream=None):
         nv = vin_dev.shape[0]
-        x = torch.empty(nv, NCHAN, m, n, dtype=torch.float32, device=self.dev)
-        _check(self.lib.mca_cnn_features(_ptr(gmap_dev), _ptr(vin_dev), nv, m, n, VSCALE, NCHAN,
-                                         _ptr(x), _stream_ptr(stream)))
+        x = self._nhwc(nv, m, n)
+        _check(self.lib.mca_cnn_features(_ptr(gmaps_dev), _ptr(map_dev), _ptr(vin_dev), _ptr(vlt),
+                                         _ptr(vlb), nv, m, n, VSCALE, BSCALE, _ptr(x),
+                                         _stream_ptr(stream)))
         return x
 
-    def targets(self, state_dev, m, n, stream=None):
+    def targets(self, vst, vsb, vlt, vlb, m, n, stream=None):
         torch = self.torch
-        nv = state_dev.shape[0]
-        y = torch.empty(nv, 2, m, n, dtype=torch.float32, device=self.dev)
-        _check(self.lib.mca_cnn_state(None, _ptr(state_dev), nv, m, n, VSCALE, BSCALE, 0, _ptr(y),
-                                      _stream_ptr(stream)))
-        return y
+        nv = vst.shape[0]
+        t = torch.empty(nv, m, n, 2, dtype=torch.float32, device=self.dev)
+        _check(self.lib.mca_cnn_target(_ptr(vst), _ptr(vsb), _ptr(vlt), _ptr(vlb), nv, m, n,
+                                       DSCALE, DSCALE, _ptr(t), _stream_ptr(stream)))
+        return t
 
-    def guess(self, gmap_dev, vin_dev, m, n, stream=None):
-        """FP64 initial states [V_t ; V_b] (nvec, 2*m*n) for Solver.solve_from."""
+    def state(self, pred, vlt, vlb, m, n, stream=None):
+        """FP64 states [V_t ; V_b] (nvec, 2*m*n): V_lin + the predicted correction, or V_lin
+        itself for pred = None."""
         torch = self.torch
-        nv = vin_dev.shape[0]
-        x = self.features(gmap_dev, vin_dev, m, n, stream)
-        y = self.forward(x, nv, m, n, stream)[-1]
+        nv = vlt.shape[0]
         st = torch.empty(nv, 2 * m * n, dtype=torch.float64, device=self.dev)
-        _check(self.lib.mca_cnn_state(_ptr(y), _ptr(st), nv, m, n, VSCALE, BSCALE, 1, None,
-                                      _stream_ptr(stream)))
+        _check(self.lib.mca_cnn_guess(_ptr(pred), _ptr(vlt), _ptr(vlb), nv, m, n, DSCALE, DSCALE,
+                                      _ptr(st), _stream_ptr(stream)))
         return st
 
-    # ---- weights file: magic, layer count, (cin, cout, d, act) per layer, FP32 w and b --
+    def check(self, stream=None):
+        _check(self.lib.mca_cnn_check(_stream_ptr(stream)))
+
+    # ---- weights file: magic, kernel size, layer count, (cin, cout, d, act) per layer, FP32
+    # w [cout][cin][K][K] and b per layer
     def save(self, path=WEIGHTS):
         os.makedirs(os.path.dirname(path), exist_ok=True)
         with open(path, "wb") as f:
             f.write(_MAGIC)
-            f.write(struct.pack("<i", len(LAYERS)))
+            f.write(struct.pack("<2i", KSIZE, len(LAYERS)))
             for spec in LAYERS:
                 f.write(struct.pack("<4i", *spec))
             for w, b in zip(self.w, self.b):
@@ -149,16 +189,17 @@ class WarmStartCNN:
         with open(path, "rb") as f:
             if f.read(8) != _MAGIC:
                 raise ValueError("not a warm-start weights file")
-            (nl,) = struct.unpack("<i", f.read(4))
-            specs = [tuple(struct.unpack("<4i", f.read(16))) for _ in range(nl)]
-            if tuple(specs) != LAYERS:
+            k, nl = struct.unpack("<2i", f.read(8))
+            specs = tuple(tuple(struct.unpack("<4i", f.read(16))) for _ in range(nl))
+            if k != KSIZE or specs != LAYERS:
                 raise ValueError("weights file was written for another architecture")
             for li, (cin, cout, d, act) in enumerate(specs):
-                w = np.frombuffer(f.read(cout * cin * 9 * 4), dtype="<f4").reshape(cout, cin, 3, 3)
+                cnt = cout * cin * KSIZE * KSIZE
+                w = np.frombuffer(f.read(cnt * 4), dtype="<f4").reshape(cout, cin, KSIZE, KSIZE)
                 b = np.frombuffer(f.read(cout * 4), dtype="<f4")
-                self.w[li] = torch.as_tensor(w.copy(), device=self.dev)
-                self.b[li] = torch.as_tensor(b.copy(), device=self.dev)
-        self._sync_bf16()
+                self.w[li].copy_(torch.as_tensor(w.copy()))
+                self.b[li].copy_(torch.as_tensor(b.copy()))
+                self.prep(li)
         return self
 
 
@@ -170,147 +211,196 @@ def _params(p, **kw):
                           g_term_bot_top=p.g_term_bot_top, g_sense=p.g_sense, b=p.b, **kw)
 
 
-def make_dataset(count, size=256, seed0=1_000_000, group=64, log=print):
-    """`count` crossbars of the small-workload distribution (log-uniform g in [1e-6,1e-4]
-    S, 1 S wires, V_in ~ U[0, 0.3]) solved to 1e-10 by the library; returns device
-    tensors (features, targets, gmaps, vins)."""
-    import torch
-    import mca_inputs as mi
-    model = WarmStartCNN.__new__(WarmStartCNN)          # feature/target helpers only
-    model.torch, model.lib, model.dev = torch, load(), torch.device("cuda")
-    X, T, G, V = [], [], [], []
-    solver = None
-    t0 = time.time()
-    for g0 in range(0, count, group):
-        k = min(group, count - g0)
-        cbs = [mi.make_crossbar(size, size, seed0 + g0 + i) for i in range(k)]
+class SolvePair:
+    """Two multi-map handles of one shape: `lin` stops after the first Newton step (V_lin),
+    `full` solves to the tolerance (V*, or the warm-started solve)."""
+
+    def __init__(self, size, count, tol=1e-8):
+        import torch
+        import mca_inputs as mi
+        self.torch, self.size, self.count = torch, size, count
+        p = mi.make_crossbar(size, size, 0).params
+        g = np.full((count, size, size), 1e-5)
+        self.lin = Solver(_params(p, precision=PREC_BF16_SPLIT, max_newton=1, max_batch=count), g)
+        self.full = Solver(_params(p, precision=PREC_BF16_SPLIT, newton_rtol=tol,
+                                   max_batch=count), g)
+        dev = torch.device("cuda")
+        z = lambda: torch.empty(count, size, size, dtype=torch.float64, device=dev)
+        self.vlt, self.vlb, self.vst, self.vsb = z(), z(), z(), z()
+        self.io = torch.empty(count, size, dtype=torch.float64, device=dev)
+        self.map_host = np.arange(count, dtype=np.int32)
+        self.map_dev = torch.as_tensor(self.map_host, device=dev)
+
+    def set(self, cbs):
+        torch = self.torch
         gm = np.stack([cb.gmap for cb in cbs])
-        vin = np.concatenate([cb.vin for cb in cbs])
-        if solver is None or solver.n_maps != k:
-            if solver is not None:
-                solver.close()
-            solver = Solver(_params(cbs[0].params, precision=PREC_BF16_SPLIT, newton_rtol=1e-10,
-                                    max_batch=k), gm)
-        else:
-            solver.set_conductances(gm)
-        vin_d = torch.as_tensor(vin, device="cuda")
-        vt = torch.empty(k, size, size, dtype=torch.float64, device="cuda")
-        vb = torch.empty_like(vt)
-        io = torch.empty(k, size, dtype=torch.float64, device="cuda")
-        solver.solve(vin_d, vt, vb, io, map_index=np.arange(k))
-        state = torch.cat([vt.reshape(k, -1), vb.reshape(k, -1)], dim=1).contiguous()
-        gm_d = torch.as_tensor(gm, device="cuda")
-        for i in range(k):
-            X.append(model.features(gm_d[i], vin_d[i:i + 1], size, size))
-        T.append(model.targets(state, size, size))
-        G.append(gm_d)
-        V.append(vin_d)
-    if solver is not None:
-        solver.close()
-    torch.cuda.synchronize()
-    log(f"dataset: {count} solves of {size}^2 in {time.time() - t0:.1f} s")
-    return torch.cat(X), torch.cat(T), torch.cat(G), torch.cat(V)
+        self.lin.set_conductances(gm)
+        self.full.set_conductances(gm)
+        self.gm_dev = torch.as_tensor(gm, device="cuda")
+        self.vin_dev = torch.as_tensor(np.concatenate([cb.vin[:1] for cb in cbs]), device="cuda")
+
+    def solve_lin(self):
+        return self.lin.solve(self.vin_dev, self.vlt, self.vlb, self.io, map_index=self.map_host,
+                              allow_not_converged=True)[3]
+
+    def solve_full(self):
+        return self.full.solve(self.vin_dev, self.vst, self.vsb, self.io, map_index=self.map_host)[3]
+
+    def close(self):
+        self.lin.close()
+        self.full.close()
 
 
-def train(model, X, T, epochs=4, batch=32, lr=2e-3, log=print):
-    import torch
-    N, _, H, W = X.shape
-    steps = epochs * ((N + batch - 1) // batch)
-    it = 0
-    losses = []
+def train(model, samples=20000, size=256, batch=32, epochs=4, lr=1e-3, seed0=1_000_000,
+          log=print, max_seconds=None):
+    """Adam on `samples` crossbars of the 32^2 workload's distribution at `size`^2
+    (log-uniform g in [1e-6, 1e-4] S, 1 S wires, V_in ~ U[0, 0.3]), generated and solved by
+    the library batch by batch (V_lin from the first Newton step, V* to 1e-10).  Stops early
+    after max_seconds (the returned step count says how far it got)."""
+    import mca_inputs as mi
+    torch = model.torch
+    pair = SolvePair(size, batch, tol=1e-10)
+    steps = epochs * (samples // batch)
+    losses, it = [], 0
     t0 = time.time()
-    for ep in range(epochs):
-        perm = torch.randperm(N, device=X.device, generator=None)
-        for s0 in range(0, N, batch):
-            idx = perm[s0:s0 + batch]
-            xb = X[idx].contiguous()
-            tb = T[idx].contiguous()
-            lr_t = 1e-4 + 0.5 * (lr - 1e-4) * (1 + np.cos(np.pi * it / max(1, steps)))
-            loss = model.train_step(xb, tb, xb.shape[0], H, W, lr_t)
-            it += 1
-            if it % 50 == 0 or it == steps:
-                losses.append(float(loss.item()))
-                log(f"epoch {ep} step {it}/{steps} loss {losses[-1]:.3e} "
-                    f"({time.time() - t0:.0f} s)")
+    try:
+        for ep in range(epochs):
+            order = np.random.default_rng(ep).permutation(samples // batch)
+            for bi in order:
+                if max_seconds is not None and time.time() - t0 > max_seconds:
+                    break
+                cbs = [mi.make_crossbar(size, size, seed0 + bi * batch + k) for k in range(batch)]
+                pair.set(cbs)
+                pair.solve_lin()
+                pair.solve_full()
+                x = model.features(pair.gm_dev, pair.map_dev, pair.vin_dev, pair.vlt, pair.vlb,
+                                   size, size)
+                t = model.targets(pair.vst, pair.vsb, pair.vlt, pair.vlb, size, size)
+                lr_t = 1e-5 + 0.5 * (lr - 1e-5) * (1 + np.cos(np.pi * it / max(1, steps)))
+                loss = model.train_step(x, t, batch, size, size, lr_t)
+                it += 1
+                if it == 1 or it % 50 == 0 or it == steps:
+                    losses.append(float(loss.item()))
+                    log(f"epoch {ep} step {it}/{steps} loss {losses[-1]:.4e} "
+                        f"({time.time() - t0:.0f} s)")
+        model.check()
+    finally:
+        pair.close()
     torch.cuda.synchronize()
-    return losses, time.time() - t0
+    if not losses or losses[-1] != float(loss.item()):
+        losses.append(float(loss.item()))
+    return losses, time.time() - t0, it
 
 
 def evaluate(model, size, count, seed0=2_000_000, log=print):
-    """Newton from V = 0 vs from the CNN guess on held-out crossbars of `size`."""
-    import torch
+    """Newton from V = 0 against the warm path (first Newton step -> V_lin, the network's
+    correction, Newton from the guess with V_lin as the fallback) on held-out crossbars."""
     import mca_inputs as mi
-    rows = []
-    for k in range(count):
-        cb = mi.make_crossbar(size, size, seed0 + k)
-        p = _params(cb.params, precision=PREC_BF16_SPLIT, newton_rtol=1e-8, max_batch=1)
-        with Solver(p, cb.gmap) as s:
-            gm_d = torch.as_tensor(cb.gmap, device="cuda")
-            vin_d = torch.as_tensor(cb.vin, device="cuda")
-            vt = torch.empty(1, size, size, dtype=torch.float64, device="cuda")
-            vb = torch.empty_like(vt)
-            io = torch.empty(1, size, dtype=torch.float64, device="cuda")
-            s.solve(vin_d, vt, vb, io)                      # warm-up (graphs)
+    torch = model.torch
+    cbs = [mi.make_crossbar(size, size, seed0 + k) for k in range(count)]
+    pair = SolvePair(size, count, tol=1e-8)
+    try:
+        pair.set(cbs)
+        n = size
+        # base: Newton from V = 0 (first call builds the CUDA graphs)
+        pair.solve_full()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st0 = pair.solve_full()
+        torch.cuda.synchronize()
+        t_base = time.perf_counter() - t
+        # warm path: V_lin, network, Newton from the guess (a first round warms it up)
+        res = None
+        for rep in range(2):
             torch.cuda.synchronize()
             t = time.perf_counter()
-            _, _, _, st0 = s.solve(vin_d, vt, vb, io)
+            st1 = pair.solve_lin()
             torch.cuda.synchronize()
-            t_base = time.perf_counter() - t
-            ref = torch.cat([vt.reshape(1, -1), vb.reshape(1, -1)], dim=1)
-            g = model.guess(gm_d, vin_d, size, size)
-            s.solve_from(vin_d, g, vt, vb, io)
-            torch.cuda.synchronize()
+            t_lin = time.perf_counter() - t
             t = time.perf_counter()
-            g = model.guess(gm_d, vin_d, size, size)
-            _, _, _, st1 = s.solve_from(vin_d, g, vt, vb, io)
+            x = model.features(pair.gm_dev, pair.map_dev, pair.vin_dev, pair.vlt, pair.vlb, n, n)
+            _, pred = model.forward(x, count, n, n)
+            guess = model.state(pred, pair.vlt, pair.vlb, n, n)
+            vlin = model.state(None, pair.vlt, pair.vlb, n, n)
             torch.cuda.synchronize()
-            t_warm = time.perf_counter() - t
-            err = float(((g - ref).abs().max() / ref.abs().max()).item())
-        rows.append(dict(newton_base=st0[0]["newton_iters"], gmres_base=st0[0]["gmres_iters"],
-                         newton_warm=st1[0]["newton_iters"], gmres_warm=st1[0]["gmres_iters"],
-                         fallback=st1[0]["fallback"], residual_warm=st1[0]["rel_residual"],
-                         guess_max_rel_err=err, t_base_ms=1e3 * t_base,
-                         t_warm_ms=1e3 * t_warm))
-        log(f"{size}^2 #{k}: {rows[-1]}")
-    agg = {key: float(np.mean([r[key] for r in rows])) for key in rows[0]}
-    agg["count"] = count
-    agg["newton_iters_saved"] = agg["newton_base"] - agg["newton_warm"]
-    agg["gmres_iters_saved"] = agg["gmres_base"] - agg["gmres_warm"]
-    agg["fallback_rate"] = agg.pop("fallback")
-    agg["max_residual_warm"] = float(max(r["residual_warm"] for r in rows))
-    return agg
+            t_cnn = time.perf_counter() - t
+            t = time.perf_counter()
+            _, _, _, st2 = pair.full.solve_from(pair.vin_dev, guess, pair.vst, pair.vsb, pair.io,
+                                                map_index=pair.map_host, fallback=vlin)
+            torch.cuda.synchronize()
+            t_from = time.perf_counter() - t
+            res = (st1, st2, t_lin, t_cnn, t_from, guess, vlin)
+        st1, st2, t_lin, t_cnn, t_from, guess, vlin = res
+        # KCL residuals of the guess and of V_lin (the library's FP64 residual kernel)
+        F = torch.empty(1, 2 * n * n, dtype=torch.float64, device="cuda")
+        D = torch.empty(1, n * n, dtype=torch.float64, device="cuda")
+        fn = torch.empty(2, dtype=torch.float64, device="cuda")
+        prm = _params(cbs[0].params)
+        ratio = []
+        for k in range(count):
+            for j, st in enumerate((guess, vlin)):
+                residual_noalloc(prm, pair.gm_dev[k], st[k:k + 1], pair.vin_dev[k:k + 1], F, D,
+                                 fn[j:j + 1])
+            f = fn.cpu().numpy()
+            ratio.append(float(f[0] / f[1]))
+    finally:
+        pair.close()
+    model.check()
+    out = {
+        "size": size, "count": count,
+        "newton_base": float(np.mean([s["newton_iters"] for s in st0])),
+        "gmres_base": float(np.mean([s["gmres_iters"] for s in st0])),
+        # warm path: the first Newton step plus the steps from the accepted start
+        "newton_warm": float(np.mean([1 + s["newton_iters"] for s in st2])),
+        "gmres_warm": float(np.mean([a["gmres_iters"] + b["gmres_iters"]
+                                     for a, b in zip(st1, st2)])),
+        "fallback_rate": float(np.mean([s["fallback"] for s in st2])),
+        "residual_ratio_guess_over_vlin": {"mean": float(np.mean(ratio)), "min": min(ratio),
+                                           "max": max(ratio)},
+        "max_residual_base": float(max(s["rel_residual"] for s in st0)),
+        "max_residual_warm": float(max(s["rel_residual"] for s in st2)),
+        "ms_per_solve_base": 1e3 * t_base / count,
+        "ms_per_solve_warm": 1e3 * (t_lin + t_cnn + t_from) / count,
+        "ms_per_solve_network": 1e3 * t_cnn / count,
+    }
+    out["newton_iters_saved"] = out["newton_base"] - out["newton_warm"]
+    out["gmres_iters_saved"] = out["gmres_base"] - out["gmres_warm"]
+    log(json.dumps(out))
+    return out
 
 
 def main():
-    ap = argparse.ArgumentParser(description="train / evaluate the warm-start CNN")
+    ap = argparse.ArgumentParser(description="train / evaluate the warm-start network")
     ap.add_argument("--samples", type=int, default=20000)
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval256", type=int, default=8)
     ap.add_argument("--eval512", type=int, default=8)
     ap.add_argument("--eval1024", type=int, default=4)
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--report", default=None, help="write the evaluation JSON here")
     ap.add_argument("--eval-only", action="store_true")
+    ap.add_argument("--max-minutes", type=float, default=None, help="training time budget")
     a = ap.parse_args()
     model = WarmStartCNN(seed=0)
-    print(f"parameters: {model.n_params()}")
-    report = {"parameters": model.n_params(), "layers": LAYERS}
+    print(f"parameters: {model.n_params()}", flush=True)
+    report = {"parameters": model.n_params(), "layers": LAYERS, "kernel": KSIZE}
     if not a.eval_only:
-        X, T, _, _ = make_dataset(a.samples, a.size)
-        losses, ttrain = train(model, X, T, a.epochs, a.batch, a.lr)
-        del X, T
+        losses, ttrain, nsteps = train(model, a.samples, a.size, a.batch, a.epochs, a.lr,
+                                       max_seconds=None if a.max_minutes is None
+                                       else 60 * a.max_minutes)
         model.save(a.out)
         report.update(train_samples=a.samples, train_size=a.size, epochs=a.epochs,
-                      final_loss=losses[-1], train_seconds=ttrain)
+                      batch=a.batch, steps=nsteps, loss_first=losses[0], loss_final=losses[-1],
+                      losses=losses, train_seconds=ttrain)
     else:
         model.load(a.out)
     report["eval_256_in_distribution"] = evaluate(model, 256, a.eval256)
     report["eval_512"] = evaluate(model, 512, a.eval512)
     report["eval_1024"] = evaluate(model, 1024, a.eval1024)
-    print(json.dumps(report))
+    print(json.dumps(report), flush=True)
     if a.report:
         with open(a.report, "w") as f:
             json.dump(report, f, indent=1)

@@ -1,211 +1,525 @@
-// Learned warm start: kernels of a small dilated CNN that maps a crossbar's conductance
-// map and input vector to a guess of both layers' node voltages, trained on solves the
-// method itself produces.  Not part of the paper (a throughput pattern layered on top of
-// the Newton solve, which remains the judge of the guess: mca_solve_from).
+// Learned warm start: kernels of the convolutional network that predicts the nonlinear
+// correction V* - V_lin of a crossbar's node voltages from its conductance map, its input
+// vector and the state V_lin after the first Newton step (the linear-circuit solve), and
+// of its training on solves the method itself produces.  Not part of the paper (a
+// throughput pattern layered on top of the Newton solve, which remains the judge of the
+// guess: mca_solve_from).
 //
-// Layout: activations NCHW FP32; weights [cout][cin][3][3] in BF16 (the FP32 master copy
-// lives with the optimiser); FP32 accumulation.  Every layer is a 3x3 convolution with
-// dilation d and zero padding d (output size = input size), plus bias and an optional
-// leaky ReLU (slope 0.1) whose derivative is read back from the output's sign.
+// Layout: activations and gradients NHWC BF16 with 32 channels ([n][y][x][c], 64 bytes per
+// pixel; channels beyond a layer's count are zero), FP32 accumulation in TMEM.  A layer is
+// a K x K convolution with dilation d and zero padding d (K - 1) / 2 (output size = input
+// size), plus bias and an optional leaky ReLU (slope 0.1).
 //
-// These are CUDA-core kernels: the network is tiny next to the solve, and a direct
-// convolution with the weights of one output-channel group staged in shared memory keeps
-// every tap in registers.
+// Convolutions are implicit GEMMs on the tcgen05 tensor cores:
+//   forward  out[p][co] = sum_t sum_ci W[t][co][ci] x[p + off_t][ci]: a CTA owns 128
+//            pixels of one image row (M = 128, TMEM lane = pixel) and all output channels
+//            (N = 16 or 32); for each of the K^2 taps one TMA box of the shifted input row
+//            (out-of-range pixels read as zero: the padding) and the tap's 32 x N weight
+//            tile land in shared memory and two MMAs (K = 16 channels each) accumulate;
+//   backward data is the same operation on the output gradient with the taps flipped and
+//            the channel roles swapped (mca_cnn_prep_weights builds both weight tiles), with
+//            the activation derivative of the layer below applied in the epilogue;
+//   weight gradient gW[t][co][ci] = sum_p gz[p][co] x[p + off_t][ci]: M = 4 taps x 32 input
+//            channels, N = 32 output channels, K = pixels; both operands come straight from
+//            the NHWC tensors as MN-major tiles (64 consecutive pixels of a row per stage),
+//            a CTA covers one group of 4 taps over a block of rows and writes FP32 partial
+//            sums that a second kernel adds in a fixed order.
+// Every mbarrier wait is bounded; an expired wait sets the module's error flag (read and
+// cleared by mca_cnn_check) and the CTA leaves after freeing its TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "mca_internal.cuh"
+#include "precond_tc.h"
+#include "tc_ptx.cuh"
 
 namespace mca {
 
 namespace {
 
-constexpr int kCoGroup = 8;    // output channels per thread in the forward pass
-constexpr int kMaxCin = 64;
+using namespace tc;
 
-__device__ __forceinline__ float act_fwd(float z, int act) {
-  return (act == 1) ? (z > 0.f ? z : 0.1f * z) : z;
-}
-__device__ __forceinline__ float act_grad(float y, int act) {
-  return (act == 1) ? (y > 0.f ? 1.f : 0.1f) : 1.f;
-}
+constexpr int kC = 32;                 // channels of every activation tensor (padded)
+constexpr int kPix = 128;              // pixels per forward tile (accumulator rows)
+constexpr int kWgPix = 64;             // pixels per weight-gradient stage (K)
+constexpr int kWgTaps = 4;             // taps per weight-gradient CTA (M = 4 x 32)
+constexpr int kWgRows = 16;            // image rows per weight-gradient CTA
+constexpr int kConvStages = 8;
+constexpr int kWgStages = 4;
+constexpr int kMaxK = 15;
 
-// y[n][co][p] = act(b[co] + sum_ci sum_k w[co][ci][k] x[n][ci][p + d*(k - 1)])
-__global__ void k_conv_fwd(const float* __restrict__ x, int N, int Cin, int H, int W,
-                           const __nv_bfloat16* __restrict__ wt, const float* __restrict__ bias,
-                           int Cout, int d, int act, float* __restrict__ y) {
-  __shared__ float ws[kCoGroup][kMaxCin * 9];
-  const int co0 = blockIdx.y * kCoGroup;
-  const int n = blockIdx.z;
-  for (int t = threadIdx.x; t < kCoGroup * Cin * 9; t += blockDim.x) {
-    const int g = t / (Cin * 9), r = t - g * (Cin * 9);
-    ws[g][r] = (co0 + g < Cout) ? __bfloat162float(wt[(size_t)(co0 + g) * Cin * 9 + r]) : 0.f;
+// module error flag (bounded waits that expired), read and cleared by mca_cnn_check
+__device__ int g_cnn_err;
+
+__device__ __forceinline__ float leaky(float z) { return z > 0.f ? z : 0.1f * z; }
+
+template <int COUT>
+struct ConvLayout {
+  static constexpr int A_BYTES = kPix * kC * 2;                       // 8 KB
+  static constexpr int B_BYTES = COUT * kC * 2;
+  static constexpr int STAGE = ((A_BYTES + B_BYTES + 1023) / 1024) * 1024;
+  static constexpr int BAR_OFF = kConvStages * STAGE;
+  static constexpr int SMEM = BAR_OFF + 256 + 1024;
+};
+
+struct ConvArgs {
+  int N, H, W;          // images, rows, columns
+  int K, d, r;          // kernel size, dilation, radius (K - 1) / 2
+  int cout;             // output channels written (the rest of the 32 are zero)
+  const float* bias;    // forward: per output channel (NULL: none)
+  int act;              // forward: leaky ReLU on the output; backward: times act'(yprev)
+  int backward;         // 0 forward, 1 backward data
+  const __nv_bfloat16* yprev;   // backward: NHWC32 output of the layer below (for act')
+  __nv_bfloat16* out;   // NHWC32 BF16 output (may be NULL)
+  float* out32;         // [N][H][W][cout] FP32 output (may be NULL)
+};
+
+template <int COUT>
+__global__ void __launch_bounds__(128, 2)
+k_conv_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+          ConvArgs a) {
+  using L = ConvLayout<COUT>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + kConvStages;
+  uint64_t* accum = empty + kConvStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x0 = blockIdx.x * kPix, y = blockIdx.y, n = blockIdx.z;
+  const int T = a.K * a.K;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kConvStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)), "r"(32u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
   __syncthreads();
-  const int HW = H * W;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= HW) return;
-  const int yy = p / W, xx = p - yy * W;
-  float acc[kCoGroup];
-#pragma unroll
-  for (int g = 0; g < kCoGroup; ++g) acc[g] = (co0 + g < Cout) ? bias[co0 + g] : 0.f;
-  const float* xn = x + (size_t)n * Cin * HW;
-  for (int ci = 0; ci < Cin; ++ci) {
-    const float* xc = xn + (size_t)ci * HW;
-    float v[9];
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky) {
-      const int sy = yy + d * (ky - 1);
-#pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        const int sx = xx + d * (kx - 1);
-        v[ky * 3 + kx] = (sy >= 0 && sy < H && sx >= 0 && sx < W) ? xc[sy * W + sx] : 0.f;
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // ---------------- TMA producer: per tap the shifted input row and the tap's weights
+    for (int t = 0; t < T; ++t) {
+      const int s = t % kConvStages;
+      const uint32_t ph = (uint32_t)(t / kConvStages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
+        break;
       }
+      uint8_t* st = smem + s * L::STAGE;
+      mbar_expect_tx(&full[s], (uint32_t)(L::A_BYTES + L::B_BYTES));
+      const int ky = t / a.K, kx = t - ky * a.K;
+      tma_load_4d(st, &tmX, 0, x0 + (kx - a.r) * a.d, y + (ky - a.r) * a.d, n, &full[s]);
+      tma_load_2d(st + L::A_BYTES, &tmW, 0, t * COUT, &full[s]);
     }
-#pragma unroll
-    for (int g = 0; g < kCoGroup; ++g) {
-      const float* wg = &ws[g][ci * 9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc[g] = fmaf(wg[k], v[k], acc[g]);
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < kCoGroup; ++g)
-    if (co0 + g < Cout) y[((size_t)n * Cout + co0 + g) * HW + p] = act_fwd(acc[g], act);
-}
-
-// gz = gy * act'(y), in place into gz (may alias gy).
-__global__ void k_act_back(const float* __restrict__ y, const float* gy, float* gz, size_t count,
-                           int act) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
-       e += (size_t)gridDim.x * blockDim.x)
-    gz[e] = gy[e] * act_grad(y[e], act);
-}
-
-// gx[n][ci][p] = sum_co sum_k w[co][ci][k] gz[n][co][p - d*(k - 1)]
-__global__ void k_conv_bwd_data(const float* __restrict__ gz, int N, int Cin, int H, int W,
-                                const __nv_bfloat16* __restrict__ wt, int Cout, int d,
-                                float* __restrict__ gx) {
-  __shared__ float ws[kCoGroup][kMaxCin * 9];   // here: [ci group][co * 9 + k]
-  const int ci0 = blockIdx.y * kCoGroup;
-  const int n = blockIdx.z;
-  for (int t = threadIdx.x; t < kCoGroup * Cout * 9; t += blockDim.x) {
-    const int g = t / (Cout * 9), r = t - g * (Cout * 9);
-    const int co = r / 9, k = r - co * 9;
-    ws[g][r] = (ci0 + g < Cin) ? __bfloat162float(wt[((size_t)co * Cin + ci0 + g) * 9 + k]) : 0.f;
-  }
-  __syncthreads();
-  const int HW = H * W;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= HW) return;
-  const int yy = p / W, xx = p - yy * W;
-  float acc[kCoGroup];
-#pragma unroll
-  for (int g = 0; g < kCoGroup; ++g) acc[g] = 0.f;
-  const float* gn = gz + (size_t)n * Cout * HW;
-  for (int co = 0; co < Cout; ++co) {
-    const float* gc = gn + (size_t)co * HW;
-    float v[9];
-#pragma unroll
-    for (int ky = 0; ky < 3; ++ky) {
-      const int sy = yy - d * (ky - 1);
-#pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        const int sx = xx - d * (kx - 1);
-        v[ky * 3 + kx] = (sy >= 0 && sy < H && sx >= 0 && sx < W) ? gc[sy * W + sx] : 0.f;
+  } else if (threadIdx.x == 32) {
+    // ---------------- MMA issuer: two K = 16 steps per tap
+    constexpr uint32_t idesc = idesc_bf16(kPix, COUT);
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+      const int s = t % kConvStages;
+      const uint32_t ph = (uint32_t)(t / kConvStages) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
+        ok = false;
+        break;
       }
-    }
+      tc_fence_after();
+      const uint8_t* st = smem + s * L::STAGE;
 #pragma unroll
-    for (int g = 0; g < kCoGroup; ++g) {
-      const float* wg = &ws[g][co * 9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc[g] = fmaf(wg[k], v[k], acc[g]);
+      for (int kk = 0; kk < 2; ++kk)
+        umma(tmem, sw64_desc(st + kk * 32), sw64_desc(st + L::A_BYTES + kk * 32), idesc,
+             (t > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty[s]);
     }
+    if (ok) umma_commit(accum);
   }
-#pragma unroll
-  for (int g = 0; g < kCoGroup; ++g)
-    if (ci0 + g < Cin) gx[((size_t)n * Cin + ci0 + g) * HW + p] = acc[g];
-}
+  __syncwarp();
 
-// Partial weight/bias gradients over a chunk of pixels of all images:
-//   part[chunk][co][ci][k] = sum_{n,p in chunk} gz[n][co][p] x[n][ci][p + d*(k - 1)]
-//   part_b[chunk][co]      = sum gz[n][co][p]
-// one block per (co, chunk), threads over pixels, fixed-order block reduction.
-__global__ void k_conv_bwd_weight(const float* __restrict__ x, const float* __restrict__ gz,
-                                  int N, int Cin, int H, int W, int Cout, int d, int chunk,
-                                  float* __restrict__ part, float* __restrict__ part_b) {
-  const int co = blockIdx.x;
-  const int ch = blockIdx.y;
-  const int HW = H * W;
-  const size_t total = (size_t)N * HW;
-  const size_t beg = (size_t)ch * chunk;
-  const size_t end = (beg + chunk < total) ? beg + chunk : total;
-  __shared__ float red[256 / 32];
-  for (int ci = 0; ci < Cin; ++ci) {
-    float acc[9];
+  // ---------------- epilogue: thread = TMEM lane = pixel x0 + 32 warp + lane
+  const bool have = __syncthreads_and(mbar_wait(accum, 0) ? 1 : 0) != 0;
+  if (!have && threadIdx.x == 0) atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
+  if (have) {
+    tc_fence_after();
+    const int x = x0 + warp * 32 + lane;
+    uint32_t v[32];
+    if (COUT == 32) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    } else {
+      uint32_t h[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), h);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
-    float accb = 0.f;
-    for (size_t q = beg + threadIdx.x; q < end; q += blockDim.x) {
-      const int n = (int)(q / HW);
-      const int p = (int)(q - (size_t)n * HW);
-      const int yy = p / W, xx = p - yy * W;
-      const float g = gz[((size_t)n * Cout + co) * HW + p];
-      if (ci == 0) accb += g;
-      const float* xc = x + ((size_t)n * Cin + ci) * HW;
+      for (int c = 0; c < 16; ++c) v[c] = h[c];
 #pragma unroll
-      for (int ky = 0; ky < 3; ++ky) {
-        const int sy = yy + d * (ky - 1);
+      for (int c = 16; c < 32; ++c) v[c] = 0u;
+    }
+    if (x < a.W) {
+      const size_t p = ((size_t)n * a.H + y) * a.W + x;
+      float o[32];
+      if (a.backward) {
+        uint4 yp[4] = {};
+        if (a.act && a.yprev) {
+          const uint4* src = reinterpret_cast<const uint4*>(a.yprev + p * kC);
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-          const int sx = xx + d * (kx - 1);
-          if (sy >= 0 && sy < H && sx >= 0 && sx < W) acc[ky * 3 + kx] = fmaf(g, xc[sy * W + sx], acc[ky * 3 + kx]);
+          for (int q = 0; q < 4; ++q) yp[q] = src[q];
+        }
+        const __nv_bfloat16* ypb = reinterpret_cast<const __nv_bfloat16*>(yp);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          float g = __uint_as_float(v[c]);
+          if (a.act && a.yprev) g *= (__bfloat162float(ypb[c]) > 0.f) ? 1.f : 0.1f;
+          o[c] = (c < a.cout) ? g : 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          float z = __uint_as_float(v[c]) + ((a.bias && c < a.cout) ? a.bias[c] : 0.f);
+          if (a.act) z = leaky(z);
+          o[c] = (c < a.cout) ? z : 0.f;
         }
       }
-    }
-    for (int k = 0; k < 10; ++k) {
-      float v = (k < 9) ? acc[k] : accb;
-      if (k == 9 && ci != 0) break;
+      if (a.out) {
+        uint4 pk[4];
+        uint32_t* w32 = reinterpret_cast<uint32_t*>(pk);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        if (k < 9)
-          part[(((size_t)ch * Cout + co) * Cin + ci) * 9 + k] = s;
-        else
-          part_b[(size_t)ch * Cout + co] = s;
+        for (int c = 0; c < 16; ++c) {
+          const __nv_bfloat162 b2 = __floats2bfloat162_rn(o[2 * c], o[2 * c + 1]);
+          w32[c] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(a.out + p * kC);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = pk[q];
       }
-      __syncthreads();
+      if (a.out32) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c < a.cout) a.out32[p * a.cout + c] = o[c];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u)
+                 : "memory");
+  }
+}
+
+// ---- weight gradient ------------------------------------------------------------------
+
+struct WgLayout {
+  static constexpr int A_TAP = kWgPix * kC * 2;                       // 4 KB per tap
+  static constexpr int A_BYTES = kWgTaps * A_TAP;
+  static constexpr int B_BYTES = kWgPix * kC * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;                     // 20 KB
+  static constexpr int BAR_OFF = kWgStages * STAGE;
+  static constexpr int SMEM = BAR_OFF + 256 + 1024;
+};
+
+struct WgArgs {
+  int N, H, W, K, d, r;
+  int rows_total;       // N * H
+  int nxc;              // 64-pixel chunks per row
+  float* part;          // [chunk][t][ci 32][co 32]
+};
+
+// CTA (group g of 4 taps, block of kWgRows image rows): D[(tap, ci)][co] accumulated over
+// the block's pixels; A tile of tap tl = 64 pixels x 32 channels of the shifted input row
+// (MN-major: the 32 channels of a pixel are one 64-byte row), B tile = the same pixels of
+// the output gradient.
+__global__ void __launch_bounds__(128, 2)
+k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmG,
+                WgArgs a) {
+  using L = WgLayout;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* empty = full + kWgStages;
+  uint64_t* accum = empty + kWgStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x, chunk = blockIdx.y;
+  const int T = a.K * a.K;
+  const int t0 = g * kWgTaps;
+  const int ntg = (T - t0 < kWgTaps) ? T - t0 : kWgTaps;
+  const int row0 = chunk * kWgRows;
+  const int nrows = (a.rows_total - row0 < kWgRows) ? a.rows_total - row0 : kWgRows;
+  const int nsteps = nrows * a.nxc;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kWgStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)), "r"(32u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    for (int it = 0; it < nsteps; ++it) {
+      const int s = it % kWgStages;
+      const uint32_t ph = (uint32_t)(it / kWgStages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
+        break;
+      }
+      uint8_t* st = smem + s * L::STAGE;
+      mbar_expect_tx(&full[s], (uint32_t)(ntg * L::A_TAP + L::B_BYTES));
+      const int row = row0 + it / a.nxc;
+      const int x0 = (it - (it / a.nxc) * a.nxc) * kWgPix;
+      const int n = row / a.H, y = row - n * a.H;
+      for (int tl = 0; tl < ntg; ++tl) {
+        const int t = t0 + tl, ky = t / a.K, kx = t - ky * a.K;
+        tma_load_4d(st + tl * L::A_TAP, &tmX, 0, x0 + (kx - a.r) * a.d, y + (ky - a.r) * a.d,
+                    n, &full[s]);
+      }
+      tma_load_4d(st + L::A_BYTES, &tmG, 0, x0, y, n, &full[s]);
+    }
+  } else if (threadIdx.x == 32) {
+    constexpr uint32_t idesc = idesc_bf16_mn(128, kC);
+    bool ok = true;
+    for (int it = 0; it < nsteps; ++it) {
+      const int s = it % kWgStages;
+      const uint32_t ph = (uint32_t)(it / kWgStages) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint8_t* st = smem + s * L::STAGE;
+      // K = 16 pixels per MMA: 16 rows of 64 bytes, two 8-row groups 512 bytes apart; the
+      // A atoms along M (one per tap) are L::A_TAP apart; B is a single atom along N, so its
+      // atom stride is never used (512 keeps every address inside the stage either way)
+#pragma unroll
+      for (int kk = 0; kk < kWgPix / 16; ++kk)
+        umma(tmem, sw64_mn_desc(st + kk * 1024, L::A_TAP, 512),
+             sw64_mn_desc(st + L::A_BYTES + kk * 1024, 512, 512), idesc,
+             (it > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    if (ok && nsteps > 0) umma_commit(accum);
+  }
+  __syncwarp();
+
+  const bool have = nsteps > 0 && __syncthreads_and(mbar_wait(accum, 0) ? 1 : 0) != 0;
+  if (nsteps > 0 && !have && threadIdx.x == 0) atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
+  if (have) {
+    tc_fence_after();
+    // thread = TMEM lane = (tap warp, input channel lane)
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    if (warp < ntg) {
+      float4* dst = reinterpret_cast<float4*>(
+          a.part + (((size_t)chunk * T + t0 + warp) * kC + lane) * kC);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                             __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32u)
+                 : "memory");
+  }
+}
+
+// gw[co][ci][t] = sum over chunks of part[chunk][t][ci][co] (fixed order), co < cout,
+// ci < cin: the master weight layout [cout][cin][K][K].
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nchunk, int T, int cin,
+                               int cout, float* __restrict__ gw) {
+  const size_t total = (size_t)T * cin * cout;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int co = (int)(e % cout);
+    const size_t r = e / cout;
+    const int ci = (int)(r % cin);
+    const int t = (int)(r / cin);
+    const size_t off = ((size_t)t * kC + ci) * kC + co;
+    float s = 0.f;
+    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * T * kC * kC + off];
+    gw[((size_t)co * cin + ci) * T + t] = s;
+  }
+}
+
+// Partial sums of the bias gradient gb[co] = sum_p gz[p][co]: block b sums its pixels.
+__global__ void k_bias_grad_part(const __nv_bfloat16* __restrict__ gz, size_t npix, int cout,
+                                 float* __restrict__ part) {
+  __shared__ float red[8][kC];
+  float acc[kC];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) acc[c] = 0.f;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const uint4* src = reinterpret_cast<const uint4*>(gz + p * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 u = src[q];
+      const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[q * 8 + c] += __bfloat162float(b[c]);
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < kC; ++c) {
+    float v = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[w][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kC) {
+    float s = 0.f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
+    part[(size_t)blockIdx.x * kC + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_bias_grad_finish(const float* __restrict__ part, int nb, int cout,
+                                   float* __restrict__ gb) {
+  const int c = threadIdx.x;
+  if (c < cout) {
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += part[(size_t)b * kC + c];
+    gb[c] = s;
+  }
+}
+
+// BF16 operand tiles from the FP32 master weights w[co][ci][K][K]:
+//   wf[t][co][ci] (forward, co padded to cout_mma rows, ci to 32),
+//   wb[t][ci][co] = w[co][ci][T - 1 - t] (backward data: flipped taps, 32 x 32).
+__global__ void k_prep_weights(const float* __restrict__ w, int cout, int cin, int T,
+                               int cout_mma, __nv_bfloat16* __restrict__ wf,
+                               __nv_bfloat16* __restrict__ wb) {
+  const size_t nf = (size_t)T * cout_mma * kC, nb = (size_t)T * kC * kC;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nf + nb;
+       e += (size_t)gridDim.x * blockDim.x) {
+    if (e < nf) {
+      const int ci = (int)(e % kC);
+      const int co = (int)((e / kC) % cout_mma);
+      const int t = (int)(e / ((size_t)kC * cout_mma));
+      const float v = (co < cout && ci < cin) ? w[((size_t)co * cin + ci) * T + t] : 0.f;
+      if (wf) wf[e] = __float2bfloat16_rn(v);
+    } else {
+      const size_t f = e - nf;
+      const int co = (int)(f % kC);
+      const int ci = (int)((f / kC) % kC);
+      const int t = (int)(f / ((size_t)kC * kC));
+      const float v = (co < cout && ci < cin) ? w[((size_t)co * cin + ci) * T + (T - 1 - t)] : 0.f;
+      if (wb) wb[f] = __float2bfloat16_rn(v);
     }
   }
 }
 
-// gw[i] = sum over chunks of part[chunk][i] (fixed order).
-__global__ void k_sum_chunks(const float* __restrict__ part, int nchunk, size_t count,
-                             float* __restrict__ out) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
-       i += (size_t)gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * count + i];
-    out[i] = s;
+// Network input, NHWC32 BF16: channel 0 = log10(g) + 5 (log-uniform [1e-6, 1e-4] S maps to
+// [-1, 1]), 1 = V_in[i] / vscale along row i, 2 = V_lin,t / vscale, 3 = V_lin,b * bscale /
+// vscale, the rest zero.  Vector b uses map map_index[b] (NULL: map 0).
+__global__ void k_features(const double* __restrict__ gmaps, const int* __restrict__ map_index,
+                           const double* __restrict__ vin, const double* __restrict__ vlt,
+                           const double* __restrict__ vlb, int m, int n, float vscale,
+                           float bscale, __nv_bfloat16* __restrict__ x) {
+  const int b = blockIdx.y;
+  const size_t mn = (size_t)m * n;
+  const double* g = gmaps + (map_index ? (size_t)map_index[b] : 0) * mn;
+  const double* lt = vlt + (size_t)b * mn;
+  const double* lb = vlb + (size_t)b * mn;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < mn;
+       c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c / n);
+    float f[kC] = {};
+    f[0] = (float)(log10(g[c]) + 5.0);
+    f[1] = (float)(vin[(size_t)b * m + i] / vscale);
+    f[2] = (float)(lt[c] / vscale);
+    f[3] = (float)(lb[c] * bscale / vscale);
+    uint4 pk[4];
+    uint32_t* w32 = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+      w32[q] = *reinterpret_cast<const uint32_t*>(&b2);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)b * mn + c) * kC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = pk[q];
   }
 }
 
-// Mean squared error and its gradient: loss_part[block] partial sums, gp = 2 (p - t) / count.
-__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ tgt, size_t count,
-                      float* __restrict__ gp, float* __restrict__ loss_part) {
+// target[p][0..1] = (V* - V_lin) * (dscale_t, dscale_b) per node (FP32); the voltages of
+// each layer are [nvec][m*n] arrays
+__global__ void k_target(const double* __restrict__ st, const double* __restrict__ sb,
+                         const double* __restrict__ lt, const double* __restrict__ lb, int mn,
+                         float dst_t, float dst_b, float* __restrict__ target) {
+  const size_t o0 = (size_t)blockIdx.y * mn;
+  float* o = target + 2 * o0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < mn; c += gridDim.x * blockDim.x) {
+    o[2 * c] = (float)((st[o0 + c] - lt[o0 + c]) * dst_t);
+    o[2 * c + 1] = (float)((sb[o0 + c] - lb[o0 + c]) * dst_b);
+  }
+}
+
+// guess = V_lin + pred / dscale as an FP64 state [V_t ; V_b] (pred NULL: V_lin itself)
+__global__ void k_guess(const float* __restrict__ pred, const double* __restrict__ lt,
+                        const double* __restrict__ lb, int mn, float dst_t, float dst_b,
+                        double* __restrict__ guess) {
+  const size_t o0 = (size_t)blockIdx.y * mn;
+  const float* p = pred ? pred + 2 * o0 : nullptr;
+  double* o = guess + 2 * o0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < mn; c += gridDim.x * blockDim.x) {
+    o[c] = lt[o0 + c] + (p ? (double)p[2 * c] / dst_t : 0.0);
+    o[mn + c] = lb[o0 + c] + (p ? (double)p[2 * c + 1] / dst_b : 0.0);
+  }
+}
+
+// Mean squared error over npix pixels x 2 channels and its gradient gz = 2 (p - t) / count
+// as NHWC32 BF16 (channels 2..31 zero); loss_part[block] partial sums.
+__global__ void k_loss(const float* __restrict__ pred, const float* __restrict__ tgt, size_t npix,
+                       __nv_bfloat16* __restrict__ gz, float* __restrict__ loss_part) {
   float s = 0.f;
-  const float sc = 2.0f / (float)count;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const float r = pred[e] - tgt[e];
-    s = fmaf(r, r, s);
-    if (gp) gp[e] = sc * r;
+  const float sc = 2.0f / (float)(2 * npix);
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < npix;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const float r0 = pred[2 * p] - tgt[2 * p], r1 = pred[2 * p + 1] - tgt[2 * p + 1];
+    s = fmaf(r0, r0, fmaf(r1, r1, s));
+    if (gz) {
+      uint4 pk[4] = {};
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(sc * r0, sc * r1);
+      pk[0].x = *reinterpret_cast<const uint32_t*>(&b2);
+      uint4* dst = reinterpret_cast<uint4*>(gz + p * kC);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = pk[q];
+    }
   }
   __shared__ float red[8];
 #pragma unroll
@@ -219,8 +533,8 @@ __global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ 
   }
 }
 
-__global__ void k_mse_finish(const float* __restrict__ part, int nb, size_t count,
-                             float* __restrict__ loss) {
+__global__ void k_loss_finish(const float* __restrict__ part, int nb, size_t count,
+                              float* __restrict__ loss) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += part[b];
@@ -228,9 +542,8 @@ __global__ void k_mse_finish(const float* __restrict__ part, int nb, size_t coun
   }
 }
 
-// Adam on the FP32 master weights, then the BF16 copy used by the convolutions.
-__global__ void k_adam(float* __restrict__ w, __nv_bfloat16* __restrict__ wb,
-                       const float* __restrict__ g, float* __restrict__ m1,
+// Adam on the FP32 master weights (Kingma & Ba, bias-corrected).
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m1,
                        float* __restrict__ m2, size_t count, float lr, float b1, float b2,
                        float eps, float bc1, float bc2) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
@@ -240,53 +553,7 @@ __global__ void k_adam(float* __restrict__ w, __nv_bfloat16* __restrict__ wb,
     const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
     m1[i] = a;
     m2[i] = b;
-    const float upd = (a / bc1) / (sqrtf(b / bc2) + eps);
-    const float nw = w[i] - lr * upd;
-    w[i] = nw;
-    if (wb) wb[i] = __float2bfloat16(nw);
-  }
-}
-
-// Network input of one crossbar and input vector: channel 0 = log10(g) + 5 (log-uniform
-// [1e-6, 1e-4] S maps to [-1, 1]), channel 1 = V_in[i] / vscale along row i, and with
-// four channels the node position j/(n-1), i/(m-1).
-__global__ void k_features(const double* __restrict__ gmap, const double* __restrict__ vin,
-                           int m, int n, float vscale, int nchan, float* __restrict__ x) {
-  const int b = blockIdx.y;
-  const int mn = m * n;
-  float* xb = x + (size_t)b * nchan * mn;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < mn; c += gridDim.x * blockDim.x) {
-    const int i = c / n, j = c - i * n;
-    xb[c] = (float)(log10(gmap[c]) + 5.0);
-    xb[mn + c] = (float)(vin[(size_t)b * m + i] / vscale);
-    if (nchan == 4) {
-      xb[2 * mn + c] = (n > 1) ? (float)j / (float)(n - 1) : 0.f;
-      xb[3 * mn + c] = (m > 1) ? (float)i / (float)(m - 1) : 0.f;
-    }
-  }
-}
-
-// Network output (2 channels) to an FP64 solver state [V_t ; V_b] (scales undone).
-__global__ void k_to_state(const float* __restrict__ y, int mn, float vscale, float bscale,
-                           double* __restrict__ x) {
-  const int b = blockIdx.y;
-  const float* yb = y + (size_t)b * 2 * mn;
-  double* xs = x + (size_t)b * 2 * mn;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < mn; c += gridDim.x * blockDim.x) {
-    xs[c] = (double)yb[c] * vscale;
-    xs[mn + c] = (double)yb[mn + c] * (vscale / bscale);
-  }
-}
-
-// FP64 solver state to the network's 2-channel target (training data).
-__global__ void k_from_state(const double* __restrict__ x, int mn, float vscale, float bscale,
-                             float* __restrict__ y) {
-  const int b = blockIdx.y;
-  const double* xs = x + (size_t)b * 2 * mn;
-  float* yb = y + (size_t)b * 2 * mn;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < mn; c += gridDim.x * blockDim.x) {
-    yb[c] = (float)(xs[c] / vscale);
-    yb[mn + c] = (float)(xs[mn + c] * bscale / vscale);
+    w[i] -= lr * ((a / bc1) / (sqrtf(b / bc2) + eps));
   }
 }
 
@@ -294,6 +561,38 @@ int grid1d(size_t count, int th) {
   size_t nb = (count + th - 1) / th;
   if (nb > 4096) nb = 4096;
   return nb < 1 ? 1 : (int)nb;
+}
+
+std::once_flag g_cfg_once;
+cudaError_t g_cfg_err = cudaSuccess;
+
+cudaError_t configure() {
+  std::call_once(g_cfg_once, [] {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ConvLayout<32>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               ConvLayout<16>::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               WgLayout::SMEM);
+    g_cfg_err = e;
+  });
+  return g_cfg_err;
+}
+
+int launch_status(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, what, __FILE__, __LINE__);
+    return MCA_ERR_CUDA;
+  }
+  return MCA_OK;
+}
+
+bool shape_ok(int n, int h, int w, int k, int d) {
+  return n >= 1 && h >= 1 && w >= 1 && k >= 1 && k <= kMaxK && (k & 1) && d >= 1 &&
+         (size_t)n * h * w < (1ull << 31) && (size_t)h * w * kC * 2 < (1ull << 40);
 }
 
 }  // namespace
@@ -304,102 +603,207 @@ using namespace mca;
 
 extern "C" {
 
-int mca_cnn_conv_forward(const float* x, int32_t n, int32_t cin, int32_t h, int32_t w,
-                         const uint16_t* wt, const float* bias, int32_t cout, int32_t dilation,
-                         int32_t act, float* y, void* stream) {
-  if (!x || !wt || !bias || !y || n < 1 || cin < 1 || cin > kMaxCin || cout < 1 || h < 1 ||
-      w < 1 || dilation < 1 || (act != 0 && act != 1))
+int mca_cnn_conv(const uint16_t* x, int32_t n, int32_t h, int32_t w, const uint16_t* wt,
+                 int32_t ksize, int32_t dilation, int32_t cout_mma, int32_t cout,
+                 const float* bias, int32_t act, int32_t backward, const uint16_t* y_prev,
+                 uint16_t* out, float* out32, void* stream) {
+  clear_error_message();
+  if (!x || !wt || !shape_ok(n, h, w, ksize, dilation) || (cout_mma != 16 && cout_mma != 32) ||
+      cout < 1 || cout > cout_mma || (!out && !out32) || (backward && cout_mma != 32)) {
+    set_error_message("mca_cnn_conv: bad arguments");
     return MCA_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int th = 128;
-  dim3 grid((h * w + th - 1) / th, (cout + kCoGroup - 1) / kCoGroup, n);
-  k_conv_fwd<<<grid, th, 0, s>>>(x, n, cin, h, w, reinterpret_cast<const __nv_bfloat16*>(wt),
-                                 bias, cout, dilation, act, y);
-  count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
-}
-
-int mca_cnn_conv_backward(const float* x, const float* y, const float* gy, int32_t n,
-                          int32_t cin, int32_t h, int32_t w, const uint16_t* wt, int32_t cout,
-                          int32_t dilation, int32_t act, float* gz_scratch, float* gx,
-                          float* gw, float* gb, float* part, int32_t nchunk, void* stream) {
-  if (!x || !y || !gy || !wt || !gz_scratch || !gw || !gb || !part || n < 1 || cin < 1 ||
-      cin > kMaxCin || cout < 1 || cout > kMaxCin || h < 1 || w < 1 || dilation < 1 ||
-      nchunk < 1)
-    return MCA_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t ycount = (size_t)n * cout * h * w;
-  k_act_back<<<grid1d(ycount, 256), 256, 0, s>>>(y, gy, gz_scratch, ycount, act);
-  count_launches(1);
-  const int th = 128;
-  if (gx) {
-    dim3 grid((h * w + th - 1) / th, (cin + kCoGroup - 1) / kCoGroup, n);
-    k_conv_bwd_data<<<grid, th, 0, s>>>(gz_scratch, n, cin, h, w,
-                                        reinterpret_cast<const __nv_bfloat16*>(wt), cout,
-                                        dilation, gx);
-    count_launches(1);
   }
-  const size_t total = (size_t)n * h * w;
-  const int chunk = (int)((total + nchunk - 1) / nchunk);
-  float* part_b = part + (size_t)nchunk * cout * cin * 9;
-  k_conv_bwd_weight<<<dim3(cout, nchunk), 256, 0, s>>>(x, gz_scratch, n, cin, h, w, cout,
-                                                       dilation, chunk, part, part_b);
-  const size_t wcount = (size_t)cout * cin * 9;
-  k_sum_chunks<<<grid1d(wcount, 256), 256, 0, s>>>(part, nchunk, wcount, gw);
-  k_sum_chunks<<<grid1d(cout, 256), 256, 0, s>>>(part_b, nchunk, cout, gb);
-  count_launches(4);
-  return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
+  if (cudaError_t e = configure(); e != cudaSuccess) {
+    set_last_cuda_error(e, "mca_cnn_conv configure", __FILE__, __LINE__);
+    return MCA_ERR_CUDA;
+  }
+  CUtensorMap tmX, tmW;
+  if (!tc::make_map_nhwc32(&tmX, x, w, h, n, kPix) ||
+      !tc::make_map(&tmW, wt, (uint64_t)ksize * ksize * cout_mma, kC, cout_mma, kC)) {
+    set_error_message("mca_cnn_conv: tensor map encoding failed");
+    return MCA_ERR_UNSUPPORTED;
+  }
+  ConvArgs a{};
+  a.N = n; a.H = h; a.W = w; a.K = ksize; a.d = dilation; a.r = (ksize - 1) / 2;
+  a.cout = cout; a.bias = bias; a.act = act; a.backward = backward;
+  a.yprev = reinterpret_cast<const __nv_bfloat16*>(y_prev);
+  a.out = reinterpret_cast<__nv_bfloat16*>(out);
+  a.out32 = out32;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dim3 grid((w + kPix - 1) / kPix, h, n);
+  if (cout_mma == 32)
+    k_conv_tc<32><<<grid, 128, ConvLayout<32>::SMEM, s>>>(tmX, tmW, a);
+  else
+    k_conv_tc<16><<<grid, 128, ConvLayout<16>::SMEM, s>>>(tmX, tmW, a);
+  count_launches(1);
+  return launch_status("mca_cnn_conv launch");
 }
 
-int mca_cnn_mse(const float* pred, const float* target, int64_t count, float* gpred,
-                float* part, float* loss, void* stream) {
-  if (!pred || !target || !part || !loss || count < 1) return MCA_ERR_INVALID_ARG;
+int64_t mca_cnn_wgrad_scratch(int32_t n, int32_t h, int32_t w, int32_t ksize) {
+  if (!shape_ok(n, h, w, ksize, 1)) return -1;
+  const int64_t nchunk = ((int64_t)n * h + kWgRows - 1) / kWgRows;
+  const int64_t nbias = grid1d((size_t)n * h * w, 256);
+  return nchunk * ksize * ksize * kC * kC + nbias * kC;
+}
+
+int mca_cnn_conv_wgrad(const uint16_t* x, const uint16_t* gz, int32_t n, int32_t h, int32_t w,
+                       int32_t ksize, int32_t dilation, int32_t cin, int32_t cout,
+                       float* scratch, float* gw, float* gb, void* stream) {
+  clear_error_message();
+  if (!x || !gz || !scratch || !gw || !shape_ok(n, h, w, ksize, dilation) || cin < 1 ||
+      cin > kC || cout < 1 || cout > kC) {
+    set_error_message("mca_cnn_conv_wgrad: bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  if (cudaError_t e = configure(); e != cudaSuccess) {
+    set_last_cuda_error(e, "mca_cnn_conv_wgrad configure", __FILE__, __LINE__);
+    return MCA_ERR_CUDA;
+  }
+  CUtensorMap tmX, tmG;
+  if (!tc::make_map_nhwc32(&tmX, x, w, h, n, kWgPix) ||
+      !tc::make_map_nhwc32(&tmG, gz, w, h, n, kWgPix)) {
+    set_error_message("mca_cnn_conv_wgrad: tensor map encoding failed");
+    return MCA_ERR_UNSUPPORTED;
+  }
+  const int T = ksize * ksize;
+  WgArgs a{};
+  a.N = n; a.H = h; a.W = w; a.K = ksize; a.d = dilation; a.r = (ksize - 1) / 2;
+  a.rows_total = n * h;
+  a.nxc = (w + kWgPix - 1) / kWgPix;
+  a.part = scratch;
+  const int nchunk = (a.rows_total + kWgRows - 1) / kWgRows;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dim3 grid((T + kWgTaps - 1) / kWgTaps, nchunk);
+  k_conv_wgrad_tc<<<grid, 128, WgLayout::SMEM, s>>>(tmX, tmG, a);
+  k_wgrad_reduce<<<grid1d((size_t)T * cin * cout, 256), 256, 0, s>>>(scratch, nchunk, T, cin,
+                                                                      cout, gw);
+  count_launches(2);
+  if (gb) {
+    const size_t npix = (size_t)n * h * w;
+    const int nb = grid1d(npix, 256);
+    float* pb = scratch + (size_t)nchunk * T * kC * kC;
+    k_bias_grad_part<<<nb, 256, 0, s>>>(reinterpret_cast<const __nv_bfloat16*>(gz), npix, cout, pb);
+    k_bias_grad_finish<<<1, 32, 0, s>>>(pb, nb, cout, gb);
+    count_launches(2);
+  }
+  return launch_status("mca_cnn_conv_wgrad launch");
+}
+
+int mca_cnn_prep_weights(const float* w, int32_t cout, int32_t cin, int32_t ksize,
+                         int32_t cout_mma, uint16_t* wf, uint16_t* wb, void* stream) {
+  clear_error_message();
+  if (!w || (!wf && !wb) || cout < 1 || cout > cout_mma || (cout_mma != 16 && cout_mma != 32) ||
+      cin < 1 || cin > kC || ksize < 1 || ksize > kMaxK || !(ksize & 1)) {
+    set_error_message("mca_cnn_prep_weights: bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  const int T = ksize * ksize;
+  const size_t count = (size_t)T * cout_mma * kC + (size_t)T * kC * kC;
+  k_prep_weights<<<grid1d(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      w, cout, cin, T, cout_mma, reinterpret_cast<__nv_bfloat16*>(wf),
+      reinterpret_cast<__nv_bfloat16*>(wb));
+  count_launches(1);
+  return launch_status("mca_cnn_prep_weights launch");
+}
+
+int mca_cnn_features(const double* gmaps, const int32_t* map_index, const double* v_in,
+                     const double* vlin_t, const double* vlin_b, int32_t nvec, int32_t m,
+                     int32_t n, float vscale, float bscale, uint16_t* x, void* stream) {
+  clear_error_message();
+  if (!gmaps || !v_in || !vlin_t || !vlin_b || !x || nvec < 1 || m < 1 || n < 1 ||
+      !(vscale > 0.f) ||
+      !(bscale > 0.f)) {
+    set_error_message("mca_cnn_features: bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  k_features<<<dim3(grid1d((size_t)m * n, 256), nvec), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      gmaps, map_index, v_in, vlin_t, vlin_b, m, n, vscale, bscale,
+      reinterpret_cast<__nv_bfloat16*>(x));
+  count_launches(1);
+  return launch_status("mca_cnn_features launch");
+}
+
+int mca_cnn_target(const double* vstar_t, const double* vstar_b, const double* vlin_t,
+                   const double* vlin_b, int32_t nvec, int32_t m, int32_t n, float dscale_t,
+                   float dscale_b, float* target, void* stream) {
+  clear_error_message();
+  if (!vstar_t || !vstar_b || !vlin_t || !vlin_b || !target || nvec < 1 || m < 1 || n < 1 ||
+      !(dscale_t > 0.f) ||
+      !(dscale_b > 0.f)) {
+    set_error_message("mca_cnn_target: bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  k_target<<<dim3(grid1d((size_t)m * n, 256), nvec), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      vstar_t, vstar_b, vlin_t, vlin_b, m * n, dscale_t, dscale_b, target);
+  count_launches(1);
+  return launch_status("mca_cnn_target launch");
+}
+
+int mca_cnn_guess(const float* pred, const double* vlin_t, const double* vlin_b, int32_t nvec,
+                  int32_t m, int32_t n, float dscale_t, float dscale_b, double* guess,
+                  void* stream) {
+  clear_error_message();
+  if (!vlin_t || !vlin_b || !guess || nvec < 1 || m < 1 || n < 1 || !(dscale_t > 0.f) ||
+      !(dscale_b > 0.f)) {
+    set_error_message("mca_cnn_guess: bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  k_guess<<<dim3(grid1d((size_t)m * n, 256), nvec), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      pred, vlin_t, vlin_b, m * n, dscale_t, dscale_b, guess);
+  count_launches(1);
+  return launch_status("mca_cnn_guess launch");
+}
+
+int mca_cnn_loss(const float* pred, const float* target, int64_t npix, uint16_t* gz,
+                 float* part, float* loss, void* stream) {
+  clear_error_message();
+  if (!pred || !target || !part || !loss || npix < 1) {
+    set_error_message("mca_cnn_loss: bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = 256;
-  k_mse<<<nb, 256, 0, s>>>(pred, target, (size_t)count, gpred, part);
-  k_mse_finish<<<1, 32, 0, s>>>(part, nb, (size_t)count, loss);
+  k_loss<<<nb, 256, 0, s>>>(pred, target, (size_t)npix, reinterpret_cast<__nv_bfloat16*>(gz),
+                            part);
+  k_loss_finish<<<1, 32, 0, s>>>(part, nb, (size_t)npix * 2, loss);
   count_launches(2);
-  return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
+  return launch_status("mca_cnn_loss launch");
 }
 
-int mca_cnn_adam(float* w, uint16_t* w_bf16, const float* g, float* m1, float* m2, int64_t count,
-                 float lr, float beta1, float beta2, float eps, int32_t step, void* stream) {
-  if (!w || !g || !m1 || !m2 || count < 1 || step < 1) return MCA_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const float bc1 = 1.f - powf(beta1, (float)step), bc2 = 1.f - powf(beta2, (float)step);
-  k_adam<<<grid1d((size_t)count, 256), 256, 0, s>>>(w, reinterpret_cast<__nv_bfloat16*>(w_bf16),
-                                                    g, m1, m2, (size_t)count, lr, beta1, beta2,
-                                                    eps, bc1, bc2);
-  count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
-}
-
-int mca_cnn_features(const double* gmap, const double* vin, int32_t nvec, int32_t m, int32_t n,
-                     float vscale, int32_t nchan, float* x, void* stream) {
-  if (!gmap || !vin || !x || nvec < 1 || m < 1 || n < 1 || !(vscale > 0.f) ||
-      (nchan != 2 && nchan != 4))
+int mca_cnn_adam(float* w, const float* g, float* m1, float* m2, int64_t count, float lr,
+                 float beta1, float beta2, float eps, int32_t step, void* stream) {
+  clear_error_message();
+  if (!w || !g || !m1 || !m2 || count < 1 || step < 1) {
+    set_error_message("mca_cnn_adam: bad arguments");
     return MCA_ERR_INVALID_ARG;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_features<<<dim3(grid1d((size_t)m * n, 256), nvec), 256, 0, s>>>(gmap, vin, m, n, vscale,
-                                                                      nchan, x);
+  }
+  const float bc1 = 1.f - powf(beta1, (float)step), bc2 = 1.f - powf(beta2, (float)step);
+  k_adam<<<grid1d((size_t)count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      w, g, m1, m2, (size_t)count, lr, beta1, beta2, eps, bc1, bc2);
   count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
+  return launch_status("mca_cnn_adam launch");
 }
 
-int mca_cnn_state(const float* y, double* x, int32_t nvec, int32_t m, int32_t n, float vscale,
-                  float bscale, int32_t to_state, float* y_out, void* stream) {
-  if (nvec < 1 || m < 1 || n < 1 || !(vscale > 0.f) || !(bscale > 0.f)) return MCA_ERR_INVALID_ARG;
+int mca_cnn_check(void* stream) {
+  clear_error_message();
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  dim3 grid(grid1d((size_t)m * n, 256), nvec);
-  if (to_state) {
-    if (!y || !x) return MCA_ERR_INVALID_ARG;
-    k_to_state<<<grid, 256, 0, s>>>(y, m * n, vscale, bscale, x);
-  } else {
-    if (!x || !y_out) return MCA_ERR_INVALID_ARG;
-    k_from_state<<<grid, 256, 0, s>>>(x, m * n, vscale, bscale, y_out);
+  int e = 0;
+  const int zero = 0;
+  cudaError_t ce = cudaMemcpyFromSymbolAsync(&e, g_cnn_err, sizeof(int), 0,
+                                             cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess && e != 0)
+    ce = cudaMemcpyToSymbolAsync(g_cnn_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    set_last_cuda_error(ce, "mca_cnn_check", __FILE__, __LINE__);
+    return MCA_ERR_CUDA;
   }
-  count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? MCA_OK : MCA_ERR_CUDA;
+  if (e != 0) {
+    set_error_message("a bounded wait of a network kernel expired");
+    return e;
+  }
+  return MCA_OK;
 }
 
 }  // extern "C"

@@ -405,7 +405,8 @@ __device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j,
   size2 = fmaf(szt, szt, fmaf(szb, szb, size2));
 }
 
-__global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl* ctl) {
+__global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl* ctl,
+                                int warm) {
   const int b = blockIdx.x;
   double s = 0.0;
   for (int i = threadIdx.x; i < gr.m; i += blockDim.x) {
@@ -418,7 +419,9 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
     VecCtl& c = ctl[b];
     const double yn = gr.g_src * sqrt(s);
     c.ynorm = yn;
-    c.fnorm = 0.0;
+    // a warm start treats V = 0, with ||F(0)|| = ||Y||, as its previous iterate, so its first
+    // forcing term follows Eisenstat-Walker instead of the cold start's eta0
+    c.fnorm = warm ? yn : 0.0;
     c.fnorm_prev = 0.0;
     c.a = 0.0;
     c.eta = 0.0;
@@ -539,7 +542,7 @@ __device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const So
     c.newton_active = 0;
   } else {
     double eta;
-    if (c.newton_iters == 0 || c.fnorm_prev <= 0.0) {
+    if (c.fnorm_prev <= 0.0) {
       eta = cfg.eta0;
     } else {
       const double r = fn / c.fnorm_prev;
@@ -924,9 +927,9 @@ int residual_nblk(int mn, int B) {
   return nb < 1 ? 1 : nb;
 }
 
-void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
+void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl, bool warm,
                           cudaStream_t s) {
-  k_setup_vectors<<<B, kThreads, 0, s>>>(gr, vin, ctl);
+  k_setup_vectors<<<B, kThreads, 0, s>>>(gr, vin, ctl, warm ? 1 : 0);
 }
 
 void launch_residual(const Grid& gr, const double* gmap, const double* vin, const double* x,

@@ -774,7 +774,7 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
   const bool tc = is_tc(h->p.precision);
   const size_t vstride = (size_t)(h->restart + 1) * h->n2;
   const size_t zstride = (size_t)h->restart * h->n2;
-  launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
+  launch_setup_vectors(h->gr, h->vin, B, h->ctl, from_guess, s);
   count_launches(1);
   if (!from_guess)
     MCA_CUDA_TRY(cudaMemsetAsync(h->x, 0, (size_t)B * h->n2 * sizeof(double), s));
@@ -1033,13 +1033,15 @@ int mca_solve(mca_handle* h, const double* v_in, int32_t nvec, double* v_top, do
 }
 
 static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
-                      const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
-                      double* i_out, mca_stats* stats, void* stream);
+                      const double* fallback, const int32_t* map_index, int32_t nvec,
+                      double* v_top, double* v_bot, double* i_out, mca_stats* stats,
+                      void* stream);
 
 int mca_solve_multi(mca_handle* h, const double* v_in, const int32_t* map_index, int32_t nvec,
                     double* v_top, double* v_bot, double* i_out, mca_stats* stats,
                     void* stream) {
-  return solve_impl(h, v_in, nullptr, map_index, nvec, v_top, v_bot, i_out, stats, stream);
+  return solve_impl(h, v_in, nullptr, nullptr, map_index, nvec, v_top, v_bot, i_out, stats,
+                    stream);
 }
 
 int mca_set_conductances(mca_handle* h, const double* g_maps) {
@@ -1066,22 +1068,25 @@ int mca_set_conductances(mca_handle* h, const double* g_maps) {
 }
 
 int mca_solve_from(mca_handle* h, const double* v_in, const double* guess,
-                   const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
-                   double* i_out, mca_stats* stats, void* stream) {
+                   const double* fallback, const int32_t* map_index, int32_t nvec,
+                   double* v_top, double* v_bot, double* i_out, mca_stats* stats, void* stream) {
   if (!guess) {
     set_error("NULL guess");
     return MCA_ERR_INVALID_ARG;
   }
-  return solve_impl(h, v_in, guess, map_index, nvec, v_top, v_bot, i_out, stats, stream);
+  return solve_impl(h, v_in, guess, fallback, map_index, nvec, v_top, v_bot, i_out, stats,
+                    stream);
 }
 
 static int solve_passes(mca_handle* h, const double* v_in, const double* guess,
+                        const double* fallback,
                         const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
                         double* i_out, mca_stats* stats, cudaStream_t s);
 
 static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
-                      const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
-                      double* i_out, mca_stats* stats, void* stream) {
+                      const double* fallback, const int32_t* map_index, int32_t nvec,
+                      double* v_top, double* v_bot, double* i_out, mca_stats* stats,
+                      void* stream) {
   g_last_error.clear();
   if (!h || !v_in || nvec < 0) {
     set_error("NULL handle/input or negative nvec");
@@ -1096,7 +1101,8 @@ static int solve_impl(mca_handle* h, const double* v_in, const double* guess,
     }
   }
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
-  int rc = solve_passes(h, v_in, guess, map_index, nvec, v_top, v_bot, i_out, stats, s);
+  int rc = solve_passes(h, v_in, guess, fallback, map_index, nvec, v_top, v_bot, i_out, stats,
+                        s);
   // the outputs of every pass are in place when the call returns
   for (int q = 0; q < 2; ++q) {
     if (!h->copy_pending[q]) continue;
@@ -1128,8 +1134,9 @@ static int stage_inputs(mca_handle* h, const double* v_in, const int32_t* map_in
 }
 
 static int solve_passes(mca_handle* h, const double* v_in, const double* guess,
-                        const int32_t* map_index, int32_t nvec, double* v_top, double* v_bot,
-                        double* i_out, mca_stats* stats, cudaStream_t s) {
+                        const double* fallback, const int32_t* map_index, int32_t nvec,
+                        double* v_top, double* v_bot, double* i_out, mca_stats* stats,
+                        cudaStream_t s) {
   const size_t m = h->m, n = h->n, mn = h->mn;
   (void)m;
   int worst = MCA_OK;
@@ -1145,27 +1152,47 @@ static int solve_passes(mca_handle* h, const double* v_in, const double* guess,
     h->map_of = h->mapbuf[q];
     std::vector<int> fell(B, 0);
     if (guess) {
-      // judge the guess: keep it only if its residual is finite and below ||F(0)|| = ||Y||
-      MCA_CUDA_TRY(cudaMemcpyAsync(h->x, guess + (size_t)v0 * h->n2,
-                                   (size_t)B * h->n2 * sizeof(double), cudaMemcpyDefault, s));
+      // judge the guess: keep it only if its residual is finite and below that of the
+      // fallback state (||F(0)|| = ||Y|| when there is none)
       const int nb = residual_nblk((int)h->mn, B);
-      launch_setup_vectors(h->gr, h->vin, B, h->ctl, s);
-      count_launches(1);
-      // residual of the guess (map-aware through the Newton kernel with max_newton = 0)
       SolverCfg probe = make_cfg(h);
       probe.max_newton = 0;
       probe.newton_rtol = 0.0;
-      launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
-                             false, h->F, h->n2, nullptr, 0, 0, h->D, h->part, nb, B, h->ctl,
-                             probe, h->cnt, nullptr, s);
-      count_launches(1);
-      MCA_TRY(read_report(h, B, nullptr, nullptr, s));
+      // ||F|| of the states now in h->x (map-aware through the Newton kernel with
+      // max_newton = 0), into fn[b]
+      auto probe_norms = [&](std::vector<double>& fn) -> int {
+        launch_setup_vectors(h->gr, h->vin, B, h->ctl, false, s);
+        count_launches(1);
+        launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
+                               false, h->F, h->n2, nullptr, 0, 0, h->D, h->part, nb, B, h->ctl,
+                               probe, h->cnt, nullptr, s);
+        count_launches(1);
+        MCA_TRY(read_report(h, B, nullptr, nullptr, s));
+        for (int b = 0; b < B; ++b)
+          fn[b] = (h->ctl_host[b].ynorm > 0.0) ? h->ctl_host[b].fnorm : 0.0;
+        return MCA_OK;
+      };
+      std::vector<double> fref(B), fg(B);
+      if (fallback) {
+        MCA_CUDA_TRY(cudaMemcpyAsync(h->x, fallback + (size_t)v0 * h->n2,
+                                     (size_t)B * h->n2 * sizeof(double), cudaMemcpyDefault, s));
+        MCA_TRY(probe_norms(fref));
+      }
+      MCA_CUDA_TRY(cudaMemcpyAsync(h->x, guess + (size_t)v0 * h->n2,
+                                   (size_t)B * h->n2 * sizeof(double), cudaMemcpyDefault, s));
+      MCA_TRY(probe_norms(fg));
       for (int b = 0; b < B; ++b) {
-        const VecCtl& c = h->ctl_host[b];
-        const bool ok = std::isfinite(c.fnorm) && c.fnorm < c.ynorm;
-        if (!ok && c.ynorm > 0.0) {
+        const double yn = h->ctl_host[b].ynorm;
+        const double ref = fallback ? fref[b] : yn;
+        const bool ok = std::isfinite(fg[b]) && fg[b] < ref;
+        if (!ok && yn > 0.0) {
           fell[b] = 1;
-          MCA_CUDA_TRY(cudaMemsetAsync(h->x + (size_t)b * h->n2, 0, h->n2 * sizeof(double), s));
+          double* xb = h->x + (size_t)b * h->n2;
+          if (fallback)
+            MCA_CUDA_TRY(cudaMemcpyAsync(xb, fallback + (size_t)(v0 + b) * h->n2,
+                                         h->n2 * sizeof(double), cudaMemcpyDefault, s));
+          else
+            MCA_CUDA_TRY(cudaMemsetAsync(xb, 0, h->n2 * sizeof(double), s));
         }
       }
     }

@@ -168,7 +168,9 @@ __device__ __forceinline__ bool warp_scatter_writer(int lane) {
 
 // ---------------------------------------------------------------- kernels (launchers)
 // stencil / residual / Jacobian (k_stencil.cu)
-void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl,
+// warm: the states are a caller's guess (the first forcing term then follows
+// Eisenstat-Walker with ||F(0)|| = ||Y|| as the previous residual)
+void launch_setup_vectors(const Grid& gr, const double* vin, int B, VecCtl* ctl, bool warm,
                           cudaStream_t s);
 // pair: the residual in FP32 pairs (requires gr.tail32), which also leaves the squared
 // term sizes' partial sums in part row 2; pair_err_bound turns their total into the bound

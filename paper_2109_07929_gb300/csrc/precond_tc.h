@@ -43,6 +43,10 @@ bool encode_available();
 // box_k: 64 (single-word GEMMs) or 32 (split GEMMs)
 bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
               uint32_t box_rows, uint32_t box_k);
+// 4-D map over an NHWC BF16 tensor with 32 channels, box = box_px pixels of one row
+// (64-byte swizzle; out-of-range elements read zero)
+bool make_map_nhwc32(CUtensorMap* map, const void* base, uint64_t W, uint64_t H, uint64_t N,
+                     uint32_t box_px);
 cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
