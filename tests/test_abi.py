@@ -50,3 +50,31 @@ def test_default_params_and_errors_without_gpu():
     rc = lib.mca_create(ctypes.byref(p), g.ctypes.data, ctypes.byref(h))
     assert rc == mca.ERR_INVALID_ARG
     assert lib.mca_solve(None, None, 0, None, None, None, None, None) == mca.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value", [
+    ("rows", 16385), ("cols", 0), ("g_wire_top", 0.0), ("g_sense", float("inf")),
+    ("b", -1.0), ("b", float("nan")), ("device_model", 9), ("precision", 99),
+    ("gmres_restart", 0), ("gmres_restart", 31), ("max_batch", 0), ("max_batch", 65),
+    ("max_newton", 0), ("flags", 0x100), ("newton_rtol", 0.0), ("eta0", -1.0)])
+def test_create_rejects_each_invalid_parameter_before_device_work(field, value):
+    """mca_create validates every parameter on the host and returns MCA_ERR_INVALID_ARG
+    with a message, before touching the device (so this runs without a GPU)."""
+    import numpy as np
+    lib = mca.load()
+    p = mca.default_params(4, 5)
+    setattr(p, field, value)
+    h = ctypes.c_void_p()
+    g = np.ones(20)
+    assert lib.mca_create(ctypes.byref(p), g.ctypes.data, ctypes.byref(h)) == mca.ERR_INVALID_ARG
+    assert not h.value
+    assert lib.mca_last_error_message().decode() != ""
+
+
+def test_yakopcic_needs_a_positive_ratio():
+    import numpy as np
+    lib = mca.load()
+    p = mca.default_params(3, 3, device_model=mca.DEVICE_YAKOPCIC, neg_ratio=0.0)
+    h = ctypes.c_void_p()
+    g = np.ones(9)
+    assert lib.mca_create(ctypes.byref(p), g.ctypes.data, ctypes.byref(h)) == mca.ERR_INVALID_ARG

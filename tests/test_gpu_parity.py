@@ -651,6 +651,50 @@ def test_zero_input_and_status_codes():
     assert e.value.code == mca.ERR_INVALID_ARG
 
 
+def test_empty_call_and_batch_and_restart_limits():
+    """nvec = 0 is a no-op; a full batch of 64 vectors (max_batch's limit) and the restart
+    limits GMRES(1) and GMRES(30) all reach the tolerance on the oracle's residual."""
+    cb = mi.make_crossbar(24, 40, 13, nvec=64)
+    p = cb.params
+    with mca.Solver(_params(p, max_batch=64, newton_rtol=1e-9), cb.gmap) as s:
+        vt, vb, io, st = s.solve(np.zeros((0, 24)))
+        assert vt.shape == (0, 24, 40) and st == []
+        vt, vb, io, st = s.solve(cb.vin)
+    for v in range(64):
+        assert st[v]["status"] == 0
+        Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], vt[v].ravel(), vb[v].ravel())
+        Yt, _ = O.source_vector(p, cb.vin[v])
+        assert np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt) <= 1.01e-9
+    for restart in (1, 30):
+        for prec in (mca.PREC_FP64, mca.PREC_BF16_SPLIT):
+            with mca.Solver(_params(p, max_batch=2, newton_rtol=1e-9, gmres_restart=restart,
+                                    precision=prec), cb.gmap) as s:
+                vt, vb, io, st = s.solve(cb.vin[:2])
+            for v in range(2):
+                assert st[v]["status"] == 0, (restart, prec, st[v])
+                Ft, Fb = O.residual(p, cb.gmap, cb.vin[v], vt[v].ravel(), vb[v].ravel())
+                Yt, _ = O.source_vector(p, cb.vin[v])
+                rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
+                assert rel <= 1.01e-9, (restart, prec, rel)
+
+
+def test_large_rectangular_4096x2048_residual():
+    """4096 x 2048 (16.8M unknowns, rectangular, the largest case here): BF16-split
+    preconditioner to 1e-8; the oracle recomputes the FP64 KCL residual and the balance."""
+    cb = mi.make_crossbar(4096, 2048, 7, g_wire_bot=0.5)
+    p = cb.params
+    with mca.Solver(_params(p, precision=mca.PREC_BF16_SPLIT, newton_rtol=1e-8, max_batch=1),
+                    cb.gmap) as s:
+        vt, vb, io, st = s.solve(cb.vin)
+    assert st[0]["status"] == 0 and st[0]["gmres_iters"] <= 20
+    Ft, Fb = O.residual(p, cb.gmap, cb.vin[0], vt[0].ravel(), vb[0].ravel())
+    Yt, _ = O.source_vector(p, cb.vin[0])
+    rel = np.linalg.norm(np.concatenate([Ft, Fb])) / np.linalg.norm(Yt)
+    assert rel <= 1e-8 * 1.01
+    assert abs(O.kcl_balance(p, cb.vin[0], vt[0], vb[0])) <= 1e-6 * O.outputs(
+        p, cb.vin[0], vt[0], vb[0])["i_in"].sum()
+
+
 def test_full_size_1024_sampled():
     """1024x1024 (2.1M unknowns), log-uniform g, wires 1 S / 0.5 S, BF16 split
     preconditioner, Newton to 1e-8: the oracle recomputes the FP64 residual of the
