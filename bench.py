@@ -551,6 +551,12 @@ def run_ours(args):
                      "GB/s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else 0.0,
                      "TFLOP/s": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
                  for f, v in prof.items() if v["launches"] > 0}
+    # both ceilings of every CUDA-core family: algorithmic bytes against the measured HBM
+    # copy rate, algorithmic FP64 flops against the FP64 pipe (152 SMs x 2 DFMA/clk x 2.07 GHz)
+    for f, b in breakdown.items():
+        if not f.startswith("precond"):
+            b["hbm_frac"] = b["GB/s"] / peaks["hbm_gbs"]
+            b["fp64_frac"] = b["TFLOP/s"] / FP64_PEAK_TFLOPS
     # precond TFLOP/s in the dense eigenbasis count, 8 m n (m + n) per apply
     pc_ms = sum(prof[f]["ms"] for f in ("precond_1", "precond_2", "precond_3", "precond_4"))
     applies = prof["precond_1"]["flops"] / (4.0 * m * n * n) if prof["precond_1"]["flops"] else 0

@@ -13,9 +13,11 @@
 // Convolutions are implicit GEMMs on the tcgen05 tensor cores:
 //   forward  out[p][co] = sum_t sum_ci W[t][co][ci] x[p + off_t][ci]: a CTA owns 128
 //            pixels of one image row (M = 128, TMEM lane = pixel) and all output channels
-//            (N = 16 or 32); for each of the K^2 taps one TMA box of the shifted input row
-//            (out-of-range pixels read as zero: the padding) and the tap's 32 x N weight
-//            tile land in shared memory and two MMAs (K = 16 channels each) accumulate;
+//            (N = 16 or 32); per kernel row ky one pipeline stage holds the shifted input
+//            row segment (128 + (K - 1) d pixels, out-of-range pixels read as zero: the
+//            padding) in the K-major layout without swizzle, whose 16-byte pixel rows let
+//            the K taps of that row start at any pixel offset of the same segment, plus the
+//            row's K weight tiles; two MMAs (K = 16 channels each) per tap accumulate;
 //   backward data is the same operation on the output gradient with the taps flipped and
 //            the channel roles swapped (mca_cnn_prep_weights builds both weight tiles), with
 //            the activation derivative of the layer below applied in the epilogue;
@@ -48,7 +50,6 @@ constexpr int kPix = 128;              // pixels per forward tile (accumulator r
 constexpr int kWgPix = 64;             // pixels per weight-gradient stage (K)
 constexpr int kWgTaps = 4;             // taps per weight-gradient CTA (M = 4 x 32)
 constexpr int kWgRows = 16;            // image rows per weight-gradient CTA
-constexpr int kConvStages = 8;
 constexpr int kWgStages = 4;
 constexpr int kMaxK = 15;
 
@@ -57,14 +58,43 @@ __device__ int g_cnn_err;
 
 __device__ __forceinline__ float leaky(float z) { return z > 0.f ? z : 0.1f * z; }
 
-template <int COUT>
-struct ConvLayout {
-  static constexpr int A_BYTES = kPix * kC * 2;                       // 8 KB
-  static constexpr int B_BYTES = COUT * kC * 2;
-  static constexpr int STAGE = ((A_BYTES + B_BYTES + 1023) / 1024) * 1024;
-  static constexpr int BAR_OFF = kConvStages * STAGE;
-  static constexpr int SMEM = BAR_OFF + 256 + 1024;
+// Pipeline plan of one convolution (host-computed): a stage is one kernel row ky, holding
+// the input row segment as 4 chunks of 8 channels (each nbox TMA boxes of wbox 16-byte
+// pixel rows, lbo bytes per chunk) and the row's K weight tiles.
+struct ConvPlan {
+  int wbox, nbox, lbo;
+  int wrows, nwbox;     // weight rows per TMA box, boxes per kernel row (K COUT rows)
+  int a_bytes, b_bytes, stage, stages;
+  int smem;             // dynamic shared memory: the stages, a guard tail, barriers
 };
+
+constexpr int kConvBarBytes = 512;
+
+template <int COUT>
+ConvPlan conv_plan(int K, int d) {
+  ConvPlan p{};
+  const int wseg = kPix + (K - 1) * d;
+  p.nbox = (wseg + 255) / 256;
+  p.wbox = ((wseg + p.nbox - 1) / p.nbox + 7) / 8 * 8;
+  p.lbo = p.nbox * p.wbox * 16;
+  p.a_bytes = (4 * p.lbo + 1023) / 1024 * 1024;
+  // the K weight tiles of a kernel row are consecutive rows of the weight tensor: one or
+  // two boxes (at most 256 rows each, whole 8-row swizzle atoms)
+  p.nwbox = (K * COUT + 255) / 256;
+  p.wrows = ((K * COUT + p.nwbox - 1) / p.nwbox + 7) / 8 * 8;
+  p.b_bytes = (p.nwbox * p.wrows * kC * 2 + 1023) / 1024 * 1024;
+  p.stage = p.a_bytes + p.b_bytes;
+  // the furthest byte an A descriptor can reach from its stage, also if the hardware took
+  // the two strides the other way round (16 row groups lbo apart): every such address stays
+  // inside the allocation
+  const int reach = 18 * p.lbo + (K - 1) * d * 16 + 256;
+  const int tail = reach > p.stage ? reach - p.stage : 0;
+  int st = (220 * 1024 - tail - kConvBarBytes - 1024) / p.stage;
+  if (st > K) st = K;
+  p.stages = st;
+  p.smem = st * p.stage + tail + kConvBarBytes + 1024;
+  return p;
+}
 
 struct ConvArgs {
   int N, H, W;          // images, rows, columns
@@ -76,26 +106,27 @@ struct ConvArgs {
   const __nv_bfloat16* yprev;   // backward: NHWC32 output of the layer below (for act')
   __nv_bfloat16* out;   // NHWC32 BF16 output (may be NULL)
   float* out32;         // [N][H][W][cout] FP32 output (may be NULL)
+  ConvPlan plan;
 };
 
 template <int COUT>
-__global__ void __launch_bounds__(128, 2)
+__global__ void __launch_bounds__(128, 1)
 k_conv_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
           ConvArgs a) {
-  using L = ConvLayout<COUT>;
+  const ConvPlan& P = a.plan;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
-  uint64_t* empty = full + kConvStages;
-  uint64_t* accum = empty + kConvStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + P.smem - kConvBarBytes - 1024);
+  uint64_t* empty = full + P.stages;
+  uint64_t* accum = empty + P.stages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int x0 = blockIdx.x * kPix, y = blockIdx.y, n = blockIdx.z;
-  const int T = a.K * a.K;
+  const int S = P.stages;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kConvStages; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -114,38 +145,50 @@ k_conv_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUten
   const uint32_t tmem = *tmem_slot;
 
   if (threadIdx.x == 0) {
-    // ---------------- TMA producer: per tap the shifted input row and the tap's weights
-    for (int t = 0; t < T; ++t) {
-      const int s = t % kConvStages;
-      const uint32_t ph = (uint32_t)(t / kConvStages) & 1u;
+    // ---------------- TMA producer: per kernel row, the input row segment (4 chunks of 8
+    // channels) and the row's K weight tiles
+    const uint32_t bytes = (uint32_t)(4 * P.nbox * P.wbox * 16 + P.nwbox * P.wrows * kC * 2);
+    const int xs = x0 - a.r * a.d;
+    for (int ky = 0; ky < a.K; ++ky) {
+      const int s = ky % S;
+      const uint32_t ph = (uint32_t)(ky / S) & 1u;
       if (!mbar_wait(&empty[s], ph ^ 1u)) {
         atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
         break;
       }
-      uint8_t* st = smem + s * L::STAGE;
-      mbar_expect_tx(&full[s], (uint32_t)(L::A_BYTES + L::B_BYTES));
-      const int ky = t / a.K, kx = t - ky * a.K;
-      tma_load_4d(st, &tmX, 0, x0 + (kx - a.r) * a.d, y + (ky - a.r) * a.d, n, &full[s]);
-      tma_load_2d(st + L::A_BYTES, &tmW, 0, t * COUT, &full[s]);
+      uint8_t* st = smem + s * P.stage;
+      mbar_expect_tx(&full[s], bytes);
+      const int yy = y + (ky - a.r) * a.d;
+      for (int kc = 0; kc < 4; ++kc)
+        for (int bx = 0; bx < P.nbox; ++bx)
+          tma_load_4d(st + kc * P.lbo + bx * P.wbox * 16, &tmX, kc * 8, xs + bx * P.wbox, yy,
+                      n, &full[s]);
+      for (int bw = 0; bw < P.nwbox; ++bw)
+        tma_load_2d(st + P.a_bytes + bw * P.wrows * kC * 2, &tmW, 0,
+                    ky * a.K * COUT + bw * P.wrows, &full[s]);
     }
   } else if (threadIdx.x == 32) {
-    // ---------------- MMA issuer: two K = 16 steps per tap
+    // ---------------- MMA issuer: per tap (ky, kx) the window starting kx d pixels into
+    // the row segment, two K = 16 steps (channel chunks 0-1 and 2-3)
     constexpr uint32_t idesc = idesc_bf16(kPix, COUT);
     bool ok = true;
-    for (int t = 0; t < T; ++t) {
-      const int s = t % kConvStages;
-      const uint32_t ph = (uint32_t)(t / kConvStages) & 1u;
+    for (int ky = 0; ky < a.K; ++ky) {
+      const int s = ky % S;
+      const uint32_t ph = (uint32_t)(ky / S) & 1u;
       if (!mbar_wait(&full[s], ph)) {
         atomicCAS(&g_cnn_err, 0, MCA_ERR_TIMEOUT);
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint8_t* st = smem + s * L::STAGE;
+      const uint8_t* st = smem + s * P.stage;
+      for (int kx = 0; kx < a.K; ++kx) {
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk)
-        umma(tmem, sw64_desc(st + kk * 32), sw64_desc(st + L::A_BYTES + kk * 32), idesc,
-             (t > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 2; ++kk)
+          umma(tmem, kmajor_noswz_desc(st + kx * a.d * 16 + kk * 2 * P.lbo, P.lbo, 128),
+               sw64_desc(st + P.a_bytes + kx * COUT * kC * 2 + kk * 32), idesc,
+               (ky > 0 || kx > 0 || kk > 0) ? 1u : 0u);
+      }
       umma_commit(&empty[s]);
     }
     if (ok) umma_commit(accum);
@@ -569,10 +612,10 @@ cudaError_t g_cfg_err = cudaSuccess;
 cudaError_t configure() {
   std::call_once(g_cfg_once, [] {
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         ConvLayout<32>::SMEM);
+                                         227 * 1024);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               ConvLayout<16>::SMEM);
+                               227 * 1024);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                WgLayout::SMEM);
@@ -617,13 +660,20 @@ int mca_cnn_conv(const uint16_t* x, int32_t n, int32_t h, int32_t w, const uint1
     set_last_cuda_error(e, "mca_cnn_conv configure", __FILE__, __LINE__);
     return MCA_ERR_CUDA;
   }
+  const ConvPlan plan = (cout_mma == 32) ? conv_plan<32>(ksize, dilation)
+                                         : conv_plan<16>(ksize, dilation);
+  if (plan.stages < 2 || plan.smem > 227 * 1024) {
+    set_error_message("mca_cnn_conv: kernel size and dilation too large for one row segment");
+    return MCA_ERR_INVALID_ARG;
+  }
   CUtensorMap tmX, tmW;
-  if (!tc::make_map_nhwc32(&tmX, x, w, h, n, kPix) ||
-      !tc::make_map(&tmW, wt, (uint64_t)ksize * ksize * cout_mma, kC, cout_mma, kC)) {
+  if (!tc::make_map_nhwc32_k8(&tmX, x, w, h, n, plan.wbox) ||
+      !tc::make_map(&tmW, wt, (uint64_t)ksize * ksize * cout_mma, kC, plan.wrows, kC)) {
     set_error_message("mca_cnn_conv: tensor map encoding failed");
     return MCA_ERR_UNSUPPORTED;
   }
   ConvArgs a{};
+  a.plan = plan;
   a.N = n; a.H = h; a.W = w; a.K = ksize; a.d = dilation; a.r = (ksize - 1) / 2;
   a.cout = cout; a.bias = bias; a.act = act; a.backward = backward;
   a.yprev = reinterpret_cast<const __nv_bfloat16*>(y_prev);
@@ -632,9 +682,9 @@ int mca_cnn_conv(const uint16_t* x, int32_t n, int32_t h, int32_t w, const uint1
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   dim3 grid((w + kPix - 1) / kPix, h, n);
   if (cout_mma == 32)
-    k_conv_tc<32><<<grid, 128, ConvLayout<32>::SMEM, s>>>(tmX, tmW, a);
+    k_conv_tc<32><<<grid, 128, plan.smem, s>>>(tmX, tmW, a);
   else
-    k_conv_tc<16><<<grid, 128, ConvLayout<16>::SMEM, s>>>(tmX, tmW, a);
+    k_conv_tc<16><<<grid, 128, plan.smem, s>>>(tmX, tmW, a);
   count_launches(1);
   return launch_status("mca_cnn_conv launch");
 }

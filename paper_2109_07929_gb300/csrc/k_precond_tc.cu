@@ -767,6 +767,20 @@ bool make_map_nhwc32(CUtensorMap* map, const void* base, uint64_t W, uint64_t H,
   return r == CUDA_SUCCESS;
 }
 
+bool make_map_nhwc32_k8(CUtensorMap* map, const void* base, uint64_t W, uint64_t H, uint64_t N,
+                        uint32_t box_px) {
+  if (!encode_available() || box_px < 1 || box_px > 256) return false;
+  cuuint64_t gdim[4] = {32, W, H, N};
+  cuuint64_t gstride[3] = {64, 64 * W, 64 * W * H};
+  cuuint32_t box[4] = {8, box_px, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base),
+                               gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s) {

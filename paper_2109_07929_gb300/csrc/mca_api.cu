@@ -793,12 +793,12 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
                            zero_state, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np,
                            h->D, h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s, pair);
     count_launches(1);
-    // FP64 flops per cell: stencils 8, sinh polynomial 16, current 4, norms 5 (the
-    // conductance cosh is FP32; the zero state only the norms); the pair form: its two
-    // final additions and the norms
+    // FP64 flops per cell (an FMA counts 2): the FP64 cell 15 in 10 instructions (device
+    // voltage, current, two stencil rows; ||F||^2 and the conductance cosh are FP32); the
+    // pair form 6 (its two final additions and the FP64 norm); the zero state none
     prof_end(h, t0, MCA_FAM_RESIDUAL, -1,
-             cells * ((zero_state ? 32.0 : 48.0) + (tc ? 4.0 : 0.0)),
-             cells * (zero_state ? 5.0 : (pair ? 6.0 : 33.0)), s);
+             cells * ((zero_state ? 36.0 : 48.0) + (tc ? 4.0 : 0.0)),
+             cells * (zero_state ? 0.0 : (pair ? 6.0 : 15.0)), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
     const int entering = n_active;
@@ -812,7 +812,7 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
                              h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s, false,
                              true);
       count_launches(1);
-      prof_end(h, t0, MCA_FAM_RESIDUAL, -2, cells * (48.0 + 4.0), cells * 33.0, s);
+      prof_end(h, t0, MCA_FAM_RESIDUAL, -2, cells * (48.0 + 4.0), cells * 15.0, s);
       MCA_CUDA_TRY(cudaGetLastError());
       MCA_CUDA_TRY(cudaStreamSynchronize(s));
     }

@@ -47,6 +47,10 @@ bool make_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
 // (64-byte swizzle; out-of-range elements read zero)
 bool make_map_nhwc32(CUtensorMap* map, const void* base, uint64_t W, uint64_t H, uint64_t N,
                      uint32_t box_px);
+// The same tensor with a box of 8 channels x box_px pixels and no swizzle: each box lands as
+// box_px consecutive 16-byte rows (one K chunk of a K-major operand without swizzling)
+bool make_map_nhwc32_k8(CUtensorMap* map, const void* base, uint64_t W, uint64_t H, uint64_t N,
+                        uint32_t box_px);
 cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);

@@ -125,6 +125,22 @@ __device__ __forceinline__ uint64_t sw64_mn_desc(const void* p, uint32_t lbo, ui
   return d;
 }
 
+// Descriptor of a K-major operand without swizzling: core matrices of 8 rows x 16 bytes
+// (8 BF16 along K) stored as 8 consecutive 16-byte rows; lbo: bytes between the core
+// matrices that follow each other along K; sbo: bytes between consecutive 8-row groups
+// along M (N).  Rows are 16 bytes apart, so a start address shifted by any whole number of
+// rows selects a shifted window of the same tile.
+__device__ __forceinline__ uint64_t kmajor_noswz_desc(const void* p, uint32_t lbo,
+                                                      uint32_t sbo) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                    // descriptor version; layout 0: no swizzle
+  return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulate, BF16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
