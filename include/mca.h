@@ -174,6 +174,49 @@ int mca_solve_many(mca_handle* const* hs, int32_t nh, const double* const* v_in,
                    double* const* v_top, double* const* v_bot, double* const* i_out,
                    mca_stats* const* stats, int32_t n_threads);
 
+/* ---- persistent batched solve: one launch for many independent solves ---------------
+ * A batch object binds handles of several shapes (each MCA_PREC_BF16_SPLIT, all on one
+ * device, all with the same device model) to one persistent kernel: every CTA runs the
+ * whole Newton / flexible-GMRES solve of one (crossbar, input vector) item (eqs. (F), (J),
+ * (Newton3), the preconditioner of eq. (P) in the Kronecker eigenbasis of Section 3.2 on
+ * the tensor cores) and then takes the next item from a device-side queue, largest items
+ * first, until the batch is done.  Each handle's own settings (wires, b, newton_rtol, eta0,
+ * eta_max, max_newton, restart) apply to its items; every Newton residual is the FP64 one.
+ * The batch owns one scratch slot per CTA sized for the largest shape and restart:
+ * about 8 * 2mn * (2 * restart + 4) bytes each, 2 CTAs per SM by default. */
+typedef struct mca_batch mca_batch;
+
+typedef struct mca_item {
+  int32_t handle;            /* index into the handles given to mca_batch_create          */
+  int32_t map;               /* conductance map of that handle (0..n_maps-1)              */
+  const double* v_in;        /* device: m input voltages                                  */
+  double* v_top;             /* device: m*n top-layer voltages out, or NULL               */
+  double* v_bot;             /* device: m*n bottom-layer voltages out, or NULL            */
+  double* i_out;             /* device: n sensed column currents out, or NULL             */
+} mca_item;
+
+/* Create a batch over nh handles (the handles must outlive it; their conductance maps are
+ * read at solve time).  max_ctas: CTAs (= scratch slots) of a launch, 0 for 2 per SM.
+ * Returns MCA_ERR_INVALID_ARG, MCA_ERR_UNSUPPORTED (a handle not in MCA_PREC_BF16_SPLIT),
+ * MCA_ERR_OOM or MCA_ERR_CUDA. */
+int mca_batch_create(mca_handle* const* hs, int32_t nh, int32_t max_ctas, mca_batch** out);
+
+/* Solve n items in one kernel launch.  items (host array) point at device buffers; stats
+ * (host, n entries, or NULL) in item order.  The call returns after the results are
+ * written.  Returns MCA_OK when every item met its newton_rtol, else the first failing
+ * status (outputs still written), MCA_ERR_INVALID_ARG for an index out of range or a NULL
+ * v_in, MCA_ERR_TIMEOUT when a bounded device wait gave up, MCA_ERR_OOM, MCA_ERR_CUDA. */
+int mca_batch_solve(mca_batch* b, const mca_item* items, int32_t n, mca_stats* stats,
+                    void* stream);
+
+/* The persistent kernel's preconditioner alone (for testing): for each item, v_top / v_bot
+ * (device, m*n each) hold r on entry and z = P^-1 r on return, with a1 = a2 = a[k] (host,
+ * n entries) in eq. (P); v_in and i_out are ignored. */
+int mca_batch_precond(mca_batch* b, const mca_item* items, const double* a, int32_t n,
+                      void* stream);
+
+void mca_batch_destroy(mca_batch* b);
+
 /* Reprogram the crossbars of a handle: replace its n_maps conductance maps (host or
  * device, n_maps*m*n, every entry finite and > 0) without redoing the eigen setup,
  * which depends only on the wires and terminations. */

@@ -50,7 +50,8 @@ EXPORTED = (
     "mca_solve_many", "mca_solve_from", "mca_cnn_conv", "mca_cnn_wgrad_scratch",
     "mca_cnn_conv_wgrad", "mca_cnn_prep_weights", "mca_cnn_features", "mca_cnn_target",
     "mca_cnn_guess", "mca_cnn_loss", "mca_cnn_adam", "mca_cnn_check", "mca_set_conductances",
-    "mca_wait_selftest", "mca_tile_config",
+    "mca_wait_selftest", "mca_tile_config", "mca_batch_create", "mca_batch_solve",
+    "mca_batch_precond", "mca_batch_destroy",
 )
 
 FAMILIES = ("residual", "spmv_dots", "reorth", "update_norm", "normalize", "small",
@@ -79,6 +80,13 @@ class Stats(ctypes.Structure):
         ("gmres_iters", ctypes.c_int32), ("fallback", ctypes.c_int32),
         ("rel_residual", ctypes.c_double), ("kcl_rel_error", ctypes.c_double),
     ]
+
+
+class Item(ctypes.Structure):
+    """One work item of a persistent batched solve (mca_item)."""
+    _fields_ = [("handle", ctypes.c_int32), ("map", ctypes.c_int32),
+                ("v_in", ctypes.c_void_p), ("v_top", ctypes.c_void_p),
+                ("v_bot", ctypes.c_void_p), ("i_out", ctypes.c_void_p)]
 
 
 class MCAError(RuntimeError):
@@ -155,6 +163,13 @@ def load(build_if_missing=True):
     for name in ("mca_solve_from", "mca_cnn_conv", "mca_cnn_conv_wgrad", "mca_cnn_prep_weights",
                  "mca_cnn_features", "mca_cnn_target", "mca_cnn_guess", "mca_cnn_loss",
                  "mca_cnn_adam", "mca_cnn_check"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.mca_batch_create.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.mca_batch_solve.argtypes = [P, P, ctypes.c_int32, P, P]
+    lib.mca_batch_precond.argtypes = [P, P, P, ctypes.c_int32, P]
+    lib.mca_batch_destroy.argtypes = [P]
+    lib.mca_batch_destroy.restype = None
+    for name in ("mca_batch_create", "mca_batch_solve", "mca_batch_precond"):
         getattr(lib, name).restype = ctypes.c_int
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
@@ -237,6 +252,69 @@ def solve_many(solvers, vins, map_indices=None, n_threads=4, outs=None):
                       fallback=x.fallback) for x in o[3]]
         res.append((o[0], o[1], o[2], stats))
     return res
+
+
+class Batch:
+    """Persistent batched solve over several Solver objects (shapes): one kernel launch
+    solves every (solver, map, input vector) item, one item per CTA at a time."""
+
+    def __init__(self, solvers, max_ctas=0):
+        self.lib = load()
+        self.solvers = list(solvers)
+        H = (ctypes.c_void_p * len(self.solvers))(*[x.h.value for x in self.solvers])
+        b = ctypes.c_void_p()
+        _check(self.lib.mca_batch_create(H, len(self.solvers), max_ctas, ctypes.byref(b)))
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mca_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @staticmethod
+    def items(handles, maps, vins, v_tops=None, v_bots=None, i_outs=None):
+        """An Item array from per-item handle and map indices and device tensors (rows of
+        2-D tensors or separate tensors; None entries give NULL)."""
+        n = len(handles)
+        arr = (Item * n)()
+        for k in range(n):
+            arr[k].handle = int(handles[k])
+            arr[k].map = int(maps[k])
+            arr[k].v_in = _ptr(vins[k])
+            arr[k].v_top = _ptr(v_tops[k]) if v_tops is not None else None
+            arr[k].v_bot = _ptr(v_bots[k]) if v_bots is not None else None
+            arr[k].i_out = _ptr(i_outs[k]) if i_outs is not None else None
+        return arr
+
+    def solve_items(self, items, stream=None, allow_not_converged=False):
+        """Solve an Item array; returns the per-item stats dicts."""
+        n = len(items)
+        st = (Stats * n)()
+        rc = self.lib.mca_batch_solve(self.b, ctypes.cast(items, ctypes.c_void_p), n,
+                                      ctypes.cast(st, ctypes.c_void_p), _stream_ptr(stream))
+        _check(rc, (ERR_NOT_CONVERGED, ERR_NONFINITE) if allow_not_converged else ())
+        return [dict(status=x.status, newton_iters=x.newton_iters, gmres_iters=x.gmres_iters,
+                     rel_residual=x.rel_residual, kcl_rel_error=x.kcl_rel_error,
+                     fallback=x.fallback) for x in st]
+
+    def precond(self, items, a, stream=None):
+        """z = P^-1 r in place on each item's (v_top, v_bot) with a1 = a2 = a[k]."""
+        n = len(items)
+        av = np.ascontiguousarray(a, np.float64)
+        _check(self.lib.mca_batch_precond(self.b, ctypes.cast(items, ctypes.c_void_p),
+                                          av.ctypes.data, n, _stream_ptr(stream)))
 
 
 def residual_noalloc(params, gmap, x, vin, F, D, fnorm=None, dmean=None, stream=None):

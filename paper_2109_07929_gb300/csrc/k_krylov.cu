@@ -18,14 +18,13 @@
 // hence deterministic.
 #include "bits.cuh"
 #include "mca_internal.cuh"
+#include "solver_dev.cuh"
 
 namespace mca {
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr double kEps = 1.1102230246251565e-16;   // 2^-53, unit roundoff of FP64
-constexpr double kOrthTol = 1e-8;                 // largest accepted loss of orthogonality
 
 template <int KP>
 __device__ __forceinline__ void block_store_partials(double (&acc)[KP], int nk,
@@ -68,48 +67,6 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
     s = warp_sum(s);
     if (l == 0) h[(size_t)b * 32 + j] = scale ? s * scale[j] : s;
   }
-}
-
-// Givens rotation of Hessenberg column k (h = h1 + h2, h2 may be NULL; h_{k+1,k} =
-// sqrt(hn2)), residual
-// estimate |g_{k+1}| and the stop test of the GMRES cycle.  One thread.
-__device__ void givens_column(VecCtl& c, int b, double hn2, const double* __restrict__ h1,
-                              const double* __restrict__ h2, int k, int restart,
-                              int32_t* host_flags) {
-  const int ld = MCA_KMAX + 1;
-  double* col = c.H + (size_t)k * ld;
-  for (int j = 0; j <= k; ++j)
-    col[j] = __ldcg(&h1[(size_t)b * 32 + j]) + (h2 ? __ldcg(&h2[(size_t)b * 32 + j]) : 0.0);
-  const double hk1 = sqrt(hn2);
-  col[k + 1] = hk1;
-  for (int j = 0; j < k; ++j) {
-    const double t = c.cs[j] * col[j] + c.sn[j] * col[j + 1];
-    col[j + 1] = -c.sn[j] * col[j] + c.cs[j] * col[j + 1];
-    col[j] = t;
-  }
-  const double rho = hypot(col[k], col[k + 1]);
-  double cs = 1.0, sn = 0.0;
-  if (rho > 0.0) {
-    cs = col[k] / rho;
-    sn = col[k + 1] / rho;
-  }
-  c.cs[k] = cs;
-  c.sn[k] = sn;
-  col[k] = rho;
-  col[k + 1] = 0.0;
-  c.g[k + 1] = -sn * c.g[k];
-  c.g[k] = cs * c.g[k];
-  const double res = fabs(c.g[k + 1]);
-  c.res_est = res;
-  c.k_done = k + 1;
-  c.gmres_iters += 1;
-  c.inv_h = (hk1 > 0.0) ? 1.0 / hk1 : 0.0;
-  c.s[k + 1] = c.inv_h;
-  const bool stop = !(res > c.tol_abs) || (k + 1 >= restart) || !(hk1 > 0.0) ||
-                    !(rho > 0.0) || !isfinite(res);
-  if (stop) c.gm_active = 0;
-  if (host_flags) host_flags[b] = c.gm_active;
-  __threadfence_system();
 }
 
 // h[b][j] = sum over blocks of part[b][j][:] for j < nk.
@@ -224,35 +181,7 @@ k_update_norm(int phase, const double* w, size_t wstride, const double* __restri
     __syncthreads();
     if (threadIdx.x == 0) {
       cnt[b] = 0;
-      VecCtl& c = ctl[b];
-      const int k = nk - 1;
-      const double grow = sqrt((double)nk) * c.orth;
-      if (phase == UPD_FIRST) {
-        double proj = 0.0;                      // |h1|^2 = |w|^2 - |u|^2
-        for (int j = 0; j < nk; ++j) {
-          const double t = __ldcg(&hc[(size_t)b * 32 + j]);
-          proj = fma(t, t, proj);
-        }
-        const double rho = (hn2 > 0.0) ? sqrt(hn2 / (hn2 + proj)) : 0.0;
-        const double est = (grow + 4.0 * nk * kEps) / rho;
-        if (hn2 > 0.0 && !(est <= kOrthTol)) {
-          c.reorth = 1;
-          c.reorth_mask |= 1u << k;
-          c.orth1 = est;
-          c.wn2 = hn2;
-          __threadfence();
-        } else {
-          if (hn2 > 0.0) c.orth = est;
-          givens_column(c, b, hn2, hc, nullptr, k, restart, host_flags);
-        }
-      } else {
-        // after the second pass: what is left of the first pass' loss orth1 is scaled by
-        // the basis' own loss, plus rounding, relative to the new norm
-        const double rho2 = (c.wn2 > 0.0 && hn2 > 0.0) ? sqrt(hn2 / c.wn2) : 0.0;
-        if (rho2 > 0.0) c.orth = fmax(c.orth, (grow * c.orth1 + 4.0 * nk * kEps) / rho2);
-        c.reorth = 0;
-        givens_column(c, b, hn2, h1, hc, k, restart, host_flags);
-      }
+      gram_schmidt_control(ctl[b], b, phase, hn2, hc, h1, nk, restart, host_flags);
     }
   }
 }
@@ -262,14 +191,7 @@ __global__ void k_lsq(VecCtl* ctl) {
   const int b = blockIdx.x;
   VecCtl& c = ctl[b];
   if (threadIdx.x != 0 || !c.newton_active) return;
-  const int kd = c.k_done;
-  const int ld = MCA_KMAX + 1;
-  for (int i = kd - 1; i >= 0; --i) {
-    double s = c.g[i];
-    for (int j = i + 1; j < kd; ++j) s -= c.H[(size_t)j * ld + i] * c.y[j];
-    const double d = c.H[(size_t)i * ld + i];
-    c.y[i] = (d != 0.0) ? s / d : 0.0;
-  }
+  lsq_solve(c);
 }
 
 __device__ __forceinline__ double widen(double x) { return x; }

@@ -18,6 +18,7 @@
 #include "bits.cuh"
 #include "mca_internal.cuh"
 #include "twofloat.cuh"
+#include "solver_dev.cuh"
 
 namespace mca {
 
@@ -141,147 +142,6 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
   }
 }
 
-// ---- FP32 pairs: a value held as the unevaluated sum h + l of two floats -------------
-
-struct F2 {
-  float h, l;   // unevaluated sum h + l
-};
-
-// x as an FP32 pair (d2f_round(x), d2f_low(x)); one range test selects the common case
-// 2^-74 <= |x| < 2^128, where both halves come from the two 32-bit words directly.
-__device__ __forceinline__ F2 split2(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const uint32_t ex = (hi >> 20) & 0x7FFu;
-  if (ex - 949u <= 201u) {
-    const uint32_t lo2 = lo + (1u << 28);                       // round at mantissa bit 29
-    const uint32_t hi2 = hi + (lo2 < lo ? 1u : 0u);
-    const uint32_t hb = ((((hi2 & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lo2 >> 29)) |
-                        (hi & 0x80000000u);                      // exponent rebiased by 896
-    const int32_t dl = (int32_t)(lo - (lo2 & 0xE0000000u));      // x - hi in ulps of x
-    const float mag = u29_to_float((uint32_t)(dl < 0 ? -dl : dl)) *
-                      __int_as_float((int)(ex - 948u) << 23);
-    const uint32_t sg = (hi & 0x80000000u) ^ (dl < 0 ? 0x80000000u : 0u);
-    return F2{__uint_as_float(hb), __uint_as_float(__float_as_uint(mag) ^ sg)};
-  }
-  return F2{d2f_round(x), d2f_low(x)};
-}
-
-// a * b for a pair a and an FP32 pair b, as a pair (not renormalised)
-__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
-  float e;
-  const float p = two_prod(a.h, b.h, e);
-  return F2{p, fmaf(a.h, b.l, fmaf(a.l, b.h, e))};
-}
-
-// P(dV^2) - 1 = t (pc1 + t (pc2 + t r)), t = dV^2, for dV = d + dl as an FP32 pair, with the
-// polynomial's tail r = pc3 + pc4 t + pc5 t^2 + pc6 t^3 in FP32 (at most x^6 / 5040 < 3.5e-5
-// of P for x = b dV, |x| < 3/4): error-free FP32 products and sums (two_prod, two_sum), the
-// low parts added in FP32.  The result carries the FP32 tail's relative error (below
-// 3e-11 of P - 1) and a few 2^-44 from the pair arithmetic.
-__device__ __forceinline__ F2 poly_m1_pair(const Grid& gr, float d, float dl) {
-  float et;
-  const float t = two_prod(d, d, et);
-  const float tl = fmaf(2.f * d, dl, et);                   // dV^2 = t + tl
-  float r = fmaf(gr.pcf[6], t, gr.pcf[5]);
-  r = fmaf(r, t, gr.pcf[4]);
-  r = fmaf(r, t, gr.pcf[3]);
-  float ea, eb, ec, ed;
-  const float a = two_prod(t, r, ea);
-  const float q2 = two_sum(gr.pcf[2], a, eb);
-  const float q2l = (gr.pc2l + fmaf(tl, r, ea)) + eb;        // pc2 + t r
-  const float bq = two_prod(t, q2, ec);
-  const float bql = fmaf(t, q2l, fmaf(tl, q2, ec));
-  const float q1 = two_sum(gr.pcf[1], bq, ed);
-  const float q1l = (gr.pc1l + bql) + ed;                    // pc1 + t q2
-  return mul2(F2{t, tl}, F2{q1, q1l});                       // P - 1
-}
-
-// Memristor current and conductance for the FP64 residual.  The current
-// (g / b) sinh(b dV) = g dV P(dV^2) with P(dV^2) = sinh(x) / x, x = b dV, enters the KCL
-// residual at FP64 accuracy: for |x| < 3/4 (range test on the high word, integer pipe),
-// P - 1 comes from the FP32-pair polynomial above (b folded into its coefficients), is
-// rounded once to FP64, and cur = fma(g dV, P - 1, g dV): three FP64 instructions where a
-// Horner evaluation in FP64 takes seven.  Outside that range the CUDA math library.  The
-// conductance g cosh(x) only shapes the Newton matrix (the Jacobian diagonal and
-// a = mean(D)), so it is evaluated in FP32 (relative error below 3e-7, which changes the
-// inexact Newton steps but not the solution the FP64 residual drives them to) and returned
-// both as float and widened.
-__device__ __forceinline__ void device_current(const Grid& gr, double g, double dv,
-                                               double& cur, double& dg, float& dgf) {
-  if (((uint32_t)__double2hiint(dv) & 0x7FFFFFFFu) < gr.dv_lim_hi && gr.tail32) {
-    const F2 d = split2(dv);
-    const F2 q = poly_m1_pair(gr, d.h, d.l);
-    const double gd = g * dv;
-    cur = fma(gd, f2d_bits(q.h) + f2d_bits(q.l), gd);
-    dgf = d2f_round(g) * coshf(d.h * gr.bf);
-    dg = f2d_bits(dgf);
-  } else if (((uint32_t)__double2hiint(dv) & 0x7FFFFFFFu) < gr.dv_lim_hi) {
-    // b outside the FP32 tail's range: Horner in FP64
-    const double t = dv * dv;
-    double ps = gr.pc[6];
-    ps = fma(ps, t, gr.pc[5]);
-    ps = fma(ps, t, gr.pc[4]);
-    ps = fma(ps, t, gr.pc[3]);
-    ps = fma(ps, t, gr.pc[2]);
-    ps = fma(ps, t, gr.pc[1]);
-    ps = fma(ps, t, gr.pc[0]);
-    cur = g * (dv * ps);
-    dgf = d2f_round(g) * coshf(d2f_round(dv) * gr.bf);
-    dg = f2d_bits(dgf);
-  } else {
-    const double x = gr.b * dv;
-    cur = g * (sinh(x) * gr.inv_b);
-    dg = g * cosh(x);
-    dgf = d2f_round(dg);
-  }
-}
-
-// Yakopcic-form device: scale the current and the conductance of a device under negative
-// bias (sign read from the bit pattern, on the integer pipe).
-__device__ __forceinline__ void negative_bias(const Grid& gr, double dv, double& cur,
-                                              double& dg, float& dgf) {
-  const uint32_t hi = (uint32_t)__double2hiint(dv), lo = (uint32_t)__double2loint(dv);
-  if ((hi >> 31) && ((hi & 0x7FFFFFFFu) | lo)) {   // dV < 0, not -0
-    cur *= gr.rneg;
-    dg *= gr.rneg;
-    dgf *= gr.rnegf;
-  }
-}
-
-// One cell of eq. (F) and the Jacobian diagonal; returns (F_t, F_b, D).  YAK: the
-// Yakopcic-form device (a compile-time choice, so the sinh device pays nothing for it).
-// FP64 instructions: the device voltage 1, the current 3 (device_current), and per layer
-// the neighbour sum and two FMAs that add the wire diagonal term and the coupling term to
-// the current (10 in all; the source term adds one on the first column).
-template <bool YAK>
-__device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
-                                              const double* __restrict__ Vt,
-                                              const double* __restrict__ Vb, double g,
-                                              double vin_i, double& ft, double& fb,
-                                              double& dg, float& dgf) {
-  const int m = gr.m, n = gr.n;
-  const double vt = Vt[c], vb = Vb[c];
-  const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
-  const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
-  const double tl = (j > 0) ? Vt[c - 1] : 0.0;
-  const double tr = (j < n - 1) ? Vt[c + 1] : 0.0;
-  const double bu = (i > 0) ? Vb[c - n] : 0.0;
-  const double bd = (i < m - 1) ? Vb[c + n] : 0.0;
-  const double dv = vt - vb;
-  double cur;                                    // device current, top to bottom
-  if (gr.b != 0.0) {
-    device_current(gr, g, dv, cur, dg, dgf);
-  } else {
-    cur = g * dv;
-    dg = g;
-    dgf = 0.f;
-  }
-  if (YAK) negative_bias(gr, dv, cur, dg, dgf);
-  ft = fma(-gr.gt, tl + tr, fma(dt, vt, cur));
-  if (j == 0) ft = fma(-gr.g_src, vin_i, ft);
-  fb = fma(-gr.gb, bu + bd, fma(db, vb, -cur));
-}
-
 // ---- the residual in FP32 pairs ------------------------------------------------------
 //
 // For Newton iterates far from convergence, whose residual only becomes the right-hand side
@@ -300,12 +160,6 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
 // current's polynomial runs in pairs up to t^2 and in FP32 beyond (tail32 is required).
 
 constexpr double kPairErrScale = 1.0 / (double)(1ull << 40);
-// smallest convergence threshold newton_rtol ||Y|| for which the FP64 residual's ||F||^2 is
-// summed in FP32: entries that matter against it are above 1e-13 / sqrt(2 m n), whose
-// squares are normal FP32 numbers for any size this library takes
-constexpr double kNorm32Min = 1e-13;
-// the pair residual is used only for iterates more than this factor above the target
-constexpr double kPairMinRatio = 10.0;
 
 // BF16 (round to nearest even) of a float; Inf / NaN kept
 __device__ __forceinline__ __nv_bfloat16 f2bf16_bits(float x) {
@@ -416,34 +270,7 @@ __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl*
   double dummy = 0.0;
   block_sum2(s, dummy);
   if (threadIdx.x == 0) {
-    VecCtl& c = ctl[b];
-    const double yn = gr.g_src * sqrt(s);
-    c.ynorm = yn;
-    // a warm start treats V = 0, with ||F(0)|| = ||Y||, as its previous iterate, so its first
-    // forcing term follows Eisenstat-Walker instead of the cold start's eta0
-    c.fnorm = warm ? yn : 0.0;
-    c.fnorm_prev = 0.0;
-    c.a = 0.0;
-    c.eta = 0.0;
-    c.tol_abs = 0.0;
-    c.newton_iters = 0;
-    c.gmres_iters = 0;
-    c.gm_active = 0;
-    c.k_done = 0;
-    c.need_fp64 = 0;
-    c.d64 = 1;
-    c.d64_next = 0;
-    c.res_est = INFINITY;          // no linear solve yet
-    if (!isfinite(yn)) {
-      c.status = MCA_ERR_NONFINITE;
-      c.newton_active = 0;
-    } else if (yn == 0.0) {          // V_in = 0: the solution is V = 0
-      c.status = MCA_OK;
-      c.newton_active = 0;
-    } else {
-      c.status = MCA_OK;
-      c.newton_active = 1;
-    }
+    init_ctl(ctl[b], gr.g_src * sqrt(s), warm != 0);
   }
 }
 
@@ -498,71 +325,6 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
     part[((size_t)b * 32 + 1) * nblk + blockIdx.x] = sd;
     if (PAIR) part[((size_t)b * 32 + 2) * nblk + blockIdx.x] = sz;
   }
-}
-
-// Newton control (eq. Newton3) for one vector from the reduced sums: ||F||, a = mean(D),
-// convergence test, forcing term of the next linear solve (first: eta0; then
-// Eisenstat-Walker 0.9 (|F_k|/|F_k-1|)^2 capped by eta_max, and never tighter than needed
-// to reach the target), GMRES cycle start.  Runs in one thread.
-// err >= 0 (the FP32-pair residual): ||F|| is known to within err.  The pair residual
-// only serves iterates that are certainly more than kPairMinRatio times the target
-// newton_rtol ||Y|| away from convergence (there it is the right-hand side of the next
-// inexact Newton step); for any other vector nothing is decided or changed here: it is
-// flagged (need_fp64, host flag 2) for the FP64 residual, which makes every convergence
-// decision.
-__device__ void newton_control(VecCtl& c, double sf, double sd, int mn, const SolverCfg& cfg,
-                               int32_t* host_flag, double err = -1.0) {
-  const double fn = sqrt(sf);
-  const double a = sd / (double)mn;
-  if (err >= 0.0 && isfinite(fn) && isfinite(a) &&
-      fn - err <= kPairMinRatio * cfg.newton_rtol * c.ynorm) {
-    c.d64_next = 0;                // the FP64 residual rewrites D
-    c.need_fp64 = 1;
-    c.gm_active = 0;
-    if (host_flag) *host_flag = 2;
-    __threadfence_system();
-    return;
-  }
-  c.need_fp64 = 0;
-  c.d64 = c.d64_next;
-  c.d64_next = 0;
-  c.fnorm_prev = c.fnorm;
-  c.fnorm = fn;
-  c.a = a;
-  c.gm_active = 0;
-  c.k_done = 0;
-  if (!isfinite(fn) || !isfinite(a)) {
-    c.status = MCA_ERR_NONFINITE;
-    c.newton_active = 0;
-  } else if (fn <= cfg.newton_rtol * c.ynorm) {
-    c.status = MCA_OK;
-    c.newton_active = 0;
-  } else if (c.newton_iters >= cfg.max_newton) {
-    c.status = MCA_ERR_NOT_CONVERGED;
-    c.newton_active = 0;
-  } else {
-    double eta;
-    if (c.fnorm_prev <= 0.0) {
-      eta = cfg.eta0;
-    } else {
-      const double r = fn / c.fnorm_prev;
-      eta = fmin(cfg.eta_max, 0.9 * r * r);
-    }
-    eta = fmax(eta, 0.5 * cfg.newton_rtol * c.ynorm / fn);
-    eta = fmin(eta, 0.5);
-    c.eta = eta;
-    c.tol_abs = eta * fn;
-    c.g[0] = fn;
-    c.s[0] = -1.0 / fn;            // v_0 = -F / ||F|| from the stored residual
-    c.orth = 0.0;
-    c.reorth = 0;
-    c.reorth_mask = 0u;
-    c.res_est = fn;
-    c.gm_active = 1;
-    c.newton_iters += 1;
-  }
-  if (host_flag) *host_flag = c.newton_active;
-  __threadfence_system();
 }
 
 // Residual of the solver loop with the Newton control in the last block of each vector.
@@ -757,41 +519,6 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
 // z is FP64, or FP32 (the tensor-core preconditioner's accumulators, widened exactly).
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
-
-// One cell of w = J z in FP32 pairs (ApplyMode kApplyPair).  The FP32 inputs a = z_t,
-// bb = z_b and the neighbours enter error-free products with the FP32 halves of the wire
-// constants and of D, and error-free sums; the low parts (each within 2^-24 of its term)
-// are added in FP32 and the pair is rounded once to FP64.  D (a - bb) is shared by the
-// two layers.  FP64 work: splitting D and the two final additions.
-__device__ __forceinline__ void apply_pair(float a, float bb, float tl, float tr, float bu,
-                                           float bd, double Dd, float dth, float dtl,
-                                           float dbh, float dbl, const Grid& gr, double& ot,
-                                           double& ob, bool dsplit) {
-  const float dh = d2f_round(Dd);
-  const float dl = dsplit ? d2f_round(Dd - f2d_bits(dh)) : 0.f;
-  float ed, e3;
-  const float d = two_sum(a, -bb, ed);
-  const float p3 = two_prod(dh, d, e3);
-  const float t3 = fmaf(dl, d, fmaf(dh, ed, e3));           // D (a - bb) = p3 + t3
-  // top: dt a - gt (tl + tr) + D (a - bb)
-  float es, e1, e2, eu, ev;
-  const float st = two_sum(tl, tr, es);
-  const float p1 = two_prod(dth, a, e1);
-  const float p2 = two_prod(gr.gtf, st, e2);
-  const float u = two_sum(p1, -p2, eu);
-  const float v = two_sum(u, p3, ev);
-  const float lt = (fmaf(dtl, a, e1) - fmaf(gr.gtl, st, fmaf(gr.gtf, es, e2))) + (t3 + (eu + ev));
-  // bottom: db bb - gb (bu + bd) - D (a - bb)
-  float fs, f1, f2, fu, fv;
-  const float sb = two_sum(bu, bd, fs);
-  const float q1 = two_prod(dbh, bb, f1);
-  const float q2 = two_prod(gr.gbf, sb, f2);
-  const float ub = two_sum(q1, -q2, fu);
-  const float vb = two_sum(ub, -p3, fv);
-  const float lb = (fmaf(dbl, bb, f1) - fmaf(gr.gbl, sb, fmaf(gr.gbf, fs, f2))) + ((fu + fv) - t3);
-  ot = f2d_bits(v) + f2d_bits(lt);
-  ob = f2d_bits(vb) + f2d_bits(lb);
-}
 
 template <int KP, typename ZT, int AM>
 __global__ void __launch_bounds__(kThreads)

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <utility>
@@ -142,6 +143,24 @@ struct mca_handle {
   int64_t prof_launches[MCA_NUM_FAMILIES] = {};
   double prof_ms[MCA_NUM_FAMILIES] = {}, prof_bytes[MCA_NUM_FAMILIES] = {},
          prof_flops[MCA_NUM_FAMILIES] = {};
+};
+
+// Persistent batched solve over the shapes of several handles (k_persist.cu).
+struct mca_batch {
+  int device = 0;
+  std::vector<mca_handle*> hs;
+  std::vector<void*> allocs;
+  PersistShape* shapes = nullptr;        // device, one per handle
+  PersistSlots slots{};
+  int grid = 0;                          // CTAs (= slots)
+  bool yak = false;
+  cudaStream_t own_stream = nullptr;
+  PersistItem* items = nullptr;          // device
+  PersistItem* items_host = nullptr;     // pinned
+  PersistResult* res = nullptr;          // device
+  PersistResult* res_host = nullptr;     // pinned
+  int cap = 0;                           // items the buffers hold
+  int* flags = nullptr;                  // device: [0] queue head, [1] error flag
 };
 
 namespace {
@@ -1281,6 +1300,249 @@ int mca_solve_many(mca_handle* const* hs, int32_t nh, const double* const* v_in,
   for (auto& t : pool) t.join();
   g_last_error = first_msg;
   return worst;
+}
+
+void mca_batch_destroy(mca_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  for (void* q : b->allocs) cudaFree(q);
+  if (b->items_host) cudaFreeHost(b->items_host);
+  if (b->res_host) cudaFreeHost(b->res_host);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
+  delete b;
+}
+
+int mca_batch_create(mca_handle* const* hs, int32_t nh, int32_t max_ctas, mca_batch** out) {
+  g_last_error.clear();
+  if (!out || !hs || nh < 1 || max_ctas < 0) {
+    set_error("bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  for (int k = 0; k < nh; ++k) {
+    const mca_handle* h = hs[k];
+    if (!h) {
+      set_error("null handle");
+      return MCA_ERR_INVALID_ARG;
+    }
+    if (h->device != hs[0]->device) {
+      set_error("handles on different devices");
+      return MCA_ERR_INVALID_ARG;
+    }
+    if (h->p.precision != MCA_PREC_BF16_SPLIT || !h->tc_ok) {
+      set_error("the persistent solve needs MCA_PREC_BF16_SPLIT handles");
+      return MCA_ERR_UNSUPPORTED;
+    }
+    if (h->gr.yak != hs[0]->gr.yak) {
+      set_error("handles with different device models");
+      return MCA_ERR_INVALID_ARG;
+    }
+  }
+  std::unique_ptr<mca_batch> b(new mca_batch);
+  b->device = hs[0]->device;
+  MCA_CUDA_TRY(cudaSetDevice(b->device));
+  b->hs.assign(hs, hs + nh);
+  b->yak = hs[0]->gr.yak != 0;
+  auto alloc = [&](void** q, size_t bytes) -> int {
+    *q = nullptr;
+    if (cudaMalloc(q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation failed");
+      return MCA_ERR_OOM;
+    }
+    b->allocs.push_back(*q);
+    return MCA_OK;
+  };
+  MCA_CUDA_TRY(cudaStreamCreate(&b->own_stream));
+  MCA_CUDA_TRY(persist_configure());
+  // eigenvector operands of each shape in the tiled layout of the persistent kernel
+  std::vector<PersistShape> shp(nh);
+  size_t n2max = 0, bfmax = 0;
+  int rmax = 1;
+  for (int k = 0; k < nh; ++k) {
+    mca_handle* h = hs[k];
+    const size_t mp = h->mp, np = h->np;
+    __nv_bfloat16* t[6];
+    const __nv_bfloat16* src[6] = {h->QrT_bf, h->QcT_bf, h->Qr_hi, h->Qr_lo, h->Qc_hi, h->Qc_lo};
+    const size_t dim[6] = {np, mp, np, np, mp, mp};
+    for (int q = 0; q < 6; ++q) {
+      MCA_TRY(alloc(reinterpret_cast<void**>(&t[q]), dim[q] * dim[q] * sizeof(__nv_bfloat16)));
+      launch_retile_bf16(src[q], (int)dim[q], (int)dim[q], t[q], b->own_stream);
+      count_launches(1);
+    }
+    PersistShape& ps = shp[k];
+    ps.gr = h->gr;
+    ps.cfg = make_cfg(h);
+    ps.mp = h->mp;
+    ps.np = h->np;
+    ps.gmaps = h->g;
+    ps.mu_f = h->mu_f;
+    ps.nu_f = h->nu_f;
+    ps.qrt = t[0];
+    ps.qct = t[1];
+    ps.qr_hi = t[2];
+    ps.qr_lo = t[3];
+    ps.qc_hi = t[4];
+    ps.qc_lo = t[5];
+    n2max = std::max(n2max, h->n2);
+    bfmax = std::max(bfmax, 2 * mp * np);
+    rmax = std::max(rmax, h->restart);
+  }
+  MCA_TRY(alloc(reinterpret_cast<void**>(&b->shapes), nh * sizeof(PersistShape)));
+  MCA_CUDA_TRY(cudaMemcpyAsync(b->shapes, shp.data(), nh * sizeof(PersistShape),
+                               cudaMemcpyHostToDevice, b->own_stream));
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  b->grid = max_ctas > 0 ? max_ctas : 2 * sms;
+  const size_t slot = persist_slot_layout(b->slots, n2max, bfmax, rmax);
+  void* base = nullptr;
+  MCA_TRY(alloc(&base, slot * (size_t)b->grid));
+  b->slots.base = static_cast<uint8_t*>(base);
+  MCA_TRY(alloc(reinterpret_cast<void**>(&b->flags), 2 * sizeof(int)));
+  MCA_CUDA_TRY(cudaGetLastError());
+  MCA_CUDA_TRY(cudaStreamSynchronize(b->own_stream));
+  *out = b.release();
+  return MCA_OK;
+}
+
+namespace {
+// Grow the item and result buffers of a batch to hold n items.
+int batch_reserve(mca_batch* b, int n) {
+  if (n <= b->cap) return MCA_OK;
+  if (b->items_host) cudaFreeHost(b->items_host);
+  if (b->res_host) cudaFreeHost(b->res_host);
+  b->items_host = nullptr;
+  b->res_host = nullptr;
+  for (void* q : {static_cast<void*>(b->items), static_cast<void*>(b->res)}) {
+    if (!q) continue;
+    cudaFree(q);
+    b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), q));
+  }
+  b->items = nullptr;
+  b->res = nullptr;
+  b->cap = 0;
+  void *pi = nullptr, *pr = nullptr;
+  if (cudaMalloc(&pi, n * sizeof(PersistItem)) != cudaSuccess ||
+      cudaMalloc(&pr, n * sizeof(PersistResult)) != cudaSuccess) {
+    cudaGetLastError();
+    if (pi) cudaFree(pi);
+    set_error("device allocation failed");
+    return MCA_ERR_OOM;
+  }
+  b->allocs.push_back(pi);
+  b->allocs.push_back(pr);
+  b->items = static_cast<PersistItem*>(pi);
+  b->res = static_cast<PersistResult*>(pr);
+  MCA_CUDA_TRY(cudaMallocHost(&b->items_host, n * sizeof(PersistItem)));
+  MCA_CUDA_TRY(cudaMallocHost(&b->res_host, n * sizeof(PersistResult)));
+  b->cap = n;
+  return MCA_OK;
+}
+
+// One launch of the persistent kernel over n items (mode 0: solve, 1: preconditioner).
+// Items are queued largest first (tensor-core work ~ m n (m + n), memory work ~ m n).
+int batch_run(mca_batch* b, const mca_item* items, const double* a, int n, int mode,
+              mca_stats* stats, cudaStream_t s) {
+  for (int k = 0; k < n; ++k) {
+    const mca_item& it = items[k];
+    if (it.handle < 0 || it.handle >= (int)b->hs.size()) {
+      set_error("item handle index out of range");
+      return MCA_ERR_INVALID_ARG;
+    }
+    const mca_handle* h = b->hs[it.handle];
+    if (it.map < 0 || it.map >= h->n_maps) {
+      set_error("item map index out of range");
+      return MCA_ERR_INVALID_ARG;
+    }
+    if (mode == 0 && !it.v_in) {
+      set_error("item without input vector");
+      return MCA_ERR_INVALID_ARG;
+    }
+    if (mode == 1 && (!it.v_top || !it.v_bot)) {
+      set_error("preconditioner item without vectors");
+      return MCA_ERR_INVALID_ARG;
+    }
+  }
+  if (n == 0) return MCA_OK;
+  MCA_TRY(batch_reserve(b, n));
+  std::vector<int> order(n);
+  std::vector<double> cost(n);
+  for (int k = 0; k < n; ++k) {
+    const mca_handle* h = b->hs[items[k].handle];
+    order[k] = k;
+    cost[k] = (double)h->mp * h->np * (1.0 + (h->mp + h->np) / 4096.0);
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return cost[x] > cost[y]; });
+  for (int q = 0; q < n; ++q) {
+    const mca_item& it = items[order[q]];
+    PersistItem& pi = b->items_host[q];
+    pi.shape = it.handle;
+    pi.map = it.map;
+    pi.vin = it.v_in;
+    pi.vt = it.v_top;
+    pi.vb = it.v_bot;
+    pi.iout = it.i_out;
+    pi.a = a ? a[order[q]] : 0.0;
+  }
+  MCA_CUDA_TRY(cudaMemcpyAsync(b->items, b->items_host, n * sizeof(PersistItem),
+                               cudaMemcpyHostToDevice, s));
+  MCA_CUDA_TRY(cudaMemsetAsync(b->flags, 0, 2 * sizeof(int), s));
+  launch_persist(b->shapes, b->items, n, b->res, b->flags, b->flags + 1, b->slots,
+                 std::min(b->grid, n), mode, b->yak, s);
+  count_launches(1);
+  MCA_CUDA_TRY(cudaGetLastError());
+  int err = 0;
+  MCA_CUDA_TRY(cudaMemcpyAsync(b->res_host, b->res, n * sizeof(PersistResult),
+                               cudaMemcpyDeviceToHost, s));
+  MCA_CUDA_TRY(cudaMemcpyAsync(&err, b->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MCA_CUDA_TRY(cudaStreamSynchronize(s));
+  if (err != 0) {
+    set_error("a bounded wait in the persistent kernel gave up");
+    return MCA_ERR_TIMEOUT;
+  }
+  if (mode != 0) return MCA_OK;
+  int worst = MCA_OK;
+  for (int q = 0; q < n; ++q) {
+    const PersistResult& r = b->res_host[q];
+    if (stats) {
+      mca_stats& st = stats[order[q]];
+      st.status = r.status;
+      st.newton_iters = r.newton_iters;
+      st.gmres_iters = r.gmres_iters;
+      st.fallback = 0;
+      st.rel_residual = (r.ynorm > 0.0) ? r.fnorm / r.ynorm : 0.0;
+      st.kcl_rel_error = r.kcl;
+    }
+    if (r.status != MCA_OK && worst == MCA_OK) worst = r.status;
+  }
+  return worst;
+}
+}  // namespace
+
+int mca_batch_solve(mca_batch* b, const mca_item* items, int32_t n, mca_stats* stats,
+                    void* stream) {
+  g_last_error.clear();
+  if (!b || (n > 0 && !items) || n < 0) {
+    set_error("bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  MCA_CUDA_TRY(cudaSetDevice(b->device));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->own_stream;
+  return batch_run(b, items, nullptr, n, 0, stats, s);
+}
+
+int mca_batch_precond(mca_batch* b, const mca_item* items, const double* a, int32_t n,
+                      void* stream) {
+  g_last_error.clear();
+  if (!b || (n > 0 && (!items || !a)) || n < 0) {
+    set_error("bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  MCA_CUDA_TRY(cudaSetDevice(b->device));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->own_stream;
+  return batch_run(b, items, a, n, 1, nullptr, s);
 }
 
 int mca_residual(mca_handle* h, const double* x, const double* v_in, int32_t nvec, double* F,

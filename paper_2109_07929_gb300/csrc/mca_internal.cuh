@@ -301,6 +301,63 @@ void launch_gemm64_tstore(const double* A, BlkAddr a, const double* Bm, double* 
 void launch_modes_2x2_f64(double* Xh, const double* mu, const double* nu, int m, int n,
                           const VecCtl* ctl, int B, int kidx, cudaStream_t s);
 
+// ---- persistent batched solve (k_persist.cu) ---------------------------------------------
+// One shape class of the batch (one handle): stencil constants, solver settings,
+// conductance maps, FP32 eigenvalues and the preconditioner's eigenvector operands in the
+// tiled layout of k_persist.cu (padded extents mp, np: multiples of 128).
+struct PersistShape {
+  Grid gr;
+  SolverCfg cfg;
+  int mp, np;
+  const double* gmaps;                  // n_maps * m*n
+  const float* mu_f;                    // np
+  const float* nu_f;                    // mp
+  const __nv_bfloat16* qrt;             // Q_r^T  [np x np]  (transform 1)
+  const __nv_bfloat16* qct;             // Q_c^T  [mp x mp]  (transform 2)
+  const __nv_bfloat16* qr_hi;           // Q_r    [np x np]  hi / lo words (transform 3)
+  const __nv_bfloat16* qr_lo;
+  const __nv_bfloat16* qc_hi;           // Q_c    [mp x mp]  hi / lo words (transform 4)
+  const __nv_bfloat16* qc_lo;
+};
+
+// One work item: an input vector of one crossbar of one shape.
+struct PersistItem {
+  int32_t shape, map;
+  const double* vin;                    // m
+  double* vt;                           // m*n or NULL (preconditioner test: r in, z out)
+  double* vb;                           // m*n or NULL
+  double* iout;                         // n or NULL
+  double a;                             // preconditioner test only: a1 = a2 = a
+};
+
+struct PersistResult {
+  int32_t status, newton_iters, gmres_iters, pad_;
+  double fnorm, ynorm, kcl;
+};
+
+// Per-CTA scratch ("slot"): the state, D, J z, the Krylov bases and the BF16 operands of one
+// solve, for the largest shape of the batch; slot b at base + b * slot_bytes.
+struct PersistSlots {
+  uint8_t* base;
+  size_t slot_bytes;
+  size_t off_x, off_d, off_w, off_v, off_z, off_ctl;
+  size_t off_bf[5];                     // X, T1, Y_hat, E hi, E lo
+  int restart;
+};
+// Fills the offsets for vectors of up to n2max doubles, BF16 operands of up to bfmax
+// elements and the given restart length; returns slot_bytes.
+size_t persist_slot_layout(PersistSlots& sl, size_t n2max, size_t bfmax, int restart);
+// Dynamic shared memory of the kernel and its one-time attribute setup.
+int persist_smem_bytes();
+cudaError_t persist_configure();
+// mode 0: solve every item; mode 1: only z = P^-1 r for each item (r, z in vt / vb).
+void launch_persist(const PersistShape* shapes, const PersistItem* items, int n_items,
+                    PersistResult* res, int* queue, int* err, const PersistSlots& sl,
+                    int grid, int mode, bool yak, cudaStream_t s);
+// dst (tiled, R x K) from the row-major BF16 matrix src (R x K); R % 8 == 0, K % 64 == 0.
+void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst,
+                        cudaStream_t s);
+
 }  // namespace mca
 
 // Report the first CUDA error of a call chain as MCA_ERR_CUDA.
