@@ -215,6 +215,16 @@ int mca_batch_solve(mca_batch* b, const mca_item* items, int32_t n, mca_stats* s
 int mca_batch_precond(mca_batch* b, const mca_item* items, const double* a, int32_t n,
                       void* stream);
 
+/* Per-phase timing of the persistent kernel.  mca_batch_profile(b, 1) zeroes and enables
+ * it (0 disables); mca_batch_profile_read fills ms[MCA_BATCH_PHASES] with the time each
+ * phase took, summed over the CTAs (CTA-milliseconds) since it was enabled, in the order
+ * residual, transform 1, transform 2 (with the modes), transform 3, transform 4, Jacobian
+ * apply + dots, update pass, second Gram-Schmidt pass, least squares + solution update,
+ * other (queue, setup, outputs). */
+#define MCA_BATCH_PHASES 10
+int mca_batch_profile(mca_batch* b, int32_t enable);
+int mca_batch_profile_read(mca_batch* b, double* ms);
+
 void mca_batch_destroy(mca_batch* b);
 
 /* Reprogram the crossbars of a handle: replace its n_maps conductance maps (host or

@@ -51,8 +51,11 @@ EXPORTED = (
     "mca_cnn_conv_wgrad", "mca_cnn_prep_weights", "mca_cnn_features", "mca_cnn_target",
     "mca_cnn_guess", "mca_cnn_loss", "mca_cnn_adam", "mca_cnn_check", "mca_set_conductances",
     "mca_wait_selftest", "mca_tile_config", "mca_batch_create", "mca_batch_solve",
-    "mca_batch_precond", "mca_batch_destroy",
+    "mca_batch_precond", "mca_batch_destroy", "mca_batch_profile", "mca_batch_profile_read",
 )
+
+BATCH_PHASES = ("residual", "transform_1", "transform_2_modes", "transform_3", "transform_4",
+                "spmv_dots", "update", "reorth", "update_x", "other")
 
 FAMILIES = ("residual", "spmv_dots", "reorth", "update_norm", "normalize", "small",
             "update_x", "precond_1", "precond_2", "precond_3", "precond_4")
@@ -167,9 +170,12 @@ def load(build_if_missing=True):
     lib.mca_batch_create.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(P)]
     lib.mca_batch_solve.argtypes = [P, P, ctypes.c_int32, P, P]
     lib.mca_batch_precond.argtypes = [P, P, P, ctypes.c_int32, P]
+    lib.mca_batch_profile.argtypes = [P, ctypes.c_int32]
+    lib.mca_batch_profile_read.argtypes = [P, P]
     lib.mca_batch_destroy.argtypes = [P]
     lib.mca_batch_destroy.restype = None
-    for name in ("mca_batch_create", "mca_batch_solve", "mca_batch_precond"):
+    for name in ("mca_batch_create", "mca_batch_solve", "mca_batch_precond",
+                 "mca_batch_profile", "mca_batch_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     lib.mca_kernel_launches.argtypes = []
     lib.mca_kernel_launches.restype = ctypes.c_int64
@@ -308,6 +314,15 @@ class Batch:
         return [dict(status=x.status, newton_iters=x.newton_iters, gmres_iters=x.gmres_iters,
                      rel_residual=x.rel_residual, kcl_rel_error=x.kcl_rel_error,
                      fallback=x.fallback) for x in st]
+
+    def profile(self, enable=True):
+        _check(self.lib.mca_batch_profile(self.b, 1 if enable else 0))
+
+    def profile_read(self):
+        """CTA-milliseconds per phase (BATCH_PHASES order) since profiling was enabled."""
+        ms = np.zeros(len(BATCH_PHASES))
+        _check(self.lib.mca_batch_profile_read(self.b, ms.ctypes.data))
+        return dict(zip(BATCH_PHASES, ms.tolist()))
 
     def precond(self, items, a, stream=None):
         """z = P^-1 r in place on each item's (v_top, v_bot) with a1 = a2 = a[k]."""

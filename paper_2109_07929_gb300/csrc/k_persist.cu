@@ -59,12 +59,19 @@ constexpr int kWarps = kPT / 32;
 constexpr int kChunk = 128 * 128;         // bytes of one 128-row x 64-K BF16 chunk
 constexpr int kStageRegion = 6 * kChunk;  // 3 stages of (A, B) or 2 of (A, A', B)
 constexpr uint32_t kTmemCols = 256;       // two 128-column accumulators
+constexpr int kU = 4;                     // entries per trip of the register-unrolled phases
+constexpr int kUR = 4;                    // the same for the residual
+constexpr int kUS = 4;                    // the same for the Jacobian apply
 
 struct PSmem {
   uint64_t full[3];
   uint64_t empty[3];
   uint64_t accb;
+  uint64_t sfull[3];                      // streamed phases: chunk s landed
+  uint64_t accb2[2];                      // overlapped GEMMs: accumulator a complete
+  uint64_t tempty2[2];                    // overlapped GEMMs: accumulator a drained
   uint32_t tmem_slot;
+  uint32_t g1;                            // overlapped-GEMM tiles so far
   int item;
   int err;
   uint32_t full_par, empty_par, pending;  // thread 0's pipeline state (bit s: stage s)
@@ -81,6 +88,26 @@ __device__ __forceinline__ size_t tix(int row, int k, int R) {
   return ((size_t)(k >> 6) * R + row) * 64 +
          (size_t)(((((k >> 3) & 7) ^ (row & 7)) << 3) | (k & 7));
 }
+
+// Optional per-phase timing (prof != NULL): thread 0 adds the %globaltimer time of each
+// phase, which ends at a CTA barrier, to prof[phase] (CTA-nanoseconds summed over CTAs).
+enum Phase {
+  PH_RESIDUAL = 0, PH_T1, PH_T2, PH_T3, PH_T4, PH_SPMV, PH_UPDATE, PH_REORTH, PH_XUPDATE,
+  PH_OTHER, PH_COUNT
+};
+static_assert(PH_COUNT == MCA_BATCH_PHASES, "phase count");
+
+struct Clock {
+  unsigned long long* prof;
+  unsigned long long t;
+  __device__ __forceinline__ void lap(int ph) {
+    if (prof != nullptr && threadIdx.x == 0) {
+      const unsigned long long now = tc::global_ns();
+      atomicAdd(&prof[ph], now - t);
+      t = now;
+    }
+  }
+};
 
 // ---------------------------------------------------------------- tensor-core GEMMs
 // O[r][c] = sum_p sum_k A_p[r][k] B_p[c][k] over 128 x 128 output tiles (r < mrows,
@@ -221,34 +248,126 @@ __device__ bool run_gemm(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
   return S.err == 0;
 }
 
-// Per-item buffers inside the CTA's slot.
+// Single-layer GEMMs (lp = 1) with the epilogue overlapped: two 128-column accumulators in
+// TMEM; thread 0 issues tile t + 1 into one while warps 4..7 drain tile t from the other
+// (warp 4 + q: TMEM lanes 32 q .., all 128 columns) and release it on tempty2.  Tiles are
+// counted over the CTA's lifetime in S.g1 (tile g uses accumulator g & 1; its accb2
+// completion has parity (g >> 1) & 1, and it waits for the drain of tile g - 2).
+template <class Epi>
+__device__ bool run_gemm_ws(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
+                            const Epi& epi) {
+  const int stage_bytes = 2 * kChunk;
+  const int nst = kStageRegion / stage_bytes;
+  const int nkc = J.K >> 6;
+  const int ntc = J.ncols >> 7;
+  const int ntile = (J.mrows >> 7) * ntc;
+  const int per_tile = J.npass * nkc;
+  const int total = ntile * per_tile;
+  const uint32_t g1 = S.g1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    int prod = 0;
+    for (; prod < total && prod < nst && ok; ++prod)
+      ok = produce(J, prod, nst, stage_bytes, stg, S, per_tile, nkc, ntc);
+    for (int t = 0; t < ntile && ok; ++t) {
+      const uint32_t g = g1 + (uint32_t)t;
+      const uint32_t acc = g & 1u;
+      if (g >= 2u && !mbar_wait(&S.tempty2[acc], ((g >> 1) - 1u) & 1u)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      for (int c = 0; c < per_tile && ok; ++c) {
+        const int gc = t * per_tile + c;
+        ok = consume(J, gc, nst, stage_bytes, stg, S, tmem + acc * 128u, c == 0);
+        if (ok && gc >= 1 && prod < total) {
+          ok = produce(J, prod, nst, stage_bytes, stg, S, per_tile, nkc, ntc);
+          ++prod;
+        }
+      }
+      if (ok) umma_commit(&S.accb2[acc]);
+    }
+    if (!ok) S.err = MCA_ERR_TIMEOUT;
+  } else if (warp >= 4) {
+    const int q = warp - 4;
+    for (int t = 0; t < ntile; ++t) {
+      const uint32_t g = g1 + (uint32_t)t;
+      const uint32_t acc = g & 1u;
+      const bool have = __all_sync(0xffffffffu, mbar_wait(&S.accb2[acc], (g >> 1) & 1u)) != 0;
+      if (!have) {
+        if (lane == 0) S.err = MCA_ERR_TIMEOUT;
+        break;
+      }
+      tc_fence_after();
+      const int r = (t / ntc) * 128 + q * 32 + lane;
+      const int c0 = (t % ntc) * 128;
+      const uint32_t lbase = tmem + acc * 128u + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        uint32_t v0[32];
+        tmem_ld32(lbase + cc * 32, v0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) epi(r, c0 + cc * 32 + j, __uint_as_float(v0[j]), 0.f);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(
+                         &S.tempty2[acc]))
+                     : "memory");
+    }
+    proxy_fence_global();          // the epilogue's stores feed the next GEMM's bulk copies
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {          // every stage's last MMAs are done: consume their phases
+    for (int s = 0; s < nst; ++s) {
+      if (S.pending & (1u << s)) {
+        if (!mbar_wait(&S.empty[s], (S.empty_par >> s) & 1u)) S.err = MCA_ERR_TIMEOUT;
+        S.empty_par ^= 1u << s;
+        S.pending &= ~(1u << s);
+      }
+    }
+    S.g1 = g1 + (uint32_t)ntile;
+  }
+  __syncthreads();
+  return S.err == 0;
+}
+
+// Per-item buffers inside the CTA's slot.  Vectors of 2 m n unknowns are stored as two
+// layers of mnp = round_up(m n, 4) entries (v_j at V + j n2s, n2s = 2 mnp), so every layer and
+// every 4-entry group starts on a 16-byte boundary (the bulk copies of the streamed phases);
+// the padding entries are never read as data.
 struct Work {
-  double* x;           // state [2][m][n]
-  double* D;           // Jacobian diagonal [m][n]
+  double* x;           // state [2][mnp]
+  double* D;           // Jacobian diagonal [mnp]
   double* W;           // J z
-  double* V;           // basis, v_j at V + j n2 (unnormalised, scale ctl.s[j])
-  float* Z;            // preconditioned basis, z_j at Z + j n2
+  double* V;           // basis, v_j at V + j n2s (unnormalised, scale ctl.s[j])
+  float* Z;            // preconditioned basis, z_j at Z + j n2s
   __nv_bfloat16* xbf;  // tiled BF16 copy of the current basis vector, [np/64][2 mp][64]
   __nv_bfloat16* t1;   // [mp/64][2 np][64]
   __nv_bfloat16* yh;   // [np/64][2 mp][64]
   __nv_bfloat16* eh;   // [mp/64][2 np][64]
   __nv_bfloat16* el;
   VecCtl* ctl;
+  int mnp, n2s;        // of the current item
 };
 
 // z = P^-1 (sc * X) with X the BF16 vector in w.xbf, a1 = a2 = a (eq. P, Section 3.2).
 __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a, float sc,
-                        uint8_t* stg, PSmem& S, uint32_t tmem, uint32_t& acc_ctr) {
+                        uint8_t* stg, PSmem& S, uint32_t tmem, uint32_t& acc_ctr,
+                        Clock& clk) {
   const int m = sh.gr.m, n = sh.gr.n, mp = sh.mp, np = sh.np;
-  const int mn = m * n;
+  const int mnp = w.mnp;
   {
     __nv_bfloat16* t1 = w.t1;
     const Job j{{w.xbf}, {sh.qrt}, 1, 2 * mp, np, np, 2 * mp, np, 1, 0};
-    if (!run_gemm(j, stg, S, tmem, acc_ctr, [=](int r, int c, float x0, float) {
+    if (!run_gemm_ws(j, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= mp ? 1 : 0;
           t1[tix(l * np + c, r - l * mp, 2 * np)] = __float2bfloat16(x0);
         }))
       return false;
+    clk.lap(PH_T1);
   }
   {
     __nv_bfloat16* yh = w.yh;
@@ -269,12 +388,13 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
           yh[tix(mp + c, r, 2 * mp)] = __float2bfloat16(y1);
         }))
       return false;
+    clk.lap(PH_T2);
   }
   {
     __nv_bfloat16* eh = w.eh;
     __nv_bfloat16* el = w.el;
     const Job j{{w.yh, w.yh}, {sh.qr_hi, sh.qr_lo}, 2, 2 * mp, np, np, 2 * mp, np, 1, 0};
-    if (!run_gemm(j, stg, S, tmem, acc_ctr, [=](int r, int c, float x0, float) {
+    if (!run_gemm_ws(j, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= mp ? 1 : 0;
           const size_t o = tix(l * np + c, r - l * mp, 2 * np);
           const __nv_bfloat16 hi = __float2bfloat16(x0);
@@ -282,16 +402,18 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
           el[o] = __float2bfloat16(x0 - __bfloat162float(hi));
         }))
       return false;
+    clk.lap(PH_T3);
   }
   {
     const Job j{{w.eh, w.el, w.eh}, {sh.qc_hi, sh.qc_hi, sh.qc_lo}, 3, 2 * np, mp, mp,
                 2 * np, mp, 1, 0};
-    if (!run_gemm(j, stg, S, tmem, acc_ctr, [=](int r, int c, float x0, float) {
+    if (!run_gemm_ws(j, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= np ? 1 : 0;
           const int jj = r - l * np;
-          if (jj < n && c < m) z[(size_t)l * mn + (size_t)c * n + jj] = x0;
+          if (jj < n && c < m) z[(size_t)l * mnp + (size_t)c * n + jj] = x0;
         }))
       return false;
+    clk.lap(PH_T4);
   }
   return true;
 }
@@ -315,64 +437,137 @@ __device__ __forceinline__ void block_reduce(double (&acc)[KP], int nk, double* 
 }
 
 // ---------------------------------------------------------------- memory-bound phases
+// Two forms, chosen per phase by measurement.  Register-unrolled: kU entries per thread and
+// trip, all loads of a trip issued before its arithmetic (residual, Jacobian apply, update
+// passes).  Streamed (the solution update): operands go through the operand stages, idle
+// outside the GEMMs, as a ring of kSStages chunks of at most kSStageBytes, each chunk one
+// bulk copy per stream completing on one mbarrier, two chunks in flight while the CTA works
+// on the third from shared memory.  Every streamed window starts and ends on a 16-byte
+// boundary.
+constexpr int kSStages = 3;
+constexpr int kSStageBytes = kStageRegion / kSStages;
+
+__device__ __forceinline__ int align4_dn(int v) { return v & ~3; }
+
+// Runs nchunks chunks: issue(c, stage) (thread 0) starts the bulk copies of chunk c and
+// returns their byte count; body(c, stage) consumes chunk c.  sctr counts the chunks the
+// CTA has streamed (stage sctr % kSStages, phase parity (sctr / kSStages) & 1).
+template <class Issue, class Body>
+__device__ bool stream_run(int nchunks, const Issue& issue, const Body& body, uint8_t* stg,
+                           PSmem& S, uint32_t& sctr) {
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < nchunks && c < kSStages - 1; ++c) {
+      const int s = (int)((sctr + c) % kSStages);
+      uint8_t* st = stg + s * kSStageBytes;
+      tc::mbar_expect_tx(&S.sfull[s], (uint32_t)issue(c, st, &S.sfull[s], true));
+      issue(c, st, &S.sfull[s], false);
+    }
+  }
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = (int)(sctr % kSStages);
+    if (!mbar_wait(&S.sfull[s], (sctr / kSStages) & 1u)) S.err = MCA_ERR_TIMEOUT;
+    body(c, stg + s * kSStageBytes);
+    __syncthreads();
+    if (threadIdx.x == 0 && c + kSStages - 1 < nchunks) {
+      const int s2 = (int)((sctr + kSStages - 1) % kSStages);
+      uint8_t* st = stg + s2 * kSStageBytes;
+      tc::mbar_expect_tx(&S.sfull[s2], (uint32_t)issue(c + kSStages - 1, st, &S.sfull[s2], true));
+      issue(c + kSStages - 1, st, &S.sfull[s2], false);
+    }
+    ++sctr;
+  }
+  return S.err == 0;
+}
+
+// One stream window: copy entries [lo, hi) of src (esz bytes each) to dst; dry: only the
+// byte count.
+__device__ __forceinline__ int window(bool dry, uint8_t*& dst, const void* src, int esz, int lo,
+                                      int hi, uint64_t* bar) {
+  const int bytes = (hi - lo) * esz;
+  if (!dry && bytes > 0)
+    bulk_load(dst, static_cast<const uint8_t*>(src) + (size_t)lo * esz, (uint32_t)bytes, bar);
+  dst += bytes;
+  return bytes;
+}
+
 // Residual of eq. (F) (FP64 cell) into v_0 = F (with its tiled BF16 copy), D, and the Newton
-// control.  ZERO: the state is V = 0 (F = -Y, D = g).
+// control.  ZERO: the state is V = 0 (F = -Y, D = g).  kU cells per trip with all their loads
+// issued before the first cell's arithmetic (the stores may alias the loads, so the compiler
+// cannot hoist them itself); each thread still visits its cells in increasing order.
 template <bool ZERO, bool YAK>
-__device__ void residual_phase(const PersistShape& sh, const double* gmap, const double* vin,
+__device__ bool residual_phase(const PersistShape& sh, const double* gmap, const double* vin,
                                const Work& w, PSmem& S) {
   const Grid& gr = sh.gr;
-  const int m = gr.m, n = gr.n, mn = m * n, mp = sh.mp;
+  const int m = gr.m, n = gr.n, mn = m * n, mp = sh.mp, mnp = w.mnp;
   const double* Vt = w.x;
-  const double* Vb = w.x + mn;
+  const double* Vb = w.x + mnp;
   double* Ft = w.V;
-  double* Fb = w.V + mn;
+  double* Fb = w.V + mnp;
   VecCtl& ctl = *w.ctl;
   const bool lin = (gr.b == 0.0);
   const bool norm32 = sh.cfg.newton_rtol * ctl.ynorm > kNorm32Min;
   double sf = 0.0, sd = 0.0;
   float sdf = 0.f, sfh = 0.f, sfl = 0.f;
   bool dnot32 = false;
-  const int Si = kPT / n, Sj = kPT - Si * n;
-  int i = threadIdx.x / n, j = threadIdx.x - (threadIdx.x / n) * n;
-  for (int c = threadIdx.x; c < mn; c += kPT) {
-    double ft, fb, dg;
-    float dgf = 0.f;
-    if (ZERO) {
-      ft = (j == 0) ? -gr.g_src * vin[i] : 0.0;
-      fb = 0.0;
-      dg = gmap[c];
-      dgf = d2f_round(dg);
-    } else {
-      cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vin[i] : 0.0, ft, fb, dg,
-                         dgf);
-    }
-    Ft[c] = ft;
-    Fb[c] = fb;
-    w.D[c] = dg;
-    {
-      const uint32_t dh = (uint32_t)__double2hiint(dg), dlw = (uint32_t)__double2loint(dg);
-      const uint32_t de = (dh >> 20) & 0x7FFu;
-      dnot32 |= ((dlw & 0x1FFFFFFFu) != 0u) || (de - 897u > 253u && ((dh & 0x7FFFFFFFu) | dlw));
-    }
-    w.xbf[tix(i, j, 2 * mp)] = d2bf16_bits(ft);
-    w.xbf[tix(mp + i, j, 2 * mp)] = d2bf16_bits(fb);
-    if (!ZERO) {
-      if (!norm32) {
-        sf = fma(ft, ft, sf);
-        sf = fma(fb, fb, sf);
-      } else {
-        const float a = d2f_round(ft), bb = d2f_round(fb);
-        float e;
-        sfh = two_sum(sfh, fmaf(a, a, bb * bb), e);
-        sfl += e;
+  for (int base = threadIdx.x; base < mn; base += kUR * kPT) {
+    int iu[kUR], ju[kUR];
+    double vt[kUR], vb[kUR], tl[kUR], tr[kUR], bu[kUR], bd[kUR], g[kUR], vi[kUR];
+#pragma unroll
+    for (int u = 0; u < kUR; ++u) {
+      const int c = base + u * kPT;
+      const int cc = c < mn ? c : base;
+      iu[u] = cc / n;
+      ju[u] = cc - iu[u] * n;
+      g[u] = gmap[cc];
+      vi[u] = (ju[u] == 0) ? vin[iu[u]] : 0.0;
+      if (!ZERO) {
+        vt[u] = Vt[cc];
+        vb[u] = Vb[cc];
+        tl[u] = (ju[u] > 0) ? Vt[cc - 1] : 0.0;
+        tr[u] = (ju[u] < n - 1) ? Vt[cc + 1] : 0.0;
+        bu[u] = (iu[u] > 0) ? Vb[cc - n] : 0.0;
+        bd[u] = (iu[u] < m - 1) ? Vb[cc + n] : 0.0;
       }
     }
-    if (lin) sd += dg; else sdf += dgf;
-    j += Sj;
-    i += Si;
-    if (j >= n) {
-      j -= n;
-      ++i;
+#pragma unroll
+    for (int u = 0; u < kUR; ++u) {
+      const int c = base + u * kPT;
+      if (c >= mn) break;
+      const int i = iu[u], j = ju[u];
+      double ft, fb, dg;
+      float dgf = 0.f;
+      if (ZERO) {
+        ft = (j == 0) ? -gr.g_src * vi[u] : 0.0;
+        fb = 0.0;
+        dg = g[u];
+        dgf = d2f_round(dg);
+      } else {
+        cell_residual_vals<YAK>(gr, i, j, vt[u], vb[u], tl[u], tr[u], bu[u], bd[u], g[u],
+                                vi[u], ft, fb, dg, dgf);
+      }
+      Ft[c] = ft;
+      Fb[c] = fb;
+      w.D[c] = dg;
+      {
+        const uint32_t dh = (uint32_t)__double2hiint(dg), dlw = (uint32_t)__double2loint(dg);
+        const uint32_t de = (dh >> 20) & 0x7FFu;
+        dnot32 |= ((dlw & 0x1FFFFFFFu) != 0u) ||
+                  (de - 897u > 253u && ((dh & 0x7FFFFFFFu) | dlw));
+      }
+      w.xbf[tix(i, j, 2 * mp)] = d2bf16_bits(ft);
+      w.xbf[tix(mp + i, j, 2 * mp)] = d2bf16_bits(fb);
+      if (!ZERO) {
+        if (!norm32) {
+          sf = fma(ft, ft, sf);
+          sf = fma(fb, fb, sf);
+        } else {
+          const float a = d2f_round(ft), bb = d2f_round(fb);
+          float e;
+          sfh = two_sum(sfh, fmaf(a, a, bb * bb), e);
+          sfl += e;
+        }
+      }
+      if (lin) sd += dg; else sdf += dgf;
     }
   }
   sd += f2d_bits(sdf);
@@ -387,144 +582,208 @@ __device__ void residual_phase(const PersistShape& sh, const double* gmap, const
   }
   proxy_fence_global();
   __syncthreads();
+  return true;
 }
 
-// w = J z (eq. J; AM: kApplyF32 or kApplyPair) and h1_j = s_j <V_j, w> for j < nk.
+// w = J z (eq. J; AM: kApplyF32 or kApplyPair) and h1_j = s_j <V_j, w> for j < nk, kU cells
+// per trip with their loads first.
 template <int KP, int AM>
-__device__ void spmv_phase(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
-  const int m = gr.m, n = gr.n, mn = m * n;
-  const size_t n2 = 2 * (size_t)mn;
+__device__ bool spmv_phase(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
+  const int m = gr.m, n = gr.n, mn = m * n, mnp = w.mnp, n2s = w.n2s;
   const float* zt = z;
-  const float* zb = z + mn;
+  const float* zb = z + mnp;
   const bool dsplit = w.ctl->d64 != 0;
   double acc[KP];
 #pragma unroll
   for (int jv = 0; jv < KP; ++jv) acc[jv] = 0.0;
-  const int Si = kPT / n, Sj = kPT - Si * n;
-  int i = threadIdx.x / n, jj = threadIdx.x - (threadIdx.x / n) * n;
-  for (int c = threadIdx.x; c < mn; c += kPT) {
-    double ot, ob;
-    if constexpr (AM == kApplyPair) {
-      const bool f = (jj == 0), l = (jj == n - 1), u = (i == 0), dn = (i == m - 1);
-      apply_pair(zt[c], zb[c], f ? 0.f : zt[c - 1], l ? 0.f : zt[c + 1],
-                 u ? 0.f : zb[c - n], dn ? 0.f : zb[c + n], w.D[c],
-                 f ? gr.dt0f : (l ? gr.dtlf : gr.dtmf), f ? gr.dt0l : (l ? gr.dtll : gr.dtml),
-                 u ? gr.db0f : (dn ? gr.dblf : gr.dbmf), u ? gr.db0l : (dn ? gr.dbll : gr.dbml),
-                 gr, ot, ob, dsplit);
-    } else {
-      const float a = zt[c], bb = zb[c];
-      const float cpl = d2f_round(w.D[c]) * (a - bb);
-      const float dt = (jj == 0) ? gr.dt0f : ((jj == n - 1) ? gr.dtlf : gr.dtmf);
-      const float db = (i == 0) ? gr.db0f : ((i == m - 1) ? gr.dblf : gr.dbmf);
-      const float tl = (jj > 0) ? zt[c - 1] : 0.f;
-      const float tr = (jj < n - 1) ? zt[c + 1] : 0.f;
-      const float bu = (i > 0) ? zb[c - n] : 0.f;
-      const float bd = (i < m - 1) ? zb[c + n] : 0.f;
-      ot = f2d_bits(fmaf(dt, a, fmaf(-gr.gtf, tl + tr, cpl)));
-      ob = f2d_bits(fmaf(db, bb, fmaf(-gr.gbf, bu + bd, -cpl)));
+  for (int base = threadIdx.x; base < mn; base += kUS * kPT) {
+    float za[kUS], zbv[kUS], tl[kUS], tr[kUS], bu[kUS], bd[kUS];
+    double Dv[kUS], ot[kUS], ob[kUS];
+    int iu[kUS], ju[kUS];
+#pragma unroll
+    for (int u = 0; u < kUS; ++u) {
+      const int c = base + u * kPT;
+      const int cc = c < mn ? c : base;
+      const int i = cc / n, jj = cc - (cc / n) * n;
+      iu[u] = i;
+      ju[u] = jj;
+      za[u] = zt[cc];
+      zbv[u] = zb[cc];
+      tl[u] = (jj > 0) ? zt[cc - 1] : 0.f;
+      tr[u] = (jj < n - 1) ? zt[cc + 1] : 0.f;
+      bu[u] = (i > 0) ? zb[cc - n] : 0.f;
+      bd[u] = (i < m - 1) ? zb[cc + n] : 0.f;
+      Dv[u] = w.D[cc];
     }
-    w.W[c] = ot;
-    w.W[mn + c] = ob;
+#pragma unroll
+    for (int u = 0; u < kUS; ++u) {
+      const int i = iu[u], jj = ju[u];
+      if constexpr (AM == kApplyPair) {
+        const bool f = (jj == 0), l = (jj == n - 1), up = (i == 0), dn = (i == m - 1);
+        apply_pair(za[u], zbv[u], tl[u], tr[u], bu[u], bd[u], Dv[u],
+                   f ? gr.dt0f : (l ? gr.dtlf : gr.dtmf), f ? gr.dt0l : (l ? gr.dtll : gr.dtml),
+                   up ? gr.db0f : (dn ? gr.dblf : gr.dbmf),
+                   up ? gr.db0l : (dn ? gr.dbll : gr.dbml), gr, ot[u], ob[u], dsplit);
+      } else {
+        const float a = za[u], bb = zbv[u];
+        const float cpl = d2f_round(Dv[u]) * (a - bb);
+        const float dt = (jj == 0) ? gr.dt0f : ((jj == n - 1) ? gr.dtlf : gr.dtmf);
+        const float db = (i == 0) ? gr.db0f : ((i == m - 1) ? gr.dblf : gr.dbmf);
+        ot[u] = f2d_bits(fmaf(dt, a, fmaf(-gr.gtf, tl[u] + tr[u], cpl)));
+        ob[u] = f2d_bits(fmaf(db, bb, fmaf(-gr.gbf, bu[u] + bd[u], -cpl)));
+      }
+      const int c = base + u * kPT;
+      if (c < mn) {
+        w.W[c] = ot[u];
+        w.W[mnp + c] = ob[u];
+      }
+    }
 #pragma unroll
     for (int jv = 0; jv < KP; ++jv) {
       if (jv < nk) {
-        const double* vj = w.V + (size_t)jv * n2;
-        acc[jv] = fma(vj[c], ot, acc[jv]);
-        acc[jv] = fma(vj[mn + c], ob, acc[jv]);
+        const double* vj = w.V + (size_t)jv * n2s;
+#pragma unroll
+        for (int u = 0; u < kUS; ++u) {
+          const int c = base + u * kPT;
+          if (c < mn) {
+            acc[jv] = fma(vj[c], ot[u], acc[jv]);
+            acc[jv] = fma(vj[mnp + c], ob[u], acc[jv]);
+          }
+        }
       }
-    }
-    jj += Sj;
-    i += Si;
-    if (jj >= n) {
-      jj -= n;
-      ++i;
     }
   }
   block_reduce<KP>(acc, nk, S.h1, w.ctl->s, S);
+  proxy_fence_global();
+  __syncthreads();
+  return true;
 }
 
-// out = src - sum_j hc_j s_j V_j (j < nk) with its tiled BF16 copy; returns ||out||^2
-// (out may alias src).
+// Entries e of a vector in the padded layout that hold data (not layer padding).
+__device__ __forceinline__ bool live(int e, int mn, int mnp) {
+  return e < mn || (e >= mnp && e - mnp < mn);
+}
+
+// out = src - sum_j hc_j s_j V_j (j < nk) with its tiled BF16 copy; ||out||^2 into *hn2
+// (out may alias src).  Each layer's m n entries in turn, kU per trip with all their loads
+// first (the stores may alias the loads of the next trip).
 template <int KP>
-__device__ double update_phase(const PersistShape& sh, const Work& w, const double* src,
-                               double* out, int nk, const double* hc, PSmem& S) {
-  const int n = sh.gr.n, mn = sh.gr.m * n, mp = sh.mp;
-  const int n2 = 2 * mn;
+__device__ bool update_phase(const PersistShape& sh, const Work& w, const double* src,
+                             double* out, int nk, const double* hc, PSmem& S, double* hn2) {
+  const int n = sh.gr.n, mn = sh.gr.m * n, mp = sh.mp, mnp = w.mnp, n2s = w.n2s;
   double hj[KP];
 #pragma unroll
   for (int jv = 0; jv < KP; ++jv) hj[jv] = (jv < nk) ? hc[jv] * w.ctl->s[jv] : 0.0;
   double acc[1] = {0.0};
-  auto finish = [&](int e, double x) {
-    out[e] = x;
-    const int l = (e >= mn) ? 1 : 0;
-    const int cell = e - l * mn;
+  auto finish = [&](int l, int cell, double x) {
+    out[l * mnp + cell] = x;
     const int i = cell / n, j = cell - i * n;
     w.xbf[tix(l * mp + i, j, 2 * mp)] = d2bf16_bits(x);
     acc[0] = fma(x, x, acc[0]);
   };
-  int e = threadIdx.x;
-  for (; e + 3 * kPT < n2; e += 4 * kPT) {
-    double x[4];
+  for (int l = 0; l < 2; ++l) {
+    const double* sl = src + l * mnp;
+    const double* Vl = w.V + l * mnp;
+    int c = threadIdx.x;
+    for (; c + (kU - 1) * kPT < mn; c += kU * kPT) {
+      double x[kU];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = src[e + u * kPT];
+      for (int u = 0; u < kU; ++u) x[u] = sl[c + u * kPT];
 #pragma unroll
-    for (int jv = 0; jv < KP; ++jv)
-      if (jv < nk) {
+      for (int jv = 0; jv < KP; ++jv)
+        if (jv < nk) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          x[u] = fma(-hj[jv], w.V[(size_t)jv * n2 + e + u * kPT], x[u]);
-      }
+          for (int u = 0; u < kU; ++u)
+            x[u] = fma(-hj[jv], Vl[(size_t)jv * n2s + c + u * kPT], x[u]);
+        }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) finish(e + u * kPT, x[u]);
-  }
-  for (; e < n2; e += kPT) {
-    double x = src[e];
+      for (int u = 0; u < kU; ++u) finish(l, c + u * kPT, x[u]);
+    }
+    for (; c < mn; c += kPT) {
+      double x = sl[c];
 #pragma unroll
-    for (int jv = 0; jv < KP; ++jv)
-      if (jv < nk) x = fma(-hj[jv], w.V[(size_t)jv * n2 + e], x);
-    finish(e, x);
+      for (int jv = 0; jv < KP; ++jv)
+        if (jv < nk) x = fma(-hj[jv], Vl[(size_t)jv * n2s + c], x);
+      finish(l, c, x);
+    }
   }
   block_reduce<1>(acc, 1, S.sc, nullptr, S);
-  return S.sc[0];
+  *hn2 = S.sc[0];
+  return true;
 }
 
 // h2_j = s_j <V_j, u> for j < nk (second Gram-Schmidt pass).
 template <int KP>
-__device__ void dots_phase(const Work& w, const double* u, int n2, int nk, PSmem& S) {
+__device__ bool dots_phase(const PersistShape& sh, const Work& w, const double* u, int nk,
+                           PSmem& S) {
+  const int mn = sh.gr.m * sh.gr.n, mnp = w.mnp, n2s = w.n2s;
   double acc[KP];
 #pragma unroll
   for (int jv = 0; jv < KP; ++jv) acc[jv] = 0.0;
-  for (int e = threadIdx.x; e < n2; e += kPT) {
+  for (int e = threadIdx.x; e < n2s; e += kPT) {
+    if (!live(e, mn, mnp)) continue;
     const double x = u[e];
 #pragma unroll
     for (int jv = 0; jv < KP; ++jv)
-      if (jv < nk) acc[jv] = fma(w.V[(size_t)jv * n2 + e], x, acc[jv]);
+      if (jv < nk) acc[jv] = fma(w.V[(size_t)jv * n2s + e], x, acc[jv]);
   }
   block_reduce<KP>(acc, nk, S.h2, w.ctl->s, S);
+  return true;
+}
+
+// x += sum_j y_j z_j (j < kd <= KP).  Streams: x and z_j over the whole padded vector.
+template <int KP>
+__device__ bool xupdate_phase(const PersistShape& sh, const Work& w, int kd, const double* y,
+                              uint8_t* stg, PSmem& S, uint32_t& sctr) {
+  const int mn = sh.gr.m * sh.gr.n, mnp = w.mnp, n2s = w.n2s;
+  double yj[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) yj[j] = (j < kd) ? y[j] : 0.0;
+  int len = align4_dn(kSStageBytes / (8 + 4 * kd));
+  if (len > n2s) len = n2s;
+  const int nchunks = (n2s + len - 1) / len;
+  auto issue = [&](int c, uint8_t* st, uint64_t* bar, bool dry) {
+    const int e0 = c * len, e1 = min(e0 + len, n2s);
+    int bytes = window(dry, st, w.x, 8, e0, e1, bar);
+    for (int j = 0; j < kd; ++j) bytes += window(dry, st, w.Z + (size_t)j * n2s, 4, e0, e1, bar);
+    return bytes;
+  };
+  auto body = [&](int c, uint8_t* st) {
+    const int e0 = c * len, e1 = min(e0 + len, n2s), L = e1 - e0;
+    const double* s_x = reinterpret_cast<const double*>(st);
+    const float* s_z = reinterpret_cast<const float*>(s_x + L);
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += kPT) {
+      if (!live(e, mn, mnp)) continue;
+      double s = s_x[e - e0];
+#pragma unroll
+      for (int j = 0; j < KP; ++j)
+        if (j < kd) s = fma(yj[j], f2d_bits(s_z[(size_t)j * L + e - e0]), s);
+      w.x[e] = s;
+    }
+  };
+  const bool ok = stream_run(nchunks, issue, body, stg, S, sctr);
+  proxy_fence_global();
+  __syncthreads();
+  return ok;
 }
 
 #define MCA_PKP(F, nk, ...)                       \
   do {                                            \
-    if ((nk) <= 1) F<1>(__VA_ARGS__);             \
-    else if ((nk) <= 2) F<2>(__VA_ARGS__);        \
-    else if ((nk) <= 4) F<4>(__VA_ARGS__);        \
-    else if ((nk) <= 8) F<8>(__VA_ARGS__);        \
-    else if ((nk) <= 16) F<16>(__VA_ARGS__);      \
-    else F<32>(__VA_ARGS__);                      \
+    if ((nk) <= 1) ok = F<1>(__VA_ARGS__);        \
+    else if ((nk) <= 2) ok = F<2>(__VA_ARGS__);   \
+    else if ((nk) <= 4) ok = F<4>(__VA_ARGS__);   \
+    else if ((nk) <= 8) ok = F<8>(__VA_ARGS__);   \
+    else if ((nk) <= 16) ok = F<16>(__VA_ARGS__); \
+    else ok = F<32>(__VA_ARGS__);                 \
   } while (0)
 
 template <int KP>
-__device__ void spmv_f32(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
-  spmv_phase<KP, kApplyF32>(gr, w, z, nk, S);
+__device__ bool spmv_f32(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
+  return spmv_phase<KP, kApplyF32>(gr, w, z, nk, S);
 }
 template <int KP>
-__device__ void spmv_pair(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
-  spmv_phase<KP, kApplyPair>(gr, w, z, nk, S);
-}
-template <int KP>
-__device__ void update_kp(const PersistShape& sh, const Work& w, const double* src, double* out,
-                          int nk, const double* hc, PSmem& S, double* hn2) {
-  *hn2 = update_phase<KP>(sh, w, src, out, nk, hc, S);
+__device__ bool spmv_pair(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
+  return spmv_phase<KP, kApplyPair>(gr, w, z, nk, S);
 }
 
 // Output currents and the Kirchhoff balance (as k_outputs); copies the state out.
@@ -533,7 +792,7 @@ __device__ void outputs_phase(const PersistShape& sh, const PersistItem& it, con
   const Grid& gr = sh.gr;
   const int m = gr.m, n = gr.n, mn = m * n;
   const double* Vt = w.x;
-  const double* Vb = w.x + mn;
+  const double* Vb = w.x + w.mnp;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};   // in, |in|, out, leaks
   for (int i = threadIdx.x; i < m; i += kPT) {
     const double iin = gr.g_src * (it.vin[i] - Vt[(size_t)i * n]);
@@ -575,55 +834,69 @@ __device__ void zero_xbf(const PersistShape& sh, const Work& w) {
 }
 
 template <bool YAK>
-__device__ bool solve_item(const PersistShape& sh, const PersistItem& it, const Work& w,
+__device__ bool solve_item(const PersistShape& sh, const PersistItem& it, Work& w,
                            PersistResult* res, uint8_t* stg, PSmem& S, uint32_t tmem,
-                           uint32_t& acc_ctr, int restart) {
+                           uint32_t& acc_ctr, uint32_t& sctr, int restart, Clock& clk) {
   const Grid& gr = sh.gr;
   const int m = gr.m, n = gr.n, mn = m * n;
-  const int n2 = 2 * mn;
+  w.mnp = (mn + 3) & ~3;
+  w.n2s = 2 * w.mnp;
+  const int n2s = w.n2s;
   VecCtl& ctl = *w.ctl;
   const double* gmap = sh.gmaps + (size_t)it.map * mn;
   zero_xbf(sh, w);
-  for (int e = threadIdx.x; e < n2; e += kPT) w.x[e] = 0.0;
+  for (int e = threadIdx.x; e < n2s; e += kPT) w.x[e] = 0.0;
   {
     double acc[1] = {0.0};
     for (int i = threadIdx.x; i < m; i += kPT) acc[0] = fma(it.vin[i], it.vin[i], acc[0]);
     block_reduce<1>(acc, 1, S.sc, nullptr, S);
     if (threadIdx.x == 0) init_ctl(ctl, gr.g_src * sqrt(S.sc[0]), false);
+    proxy_fence_global();
     __syncthreads();
   }
+  clk.lap(PH_OTHER);
+  bool ok = true;
   for (int itn = 0; itn <= sh.cfg.max_newton; ++itn) {
     if (!ctl.newton_active) break;
     if (itn == 0)
-      residual_phase<true, false>(sh, gmap, it.vin, w, S);
+      ok = residual_phase<true, false>(sh, gmap, it.vin, w, S);
     else
-      residual_phase<false, YAK>(sh, gmap, it.vin, w, S);
+      ok = residual_phase<false, YAK>(sh, gmap, it.vin, w, S);
+    if (!ok) return false;
+    clk.lap(PH_RESIDUAL);
     if (!ctl.newton_active) break;
     const bool f32 = (itn == 0) && sh.cfg.eta0 >= kF32ApplyMinEta;
     for (int k = 0; k < restart; ++k) {
-      float* zk = w.Z + (size_t)k * n2;
-      if (!precond(sh, w, zk, (float)ctl.a, (float)ctl.s[k], stg, S, tmem, acc_ctr))
+      float* zk = w.Z + (size_t)k * n2s;
+      if (!precond(sh, w, zk, (float)ctl.a, (float)ctl.s[k], stg, S, tmem, acc_ctr, clk))
         return false;
       const int nk = k + 1;
       if (f32)
         MCA_PKP(spmv_f32, nk, gr, w, zk, nk, S);
       else
         MCA_PKP(spmv_pair, nk, gr, w, zk, nk, S);
-      double* vnext = w.V + (size_t)(k + 1) * n2;
+      if (!ok) return false;
+      clk.lap(PH_SPMV);
+      double* vnext = w.V + (size_t)(k + 1) * n2s;
       double hn2 = 0.0;
-      MCA_PKP(update_kp, nk, sh, w, w.W, vnext, nk, S.h1, S, &hn2);
+      MCA_PKP(update_phase, nk, sh, w, w.W, vnext, nk, S.h1, S, &hn2);
+      if (!ok) return false;
       if (threadIdx.x == 0)
         gram_schmidt_control<false>(ctl, 0, UPD_FIRST, hn2, S.h1, S.h1, nk, restart, nullptr);
       proxy_fence_global();
       __syncthreads();
+      clk.lap(PH_UPDATE);
       if (ctl.reorth) {
-        MCA_PKP(dots_phase, nk, w, vnext, n2, nk, S);
-        MCA_PKP(update_kp, nk, sh, w, vnext, vnext, nk, S.h2, S, &hn2);
+        MCA_PKP(dots_phase, nk, sh, w, vnext, nk, S);
+        if (!ok) return false;
+        MCA_PKP(update_phase, nk, sh, w, vnext, vnext, nk, S.h2, S, &hn2);
+        if (!ok) return false;
         if (threadIdx.x == 0)
           gram_schmidt_control<false>(ctl, 0, UPD_REORTH, hn2, S.h2, S.h1, nk, restart,
                                       nullptr);
         proxy_fence_global();
         __syncthreads();
+        clk.lap(PH_REORTH);
       }
       if (!ctl.gm_active) break;
     }
@@ -633,24 +906,26 @@ __device__ bool solve_item(const PersistShape& sh, const PersistItem& it, const 
       const int kd = ctl.k_done;
       if (threadIdx.x < 32) S.h2[threadIdx.x] = (threadIdx.x < kd) ? ctl.y[threadIdx.x] : 0.0;
       __syncthreads();
-      for (int e = threadIdx.x; e < n2; e += kPT) {
-        double s = w.x[e];
-        const float* zj = w.Z + e;
-        for (int j = 0; j < kd; ++j, zj += n2) s = fma(S.h2[j], f2d_bits(*zj), s);
-        w.x[e] = s;
+      if (kd > 0) {
+        MCA_PKP(xupdate_phase, kd, sh, w, kd, S.h2, stg, S, sctr);
+        if (!ok) return false;
       }
-      __syncthreads();
     }
+    clk.lap(PH_XUPDATE);
   }
   outputs_phase(sh, it, w, res, S);
   __syncthreads();
+  clk.lap(PH_OTHER);
   return true;
 }
 
 // Preconditioner test: z = P^-1 r for r in (vt, vb), written back there.
-__device__ bool precond_item(const PersistShape& sh, const PersistItem& it, const Work& w,
-                             uint8_t* stg, PSmem& S, uint32_t tmem, uint32_t& acc_ctr) {
+__device__ bool precond_item(const PersistShape& sh, const PersistItem& it, Work& w,
+                             uint8_t* stg, PSmem& S, uint32_t tmem, uint32_t& acc_ctr,
+                             Clock& clk) {
   const int m = sh.gr.m, n = sh.gr.n, mn = m * n, mp = sh.mp;
+  w.mnp = (mn + 3) & ~3;
+  w.n2s = 2 * w.mnp;
   zero_xbf(sh, w);
   __syncthreads();
   for (int c = threadIdx.x; c < mn; c += kPT) {
@@ -660,10 +935,10 @@ __device__ bool precond_item(const PersistShape& sh, const PersistItem& it, cons
   }
   proxy_fence_global();
   __syncthreads();
-  if (!precond(sh, w, w.Z, (float)it.a, 1.f, stg, S, tmem, acc_ctr)) return false;
+  if (!precond(sh, w, w.Z, (float)it.a, 1.f, stg, S, tmem, acc_ctr, clk)) return false;
   for (int c = threadIdx.x; c < mn; c += kPT) {
     it.vt[c] = f2d_bits(w.Z[c]);
-    it.vb[c] = f2d_bits(w.Z[mn + c]);
+    it.vb[c] = f2d_bits(w.Z[w.mnp + c]);
   }
   __syncthreads();
   return true;
@@ -672,7 +947,8 @@ __device__ bool precond_item(const PersistShape& sh, const PersistItem& it, cons
 template <bool YAK>
 __global__ void __launch_bounds__(kPT, 2)
 k_persist(const PersistShape* __restrict__ shapes, const PersistItem* __restrict__ items,
-          int n_items, PersistResult* res, int* queue, int* err, PersistSlots sl, int mode) {
+          int n_items, PersistResult* res, int* queue, int* err, PersistSlots sl, int mode,
+          unsigned long long* prof) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* stg = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -682,10 +958,16 @@ k_persist(const PersistShape* __restrict__ shapes, const PersistItem* __restrict
     for (int s = 0; s < 3; ++s) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
+      mbar_init(&S.sfull[s], 1);
     }
     mbar_init(&S.accb, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&S.accb2[a], 1);
+      mbar_init(&S.tempty2[a], 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.full_par = S.empty_par = S.pending = 0u;
+    S.g1 = 0u;
     S.err = 0;
   }
   if (warp == 0) {
@@ -712,7 +994,9 @@ k_persist(const PersistShape* __restrict__ shapes, const PersistItem* __restrict
   w.eh = reinterpret_cast<__nv_bfloat16*>(slot + sl.off_bf[3]);
   w.el = reinterpret_cast<__nv_bfloat16*>(slot + sl.off_bf[4]);
   w.ctl = reinterpret_cast<VecCtl*>(slot + sl.off_ctl);
-  uint32_t acc_ctr = 0;
+  w.mnp = w.n2s = 0;
+  uint32_t acc_ctr = 0, sctr = 0;
+  Clock clk{prof, prof ? tc::global_ns() : 0ull};
   for (;;) {
     if (threadIdx.x == 0) S.item = atomicAdd(queue, 1);
     __syncthreads();
@@ -720,9 +1004,10 @@ k_persist(const PersistShape* __restrict__ shapes, const PersistItem* __restrict
     if (k >= n_items || S.err) break;
     const PersistItem it = items[k];
     const PersistShape& sh = shapes[it.shape];
-    const bool ok = (mode == 1) ? precond_item(sh, it, w, stg, S, tmem, acc_ctr)
+    clk.lap(PH_OTHER);
+    const bool ok = (mode == 1) ? precond_item(sh, it, w, stg, S, tmem, acc_ctr, clk)
                                 : solve_item<YAK>(sh, it, w, res + k, stg, S, tmem, acc_ctr,
-                                                  sh.cfg.restart);
+                                                  sctr, sh.cfg.restart, clk);
     __syncthreads();
     if (!ok || S.err) break;
   }
@@ -782,13 +1067,13 @@ cudaError_t persist_configure() {
 
 void launch_persist(const PersistShape* shapes, const PersistItem* items, int n_items,
                     PersistResult* res, int* queue, int* err, const PersistSlots& sl,
-                    int grid, int mode, bool yak, cudaStream_t s) {
+                    int grid, int mode, bool yak, unsigned long long* prof, cudaStream_t s) {
   if (yak)
     k_persist<true><<<grid, kPT, kSmemBytes, s>>>(shapes, items, n_items, res, queue, err, sl,
-                                                  mode);
+                                                  mode, prof);
   else
     k_persist<false><<<grid, kPT, kSmemBytes, s>>>(shapes, items, n_items, res, queue, err, sl,
-                                                   mode);
+                                                   mode, prof);
 }
 
 void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst,

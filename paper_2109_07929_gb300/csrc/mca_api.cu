@@ -161,6 +161,7 @@ struct mca_batch {
   PersistResult* res_host = nullptr;     // pinned
   int cap = 0;                           // items the buffers hold
   int* flags = nullptr;                  // device: [0] queue head, [1] error flag
+  unsigned long long* prof = nullptr;    // device: CTA-ns per phase (NULL: off)
 };
 
 namespace {
@@ -1385,7 +1386,7 @@ int mca_batch_create(mca_handle* const* hs, int32_t nh, int32_t max_ctas, mca_ba
     ps.qr_lo = t[3];
     ps.qc_hi = t[4];
     ps.qc_lo = t[5];
-    n2max = std::max(n2max, h->n2);
+    n2max = std::max(n2max, 2 * ((h->mn + 3) / 4 * 4));   // two layers padded to 4 entries
     bfmax = std::max(bfmax, 2 * mp * np);
     rmax = std::max(rmax, h->restart);
   }
@@ -1490,7 +1491,7 @@ int batch_run(mca_batch* b, const mca_item* items, const double* a, int n, int m
                                cudaMemcpyHostToDevice, s));
   MCA_CUDA_TRY(cudaMemsetAsync(b->flags, 0, 2 * sizeof(int), s));
   launch_persist(b->shapes, b->items, n, b->res, b->flags, b->flags + 1, b->slots,
-                 std::min(b->grid, n), mode, b->yak, s);
+                 std::min(b->grid, n), mode, b->yak, b->prof, s);
   count_launches(1);
   MCA_CUDA_TRY(cudaGetLastError());
   int err = 0;
@@ -1531,6 +1532,45 @@ int mca_batch_solve(mca_batch* b, const mca_item* items, int32_t n, mca_stats* s
   MCA_CUDA_TRY(cudaSetDevice(b->device));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->own_stream;
   return batch_run(b, items, nullptr, n, 0, stats, s);
+}
+
+int mca_batch_profile(mca_batch* b, int32_t enable) {
+  g_last_error.clear();
+  if (!b) {
+    set_error("bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  MCA_CUDA_TRY(cudaSetDevice(b->device));
+  if (!enable) {
+    b->prof = nullptr;
+    return MCA_OK;
+  }
+  static_assert(MCA_BATCH_PHASES <= 16, "profile buffer");
+  if (!b->prof) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation failed");
+      return MCA_ERR_OOM;
+    }
+    b->allocs.push_back(q);
+    b->prof = static_cast<unsigned long long*>(q);
+  }
+  MCA_CUDA_TRY(cudaMemset(b->prof, 0, 16 * sizeof(unsigned long long)));
+  return MCA_OK;
+}
+
+int mca_batch_profile_read(mca_batch* b, double* ms) {
+  g_last_error.clear();
+  if (!b || !ms || !b->prof) {
+    set_error(b && !b->prof ? "profiling is not enabled" : "bad arguments");
+    return MCA_ERR_INVALID_ARG;
+  }
+  MCA_CUDA_TRY(cudaSetDevice(b->device));
+  unsigned long long ns[MCA_BATCH_PHASES];
+  MCA_CUDA_TRY(cudaMemcpy(ns, b->prof, sizeof(ns), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < MCA_BATCH_PHASES; ++k) ms[k] = (double)ns[k] * 1e-6;
+  return MCA_OK;
 }
 
 int mca_batch_precond(mca_batch* b, const mca_item* items, const double* a, int32_t n,

@@ -344,16 +344,18 @@ struct PersistSlots {
   size_t off_bf[5];                     // X, T1, Y_hat, E hi, E lo
   int restart;
 };
-// Fills the offsets for vectors of up to n2max doubles, BF16 operands of up to bfmax
+// Fills the offsets for vectors of up to n2max doubles (two layers of m n entries, each
+// padded to a multiple of 4), BF16 operands of up to bfmax
 // elements and the given restart length; returns slot_bytes.
 size_t persist_slot_layout(PersistSlots& sl, size_t n2max, size_t bfmax, int restart);
 // Dynamic shared memory of the kernel and its one-time attribute setup.
 int persist_smem_bytes();
 cudaError_t persist_configure();
 // mode 0: solve every item; mode 1: only z = P^-1 r for each item (r, z in vt / vb).
+// prof (device, MCA_BATCH_PHASES entries, or NULL): CTA-nanoseconds per phase are added.
 void launch_persist(const PersistShape* shapes, const PersistItem* items, int n_items,
                     PersistResult* res, int* queue, int* err, const PersistSlots& sl,
-                    int grid, int mode, bool yak, cudaStream_t s);
+                    int grid, int mode, bool yak, unsigned long long* prof, cudaStream_t s);
 // dst (tiled, R x K) from the row-major BF16 matrix src (R x K); R % 8 == 0, K % 64 == 0.
 void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst,
                         cudaStream_t s);

@@ -133,20 +133,17 @@ __device__ __forceinline__ void negative_bias(const Grid& gr, double dv, double&
 // FP64 instructions: the device voltage 1, the current 3 (device_current), and per layer
 // the neighbour sum and two FMAs that add the wire diagonal term and the coupling term to
 // the current (10 in all; the source term adds one on the first column).
+// The arithmetic of cell_residual on the cell's loaded voltages (vt, vb), its neighbours
+// (tl, tr along the top row, bu, bd along the bottom column; 0 outside the array) and g.
 template <bool YAK>
-__device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
-                                              const double* __restrict__ Vt,
-                                              const double* __restrict__ Vb, double g,
-                                              double vin_i, double& ft, double& fb,
-                                              double& dg, float& dgf) {
+__device__ __forceinline__ void cell_residual_vals(const Grid& gr, int i, int j, double vt,
+                                                   double vb, double tl, double tr,
+                                                   double bu, double bd, double g,
+                                                   double vin_i, double& ft, double& fb,
+                                                   double& dg, float& dgf) {
   const int m = gr.m, n = gr.n;
-  const double vt = Vt[c], vb = Vb[c];
   const double dt = (j == 0) ? gr.dt0 : ((j == n - 1) ? gr.dtl : gr.dtm);
   const double db = (i == 0) ? gr.db0 : ((i == m - 1) ? gr.dbl : gr.dbm);
-  const double tl = (j > 0) ? Vt[c - 1] : 0.0;
-  const double tr = (j < n - 1) ? Vt[c + 1] : 0.0;
-  const double bu = (i > 0) ? Vb[c - n] : 0.0;
-  const double bd = (i < m - 1) ? Vb[c + n] : 0.0;
   const double dv = vt - vb;
   double cur;                                    // device current, top to bottom
   if (gr.b != 0.0) {
@@ -160,6 +157,21 @@ __device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int 
   ft = fma(-gr.gt, tl + tr, fma(dt, vt, cur));
   if (j == 0) ft = fma(-gr.g_src, vin_i, ft);
   fb = fma(-gr.gb, bu + bd, fma(db, vb, -cur));
+}
+
+template <bool YAK>
+__device__ __forceinline__ void cell_residual(const Grid& gr, int i, int j, int c,
+                                              const double* __restrict__ Vt,
+                                              const double* __restrict__ Vb, double g,
+                                              double vin_i, double& ft, double& fb,
+                                              double& dg, float& dgf) {
+  const int m = gr.m, n = gr.n;
+  const double vt = Vt[c], vb = Vb[c];
+  const double tl = (j > 0) ? Vt[c - 1] : 0.0;
+  const double tr = (j < n - 1) ? Vt[c + 1] : 0.0;
+  const double bu = (i > 0) ? Vb[c - n] : 0.0;
+  const double bd = (i < m - 1) ? Vb[c + n] : 0.0;
+  cell_residual_vals<YAK>(gr, i, j, vt, vb, tl, tr, bu, bd, g, vin_i, ft, fb, dg, dgf);
 }
 
 // One cell of w = J z in FP32 pairs (ApplyMode kApplyPair).  The FP32 inputs a = z_t,
