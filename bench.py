@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--oracle-configs", action="store_true",
                     help="(internal) time the oracle on the 32^2 and 256^2 configurations "
                          "and print one JSON line; bench.py runs it in child processes")
+    ap.add_argument("--batch-profile", choices=["c4", "small"], default=None,
+                    help="only the persistent batched launch on the statistical mix (c4) "
+                         "or its {64,128} subset (small), with per-phase timers")
     ap.add_argument("--table1", action="store_true",
                     help="GPU version of the paper's Table 1 (GMRES steps per preconditioner)")
     return ap.parse_args()
@@ -637,6 +640,83 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def batch_workload(mca, torch, cbs, nvec, restart=16):
+    """Crossbars of one shape as one multi-map Solver each (max_batch: the group's vectors,
+    at most 64), their input vectors and output buffers on the device, and the items of a
+    persistent launch (one per crossbar and input vector)."""
+    groups = {}
+    for k, cb in enumerate(cbs):
+        groups.setdefault((cb.params.rows, cb.params.cols), []).append(k)
+    solvers, vins, maps = [], [], []
+    for (m, n), ks in sorted(groups.items()):
+        p = cbs[ks[0]].params
+        B = min(64, len(ks) * nvec)   # one pass per shape group where it fits
+        solvers.append(mca.Solver(params_for(mca, p, mca.PREC_BF16_SPLIT, B, restart=restart),
+                                  np.stack([cbs[k].gmap for k in ks])))
+        vins.append(np.concatenate([cbs[k].vin for k in ks]))
+        maps.append(np.repeat(np.arange(len(ks)), nvec))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vins_d = [torch.as_tensor(v, device=dev) for v in vins]
+    outs_d = [(torch.empty(v.shape[0], s.m, s.n, dtype=torch.float64, device=dev),
+               torch.empty(v.shape[0], s.m, s.n, dtype=torch.float64, device=dev),
+               torch.empty(v.shape[0], s.n, dtype=torch.float64, device=dev))
+              for s, v in zip(solvers, vins)]
+    hs, mp_, vi, vt, vb, io = [], [], [], [], [], []
+    for k in range(len(solvers)):
+        for r in range(vins_d[k].shape[0]):
+            hs.append(k)
+            mp_.append(int(maps[k][r]))
+            vi.append(vins_d[k][r])
+            vt.append(outs_d[k][0][r])
+            vb.append(outs_d[k][1][r])
+            io.append(outs_d[k][2][r])
+    items = mca.Batch.items(hs, mp_, vi, vt, vb, io)
+    return dict(groups=groups, solvers=solvers, maps=maps, vins=vins_d, outs=outs_d,
+                items=items)
+
+
+def run_batch_profile(args):
+    """--batch-profile MIX: the persistent launch alone on the statistical mix (c4: 128
+    crossbars from {64,128,256,512}; small: 32 crossbars from {64,128}; 16 input vectors
+    each, restart 16, Newton to 1e-8): wall time of one launch (best of 3, after a warm-up),
+    then one launch with the per-phase timers (CTA-milliseconds summed over the CTAs).  One
+    JSON line."""
+    import torch
+    import paper_2109_07929_gb300 as mca
+    torch.cuda.set_device(0)
+    if args.batch_profile == "small":
+        cbs = mi.config_batched(count=32, nvec=16, base_seed=5000, sizes=(64, 128))
+    else:
+        cbs = mi.config_batched(count=128, nvec=16)
+    W = batch_workload(mca, torch, cbs, 16)
+    try:
+        with mca.Batch(W["solvers"]) as b:
+            b.solve_items(W["items"])
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                st = b.solve_items(W["items"])
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            b.profile(True)
+            b.solve_items(W["items"])
+            torch.cuda.synchronize()
+            prof = b.profile_read()
+    finally:
+        for s in W["solvers"]:
+            s.close()
+    tot = sum(prof.values())
+    cells = sum(cb.params.rows * cb.params.cols for cb in cbs) * 16
+    print(json.dumps({"batch_profile": args.batch_profile, "solves": len(st),
+                      "cells_solved": cells, "ms": min(ts) * 1e3,
+                      "solves_per_s": len(st) / min(ts),
+                      "gmres_iters_per_solve": float(np.mean([x["gmres_iters"] for x in st])),
+                      "max_rel_residual": max(x["rel_residual"] for x in st),
+                      "phase_cta_ms": {k: round(v, 1) for k, v in prof.items()},
+                      "phase_share": {k: round(v / tot, 4) for k, v in prof.items()}}))
+
+
 def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
     """Statistical characterisation: `count` crossbars with rows/cols drawn from
     {64,128,256,512}, log-uniform g with lognormal 0.1 variation, `nvec` input vectors
@@ -648,24 +728,9 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
     after the other.  Wall-clock time of the solves only (handles and the batch object
     are created beforehand)."""
     cbs = mi.config_batched(count=count, nvec=nvec)
-    groups = {}
-    for k, cb in enumerate(cbs):
-        groups.setdefault((cb.params.rows, cb.params.cols), []).append(k)
-
-    solvers, vins, maps = [], [], []
-    for (m, n), ks in sorted(groups.items()):
-        p = cbs[ks[0]].params
-        B = min(64, len(ks) * nvec)   # one pass per shape group where it fits
-        solvers.append(mca.Solver(params_for(mca, p, mca.PREC_BF16_SPLIT, B, restart=16),
-                                  np.stack([cbs[k].gmap for k in ks])))
-        vins.append(np.concatenate([cbs[k].vin for k in ks]))
-        maps.append(np.repeat(np.arange(len(ks)), nvec))
-    dev = torch.device("cuda", torch.cuda.current_device())
-    vins_d = [torch.as_tensor(v, device=dev) for v in vins]
-    outs_d = [(torch.empty(v.shape[0], s.m, s.n, dtype=torch.float64, device=dev),
-               torch.empty(v.shape[0], s.m, s.n, dtype=torch.float64, device=dev),
-               torch.empty(v.shape[0], s.n, dtype=torch.float64, device=dev))
-              for s, v in zip(solvers, vins)]
+    W = batch_workload(mca, torch, cbs, nvec)
+    groups, solvers, maps, vins_d, outs_d = (W["groups"], W["solvers"], W["maps"], W["vins"],
+                                              W["outs"])
     mca.solve_many(solvers, vins_d, map_indices=maps, n_threads=threads, outs=outs_d)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -673,17 +738,8 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
     torch.cuda.synchronize()
     t_groups = time.perf_counter() - t0
     # one persistent launch over every (crossbar, vector) item
-    hs, mp_, vi, vt, vb, io = [], [], [], [], [], []
-    for k in range(len(solvers)):
-        for r in range(vins_d[k].shape[0]):
-            hs.append(k)
-            mp_.append(int(maps[k][r]))
-            vi.append(vins_d[k][r])
-            vt.append(outs_d[k][0][r])
-            vb.append(outs_d[k][1][r])
-            io.append(outs_d[k][2][r])
     with mca.Batch(solvers) as batch:
-        items = mca.Batch.items(hs, mp_, vi, vt, vb, io)
+        items = W["items"]
         batch.solve_items(items)                                        # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -815,6 +871,8 @@ def main():
     if args.oracle_configs:
         print(json.dumps(oracle_configs()), flush=True)
         return
+    if args.batch_profile:
+        return run_batch_profile(args)
     if args.table1:
         run_table1(args)
         return

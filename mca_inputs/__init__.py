@@ -132,13 +132,13 @@ def config_large_set(n, seeds=(0, 1, 2, 3), nvec=4):
 BATCH_SIZES = (64, 128, 256, 512)
 
 
-def config_batched(count=128, nvec=16, base_seed=1000):
+def config_batched(count=128, nvec=16, base_seed=1000, sizes=BATCH_SIZES):
     """Statistical characterisation: ``count`` crossbars, rows and cols each drawn
-    from {64,128,256,512} (by a size rng seeded with base_seed), log-uniform g with
-    lognormal sigma 0.1 variation, ``nvec`` input vectors each; crossbar c uses seed
+    from ``sizes`` ({64,128,256,512}; by a size rng seeded with base_seed), log-uniform g
+    with lognormal sigma 0.1 variation, ``nvec`` input vectors each; crossbar c uses seed
     base_seed + c for its own draws."""
     srng = np.random.default_rng(base_seed)
-    dims = srng.choice(BATCH_SIZES, size=(count, 2))
+    dims = srng.choice(sizes, size=(count, 2))
     out = []
     for c in range(count):
         out.append(make_crossbar(int(dims[c, 0]), int(dims[c, 1]), base_seed + c,

@@ -63,9 +63,11 @@ constexpr int kU = 4;                     // entries per trip of the register-un
 constexpr int kUR = 4;                    // the same for the residual
 constexpr int kUS = 4;                    // the same for the Jacobian apply
 
+constexpr int kMaxStages = 4;             // GEMM stages: 4 of 24 KB down to 2 of 48 KB
+
 struct PSmem {
-  uint64_t full[3];
-  uint64_t empty[3];
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
   uint64_t accb;
   uint64_t sfull[3];                      // streamed phases: chunk s landed
   uint64_t accb2[2];                      // overlapped GEMMs: accumulator a complete
@@ -87,6 +89,13 @@ constexpr int kSmemBytes = 1024 + kStageRegion + (int)((sizeof(PSmem) + 127) / 1
 __device__ __forceinline__ size_t tix(int row, int k, int R) {
   return ((size_t)(k >> 6) * R + row) * 64 +
          (size_t)(((((k >> 3) & 7) ^ (row & 7)) << 3) | (k & 7));
+}
+
+// The same for the 32-wide K chunks of the split GEMMs' operands: K/32 chunks of R rows x
+// 64 bytes in the 64-byte-swizzled order (16-byte unit u of row r at u ^ ((r / 2) % 4)).
+__device__ __forceinline__ size_t tix32(int row, int k, int R) {
+  return ((size_t)(k >> 5) * R + row) * 32 +
+         (size_t)(((((k >> 3) & 3) ^ ((row >> 1) & 3)) << 3) | (k & 7));
 }
 
 // Optional per-phase timing (prof != NULL): thread 0 adds the %globaltimer time of each
@@ -165,6 +174,75 @@ __device__ __forceinline__ bool consume(const Job& J, int g, int nst, int stage_
   return true;
 }
 
+// Split GEMM in one pass: 32-wide K chunks (64-byte swizzle, 8 KB per 128 rows), a stage
+// holds the na A words and nb B words of one K chunk, and each of the np_ products
+// A[pa] B[pb]^T reads them from the same stage.
+constexpr int kChunk32 = 128 * 64;
+struct Job32 {
+  const __nv_bfloat16* A[2];
+  const __nv_bfloat16* B[2];
+  int na, nb, np_;
+  int pa[3], pb[3];
+  int RA, RB, K, mrows, ncols;
+  __device__ __forceinline__ int stage_bytes() const { return (na + nb) * kChunk32; }
+  __device__ __forceinline__ int chunks_per_tile() const { return K >> 5; }
+  __device__ __forceinline__ bool produce(int g, int nst, uint8_t* stg, PSmem& S,
+                                          int ntc) const {
+    const int s = g % nst;
+    if (S.pending & (1u << s)) {
+      if (!mbar_wait(&S.empty[s], (S.empty_par >> s) & 1u)) return false;
+      S.empty_par ^= 1u << s;
+      S.pending &= ~(1u << s);
+    }
+    const int nkc = K >> 5;
+    const int t = g / nkc, kc = g - t * nkc;
+    const int r0 = (t / ntc) * 128, c0 = (t % ntc) * 128;
+    uint8_t* st = stg + s * stage_bytes();
+    mbar_expect_tx(&S.full[s], (uint32_t)stage_bytes());
+    for (int a = 0; a < na; ++a)
+      bulk_load(st + a * kChunk32, A[a] + ((size_t)kc * RA + r0) * 32, kChunk32, &S.full[s]);
+    for (int b = 0; b < nb; ++b)
+      bulk_load(st + (na + b) * kChunk32, B[b] + ((size_t)kc * RB + c0) * 32, kChunk32,
+                &S.full[s]);
+    return true;
+  }
+  __device__ __forceinline__ bool consume(int g, int nst, uint8_t* stg, PSmem& S,
+                                          uint32_t tmem, bool first) const {
+    const int s = g % nst;
+    if (!mbar_wait(&S.full[s], (S.full_par >> s) & 1u)) return false;
+    S.full_par ^= 1u << s;
+    tc_fence_after();
+    const uint8_t* st = stg + s * stage_bytes();
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      for (int p = 0; p < np_; ++p) {
+        const uint64_t ad = tc::sw64_desc(st + pa[p] * kChunk32 + kk * 32);
+        const uint64_t bd = tc::sw64_desc(st + (na + pb[p]) * kChunk32 + kk * 32);
+        umma(tmem, ad, bd, idesc, (first && kk == 0 && p == 0) ? 0u : 1u);
+      }
+    }
+    umma_commit(&S.empty[s]);
+    S.pending |= 1u << s;
+    return true;
+  }
+};
+
+// The single-pass K64 jobs of the overlapped path (lp = 1) through the same interface.
+struct Job64 {
+  Job J;
+  __device__ __forceinline__ int stage_bytes() const { return 2 * kChunk; }
+  __device__ __forceinline__ int chunks_per_tile() const { return J.npass * (J.K >> 6); }
+  __device__ __forceinline__ bool produce(int g, int nst, uint8_t* stg, PSmem& S,
+                                          int ntc) const {
+    return mca::produce(J, g, nst, stage_bytes(), stg, S, chunks_per_tile(), J.K >> 6, ntc);
+  }
+  __device__ __forceinline__ bool consume(int g, int nst, uint8_t* stg, PSmem& S,
+                                          uint32_t tmem, bool first) const {
+    return mca::consume(J, g, nst, stage_bytes(), stg, S, tmem, first);
+  }
+};
+
 // The whole GEMM by the CTA: thread 0 streams the chunks (up to nst in flight, running ahead
 // across tiles) and issues the MMAs; all 8 warps drain each finished tile (warp w: TMEM lanes
 // 32 (w % 4) .., columns 64 (w / 4) ..) through epi(r, c, x0, x1).  Returns false after a
@@ -173,7 +251,7 @@ template <class Epi>
 __device__ bool run_gemm(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
                          uint32_t& acc_ctr, const Epi& epi) {
   const int stage_bytes = (J.lp + 1) * kChunk;
-  const int nst = kStageRegion / stage_bytes;
+  const int nst = min(kMaxStages, kStageRegion / stage_bytes);
   const int nkc = J.K >> 6;
   const int ntc = J.ncols >> 7;
   const int ntile = (J.mrows >> 7) * ntc;
@@ -253,23 +331,20 @@ __device__ bool run_gemm(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
 // (warp 4 + q: TMEM lanes 32 q .., all 128 columns) and release it on tempty2.  Tiles are
 // counted over the CTA's lifetime in S.g1 (tile g uses accumulator g & 1; its accb2
 // completion has parity (g >> 1) & 1, and it waits for the drain of tile g - 2).
-template <class Epi>
-__device__ bool run_gemm_ws(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
-                            const Epi& epi) {
-  const int stage_bytes = 2 * kChunk;
-  const int nst = kStageRegion / stage_bytes;
-  const int nkc = J.K >> 6;
-  const int ntc = J.ncols >> 7;
-  const int ntile = (J.mrows >> 7) * ntc;
-  const int per_tile = J.npass * nkc;
+template <class JobT, class Epi>
+__device__ bool run_gemm_ws(const JobT& J, int mrows, int ncols, uint8_t* stg, PSmem& S,
+                            uint32_t tmem, const Epi& epi) {
+  const int nst = min(kMaxStages, kStageRegion / J.stage_bytes());
+  const int ntc = ncols >> 7;
+  const int ntile = (mrows >> 7) * ntc;
+  const int per_tile = J.chunks_per_tile();
   const int total = ntile * per_tile;
   const uint32_t g1 = S.g1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     bool ok = true;
     int prod = 0;
-    for (; prod < total && prod < nst && ok; ++prod)
-      ok = produce(J, prod, nst, stage_bytes, stg, S, per_tile, nkc, ntc);
+    for (; prod < total && prod < nst && ok; ++prod) ok = J.produce(prod, nst, stg, S, ntc);
     for (int t = 0; t < ntile && ok; ++t) {
       const uint32_t g = g1 + (uint32_t)t;
       const uint32_t acc = g & 1u;
@@ -280,9 +355,9 @@ __device__ bool run_gemm_ws(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
       tc_fence_after();
       for (int c = 0; c < per_tile && ok; ++c) {
         const int gc = t * per_tile + c;
-        ok = consume(J, gc, nst, stage_bytes, stg, S, tmem + acc * 128u, c == 0);
+        ok = J.consume(gc, nst, stg, S, tmem + acc * 128u, c == 0);
         if (ok && gc >= 1 && prod < total) {
-          ok = produce(J, prod, nst, stage_bytes, stg, S, per_tile, nkc, ntc);
+          ok = J.produce(prod, nst, stg, S, ntc);
           ++prod;
         }
       }
@@ -361,8 +436,8 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
   const int mnp = w.mnp;
   {
     __nv_bfloat16* t1 = w.t1;
-    const Job j{{w.xbf}, {sh.qrt}, 1, 2 * mp, np, np, 2 * mp, np, 1, 0};
-    if (!run_gemm_ws(j, stg, S, tmem, [=](int r, int c, float x0, float) {
+    const Job64 j{{{w.xbf}, {sh.qrt}, 1, 2 * mp, np, np, 2 * mp, np, 1, 0}};
+    if (!run_gemm_ws(j, 2 * mp, np, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= mp ? 1 : 0;
           t1[tix(l * np + c, r - l * mp, 2 * np)] = __float2bfloat16(x0);
         }))
@@ -384,8 +459,8 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
             y0 = ((nu + a) * x0 + a * x1) * inv;
             y1 = (a * x0 + (mu + a) * x1) * inv;
           }
-          yh[tix(c, r, 2 * mp)] = __float2bfloat16(y0);
-          yh[tix(mp + c, r, 2 * mp)] = __float2bfloat16(y1);
+          yh[tix32(c, r, 2 * mp)] = __float2bfloat16(y0);
+          yh[tix32(mp + c, r, 2 * mp)] = __float2bfloat16(y1);
         }))
       return false;
     clk.lap(PH_T2);
@@ -393,10 +468,12 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
   {
     __nv_bfloat16* eh = w.eh;
     __nv_bfloat16* el = w.el;
-    const Job j{{w.yh, w.yh}, {sh.qr_hi, sh.qr_lo}, 2, 2 * mp, np, np, 2 * mp, np, 1, 0};
-    if (!run_gemm_ws(j, stg, S, tmem, [=](int r, int c, float x0, float) {
+    // A = Y_hat (one word), B = Q_r hi, lo: products A Bh + A Bl
+    const Job32 j{{w.yh, nullptr}, {sh.qr_hi, sh.qr_lo}, 1, 2, 2, {0, 0, 0}, {0, 1, 0},
+                  2 * mp, np, np, 2 * mp, np};
+    if (!run_gemm_ws(j, 2 * mp, np, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= mp ? 1 : 0;
-          const size_t o = tix(l * np + c, r - l * mp, 2 * np);
+          const size_t o = tix32(l * np + c, r - l * mp, 2 * np);
           const __nv_bfloat16 hi = __float2bfloat16(x0);
           eh[o] = hi;
           el[o] = __float2bfloat16(x0 - __bfloat162float(hi));
@@ -405,9 +482,10 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
     clk.lap(PH_T3);
   }
   {
-    const Job j{{w.eh, w.el, w.eh}, {sh.qc_hi, sh.qc_hi, sh.qc_lo}, 3, 2 * np, mp, mp,
-                2 * np, mp, 1, 0};
-    if (!run_gemm_ws(j, stg, S, tmem, [=](int r, int c, float x0, float) {
+    // A = E hi, lo and B = Q_c hi, lo: products Eh Qh + El Qh + Eh Ql
+    const Job32 j{{w.eh, w.el}, {sh.qc_hi, sh.qc_lo}, 2, 2, 3, {0, 1, 0}, {0, 0, 1},
+                  2 * np, mp, mp, 2 * np, mp};
+    if (!run_gemm_ws(j, 2 * np, mp, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= np ? 1 : 0;
           const int jj = r - l * np;
           if (jj < n && c < m) z[(size_t)l * mnp + (size_t)c * n + jj] = x0;
@@ -547,15 +625,17 @@ __device__ bool residual_phase(const PersistShape& sh, const double* gmap, const
       }
       Ft[c] = ft;
       Fb[c] = fb;
-      w.D[c] = dg;
+      if (!ZERO) w.D[c] = dg;        // (the zero state's D is g: the apply reads the map)
       {
         const uint32_t dh = (uint32_t)__double2hiint(dg), dlw = (uint32_t)__double2loint(dg);
         const uint32_t de = (dh >> 20) & 0x7FFu;
         dnot32 |= ((dlw & 0x1FFFFFFFu) != 0u) ||
                   (de - 897u > 253u && ((dh & 0x7FFFFFFFu) | dlw));
       }
-      w.xbf[tix(i, j, 2 * mp)] = d2bf16_bits(ft);
-      w.xbf[tix(mp + i, j, 2 * mp)] = d2bf16_bits(fb);
+      if (!ZERO || j == 0) {         // the zero state's F is zero off the first column, and
+        w.xbf[tix(i, j, 2 * mp)] = d2bf16_bits(ft);   // the BF16 copy starts zeroed
+        if (!ZERO) w.xbf[tix(mp + i, j, 2 * mp)] = d2bf16_bits(fb);
+      }
       if (!ZERO) {
         if (!norm32) {
           sf = fma(ft, ft, sf);
@@ -588,7 +668,8 @@ __device__ bool residual_phase(const PersistShape& sh, const double* gmap, const
 // w = J z (eq. J; AM: kApplyF32 or kApplyPair) and h1_j = s_j <V_j, w> for j < nk, kU cells
 // per trip with their loads first.
 template <int KP, int AM>
-__device__ bool spmv_phase(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
+__device__ bool spmv_phase(const Grid& gr, const Work& w, const double* D, const float* z,
+                           int nk, PSmem& S) {
   const int m = gr.m, n = gr.n, mn = m * n, mnp = w.mnp, n2s = w.n2s;
   const float* zt = z;
   const float* zb = z + mnp;
@@ -613,7 +694,7 @@ __device__ bool spmv_phase(const Grid& gr, const Work& w, const float* z, int nk
       tr[u] = (jj < n - 1) ? zt[cc + 1] : 0.f;
       bu[u] = (i > 0) ? zb[cc - n] : 0.f;
       bd[u] = (i < m - 1) ? zb[cc + n] : 0.f;
-      Dv[u] = w.D[cc];
+      Dv[u] = D[cc];
     }
 #pragma unroll
     for (int u = 0; u < kUS; ++u) {
@@ -778,12 +859,14 @@ __device__ bool xupdate_phase(const PersistShape& sh, const Work& w, int kd, con
   } while (0)
 
 template <int KP>
-__device__ bool spmv_f32(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
-  return spmv_phase<KP, kApplyF32>(gr, w, z, nk, S);
+__device__ bool spmv_f32(const Grid& gr, const Work& w, const double* D, const float* z,
+                         int nk, PSmem& S) {
+  return spmv_phase<KP, kApplyF32>(gr, w, D, z, nk, S);
 }
 template <int KP>
-__device__ bool spmv_pair(const Grid& gr, const Work& w, const float* z, int nk, PSmem& S) {
-  return spmv_phase<KP, kApplyPair>(gr, w, z, nk, S);
+__device__ bool spmv_pair(const Grid& gr, const Work& w, const double* D, const float* z,
+                          int nk, PSmem& S) {
+  return spmv_phase<KP, kApplyPair>(gr, w, D, z, nk, S);
 }
 
 // Output currents and the Kirchhoff balance (as k_outputs); copies the state out.
@@ -871,10 +954,12 @@ __device__ bool solve_item(const PersistShape& sh, const PersistItem& it, Work& 
       if (!precond(sh, w, zk, (float)ctl.a, (float)ctl.s[k], stg, S, tmem, acc_ctr, clk))
         return false;
       const int nk = k + 1;
+      // D of the zero state is the conductance map itself
+      const double* D = (itn == 0) ? gmap : w.D;
       if (f32)
-        MCA_PKP(spmv_f32, nk, gr, w, zk, nk, S);
+        MCA_PKP(spmv_f32, nk, gr, w, D, zk, nk, S);
       else
-        MCA_PKP(spmv_pair, nk, gr, w, zk, nk, S);
+        MCA_PKP(spmv_pair, nk, gr, w, D, zk, nk, S);
       if (!ok) return false;
       clk.lap(PH_SPMV);
       double* vnext = w.V + (size_t)(k + 1) * n2s;
@@ -955,11 +1040,11 @@ k_persist(const PersistShape* __restrict__ shapes, const PersistItem* __restrict
   PSmem& S = *reinterpret_cast<PSmem*>(stg + kStageRegion);
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 3; ++s) {
+    for (int s = 0; s < kMaxStages; ++s) {
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
-      mbar_init(&S.sfull[s], 1);
     }
+    for (int s = 0; s < kSStages; ++s) mbar_init(&S.sfull[s], 1);
     mbar_init(&S.accb, 1);
     for (int a = 0; a < 2; ++a) {
       mbar_init(&S.accb2[a], 1);
@@ -1023,12 +1108,12 @@ k_persist(const PersistShape* __restrict__ shapes, const PersistItem* __restrict
 }
 
 __global__ void k_retile(const __nv_bfloat16* __restrict__ src, int R, int K,
-                         __nv_bfloat16* __restrict__ dst) {
+                         __nv_bfloat16* __restrict__ dst, int k32) {
   const size_t total = (size_t)R * K;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / K), k = (int)(e - (size_t)r * K);
-    dst[tix(r, k, R)] = src[e];
+    dst[k32 ? tix32(r, k, R) : tix(r, k, R)] = src[e];
   }
 }
 
@@ -1076,12 +1161,12 @@ void launch_persist(const PersistShape* shapes, const PersistItem* items, int n_
                                                    mode, prof);
 }
 
-void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst,
+void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst, bool k32,
                         cudaStream_t s) {
   const size_t total = (size_t)R * K;
   int nb = (int)((total + 255) / 256);
   if (nb > 1216) nb = 1216;
-  k_retile<<<nb, 256, 0, s>>>(src, R, K, dst);
+  k_retile<<<nb, 256, 0, s>>>(src, R, K, dst, k32 ? 1 : 0);
 }
 
 }  // namespace mca

@@ -356,8 +356,9 @@ cudaError_t persist_configure();
 void launch_persist(const PersistShape* shapes, const PersistItem* items, int n_items,
                     PersistResult* res, int* queue, int* err, const PersistSlots& sl,
                     int grid, int mode, bool yak, unsigned long long* prof, cudaStream_t s);
-// dst (tiled, R x K) from the row-major BF16 matrix src (R x K); R % 8 == 0, K % 64 == 0.
-void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst,
+// dst (tiled, R x K) from the row-major BF16 matrix src (R x K); R % 8 == 0, K % 64 == 0;
+// k32: the 32-wide K chunks of the split GEMMs' operands, else 64-wide.
+void launch_retile_bf16(const __nv_bfloat16* src, int R, int K, __nv_bfloat16* dst, bool k32,
                         cudaStream_t s);
 
 }  // namespace mca
