@@ -713,12 +713,8 @@ __device__ bool spmv_phase(const Grid& gr, const Work& w, const double* D, const
         ot[u] = f2d_bits(fmaf(dt, a, fmaf(-gr.gtf, tl[u] + tr[u], cpl)));
         ob[u] = f2d_bits(fmaf(db, bb, fmaf(-gr.gbf, bu[u] + bd[u], -cpl)));
       }
-      const int c = base + u * kPT;
-      if (c < mn) {
-        w.W[c] = ot[u];
-        w.W[mnp + c] = ob[u];
-      }
     }
+    // the dots' loads before the stores of w (which may alias them for the compiler)
 #pragma unroll
     for (int jv = 0; jv < KP; ++jv) {
       if (jv < nk) {
@@ -731,6 +727,14 @@ __device__ bool spmv_phase(const Grid& gr, const Work& w, const double* D, const
             acc[jv] = fma(vj[mnp + c], ob[u], acc[jv]);
           }
         }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUS; ++u) {
+      const int c = base + u * kPT;
+      if (c < mn) {
+        w.W[c] = ot[u];
+        w.W[mnp + c] = ob[u];
       }
     }
   }
