@@ -746,6 +746,12 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
         st = batch.solve_items(items)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
+        # one more launch with the per-phase timers (not timed)
+        batch.profile(True)
+        batch.solve_items(items)
+        torch.cuda.synchronize()
+        prof = batch.profile_read()
+    ptot = sum(prof.values())
     worst = max(x["rel_residual"] for x in st)
     its = float(np.mean([x["gmres_iters"] for x in st]))
     newton = float(np.mean([x["newton_iters"] for x in st]))
@@ -774,6 +780,7 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
             "crossbars": count, "shape_groups": len(groups),
             "max_rel_residual": worst, "gmres_iters_per_solve": its,
             "newton_iters_per_solve": newton,
+            "phase_share": {k: round(v / ptot, 4) for k, v in prof.items()},
             "grouped_handles_value": count * nvec / t_groups, "grouped_handles_threads": threads,
             "grouped_handles_max_rel_residual": worst_groups,
             "one_handle_per_crossbar_value": len(sample) * nvec / tb,
