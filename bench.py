@@ -822,13 +822,16 @@ def committed_traffic(fam, fp):
     ent = d.get(fam)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_2109_07929_gb300", "csrc", ent.get("source", ""))
-    if not os.path.exists(src):
-        return None
+    # the capture is keyed to the sources of the kernel (their bytes in order)
     import hashlib
-    with open(src, "rb") as f:
-        h = hashlib.sha1(f.read()).hexdigest()
-    if h != ent.get("sha1"):
+    h = hashlib.sha1()
+    for name in ent.get("sources", [ent.get("source", "")]):
+        src = os.path.join(ROOT, "paper_2109_07929_gb300", "csrc", name)
+        if not os.path.exists(src):
+            return None
+        with open(src, "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != ent.get("sha1"):
         return None
     if "ratio_to_algorithmic" in ent:
         return ent["ratio_to_algorithmic"] * fp["bytes"] / max(1, fp["launches"])
