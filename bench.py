@@ -759,6 +759,7 @@ def run_batched_c4(mca, torch, count=128, nvec=16, threads=4):
     for s in solvers:
         s.close()
     # baseline: one handle per crossbar, sequential (a sample of 16 crossbars, scaled)
+    dev = torch.device("cuda", torch.cuda.current_device())
     sample = list(range(0, count, max(1, count // 16)))
     tb = 0.0
     for k in sample:
