@@ -238,3 +238,47 @@ def test_persistent_statistical_mix_sample():
     finally:
         for s in solvers:
             s.close()
+
+
+def test_persistent_long_cycles_and_per_handle_settings():
+    """The paper's normalised regime (wires and terminations 1 S, linear devices with g in
+    [0, 0.4]; the oracle's exact-P GMRES needs 21 iterations to 5e-12 on it) with a tiny
+    first forcing term: the linear solve runs long GMRES cycles (basis widths past 16, the
+    widest Gram-Schmidt passes).  A second handle in the same launch keeps the default
+    forcing terms and its own tolerance.  Every item against the oracle, and against the
+    handle path with the same settings."""
+    cb_long = mi.make_crossbar(40, 56, 31, nvec=2, gdist="uniform_paper", g_src=1.0,
+                               g_term_top_right=1.0, g_term_bot_top=1.0, g_sense=1.0, b=0.0)
+    cb_loose = mi.make_crossbar(72, 24, 32, nvec=2, sigma=0.1)
+    s_long = mca.Solver(_params(cb_long.params, newton_rtol=1e-11, eta0=1e-12, eta_max=1e-12,
+                                gmres_restart=30), cb_long.gmap)
+    s_loose = mca.Solver(_params(cb_loose.params, newton_rtol=1e-8), cb_loose.gmap)
+    try:
+        items_in = []
+        for k, (s, cb) in enumerate(((s_long, cb_long), (s_loose, cb_loose))):
+            m, n = cb.params.rows, cb.params.cols
+            for v in range(2):
+                items_in.append((k, cb, v, torch.empty(m, n, dtype=torch.float64, device=DEV),
+                                 torch.empty(m, n, dtype=torch.float64, device=DEV),
+                                 torch.empty(n, dtype=torch.float64, device=DEV)))
+        vins = [_t(cb.vin[v]) for _, cb, v, *_ in items_in]
+        with mca.Batch([s_long, s_loose]) as b:
+            items = mca.Batch.items([x[0] for x in items_in], [0] * len(items_in), vins,
+                                    [x[3] for x in items_in], [x[4] for x in items_in],
+                                    [x[5] for x in items_in])
+            st = b.solve_items(items)
+        torch.cuda.synchronize()
+        for (k, cb, v, vt, vb, io), sq in zip(items_in, st):
+            tol = 1e-11 if k == 0 else 1e-8
+            _check_item(cb.params, cb.gmap, cb.vin[v], vt.cpu().numpy(), vb.cpu().numpy(),
+                        io.cpu().numpy(), sq, tol, vtol=1e-7 if k == 0 else 1e-6)
+        long_iters = [sq["gmres_iters"] for (k, *_), sq in zip(items_in, st) if k == 0]
+        assert min(long_iters) > 16, long_iters
+        # the handle path with the same settings reaches the same solution
+        vt1, vb1, _, st1 = s_long.solve(cb_long.vin[:2])
+        for v in range(2):
+            vt = items_in[v][3].cpu().numpy()
+            assert np.abs(vt - vt1[v]).max() <= 1e-9 * np.abs(vt1[v]).max()
+    finally:
+        s_long.close()
+        s_loose.close()
