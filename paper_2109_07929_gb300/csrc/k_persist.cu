@@ -24,10 +24,11 @@
 //     copy); the optional second pass; the Givens column (one thread).
 // The residual is the FP64 cell of eq. (F) for every Newton iterate.
 //
-// Tiled BF16 operand layout (tix below): a K-major matrix of R rows is stored as
-// K/64 column chunks of R rows x 128 bytes in the 128-byte-swizzled order of the MMA's
-// shared-memory operands (16-byte unit u of row r at position u ^ (r % 8)), so a 128-row
-// tile of one chunk is one contiguous 16 KB bulk copy.
+// Tiled BF16 operand layout (tix, tix32 below): a K-major matrix of R rows is stored as
+// column chunks of R rows in the swizzled order of the MMA's shared-memory operands, so a
+// 128-row tile of one chunk is one contiguous bulk copy: transform 1 takes K/64 chunks of
+// 128-byte rows (128-byte swizzle), transforms 2-4 K/32 chunks of 64-byte rows (64-byte
+// swizzle), so that one stage holds every word its products need.
 //
 // Every wait is bounded (2 s of %globaltimer); on expiry the CTA records MCA_ERR_TIMEOUT,
 // stops taking items, frees its TMEM and returns.
@@ -174,17 +175,44 @@ __device__ __forceinline__ bool consume(const Job& J, int g, int nst, int stage_
   return true;
 }
 
-// Split GEMM in one pass: 32-wide K chunks (64-byte swizzle, 8 KB per 128 rows), a stage
-// holds the na A words and nb B words of one K chunk, and each of the np_ products
-// A[pa] B[pb]^T reads them from the same stage.
+// GEMM in one pass over 32-wide K chunks (64-byte swizzle, 8 KB per 128 rows): a stage holds
+// the NA A words and NB B words of one K chunk, and each product of the table P (KIND) reads
+// them from the same stage into its accumulator:
+//   KIND 2 (transform 2): A = both layers' rows of T1, one B: A0 B -> acc 0, A1 B -> acc 128
+//   KIND 3 (transform 3): A = Y_hat, B = Q_r hi, lo:       A Bh + A Bl           -> acc 0
+//   KIND 4 (transform 4): A = E hi, lo, B = Q_c hi, lo:    Ah Bh + Al Bh + Ah Bl -> acc 0
 constexpr int kChunk32 = 128 * 64;
+template <int KIND>
+struct Prod;
+template <>
+struct Prod<2> {
+  static constexpr int NA = 2, NB = 1, NP = 2;
+  __device__ static constexpr int pa(int p) { return p; }
+  __device__ static constexpr int pb(int) { return 0; }
+  __device__ static constexpr int acc(int p) { return 128 * p; }
+};
+template <>
+struct Prod<3> {
+  static constexpr int NA = 1, NB = 2, NP = 2;
+  __device__ static constexpr int pa(int) { return 0; }
+  __device__ static constexpr int pb(int p) { return p; }
+  __device__ static constexpr int acc(int) { return 0; }
+};
+template <>
+struct Prod<4> {
+  static constexpr int NA = 2, NB = 2, NP = 3;
+  __device__ static constexpr int pa(int p) { return p == 1 ? 1 : 0; }
+  __device__ static constexpr int pb(int p) { return p == 2 ? 1 : 0; }
+  __device__ static constexpr int acc(int) { return 0; }
+};
+
+template <int KIND>
 struct Job32 {
+  using P = Prod<KIND>;
   const __nv_bfloat16* A[2];
   const __nv_bfloat16* B[2];
-  int na, nb, np_;
-  int pa[3], pb[3];
-  int RA, RB, K, mrows, ncols;
-  __device__ __forceinline__ int stage_bytes() const { return (na + nb) * kChunk32; }
+  int RA, RB, K;
+  __device__ __forceinline__ int stage_bytes() const { return (P::NA + P::NB) * kChunk32; }
   __device__ __forceinline__ int chunks_per_tile() const { return K >> 5; }
   __device__ __forceinline__ bool produce(int g, int nst, uint8_t* stg, PSmem& S,
                                           int ntc) const {
@@ -199,10 +227,12 @@ struct Job32 {
     const int r0 = (t / ntc) * 128, c0 = (t % ntc) * 128;
     uint8_t* st = stg + s * stage_bytes();
     mbar_expect_tx(&S.full[s], (uint32_t)stage_bytes());
-    for (int a = 0; a < na; ++a)
+#pragma unroll
+    for (int a = 0; a < P::NA; ++a)
       bulk_load(st + a * kChunk32, A[a] + ((size_t)kc * RA + r0) * 32, kChunk32, &S.full[s]);
-    for (int b = 0; b < nb; ++b)
-      bulk_load(st + (na + b) * kChunk32, B[b] + ((size_t)kc * RB + c0) * 32, kChunk32,
+#pragma unroll
+    for (int b = 0; b < P::NB; ++b)
+      bulk_load(st + (P::NA + b) * kChunk32, B[b] + ((size_t)kc * RB + c0) * 32, kChunk32,
                 &S.full[s]);
     return true;
   }
@@ -216,10 +246,13 @@ struct Job32 {
     constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
 #pragma unroll
     for (int kk = 0; kk < 2; ++kk) {
-      for (int p = 0; p < np_; ++p) {
-        const uint64_t ad = tc::sw64_desc(st + pa[p] * kChunk32 + kk * 32);
-        const uint64_t bd = tc::sw64_desc(st + (na + pb[p]) * kChunk32 + kk * 32);
-        umma(tmem, ad, bd, idesc, (first && kk == 0 && p == 0) ? 0u : 1u);
+#pragma unroll
+      for (int p = 0; p < P::NP; ++p) {
+        const uint64_t ad = tc::sw64_desc(st + P::pa(p) * kChunk32 + kk * 32);
+        const uint64_t bd = tc::sw64_desc(st + (P::NA + P::pb(p)) * kChunk32 + kk * 32);
+        // the first product into each accumulator overwrites it
+        const bool opens = first && kk == 0 && (p == 0 || P::acc(p) != P::acc(0));
+        umma(tmem + (uint32_t)P::acc(p), ad, bd, idesc, opens ? 0u : 1u);
       }
     }
     umma_commit(&S.empty[s]);
@@ -247,21 +280,18 @@ struct Job64 {
 // across tiles) and issues the MMAs; all 8 warps drain each finished tile (warp w: TMEM lanes
 // 32 (w % 4) .., columns 64 (w / 4) ..) through epi(r, c, x0, x1).  Returns false after a
 // timeout (S.err set).
-template <class Epi>
-__device__ bool run_gemm(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
-                         uint32_t& acc_ctr, const Epi& epi) {
-  const int stage_bytes = (J.lp + 1) * kChunk;
-  const int nst = min(kMaxStages, kStageRegion / stage_bytes);
-  const int nkc = J.K >> 6;
-  const int ntc = J.ncols >> 7;
-  const int ntile = (J.mrows >> 7) * ntc;
-  const int per_tile = J.npass * nkc;
+template <class JobT, class Epi>
+__device__ bool run_gemm(const JobT& J, int mrows, int ncols, uint8_t* stg, PSmem& S,
+                         uint32_t tmem, uint32_t& acc_ctr, const Epi& epi) {
+  const int nst = min(kMaxStages, kStageRegion / J.stage_bytes());
+  const int ntc = ncols >> 7;
+  const int ntile = (mrows >> 7) * ntc;
+  const int per_tile = J.chunks_per_tile();
   const int total = ntile * per_tile;
   int prod = 0;
   if (threadIdx.x == 0) {
     bool ok = true;
-    for (; prod < total && prod < nst && ok; ++prod)
-      ok = produce(J, prod, nst, stage_bytes, stg, S, per_tile, nkc, ntc);
+    for (; prod < total && prod < nst && ok; ++prod) ok = J.produce(prod, nst, stg, S, ntc);
     if (!ok) S.err = MCA_ERR_TIMEOUT;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -272,9 +302,9 @@ __device__ bool run_gemm(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
       bool ok = true;
       for (int c = 0; c < per_tile && ok; ++c) {
         const int g = t * per_tile + c;
-        ok = consume(J, g, nst, stage_bytes, stg, S, tmem, c == 0);
+        ok = J.consume(g, nst, stg, S, tmem, c == 0);
         if (ok && g >= 1 && prod < total) {
-          ok = produce(J, prod, nst, stage_bytes, stg, S, per_tile, nkc, ntc);
+          ok = J.produce(prod, nst, stg, S, ntc);
           ++prod;
         }
       }
@@ -299,12 +329,7 @@ __device__ bool run_gemm(const Job& J, uint8_t* stg, PSmem& S, uint32_t tmem,
     for (int cc = 0; cc < 2; ++cc) {
       uint32_t v0[32], v1[32];
       tmem_ld32(lbase + cc * 32, v0);
-      if (J.lp == 2) {
-        tmem_ld32(lbase + 128 + cc * 32, v1);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v1[j] = 0u;
-      }
+      tmem_ld32(lbase + 128 + cc * 32, v1);
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         epi(r, c0 + cc * 32 + j, __uint_as_float(v0[j]), __uint_as_float(v1[j]));
@@ -439,7 +464,7 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
     const Job64 j{{{w.xbf}, {sh.qrt}, 1, 2 * mp, np, np, 2 * mp, np, 1, 0}};
     if (!run_gemm_ws(j, 2 * mp, np, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= mp ? 1 : 0;
-          t1[tix(l * np + c, r - l * mp, 2 * np)] = __float2bfloat16(x0);
+          t1[tix32(l * np + c, r - l * mp, 2 * np)] = __float2bfloat16(x0);
         }))
       return false;
     clk.lap(PH_T1);
@@ -448,8 +473,9 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
     __nv_bfloat16* yh = w.yh;
     const float* mu_f = sh.mu_f;
     const float* nu_f = sh.nu_f;
-    const Job j{{w.t1}, {sh.qct}, 1, 2 * np, mp, mp, np, mp, 2, np};
-    if (!run_gemm(j, stg, S, tmem, acc_ctr, [=](int r, int c, float x0, float x1) {
+    // both layers of a mode in one tile: A rows r (layer 0) and np + r (layer 1), one B
+    const Job32<2> j{{w.t1, w.t1 + (size_t)np * 32}, {sh.qct, nullptr}, 2 * np, mp, mp};
+    if (!run_gemm(j, np, mp, stg, S, tmem, acc_ctr, [=](int r, int c, float x0, float x1) {
           // [y_t; y_b] = (1/det) [[nu + a, a], [a, mu + a]] [x_t; x_b] for mode (r, c)
           float y0 = 0.f, y1 = 0.f;
           if (r < n && c < m) {
@@ -469,8 +495,7 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
     __nv_bfloat16* eh = w.eh;
     __nv_bfloat16* el = w.el;
     // A = Y_hat (one word), B = Q_r hi, lo: products A Bh + A Bl
-    const Job32 j{{w.yh, nullptr}, {sh.qr_hi, sh.qr_lo}, 1, 2, 2, {0, 0, 0}, {0, 1, 0},
-                  2 * mp, np, np, 2 * mp, np};
+    const Job32<3> j{{w.yh, nullptr}, {sh.qr_hi, sh.qr_lo}, 2 * mp, np, np};
     if (!run_gemm_ws(j, 2 * mp, np, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= mp ? 1 : 0;
           const size_t o = tix32(l * np + c, r - l * mp, 2 * np);
@@ -483,8 +508,7 @@ __device__ bool precond(const PersistShape& sh, const Work& w, float* z, float a
   }
   {
     // A = E hi, lo and B = Q_c hi, lo: products Eh Qh + El Qh + Eh Ql
-    const Job32 j{{w.eh, w.el}, {sh.qc_hi, sh.qc_lo}, 2, 2, 3, {0, 1, 0}, {0, 0, 1},
-                  2 * np, mp, mp, 2 * np, mp};
+    const Job32<4> j{{w.eh, w.el}, {sh.qc_hi, sh.qc_lo}, 2 * np, mp, mp};
     if (!run_gemm_ws(j, 2 * np, mp, stg, S, tmem, [=](int r, int c, float x0, float) {
           const int l = r >= np ? 1 : 0;
           const int jj = r - l * np;

@@ -1369,8 +1369,8 @@ int mca_batch_create(mca_handle* const* hs, int32_t nh, int32_t max_ctas, mca_ba
     const size_t dim[6] = {np, mp, np, np, mp, mp};
     for (int q = 0; q < 6; ++q) {
       MCA_TRY(alloc(reinterpret_cast<void**>(&t[q]), dim[q] * dim[q] * sizeof(__nv_bfloat16)));
-      // transforms 3 and 4 (Q_r, Q_c as hi + lo) take 32-wide K chunks
-      launch_retile_bf16(src[q], (int)dim[q], (int)dim[q], t[q], q >= 2, b->own_stream);
+      // transforms 2, 3 and 4 take 32-wide K chunks, transform 1 64-wide
+      launch_retile_bf16(src[q], (int)dim[q], (int)dim[q], t[q], q >= 1, b->own_stream);
       count_launches(1);
     }
     PersistShape& ps = shp[k];
