@@ -85,11 +85,13 @@ __global__ void k_reduce_dots(const double* __restrict__ part, int nblk, int nk,
 
 // pass 3 (marked vectors only): partial dots <V_j, u> of the new vector u, reduced by the
 // last block into h2_j = s_j <V_j, u>.
-template <int KP>
+// ZS: the Newton step from V = 0, whose v_0 is stored in the first column of the top layer
+// only (the residual's sparse_f); its other entries are not read.
+template <int KP, bool ZS = false>
 __global__ void __launch_bounds__(kThreads)
 k_reorth_dots(const double* __restrict__ u, const double* __restrict__ V, size_t vstride,
               size_t n2, int nk, double* __restrict__ part, int nblk,
-              const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h2) {
+              const VecCtl* __restrict__ ctl, unsigned int* cnt, double* h2, int ncols) {
   const int b = blockIdx.y;
   if (!ctl[b].gm_active || !ctl[b].reorth) return;
   double acc[KP];
@@ -98,11 +100,13 @@ k_reorth_dots(const double* __restrict__ u, const double* __restrict__ V, size_t
   const double* ub = u + (size_t)b * vstride;
   const double* Vb = V + (size_t)b * vstride;
   const int N2 = (int)n2;
+  const int mn = N2 / 2, n = ncols;
   for (int e = blockIdx.x * kThreads + threadIdx.x; e < N2; e += nblk * kThreads) {
     const double x = ub[e];
+    const bool v0 = !ZS || (e < mn && e % n == 0);
 #pragma unroll
     for (int j = 0; j < KP; ++j)
-      if (j < nk) acc[j] = fma(Vb[(size_t)j * n2 + e], x, acc[j]);
+      if (j < nk && (!ZS || j > 0 || v0)) acc[j] = fma(Vb[(size_t)j * n2 + e], x, acc[j]);
   }
   block_store_partials<KP>(acc, nk, part, b, nblk);
   if (last_block(cnt, b, nblk)) {
@@ -114,7 +118,7 @@ k_reorth_dots(const double* __restrict__ u, const double* __restrict__ V, size_t
 // Passes 2 and 4: out <- w - sum_j hc_j v_j (the next, unnormalised basis vector, with
 // its BF16 copy for the tensor-core preconditioner), then the partial ||out||^2; the last
 // block of each vector runs the phase's control step (UpdPhase).
-template <int KP>
+template <int KP, bool ZS = false>
 __global__ void __launch_bounds__(kThreads)
 k_update_norm(int phase, const double* w, size_t wstride, const double* __restrict__ V,
               size_t vstride, size_t n2, int nk, const double* __restrict__ hc,
@@ -148,6 +152,8 @@ k_update_norm(int phase, const double* w, size_t wstride, const double* __restri
   // alias w, so the compiler cannot move loads of the next trip above the stores)
   const size_t st = (size_t)nblk * kThreads;
   size_t e = blockIdx.x * (size_t)kThreads + threadIdx.x;
+  // ZS: v_0 is stored (and nonzero) in the first column of the top layer only
+  auto v0 = [&](size_t e) { return !ZS || (e < mn && e % (size_t)n == 0); };
   for (; e + 3 * st < n2; e += 4 * st) {
     double x[4];
 #pragma unroll
@@ -156,7 +162,9 @@ k_update_norm(int phase, const double* w, size_t wstride, const double* __restri
     for (int j = 0; j < KP; ++j)
       if (j < nk) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = fma(-hj[j], Vb[(size_t)j * n2 + e + u * st], x[u]);
+        for (int u = 0; u < 4; ++u)
+          if (!ZS || j > 0 || v0(e + u * st))
+            x[u] = fma(-hj[j], Vb[(size_t)j * n2 + e + u * st], x[u]);
       }
 #pragma unroll
     for (int u = 0; u < 4; ++u) finish(e + u * st, x[u]);
@@ -165,7 +173,7 @@ k_update_norm(int phase, const double* w, size_t wstride, const double* __restri
     double x = wb[e];
 #pragma unroll
     for (int j = 0; j < KP; ++j)
-      if (j < nk) x = fma(-hj[j], Vb[(size_t)j * n2 + e], x);
+      if (j < nk && (!ZS || j > 0 || v0(e))) x = fma(-hj[j], Vb[(size_t)j * n2 + e], x);
     finish(e, x);
   }
   block_store_partials<1>(acc, 1, part, b, nblk);
@@ -323,30 +331,37 @@ void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
   k_reduce_dots<<<B, kThreads, 0, s>>>(part, nblk, nk, h, ctl);
 }
 
-#define MCA_KP_DISPATCH(KERN, nk, grid, ...)                                  \
+#define MCA_KP_DISPATCH1(KERN, ZS_, nk, grid, ...)                             \
   do {                                                                        \
-    if ((nk) <= 1) KERN<1><<<grid, kThreads, 0, s>>>(__VA_ARGS__);            \
-    else if ((nk) <= 2) KERN<2><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
-    else if ((nk) <= 4) KERN<4><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
-    else if ((nk) <= 8) KERN<8><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
-    else if ((nk) <= 16) KERN<16><<<grid, kThreads, 0, s>>>(__VA_ARGS__);     \
-    else KERN<32><<<grid, kThreads, 0, s>>>(__VA_ARGS__);                     \
+    if ((nk) <= 1) KERN<1, ZS_><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
+    else if ((nk) <= 2) KERN<2, ZS_><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
+    else if ((nk) <= 4) KERN<4, ZS_><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
+    else if ((nk) <= 8) KERN<8, ZS_><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
+    else if ((nk) <= 16) KERN<16, ZS_><<<grid, kThreads, 0, s>>>(__VA_ARGS__); \
+    else KERN<32, ZS_><<<grid, kThreads, 0, s>>>(__VA_ARGS__);                \
+  } while (0)
+#define MCA_KP_DISPATCH(KERN, zs, nk, grid, ...)                              \
+  do {                                                                        \
+    if (zs) MCA_KP_DISPATCH1(KERN, true, nk, grid, __VA_ARGS__);              \
+    else MCA_KP_DISPATCH1(KERN, false, nk, grid, __VA_ARGS__);                \
   } while (0)
 
 void launch_reorth_dots(const double* u, const double* V, size_t vstride, size_t n2, int nk,
                         double* part, int nblk, int B, const VecCtl* ctl, unsigned int* cnt,
-                        double* h2, cudaStream_t s) {
+                        double* h2, cudaStream_t s, bool zs, int ncols) {
   dim3 grid(nblk, B);
-  MCA_KP_DISPATCH(k_reorth_dots, nk, grid, u, V, vstride, n2, nk, part, nblk, ctl, cnt, h2);
+  MCA_KP_DISPATCH(k_reorth_dots, zs, nk, grid, u, V, vstride, n2, nk, part, nblk, ctl, cnt, h2,
+                  ncols);
 }
 
 void launch_update_norm(int phase, const double* w, size_t wstride, const double* V,
                         size_t vstride, size_t n2, int nk, const double* hc, double* part,
                         int nblk, int B, VecCtl* ctl, unsigned int* cnt, const double* h1,
                         int restart, int32_t* host_flags, double* out, size_t ostride,
-                        __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s) {
+                        __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s,
+                        bool zs) {
   dim3 grid(nblk, B);
-  MCA_KP_DISPATCH(k_update_norm, nk, grid, phase, w, wstride, V, vstride, n2, nk, hc, part,
+  MCA_KP_DISPATCH(k_update_norm, zs, nk, grid, phase, w, wstride, V, vstride, n2, nk, hc, part,
                   nblk, ctl, cnt, h1, restart, host_flags, out, ostride, xbf, mp, np, m, n);
 }
 

@@ -342,8 +342,12 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
                   const double* __restrict__ x, double* __restrict__ F, size_t fstride,
                   __nv_bfloat16* __restrict__ xbf, int mp, int np,
                   double* __restrict__ D, double* __restrict__ part, int nblk, VecCtl* ctl,
-                  SolverCfg cfg, unsigned int* cnt, int32_t* host_flags, int confirm) {
+                  SolverCfg cfg, unsigned int* cnt, int32_t* host_flags, int opts) {
   const int b = blockIdx.y;
+  const bool confirm = (opts & 1) != 0;
+  // the zero state's F = -Y is zero off the first column of the top layer; with sparse_f
+  // only that column is stored (the first Newton step's kernels read v_0 there only)
+  const bool sparse_f = ZERO && (opts & 2) != 0;
   if (confirm ? !ctl[b].need_fp64 : !ctl[b].newton_active) return;
   // PAIR: a vector whose last linear solve ended within kPairMinRatio of the target (its
   // new residual may decide convergence) takes the FP64 cell right away
@@ -394,8 +398,8 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
       cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
                          dgf);
     }
-    Ft[c] = ft;
-    Fb[c] = fb;
+    if (!sparse_f || j == 0) Ft[c] = ft;
+    if (!sparse_f) Fb[c] = fb;
     Db[c] = dg;
     {
       // D is an FP32 number when its low 29 mantissa bits are clear and its exponent is
@@ -520,7 +524,7 @@ __device__ __forceinline__ void block_reduce_rows(const double* __restrict__ par
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float x) { return f2d_bits(x); }
 
-template <int KP, typename ZT, int AM>
+template <int KP, typename ZT, int AM, bool ZS = false>
 __global__ void __launch_bounds__(kThreads)
 k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
             size_t zstride, double* __restrict__ w, const double* __restrict__ V,
@@ -583,8 +587,12 @@ k_spmv_dots(Grid gr, const double* __restrict__ D, const ZT* __restrict__ z,
       for (int j = 0; j < KP; ++j) {
         if (j < nk) {
           const double* vj = Vb_ + (size_t)j * n2;
-          acc[j] = fma(vj[c], ot, acc[j]);
-          acc[j] = fma(vj[mn + c], ob, acc[j]);
+          if (ZS && j == 0) {            // v_0 of the zero state: first top column only
+            if (jj == 0) acc[0] = fma(vj[c], ot, acc[0]);
+          } else {
+            acc[j] = fma(vj[c], ot, acc[j]);
+            acc[j] = fma(vj[mn + c], ob, acc[j]);
+          }
         }
       }
     }
@@ -680,13 +688,14 @@ void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_
                             size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
                             double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
                             unsigned int* cnt, int32_t* host_flags, cudaStream_t s, bool pair,
-                            bool confirm) {
+                            bool confirm, bool sparse_f) {
   dim3 grid(nblk, B);
+  const int opts = (confirm ? 1 : 0) | (sparse_f ? 2 : 0);
 #define MCA_RESN(Z_, Y_, P_)                                                                \
   k_residual_newton<Z_, Y_, P_><<<grid, kThreads, 0, s>>>(gr, gmaps, map_of, vin, x, F,      \
                                                           fstride, xbf, mp, np, D, part,     \
                                                           nblk, ctl, cfg, cnt, host_flags,   \
-                                                          confirm ? 1 : 0)
+                                                          opts)
   // (the zero state has dV = 0 everywhere: no device is under negative bias)
   if (zero_state)
     MCA_RESN(true, false, false);
@@ -706,7 +715,7 @@ void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
   k_init_basis<<<dim3(nb, B), kThreads, 0, s>>>(F, sign, V0, vstride, xbf, mp, np, m, n, ctl);
 }
 
-template <typename ZT, int AM>
+template <typename ZT, int AM, bool ZS = false>
 void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, double* w,
                const double* V, size_t vstride, int nk, double* part, int nblk, int B,
                const VecCtl* ctl, unsigned int* cnt, double* h, cudaStream_t s) {
@@ -714,7 +723,7 @@ void spmv_dots(const Grid& gr, const double* D, const ZT* z, size_t zstride, dou
   // 0 of batch entry 0 (nk vectors N2 apart, entries vstride apart), or NULL.
   dim3 grid(nblk, B);
 #define MCA_SPMV(KP_)                                                                      \
-  k_spmv_dots<KP_, ZT, AM><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, \
+  k_spmv_dots<KP_, ZT, AM, ZS><<<grid, kThreads, 0, s>>>(gr, D, z, zstride, w, V, vstride, nk, \
                                                       part, nblk, ctl, cnt, h)
   if (nk <= 1) MCA_SPMV(1);
   else if (nk <= 2) MCA_SPMV(2);
@@ -737,7 +746,10 @@ void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zs
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
                       cudaStream_t s, int apply) {
-  if (apply == kApplyF32)
+  if (apply == kApplyF32Zero)
+    spmv_dots<float, kApplyF32, true>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl,
+                                      cnt, h, s);
+  else if (apply == kApplyF32)
     spmv_dots<float, kApplyF32>(gr, D, z, zstride, w, V, vstride, nk, part, nblk, B, ctl, cnt,
                                 h, s);
   else if (apply == kApplyF64)

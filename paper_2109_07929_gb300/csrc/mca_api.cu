@@ -679,8 +679,10 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
     MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k,
                           true));
     t0 = prof_begin(h, s);
+    // the FP32 apply runs in the Newton step from V = 0, whose v_0 the residual stored in
+    // the first column of the top layer only (sparse_f): its dots read v_0 there only
     launch_spmv_dots(h->gr, D, zk, zstride, h->W, h->V, vstride, k + 1, h->part, nbS, B,
-                     h->ctl, h->cnt, h->h1, s, f32 ? kApplyF32 : kApplyPair);
+                     h->ctl, h->cnt, h->h1, s, f32 ? kApplyF32Zero : kApplyPair);
   } else {
     double* zk = h->Z + (size_t)k * n2;
     MCA_TRY(precond_apply(h, h->p.precision, vk, vstride, zk, zstride, B, h->ctl, s, k, D, k));
@@ -690,29 +692,31 @@ int enqueue_iteration(mca_handle* h, const double* D, int B, int k, cudaStream_t
   }
   count_launches(1);
   // FP64 flops per cell: the stencil's 12 when the apply runs in FP64 (FP64 z), 3 in the
-  // FP32-pair apply (splitting D, forming the two results), none in the FP32 apply
-  prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * ((tc ? 32.0 : 40.0) + 16.0 * nk),
-           cells * ((tc ? (f32 ? 0.0 : 3.0) : 12.0) + 4.0 * nk), s);
+  // FP32-pair apply (splitting D, forming the two results), none in the FP32 apply; the
+  // sparse v_0 of the zero-state step counts neither bytes nor flops
+  const double nkd = f32 ? nk - 1.0 : nk;     // basis vectors read in full
+  prof_end(h, t0, MCA_FAM_SPMV_DOTS, k, cells * ((tc ? 32.0 : 40.0) + 16.0 * nkd),
+           cells * ((tc ? (f32 ? 0.0 : 3.0) : 12.0) + 4.0 * nkd), s);
   double* vnext = h->V + (size_t)(k + 1) * n2;
   __nv_bfloat16* xbf = tc ? h->Xbf : nullptr;
   t0 = prof_begin(h, s);
   launch_update_norm(UPD_FIRST, h->W, n2, h->V, vstride, n2, k + 1, h->h1, h->part, nbV, B,
                      h->ctl, h->cnt, h->h1, h->restart, h->hflags_dev, vnext, vstride, xbf,
-                     h->mp, h->np, h->m, h->n, s);
+                     h->mp, h->np, h->m, h->n, s, f32);
   count_launches(1);
-  prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nk + (tc ? 4.0 : 0.0)),
-           cells * (4.0 * nk + 4.0), s);
+  prof_end(h, t0, MCA_FAM_UPDATE_NORM, k, cells * (32.0 + 16.0 * nkd + (tc ? 4.0 : 0.0)),
+           cells * (4.0 * nkd + 4.0), s);
   // second pass, a no-op for the vectors whose orthogonality estimate did not ask for it
   t0 = prof_begin(h, s);
   launch_reorth_dots(vnext, h->V, vstride, n2, k + 1, h->part, nbV, B, h->ctl, h->cnt, h->h2,
-                     s);
+                     s, f32, h->n);
   launch_update_norm(UPD_REORTH, vnext, vstride, h->V, vstride, n2, k + 1, h->h2, h->part,
                      nbV, B, h->ctl, h->cnt, h->h1, h->restart, h->hflags_dev, vnext, vstride,
-                     xbf, h->mp, h->np, h->m, h->n, s);
+                     xbf, h->mp, h->np, h->m, h->n, s, f32);
   count_launches(2);
   prof_end(h, t0, MCA_FAM_UPDATE_DOTS, k,
-           cells * (48.0 + 32.0 * nk + (tc ? 4.0 : 0.0)),
-           cells * (8.0 * nk + 4.0), s, true);
+           cells * (48.0 + 32.0 * nkd + (tc ? 4.0 : 0.0)),
+           cells * (8.0 * nkd + 4.0), s, true);
   MCA_CUDA_TRY(cudaGetLastError());
   return MCA_OK;
 }
@@ -809,15 +813,21 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     // above the target take the residual in FP32 pairs; a vector whose pair ||F|| is not
     // certainly far above the target gets the FP64 residual, which decides convergence
     const bool pair = tc && !zero_state && h->gr.tail32;
+    // the first step from V = 0 solves to the loosest forcing term, eta0: with the
+    // tensor-core forms its Jacobian applies run in FP32 when eta0 allows it, and that step's
+    // kernels read v_0 only where F(0) = -Y is nonzero (the first column of the top layer),
+    // so the residual stores only that column of F
+    const bool f32 = tc && zero_state && h->p.eta0 >= kF32ApplyMinEta;
     launch_residual_newton(h->gr, h->g, h->n_maps > 1 ? h->map_of : nullptr, h->vin, h->x,
                            zero_state, h->V, vstride, tc ? h->Xbf : nullptr, h->mp, h->np,
-                           h->D, h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s, pair);
+                           h->D, h->part, nbR, B, h->ctl, cfg, h->cnt, h->hflags_dev, s, pair,
+                           false, f32);
     count_launches(1);
     // FP64 flops per cell (an FMA counts 2): the FP64 cell 15 in 10 instructions (device
     // voltage, current, two stencil rows; ||F||^2 and the conductance cosh are FP32); the
     // pair form 6 (its two final additions and the FP64 norm); the zero state none
     prof_end(h, t0, MCA_FAM_RESIDUAL, -1,
-             cells * ((zero_state ? 36.0 : 48.0) + (tc ? 4.0 : 0.0)),
+             cells * ((zero_state ? (f32 ? 20.0 : 36.0) : 48.0) + (tc ? 4.0 : 0.0)),
              cells * (zero_state ? 0.0 : (pair ? 6.0 : 15.0)), s);
     MCA_CUDA_TRY(cudaGetLastError());
     MCA_CUDA_TRY(cudaStreamSynchronize(s));
@@ -840,9 +850,6 @@ int solve_pass(mca_handle* h, int B, cudaStream_t s, bool from_guess = false) {
     for (int b = 0; b < B; ++b) n_active += hf[b] ? 1 : 0;
     prof_flush(h, [&](int k, bool) { return k == -2 ? undecided : entering; });
     if (n_active == 0) break;
-    // the first step from V = 0 solves to the loosest forcing term, eta0: with the
-    // tensor-core forms its Jacobian applies run in FP32 when eta0 allows it
-    const bool f32 = tc && zero_state && h->p.eta0 >= kF32ApplyMinEta;
     MCA_TRY(gmres_cycle(h, h->D, B, s, f32));
     t0 = prof_begin(h, s);
     if (tc)

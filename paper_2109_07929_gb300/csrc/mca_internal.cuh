@@ -191,12 +191,15 @@ double pair_err_bound(double size2_sum);
 // ||F|| only when, within its error bound, it is still more than 10 times above the target,
 // and otherwise leaves the vector undecided (host flag 2, need_fp64); confirm: the FP64
 // residual for exactly those vectors.
+// sparse_f (zero_state only): F = -Y is stored in the first column of the top layer only
+// (its other entries are zero and left unwritten); the step's kernels must then read v_0
+// there only (kApplyF32Zero, the update passes' zs).
 void launch_residual_newton(const Grid& gr, const double* gmaps, const int* map_of,
                             const double* vin, const double* x, bool zero_state, double* F,
                             size_t fstride, __nv_bfloat16* xbf, int mp, int np, double* D,
                             double* part, int nblk, int B, VecCtl* ctl, SolverCfg cfg,
                             unsigned int* cnt, int32_t* host_flags, cudaStream_t s,
-                            bool pair = false, bool confirm = false);
+                            bool pair = false, bool confirm = false, bool sparse_f = false);
 void launch_init_basis(const double* F, double sign, double* V0, size_t vstride,
                        __nv_bfloat16* xbf, int mp, int np, int m, int n, const VecCtl* ctl,
                        int B, cudaStream_t s);
@@ -215,7 +218,9 @@ void launch_spmv_dots(const Grid& gr, const double* D, const double* z, size_t z
 //   kApplyF64: FP64 on z widened exactly;
 //   kApplyF32: plain FP32 (w rounded to FP32, then widened), for linear solves whose
 //     forcing term is loose (kF32ApplyMinEta).
-enum ApplyMode { kApplyF64 = 0, kApplyF32 = 1, kApplyPair = 2 };
+//   kApplyF32Zero: kApplyF32 in the Newton step from V = 0 whose v_0 is stored in the first
+//     column of the top layer only (the residual's sparse_f): the dots read it there only.
+enum ApplyMode { kApplyF64 = 0, kApplyF32 = 1, kApplyPair = 2, kApplyF32Zero = 3 };
 void launch_spmv_dots(const Grid& gr, const double* D, const float* z, size_t zstride,
                       double* w, const double* V, size_t vstride, int nk, double* part,
                       int nblk, int B, const VecCtl* ctl, unsigned int* cnt, double* h,
@@ -251,15 +256,17 @@ void launch_reduce_dots(const double* part, int nblk, int nk, double* h, int B,
 enum UpdPhase { UPD_PLAIN = 0, UPD_FIRST = 1, UPD_REORTH = 2 };
 // second-pass dots h2 = V^T u (j < nk) of the new vector u (u[b] at u + b*vstride), only
 // for the vectors marked by UPD_FIRST
+// zs: the Newton step from V = 0 with a sparse v_0 (see launch_residual_newton), ncols = n
 void launch_reorth_dots(const double* u, const double* V, size_t vstride, size_t n2, int nk,
                         double* part, int nblk, int B, const VecCtl* ctl, unsigned int* cnt,
-                        double* h2, cudaStream_t s);
+                        double* h2, cudaStream_t s, bool zs = false, int ncols = 1);
 // out[b] at out + b*ostride, w[b] at w + b*wstride; BF16 copy of out in xbf (may be NULL)
 void launch_update_norm(int phase, const double* w, size_t wstride, const double* V,
                         size_t vstride, size_t n2, int nk, const double* hc, double* part,
                         int nblk, int B, VecCtl* ctl, unsigned int* cnt, const double* h1,
                         int restart, int32_t* host_flags, double* out, size_t ostride,
-                        __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s);
+                        __nv_bfloat16* xbf, int mp, int np, int m, int n, cudaStream_t s,
+                        bool zs = false);
 void launch_lsq_update(double* x, const double* Z, size_t zstride, size_t n2, VecCtl* ctl,
                        int B, cudaStream_t s);
 void launch_lsq_update(double* x, const float* Z, size_t zstride, size_t n2, VecCtl* ctl,
