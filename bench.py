@@ -798,7 +798,8 @@ def gemm_tiles(solver):
     for name, (ws, bn, lp) in zip(names, solver.tile_config()):
         if ws < 0:
             return None
-        out[name] = {"kernel": "persistent" if ws else "tile-per-cta", "tile": f"128x{bn}",
+        kind = {0: "tile-per-cta", 1: "persistent", 2: "persistent, CTA pairs (cta_group::2)"}
+        out[name] = {"kernel": kind.get(ws, str(ws)), "tile": f"{256 if ws == 2 else 128}x{bn}",
                      "layers_per_tile": lp}
     return out
 

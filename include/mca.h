@@ -103,6 +103,10 @@ typedef struct mca_params {
 /* ---- flags --------------------------------------------------------------------------- */
 #define MCA_FLAG_GRAPHS 1      /* replay each GMRES iteration as a captured CUDA graph      */
 #define MCA_FLAG_AUTOTUNE 2    /* time the tensor-core tile widths at create, keep the best */
+#define MCA_FLAG_PAIR_GEMM 4   /* the two-SM form of the persistent GEMM (CTA pairs,        */
+                               /* cta_group::2 MMAs, 256 x 256 tiles) for transforms 1, 3    */
+                               /* and 4 where rows and columns are multiples of 256: with    */
+                               /* AUTOTUNE one more timed candidate, without it always used  */
 
 typedef struct mca_stats {
   int32_t status;            /* MCA_OK, MCA_ERR_NOT_CONVERGED or MCA_ERR_NONFINITE       */
@@ -117,8 +121,8 @@ typedef struct mca_handle mca_handle;
 
 /* Fill *p with the defaults: 1 S wires, 10 ohm driver and sense, 1 kohm terminations,
  * b = 2, MCA_PREC_BF16_SPLIT, restart 30, max_newton 20, max_batch 4, newton_rtol 1e-8,
- * eta0 1e-3, eta_max 1e-2, flags MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE.  rows/cols are
- * left at 0 and must be set. */
+ * eta0 1e-3, eta_max 1e-2, flags MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE | MCA_FLAG_PAIR_GEMM.
+ * rows/cols are left at 0 and must be set. */
 void mca_default_params(mca_params* p);
 
 /* Create a solver for one crossbar.

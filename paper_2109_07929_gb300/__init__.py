@@ -23,6 +23,7 @@ PREC_NONE = 5
 
 FLAG_GRAPHS = 1
 FLAG_AUTOTUNE = 2
+FLAG_PAIR_GEMM = 4
 
 DEVICE_SINH = 0
 DEVICE_YAKOPCIC = 1

@@ -76,21 +76,27 @@ struct Layout {
 };
 
 // Instantiations of the persistent kernel (BN, SPLIT, EPI, LP).
-#define MCA_WS_LIST(X)                 \
-  X(128, SPLIT_NONE, EPI_BF16, 1)      \
-  X(256, SPLIT_NONE, EPI_BF16, 1)      \
-  X(64, SPLIT_NONE, EPI_MODES, 2)      \
-  X(128, SPLIT_NONE, EPI_MODES, 2)     \
-  X(128, SPLIT_B, EPI_SPLIT, 1)        \
-  X(256, SPLIT_B, EPI_SPLIT, 1)        \
-  X(128, SPLIT_NONE, EPI_F64, 1)       \
-  X(256, SPLIT_NONE, EPI_F64, 1)       \
-  X(128, SPLIT_AB, EPI_F64, 1)         \
-  X(256, SPLIT_AB, EPI_F64, 1)         \
-  X(128, SPLIT_NONE, EPI_F32, 1)       \
-  X(256, SPLIT_NONE, EPI_F32, 1)       \
-  X(128, SPLIT_AB, EPI_F32, 1)         \
-  X(256, SPLIT_AB, EPI_F32, 1)
+#define MCA_WS_LIST(X)                    \
+  X(128, SPLIT_NONE, EPI_BF16, 1, 1)      \
+  X(256, SPLIT_NONE, EPI_BF16, 1, 1)      \
+  X(64, SPLIT_NONE, EPI_MODES, 2, 1)      \
+  X(128, SPLIT_NONE, EPI_MODES, 2, 1)     \
+  X(128, SPLIT_B, EPI_SPLIT, 1, 1)        \
+  X(256, SPLIT_B, EPI_SPLIT, 1, 1)        \
+  X(128, SPLIT_NONE, EPI_F64, 1, 1)       \
+  X(256, SPLIT_NONE, EPI_F64, 1, 1)       \
+  X(128, SPLIT_AB, EPI_F64, 1, 1)         \
+  X(256, SPLIT_AB, EPI_F64, 1, 1)         \
+  X(128, SPLIT_NONE, EPI_F32, 1, 1)       \
+  X(256, SPLIT_NONE, EPI_F32, 1, 1)       \
+  X(128, SPLIT_AB, EPI_F32, 1, 1)         \
+  X(256, SPLIT_AB, EPI_F32, 1, 1)         \
+  X(256, SPLIT_NONE, EPI_BF16, 1, 2)      \
+  X(256, SPLIT_B, EPI_SPLIT, 1, 2)        \
+  X(256, SPLIT_NONE, EPI_F64, 1, 2)       \
+  X(256, SPLIT_AB, EPI_F64, 1, 2)         \
+  X(256, SPLIT_NONE, EPI_F32, 1, 2)       \
+  X(256, SPLIT_AB, EPI_F32, 1, 2)
 
 // Instantiations of the one-CTA-per-tile kernel (BN, SPLIT, EPI).
 #define MCA_TC_LIST(X)                 \
@@ -333,13 +339,22 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // per-mode 2x2 epilogue), LP = 1 makes twice as many single-layer tiles (better balance
 // of the tiles over the SMs).  BF16 outputs are transposed through a small staging tile per
 // epilogue warp, one output at a time, and leave in 16-byte chunks.
+//
+// CG = 2: a cluster of two CTAs on two SMs computes one 256 x BN tile of one layer with
+// pair MMAs (cta_group::2).  Each CTA loads its 128 rows of A and half of B's BN rows, so a
+// stage carries a third fewer bytes per MMA than with CG = 1 and more stages fit; each
+// CTA's TMEM holds its 128 output rows.  Both CTAs' TMA loads of a stage complete on the
+// even CTA's stage barrier, which expects the bytes of both; the even CTA's thread issues
+// the MMAs; their completions arrive at both CTAs' barriers (multicast commit); the odd
+// CTA's epilogue warps report a drained accumulator to the even CTA.
 constexpr int kWsSmemMax = 227 * 1024;
 
-template <int BN, int SPLIT, int EPI, int LP>
+template <int BN, int SPLIT, int EPI, int LP, int CG = 1>
 struct WsLayout {
+  static_assert(CG == 1 || (CG == 2 && LP == 1), "CTA pairs take single-layer tiles");
   static constexpr int BKT = SPLIT ? BK_SPLIT : BK;
   static constexpr int A_BYTES = BM * BKT * 2;
-  static constexpr int B_BYTES = BN * BKT * 2;
+  static constexpr int B_BYTES = (BN / CG) * BKT * 2;      // this CTA's rows of B
   static constexpr int HALF = LP * A_BYTES + B_BYTES;      // hi words: LP layers of A, B
   static constexpr int STAGE = SPLIT == SPLIT_AB ? 2 * HALF :
                                (SPLIT == SPLIT_B ? HALF + B_BYTES : HALF);
@@ -362,12 +377,23 @@ struct WsLayout {
   static_assert(SMEM <= kWsSmemMax, "shared memory plan too large");
 };
 
-template <int BN, int SPLIT, int EPI, int LP>
-__global__ void __launch_bounds__(WsLayout<BN, SPLIT, EPI, LP>::THREADS, 1)
+template <int CG>
+__device__ __forceinline__ void umma_cg(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t acc) {
+  if constexpr (CG == 2) umma_pair(d, a, b, idesc, acc); else umma(d, a, b, idesc, acc);
+}
+
+template <int CG>
+__device__ __forceinline__ void commit_cg(uint64_t* bar) {
+  if constexpr (CG == 2) umma_commit_pair(bar); else umma_commit(bar);
+}
+
+template <int BN, int SPLIT, int EPI, int LP, int CG>
+__global__ void __launch_bounds__(WsLayout<BN, SPLIT, EPI, LP, CG>::THREADS, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAl,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBl,
           GemmEpi ep, int B) {
-  using L = WsLayout<BN, SPLIT, EPI, LP>;
+  using L = WsLayout<BN, SPLIT, EPI, LP, CG>;
   static_assert(LP == 2 || EPI != EPI_MODES, "the modes epilogue needs both layers in one tile");
   constexpr int BKT = L::BKT;
   extern __shared__ uint8_t smem_raw[];
@@ -379,10 +405,15 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   uint64_t* tempty = tfull + 2;                  // [2] accumulator drained
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // CG = 2: this CTA's rank in the pair; the even CTA issues the MMAs
+  const uint32_t rank = (CG == 2) ? cluster_ctarank() : 0u;
+  const bool issuer = (rank == 0);
+  const int first = (CG == 2) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int step = (CG == 2) ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
-  // tiles: column tile fastest (neighbouring CTAs share their A rows in L2), then row
-  // tile, then layer (LP = 1), then vector
-  const int tr = ep.R / BM, tc = ep.C / BN;
+  // tiles (of BM * CG rows): column tile fastest (neighbouring CTAs share their A rows in
+  // L2), then row tile, then layer (LP = 1), then vector
+  const int tr = ep.R / (BM * CG), tc = ep.C / BN;
   const int per_vec = tr * tc * (LP == 1 ? 2 : 1);
   const int ntiles = per_vec * B;
   const int nkb = ep.K / BKT;
@@ -394,7 +425,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       layer = u / (tr * tc);
       u -= layer * tr * tc;
     }
-    r0 = (u / tc) * BM;
+    r0 = (u / tc) * (BM * CG);
     c0 = (u % tc) * BN;
   };
   auto active = [&](int b) { return ep.ctl == nullptr || ep.ctl[b].gm_active; };
@@ -406,19 +437,29 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], L::EW);
+      mbar_init(&tempty[a], L::EW * CG);        // CG = 2: both CTAs' epilogue warps
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"((uint32_t)L::TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    // CG = 2: one warp of each CTA allocates the same columns in both
+    if (CG == 2) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"((uint32_t)L::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"((uint32_t)L::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if (CG == 2) cluster_sync();      // both CTAs' barriers initialised before any remote arrive
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -427,11 +468,13 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (lane == 0) {
       int it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int t = first; t < ntiles && ok; t += step) {
         int b, layer, r0, c0;
         decode(t, b, layer, r0, c0);
         if (!active(b)) continue;
-        const int row0 = (2 * b + layer) * ep.R + r0;     // first A row (layer 0 of LP = 2)
+        // first A row (layer 0 of LP = 2; this CTA's half of a pair tile)
+        const int row0 = (2 * b + layer) * ep.R + r0 + (int)rank * BM;
+        const int cb = c0 + (int)rank * (BN / CG);        // this CTA's rows of B
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % L::STAGES;
           const uint32_t ph = (uint32_t)(it / L::STAGES) & 1u;
@@ -441,37 +484,64 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             break;
           }
           uint8_t* st = smem + s * L::STAGE;
-          mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
           const int k0 = kb * BKT;
+          if (CG == 2) {
+            // both CTAs' bytes complete on the even CTA's barrier, which expects them all
+            if (issuer) mbar_expect_tx(&full[s], (uint32_t)(2 * L::STAGE));
+            const uint32_t bar = peer_addr(&full[s], 0);
+            tma_load_2d_pair(st, &tmA, k0, row0, bar);
+            tma_load_2d_pair(st + L::A_BYTES, &tmB, k0, cb, bar);
+            if (SPLIT == SPLIT_AB) {
+              tma_load_2d_pair(st + L::HALF, &tmAl, k0, row0, bar);
+              tma_load_2d_pair(st + L::HALF + L::A_BYTES, &tmBl, k0, cb, bar);
+            } else if (SPLIT == SPLIT_B) {
+              tma_load_2d_pair(st + L::HALF, &tmBl, k0, cb, bar);
+            }
+            continue;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
 #pragma unroll
           for (int l = 0; l < LP; ++l)
             tma_load_2d(st + l * L::A_BYTES, &tmA, k0, row0 + l * ep.R, &full[s]);
-          tma_load_2d(st + LP * L::A_BYTES, &tmB, k0, c0, &full[s]);
+          tma_load_2d(st + LP * L::A_BYTES, &tmB, k0, cb, &full[s]);
           if (SPLIT == SPLIT_AB) {
             uint8_t* sl = st + L::HALF;
 #pragma unroll
             for (int l = 0; l < LP; ++l)
               tma_load_2d(sl + l * L::A_BYTES, &tmAl, k0, row0 + l * ep.R, &full[s]);
-            tma_load_2d(sl + LP * L::A_BYTES, &tmBl, k0, c0, &full[s]);
+            tma_load_2d(sl + LP * L::A_BYTES, &tmBl, k0, cb, &full[s]);
           } else if (SPLIT == SPLIT_B) {
-            tma_load_2d(st + L::HALF, &tmBl, k0, c0, &full[s]);
+            tma_load_2d(st + L::HALF, &tmBl, k0, cb, &full[s]);
+          }
+        }
+      }
+      if (CG == 2 && ok) {
+        // the pair MMAs' completions still due to arrive at this CTA's stage barriers: wait
+        // for them, so that no arrive reaches a CTA that has exited
+        for (int i = 0; i < L::STAGES; ++i, ++it) {
+          if (!mbar_wait(&empty[it % L::STAGES], ((uint32_t)(it / L::STAGES) & 1u) ^ 1u)) {
+            record_error(ep.err, MCA_ERR_TIMEOUT);
+            break;
           }
         }
       }
     }
+  } else if (warp == 1 && !issuer) {
+    // CG = 2, odd CTA: the even CTA's thread issues the pair's MMAs
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread)
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      constexpr uint32_t idesc = idesc_bf16(BM * CG, BN);
       int it = 0, tl = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int t = first; t < ntiles && ok; t += step) {
         int b, layer, r0, c0;
         decode(t, b, layer, r0, c0);
         if (!active(b)) continue;
         const int acc = tl & 1;
         const uint32_t aph = (uint32_t)(tl >> 1) & 1u;
-        if (!mbar_wait(&tempty[acc], aph ^ 1u)) {
+        if (!(CG == 2 ? mbar_wait_cluster(&tempty[acc], aph ^ 1u)
+                      : mbar_wait(&tempty[acc], aph ^ 1u))) {
           record_error(ep.err, MCA_ERR_TIMEOUT);
           break;
         }
@@ -495,22 +565,22 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
             for (int l = 0; l < LP; ++l) {
               const uint64_t ad = tile_desc<BKT>(st + l * L::A_BYTES + off);
-              umma(dacc + l * BN, ad, bd, idesc, accf);
+              umma_cg<CG>(dacc + l * BN, ad, bd, idesc, accf);
               if (SPLIT == SPLIT_AB) {
                 const uint8_t* sl = st + L::HALF;
                 const uint64_t adl = tile_desc<BKT>(sl + l * L::A_BYTES + off);
                 const uint64_t bdl = tile_desc<BKT>(sl + LP * L::A_BYTES + off);
-                umma(dacc + l * BN, adl, bd, idesc, 1u);
-                umma(dacc + l * BN, ad, bdl, idesc, 1u);
+                umma_cg<CG>(dacc + l * BN, adl, bd, idesc, 1u);
+                umma_cg<CG>(dacc + l * BN, ad, bdl, idesc, 1u);
               } else if (SPLIT == SPLIT_B) {
-                umma(dacc + l * BN, ad, tile_desc<BKT>(st + L::HALF + off), idesc, 1u);
+                umma_cg<CG>(dacc + l * BN, ad, tile_desc<BKT>(st + L::HALF + off), idesc, 1u);
               }
             }
           }
-          umma_commit(&empty[s]);
+          commit_cg<CG>(&empty[s]);
         }
         if (!ok) break;
-        umma_commit(&tfull[acc]);
+        commit_cg<CG>(&tfull[acc]);
         ++tl;
       }
     }
@@ -525,7 +595,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __nv_bfloat16* stg =
         reinterpret_cast<__nv_bfloat16*>(smem + L::STG_OFF + (warp - 2) * L::STG_WARP);
     int tl = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = first; t < ntiles; t += step) {
       int b, layer, r0, c0;
       decode(t, b, layer, r0, c0);
       if (!active(b)) continue;
@@ -537,7 +607,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         break;
       }
       tc_fence_after();
-      const int r = r0 + rl;
+      const int r = r0 + (int)rank * BM + rl;
       const bool r_ok = r < ep.R_valid;
       const uint32_t lane_base =
           tmem + (uint32_t)(acc * L::ACC_COLS) + ((uint32_t)(q * 32) << 16);
@@ -608,7 +678,8 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
             __syncwarp();
             __nv_bfloat16* out = static_cast<__nv_bfloat16*>(lo ? ep.out_lo : ep.out);
-            const size_t base = (size_t)b * ep.o_bs + (size_t)(layer + l) * ep.o_ls + r0 + q * 32;
+            const size_t base = (size_t)b * ep.o_bs + (size_t)(layer + l) * ep.o_ls + r0 +
+                                (int)rank * BM + q * 32;
 #pragma unroll
             for (int i = 0; i < CW / 8; ++i) {
               const int id = lane + 32 * i;
@@ -624,19 +695,29 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       // accumulator drained: the MMA warp may reuse it
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
-                                      smem_u32(&tempty[acc]))
-                                  : "memory");
+      if (lane == 0) {
+        if (CG == 2 && !issuer)
+          mbar_arrive_cluster(peer_addr(&tempty[acc], 0));
+        else
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[acc]))
+                       : "memory");
+      }
       ++tl;
     }
   }
   tc_fence_before();
   __syncthreads();
+  if (CG == 2) cluster_sync();      // no remote arrive or pair MMA still due at either CTA
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"((uint32_t)L::TMEM_COLS)
-                 : "memory");
+    if (CG == 2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"((uint32_t)L::TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"((uint32_t)L::TMEM_COLS)
+                   : "memory");
   }
 }
 
@@ -695,11 +776,34 @@ cudaError_t launch_one(const CUtensorMap& a, const CUtensorMap& al, const CUtens
 constexpr int kMaxDevices = 64;
 std::atomic<int> g_num_sms[kMaxDevices] = {};
 
-template <int BN, int SPLIT, int EPI, int LP>
+// Co-resident two-CTA clusters of each pair instantiation per device ordinal (set by
+// configure_all before any launch, 0 = not known: the launch is refused).
+template <int BN, int SPLIT, int EPI, int LP, int CG>
+std::atomic<int> g_pair_clusters[kMaxDevices] = {};
+
+template <int BN, int SPLIT, int EPI, int LP, int CG>
+cudaLaunchConfig_t pair_config(int grid, cudaStream_t s, cudaLaunchAttribute* at) {
+  using L = WsLayout<BN, SPLIT, EPI, LP, CG>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(L::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = L::SMEM;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int BN, int SPLIT, int EPI, int LP, int CG>
 cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& al, const CUtensorMap& bm,
                       const CUtensorMap& bml, const GemmEpi& ep, int B, cudaStream_t s) {
-  using L = WsLayout<BN, SPLIT, EPI, LP>;
-  if (ep.R % BM != 0 || ep.C % BN != 0 || ep.K % L::BKT != 0) return cudaErrorInvalidValue;
+  using L = WsLayout<BN, SPLIT, EPI, LP, CG>;
+  if (ep.R % (BM * CG) != 0 || ep.C % BN != 0 || ep.K % L::BKT != 0)
+    return cudaErrorInvalidValue;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return cudaErrorInvalidValue;
@@ -710,9 +814,18 @@ cudaError_t launch_ws(const CUtensorMap& a, const CUtensorMap& al, const CUtenso
       return cudaErrorInvalidValue;
     g_num_sms[dev].store(nsm, std::memory_order_relaxed);
   }
-  const int ntiles = (ep.R / BM) * (ep.C / BN) * (LP == 1 ? 2 : 1) * B;
+  const int ntiles = (ep.R / (BM * CG)) * (ep.C / BN) * (LP == 1 ? 2 : 1) * B;
+  if (CG == 2) {
+    // one cluster per co-resident pair of SMs, each walking the pair tiles
+    const int ncl = g_pair_clusters<BN, SPLIT, EPI, LP, CG>[dev].load(std::memory_order_relaxed);
+    if (ncl <= 0) return cudaErrorInvalidValue;
+    const int grid = 2 * (ntiles < ncl ? ntiles : ncl);
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = pair_config<BN, SPLIT, EPI, LP, CG>(grid, s, at);
+    return cudaLaunchKernelEx(&cfg, k_gemm_ws<BN, SPLIT, EPI, LP, CG>, a, al, bm, bml, ep, B);
+  }
   const int grid = ntiles < nsm ? ntiles : nsm;
-  k_gemm_ws<BN, SPLIT, EPI, LP><<<grid, L::THREADS, L::SMEM, s>>>(a, al, bm, bml, ep, B);
+  k_gemm_ws<BN, SPLIT, EPI, LP, CG><<<grid, L::THREADS, L::SMEM, s>>>(a, al, bm, bml, ep, B);
   return cudaGetLastError();
 }
 
@@ -792,12 +905,12 @@ cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtenso
   return cudaErrorInvalidValue;
 }
 
-cudaError_t gemm_ws(int bn, int lp, int split, int epi, const CUtensorMap& a,
+cudaError_t gemm_ws(int bn, int lp, int cg, int split, int epi, const CUtensorMap& a,
                     const CUtensorMap& al, const CUtensorMap& bm, const CUtensorMap& bml,
                     const GemmEpi& ep, int B, cudaStream_t s) {
-#define MCA_WS_CASE(BN_, SPLIT_, EPI_, LP_)                                  \
-  if (bn == BN_ && split == SPLIT_ && epi == EPI_ && lp == LP_)              \
-    return launch_ws<BN_, SPLIT_, EPI_, LP_>(a, al, bm, bml, ep, B, s);
+#define MCA_WS_CASE(BN_, SPLIT_, EPI_, LP_, CG_)                                  \
+  if (bn == BN_ && split == SPLIT_ && epi == EPI_ && lp == LP_ && cg == CG_)      \
+    return launch_ws<BN_, SPLIT_, EPI_, LP_, CG_>(a, al, bm, bml, ep, B, s);
   MCA_WS_LIST(MCA_WS_CASE)
 #undef MCA_WS_CASE
   return cudaErrorInvalidValue;
@@ -815,16 +928,40 @@ cudaError_t configure_all() {
   }
   MCA_TC_LIST(MCA_TC_CFG)
 #undef MCA_TC_CFG
-#define MCA_WS_CFG(BN_, SPLIT_, EPI_, LP_)                                              \
-  {                                                                                     \
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_ws<BN_, SPLIT_, EPI_, LP_>,             \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                         WsLayout<BN_, SPLIT_, EPI_, LP_>::SMEM);       \
-    if (e != cudaSuccess) return e;                                                     \
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return cudaErrorInvalidValue;
+#define MCA_WS_CFG(BN_, SPLIT_, EPI_, LP_, CG_)                                        \
+  {                                                                                    \
+    auto kern = k_gemm_ws<BN_, SPLIT_, EPI_, LP_, CG_>;                                \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         WsLayout<BN_, SPLIT_, EPI_, LP_, CG_>::SMEM); \
+    if (e != cudaSuccess) return e;                                                    \
+    if (CG_ == 2) {                                                                    \
+      cudaLaunchAttribute at[1];                                                       \
+      const cudaLaunchConfig_t cfg = pair_config<BN_, SPLIT_, EPI_, LP_, CG_>(2, 0, at); \
+      int ncl = 0;                                                                     \
+      if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess) {           \
+        (void)cudaGetLastError();   /* no pair form on this device */                  \
+        ncl = 0;                                                                       \
+      }                                                                                \
+      g_pair_clusters<BN_, SPLIT_, EPI_, LP_, CG_>[dev].store(ncl);                    \
+    }                                                                                  \
   }
   MCA_WS_LIST(MCA_WS_CFG)
 #undef MCA_WS_CFG
   return cudaSuccess;
+}
+
+bool pair_available() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+  bool ok = true;
+#define MCA_WS_PAIR_OK(BN_, SPLIT_, EPI_, LP_, CG_) \
+  if (CG_ == 2) ok = ok && g_pair_clusters<BN_, SPLIT_, EPI_, LP_, CG_>[dev].load() > 0;
+  MCA_WS_LIST(MCA_WS_PAIR_OK)
+#undef MCA_WS_PAIR_OK
+  return ok;
 }
 
 cudaError_t wait_selftest(unsigned long long limit_ns, int* err, cudaStream_t s) {

@@ -103,7 +103,8 @@ struct mca_handle {
   // B operands for 128-, 64- and 256-column tiles
   CUtensorMap mB1[3], mB2[3], mB3h[3], mB3l[3], mB4h[3], mB4l[3];
   // GEMM form of each transform: ws = 1 persistent warp-specialised kernel (tiles of
-  // 128 x bn with lp layers), ws = 0 one CTA per 128 x bn two-layer tile
+  // 128 x bn with lp layers), ws = 2 its two-SM form (CTA pairs over 256 x bn tiles of one
+  // layer), ws = 0 one CTA per 128 x bn two-layer tile
   int bn[4] = {128, 128, 128, 128};
   int ws[4] = {0, 0, 0, 0};
   int lp[4] = {2, 2, 2, 2};
@@ -236,7 +237,7 @@ int validate(const mca_params* p) {
     set_error("gmres_restart in 1..30, max_newton >= 1, max_batch in 1..64");
     return MCA_ERR_INVALID_ARG;
   }
-  if (p->flags & ~(MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE)) {
+  if (p->flags & ~(MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE | MCA_FLAG_PAIR_GEMM)) {
     set_error("unknown flag bits");
     return MCA_ERR_INVALID_ARG;
   }
@@ -297,6 +298,12 @@ int setup_tc(mca_handle* h) {
     h->ws[s] = 1;
     h->lp[s] = (s == 1) ? 2 : 1;
     if (s != 1) h->bn[s] = 128;
+    // two-SM form asked for without the autotuner: wherever the tile fits
+    if (s != 1 && (h->p.flags & MCA_FLAG_PAIR_GEMM) && !(h->p.flags & MCA_FLAG_AUTOTUNE) &&
+        R[s] % 256 == 0 && C[s] % 256 == 0 && tc::pair_available()) {
+      h->ws[s] = 2;
+      h->bn[s] = 256;
+    }
   }
   h->tc_ok = true;
   return MCA_OK;
@@ -457,11 +464,14 @@ int tc_step(mca_handle* h, int step, bool split, void* zout, size_t zstride, int
             const VecCtl* ctl, cudaStream_t s, int prof_k, int kidx = -1, bool z32 = false) {
   const int m = h->m, n = h->n;
   const size_t mn = h->mn, mp = h->mp, np = h->np;
-  auto q = [](int bn) { return bn == 128 ? 0 : (bn == 64 ? 1 : 2); };
   const int bn = h->bn[step];
+  // B maps by box rows (the two-SM form loads bn / 2 rows of B per CTA)
+  const int boxb = (h->ws[step] == 2) ? bn / 2 : bn;
+  auto q = [boxb](int) { return boxb == 128 ? 0 : (boxb == 64 ? 1 : 2); };
   auto run = [&](int sp_, int epi, const CUtensorMap& a, const CUtensorMap& al,
                  const CUtensorMap& bm, const CUtensorMap& bml, const tc::GemmEpi& ep) {
-    return h->ws[step] ? tc::gemm_ws(bn, h->lp[step], sp_, epi, a, al, bm, bml, ep, B, s)
+    return h->ws[step] ? tc::gemm_ws(bn, h->lp[step], h->ws[step], sp_, epi, a, al, bm, bml,
+                                     ep, B, s)
                        : tc::gemm(bn, sp_, epi, a, al, bm, bml, ep, B, s);
   };
   // executed MMA FLOPs per vector: 2 layers x 2 M N K; when split, two products in
@@ -540,13 +550,17 @@ int autotune_tiles(mca_handle* h) {
     int best_bn = h->bn[step], best_ws = h->ws[step], best_lp = h->lp[step];
     const int Cs = (step == 0 || step == 2) ? h->np : h->mp;
     // candidates (ws, bn, lp): the one-CTA-per-tile kernel with 128 / 64 columns, the
-    // persistent kernel with its instantiated tile shapes
+    // persistent kernel with its instantiated tile shapes, its two-SM form (256-row tiles)
     const int cands[][3] = {{0, 128, 2}, {0, 64, 2}, {1, 128, 1}, {1, 256, 1},
-                            {1, 64, 2}, {1, 128, 2}};
+                            {1, 64, 2}, {1, 128, 2}, {2, 256, 1}};
+    const int Rs = (step == 0 || step == 2) ? h->mp : h->np;
     for (const auto& cd : cands) {
       const int ws = cd[0], bn = cd[1], lp = cd[2];
       if (Cs % bn != 0) continue;
-      if (ws == 1 && ((step == 1) != (lp == 2))) continue;   // modes: 2 layers; others: 1
+      if (ws >= 1 && ((step == 1) != (lp == 2))) continue;   // modes: 2 layers; others: 1
+      if (ws == 2 && (Rs % 256 != 0 || !(h->p.flags & MCA_FLAG_PAIR_GEMM) ||
+                      !tc::pair_available()))
+        continue;
       h->ws[step] = ws;
       h->bn[step] = bn;
       h->lp[step] = lp;
@@ -904,7 +918,7 @@ void mca_default_params(mca_params* p) {
   p->newton_rtol = 1e-8;
   p->eta0 = 1e-3;
   p->eta_max = 1e-2;
-  p->flags = MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE;
+  p->flags = MCA_FLAG_GRAPHS | MCA_FLAG_AUTOTUNE | MCA_FLAG_PAIR_GEMM;
 }
 
 const char* mca_strerror(int code) {
@@ -1725,9 +1739,10 @@ int mca_precond_apply(mca_handle* h, const double* a, const double* r, double* z
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MCA_TRY(load_ctl_a(h, a, nvec, s));
-  if (is_tc(precision))
+  if (is_tc(precision)) {
     tc::cast_pad(r, h->n2, h->Xbf, h->m, h->n, h->mp, h->np, nvec, s);
     count_launches(1);
+  }
   MCA_TRY(precond_apply(h, precision, r, h->n2, z, h->n2, nvec, h->ctl, s));
   MCA_CUDA_TRY(cudaStreamSynchronize(s));
   return check_device_error(h);

@@ -55,11 +55,15 @@ cudaError_t gemm(int bn, int split, int epi, const CUtensorMap& a, const CUtenso
                  const CUtensorMap& bm, const CUtensorMap& bml, const GemmEpi& ep, int B,
                  cudaStream_t s);
 // Persistent warp-specialised form: one CTA per SM over tiles of 128 x bn with lp layers
-// (lp = 2 for the modes epilogues, which need both layers of a mode in one CTA).
-cudaError_t gemm_ws(int bn, int lp, int split, int epi, const CUtensorMap& a,
+// (lp = 2 for the modes epilogues, which need both layers of a mode in one CTA); cg = 2:
+// pairs of CTAs on two SMs over tiles of 256 x bn (bn = 256, lp = 1), B's maps with boxes
+// of bn / 2 rows.
+cudaError_t gemm_ws(int bn, int lp, int cg, int split, int epi, const CUtensorMap& a,
                     const CUtensorMap& al, const CUtensorMap& bm, const CUtensorMap& bml,
                     const GemmEpi& ep, int B, cudaStream_t s);
 cudaError_t configure_all();
+// After configure_all on this device: every two-SM instantiation can be launched.
+bool pair_available();
 cudaError_t wait_selftest(unsigned long long limit_ns, int* err, cudaStream_t s);
 void cast_pad(const double* x, size_t xstride, __nv_bfloat16* xbf, int m, int n, int mp,
               int np, int B, cudaStream_t s);

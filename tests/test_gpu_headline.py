@@ -68,9 +68,11 @@ def test_headline_configuration_against_oracle():
     p = ws.params
     tiles, outs, stats = _solve_two_handles(ws, 1e-8)
     for cfg in tiles:
-        # (persistent, tile columns, layers per tile) of transforms 1..4
+        # (form, tile columns, layers per tile) of transforms 1..4: the autotuner picks the
+        # persistent kernel with 256-column single-layer tiles, on one SM (form 1) or on CTA
+        # pairs (form 2) by timing; the modes transform stays on one SM with both layers
         for s in (0, 2, 3):
-            assert cfg[s] == (1, 256, 1), cfg
+            assert cfg[s] in ((1, 256, 1), (2, 256, 1)), cfg
         assert cfg[1][0] == 1, cfg
     assert len(stats) == H * B
     for st in stats:
