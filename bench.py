@@ -507,7 +507,8 @@ def run_ours(args):
     e2e = {"value": world * ke * P * S / te, "unit": "solves/s",
            "h2d_bytes_per_step": P * S * (m * 8 + 4),
            "d2h_bytes_per_step": P * S * (2 * m * n + n) * 8 + P * S * mca.ctypes.sizeof(mca.Stats),
-           "solves_per_call": P * S, "calls": ke}
+           "solves_per_call": P * S, "calls": ke,
+           "d2h_gbs_of_this_host": d2h_rate(torch, dev)}
 
     # ---- per-family kernel timing (CUDA events on the solve stream, separate pass of one
     # handle alone: the concurrent handles' kernels overlap, which per-launch events cannot
@@ -802,6 +803,24 @@ def gemm_tiles(solver):
         out[name] = {"kernel": kind.get(ws, str(ws)), "tile": f"{256 if ws == 2 else 128}x{bn}",
                      "layers_per_tile": lp}
     return out
+
+
+def d2h_rate(torch, dev, nbytes=1 << 30):
+    """Device-to-host copy rate of this machine into pinned memory (GB/s): the end-to-end figure
+    moves every solve's node voltages to the host, so where this link is slow it bounds e2e."""
+    d = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+    h = torch.empty(nbytes // 8, dtype=torch.float64).pin_memory()
+    st = torch.cuda.current_stream()
+    h.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(2):
+        h.copy_(d, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return round(2 * nbytes / (e0.elapsed_time(e1) * 1e6), 1)
 
 
 # Batches per end-to-end call (see the e2e block in run_bench).
