@@ -203,6 +203,14 @@ def workload_config(args, batch):
     }
 
 
+def step_config(args):
+    """The `config` both arms print: one step solves --handles x --batch vectors of the
+    workload (the reference arm times a bounded sample of that step's solves)."""
+    H, B = max(1, args.handles), args.batch
+    return dict(workload_config(args, H * B), handles=H, batch_per_handle=B,
+                profile_pass="kernel_breakdown and roofline: one handle alone")
+
+
 def make_workload(args, rank, nvec):
     """The timed crossbars: four log-uniform crossbars with sinh devices and V_in >= 0
     (seeds 4r .. 4r + 3), or one Yakopcic-form crossbar (a2/a1 = --neg-ratio) with inputs
@@ -229,10 +237,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, 1),
+        "config": step_config(args),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} oracle solves of the {args.size}^2 crossbars, "
-                                   "one input vector each"},
+                                   "one input vector each (one solve per step out of the "
+                                   "step's handles x batch)"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -578,8 +587,7 @@ def run_ours(args):
         "warmup": W, "ms_per_step": 1000 * t / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+bf16" if prec in (mca.PREC_BF16, mca.PREC_BF16_SPLIT) else "f64",
         "data": "synthetic",
-        "config": dict(workload_config(args, S), handles=H, batch_per_handle=B,
-                       profile_pass="kernel_breakdown and roofline: one handle alone"),
+        "config": step_config(args),
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
         "precond_tflops": precond_tflops, "precond_frac": precond_frac,
         "kernel_breakdown": breakdown,
