@@ -188,20 +188,16 @@ __device__ __forceinline__ F2 current_pair(const Grid& gr, float d, float dl) {
   return split2(sinh(x) * gr.inv_b);
 }
 
+// The pair cell from its voltages already split: vt, vb at (i, j), tl, tr the top layer at
+// j - 1, j + 1 and bu, bd the bottom layer at i - 1, i + 1 (zero pairs off the grid).
 template <bool YAK>
-__device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j, int c,
-                                                   const double* __restrict__ Vt,
-                                                   const double* __restrict__ Vb, double g64,
-                                                   double vin_i, double& ft, double& fb,
-                                                   double& dg, float& dgf, float& size2,
-                                                   float& ft32, float& fb32) {
+__device__ __forceinline__ void cell_residual_pair_split(const Grid& gr, int i, int j, F2 vt,
+                                                         F2 vb, F2 tl, F2 tr, F2 bu, F2 bd,
+                                                         double g64, double vin_i, double& ft,
+                                                         double& fb, double& dg, float& dgf,
+                                                         float& size2, float& ft32,
+                                                         float& fb32) {
   const int m = gr.m, n = gr.n;
-  const F2 z0{0.f, 0.f};
-  const F2 vt = split2(Vt[c]), vb = split2(Vb[c]);
-  const F2 tl = (j > 0) ? split2(Vt[c - 1]) : z0;
-  const F2 tr = (j < n - 1) ? split2(Vt[c + 1]) : z0;
-  const F2 bu = (i > 0) ? split2(Vb[c - n]) : z0;
-  const F2 bd = (i < m - 1) ? split2(Vb[c + n]) : z0;
   const bool jf = (j == 0), jl = (j == n - 1), iu = (i == 0), il = (i == m - 1);
   const F2 dt{jf ? gr.dt0f : (jl ? gr.dtlf : gr.dtmf), jf ? gr.dt0l : (jl ? gr.dtll : gr.dtml)};
   const F2 db{iu ? gr.db0f : (il ? gr.dblf : gr.dbmf), iu ? gr.db0l : (il ? gr.dbll : gr.dbml)};
@@ -259,6 +255,107 @@ __device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j,
   size2 = fmaf(szt, szt, fmaf(szb, szb, size2));
 }
 
+// The pair cell at c = i n + j, loading and splitting its own six voltages.
+template <bool YAK>
+__device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j, int c,
+                                                   const double* __restrict__ Vt,
+                                                   const double* __restrict__ Vb, double g64,
+                                                   double vin_i, double& ft, double& fb,
+                                                   double& dg, float& dgf, float& size2,
+                                                   float& ft32, float& fb32) {
+  const int m = gr.m, n = gr.n;
+  const F2 z0{0.f, 0.f};
+  const F2 vt = split2(Vt[c]), vb = split2(Vb[c]);
+  const F2 tl = (j > 0) ? split2(Vt[c - 1]) : z0;
+  const F2 tr = (j < n - 1) ? split2(Vt[c + 1]) : z0;
+  const F2 bu = (i > 0) ? split2(Vb[c - n]) : z0;
+  const F2 bd = (i < m - 1) ? split2(Vb[c + n]) : z0;
+  cell_residual_pair_split<YAK>(gr, i, j, vt, vb, tl, tr, bu, bd, g64, vin_i, ft, fb, dg, dgf,
+                                size2, ft32, fb32);
+}
+
+// Column-strip walk of the pair cells with shared-memory halo staging.  The top layer
+// couples a node to j - 1 and j + 1 in its row, the bottom layer to i - 1 and i + 1 in its
+// column, and a pair cell needs all six voltages as FP32 pairs; splitting one costs about
+// a few dozen integer instructions, and a cell that splits its own
+// neighbours splits every voltage three times (those splits were a third of the pair
+// cell's instructions).  Here the block's cells are columns of
+// strips kThreads wide: block bx of nblk owns the units [U bx / nblk, U (bx + 1) / nblk) of
+// the strip-major list of U = m * strips (strip, row) units, and each thread walks down its
+// column of each strip segment.  The bottom layer's rows i - 1, i, i + 1 stay split in
+// registers; the top layer's row is split once into shared memory, with one halo entry on
+// each side of the strip (threads 0 and kThreads - 1); the next row's voltages are loaded
+// before the current row is evaluated.  Each voltage is split about once (twice per segment
+// start for the bottom layer).  fn(i, j, c, vt, vb, tl, tr, bu, bd) evaluates cell
+// c = i n + j from its pairs.  Every thread of the block calls this: it synchronises once
+// per row (the row buffer alternates, so a row's writes never meet the previous row's
+// reads).
+__device__ __forceinline__ bool strip_walk_fits(int n) {
+  // lanes past n in the last strip idle: walk only when at least 3/4 of them work
+  const int strips = (n + kThreads - 1) / kThreads;
+  return 4 * n >= 3 * strips * kThreads;
+}
+
+template <typename Fn>
+__device__ __forceinline__ void pair_strip_walk(int m, int n, const double* __restrict__ Vt,
+                                                const double* __restrict__ Vb, int nblk,
+                                                Fn&& fn) {
+  __shared__ F2 row[2][kThreads + 2];
+  const F2 z0{0.f, 0.f};
+  const int strips = (n + kThreads - 1) / kThreads;
+  const long long U = (long long)m * strips;
+  long long u = U * blockIdx.x / nblk;
+  const long long u1 = U * (blockIdx.x + 1) / nblk;
+  const int t = threadIdx.x;
+  int buf = 0;
+  while (u < u1) {
+    const int st = (int)(u / m);
+    const int i0 = (int)(u - (long long)st * m);
+    const int i1 = (int)min((long long)m, (long long)i0 + (u1 - u));
+    const int j0 = st * kThreads;
+    const int j = j0 + t;
+    const bool col = j < n;
+    // halo columns of the top row: j0 - 1 (thread 0) and j0 + kThreads (the last thread)
+    const int jh = (t == 0) ? j0 - 1 : j0 + kThreads;
+    const bool halo = (t == 0 && j0 > 0) || (t == kThreads - 1 && jh < n);
+    const int hs = (t == 0) ? 0 : kThreads + 1;          // its shared-memory slot
+    F2 bu = z0, bc = z0;
+    // raw voltages of the current row: Vt[i][j], Vb[i + 1][j] and the halo Vt[i][jh]
+    double rt = 0.0, rb = 0.0, rh = 0.0;
+    if (col) {
+      if (i0 > 0) bu = split2(Vb[(size_t)(i0 - 1) * n + j]);
+      bc = split2(Vb[(size_t)i0 * n + j]);
+      rt = Vt[(size_t)i0 * n + j];
+      if (i0 < m - 1) rb = Vb[(size_t)(i0 + 1) * n + j];
+    }
+    if (halo) rh = Vt[(size_t)i0 * n + jh];
+    for (int i = i0; i < i1; ++i) {
+      const F2 vt = split2(rt);
+      const F2 bd = (i < m - 1) ? split2(rb) : z0;
+      const F2 hv = halo ? split2(rh) : z0;
+      if (i + 1 < i1) {
+        if (col) {
+          rt = Vt[(size_t)(i + 1) * n + j];
+          rb = (i + 1 < m - 1) ? Vb[(size_t)(i + 2) * n + j] : 0.0;
+        }
+        if (halo) rh = Vt[(size_t)(i + 1) * n + jh];
+      }
+      row[buf][t + 1] = vt;
+      if (halo) row[buf][hs] = hv;
+      __syncthreads();
+      if (col) {
+        const F2 tl = (j > 0) ? row[buf][t] : z0;
+        const F2 tr = (j < n - 1) ? row[buf][t + 2] : z0;
+        fn(i, j, i * n + j, vt, bc, tl, tr, bu, bd);
+      }
+      bu = bc;
+      bc = bd;
+      buf ^= 1;
+    }
+    u += i1 - i0;
+  }
+}
+
 __global__ void k_setup_vectors(Grid gr, const double* __restrict__ vin, VecCtl* ctl,
                                 int warm) {
   const int b = blockIdx.x;
@@ -298,24 +395,44 @@ k_residual(Grid gr, const double* __restrict__ gmap, const double* __restrict__ 
   const bool lin = (gr.b == 0.0);
   double sf = 0.0, sd = 0.0;
   float sdf = 0.f, ss = 0.f;
-  for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
-    const int i = c / n;
-    const int j = c - i * n;
-    double ft, fb, dg;
-    float dgf;
-    float f32a, f32b;
-    if constexpr (PAIR)
-      cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
-                              dg, dgf, ss, f32a, f32b);
-    else
-      cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
-                         dgf);
+  auto emit = [&](int c, double ft, double fb, double dg, float dgf) {
     Ft[c] = ft;
     Fb[c] = fb;
     Db[c] = dg;
     sf = fma(ft, ft, sf);
     sf = fma(fb, fb, sf);
     if (lin) sd += dg; else sdf += dgf;
+  };
+  bool walked = false;
+  if constexpr (PAIR) {
+    if (strip_walk_fits(n)) {
+      pair_strip_walk(m, n, Vt, Vb, nblk,
+                      [&](int i, int j, int c, F2 vt, F2 vb, F2 tl, F2 tr, F2 bu, F2 bd) {
+                        double ft, fb, dg;
+                        float dgf, f32a, f32b;
+                        cell_residual_pair_split<YAK>(gr, i, j, vt, vb, tl, tr, bu, bd, gmap[c],
+                                                      (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
+                                                      dgf, ss, f32a, f32b);
+                        emit(c, ft, fb, dg, dgf);
+                      });
+      walked = true;
+    }
+  }
+  if (!walked) {
+    for (int c = blockIdx.x * kThreads + threadIdx.x; c < mn; c += nblk * kThreads) {
+      const int i = c / n;
+      const int j = c - i * n;
+      double ft, fb, dg;
+      float dgf;
+      float f32a, f32b;
+      if constexpr (PAIR)
+        cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
+                                dg, dgf, ss, f32a, f32b);
+      else
+        cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
+                           dgf);
+      emit(c, ft, fb, dg, dgf);
+    }
   }
   sd += f2d_bits(sdf);
   double sz = f2d_bits(ss);
@@ -379,25 +496,9 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
   bool dnot32 = false;
   // grid-stride walk over the cells with (i, j) advanced incrementally (no division per
   // cell); the BF16 copy sits in the padded [layer][mp][np] layout at row offset i * np
-  const int S = nblk * kThreads;
-  const int Si = S / n, Sj = S - Si * n;
-  int c = blockIdx.x * kThreads + threadIdx.x;
-  int i = c / n, j = c - (c / n) * n;
-  for (; c < mn; c += S) {
-    double ft, fb, dg;
-    float dgf = 0.f, ft32, fb32;
-    if (ZERO) {
-      ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
-      fb = 0.0;
-      dg = gmap[c];
-      dgf = d2f_round(dg);
-    } else if (PAIR && use_pair) {
-      cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
-                              dg, dgf, ss, ft32, fb32);
-    } else {
-      cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
-                         dgf);
-    }
+  // the stores and sums of one cell (both cell forms and both walks)
+  auto emit = [&](int i, int j, int c, double ft, double fb, double dg, float dgf, float ft32,
+                  float fb32) {
     if (!sparse_f || j == 0) Ft[c] = ft;
     if (!sparse_f) Fb[c] = fb;
     Db[c] = dg;
@@ -430,11 +531,50 @@ k_residual_newton(Grid gr, const double* __restrict__ gmaps, const int* __restri
       }
     }
     if (lin) sd += dg; else sdf += dgf;
-    j += Sj;
-    i += Si;
-    if (j >= n) {
-      j -= n;
-      ++i;
+  };
+  bool walked = false;
+  if constexpr (PAIR && !ZERO) {
+    // pair cells of a grid whose columns fill the strips: split each voltage once
+    if (use_pair && strip_walk_fits(n)) {
+      pair_strip_walk(m, n, Vt, Vb, nblk,
+                      [&](int i, int j, int c, F2 vt, F2 vb, F2 tl, F2 tr, F2 bu, F2 bd) {
+                        double ft, fb, dg;
+                        float dgf, ft32, fb32;
+                        cell_residual_pair_split<YAK>(gr, i, j, vt, vb, tl, tr, bu, bd, gmap[c],
+                                                      (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
+                                                      dgf, ss, ft32, fb32);
+                        emit(i, j, c, ft, fb, dg, dgf, ft32, fb32);
+                      });
+      walked = true;
+    }
+  }
+  if (!walked) {
+    const int S = nblk * kThreads;
+    const int Si = S / n, Sj = S - Si * n;
+    int c = blockIdx.x * kThreads + threadIdx.x;
+    int i = c / n, j = c - (c / n) * n;
+    for (; c < mn; c += S) {
+      double ft, fb, dg;
+      float dgf = 0.f, ft32 = 0.f, fb32 = 0.f;
+      if (ZERO) {
+        ft = (j == 0) ? -gr.g_src * vinb[i] : 0.0;
+        fb = 0.0;
+        dg = gmap[c];
+        dgf = d2f_round(dg);
+      } else if (PAIR && use_pair) {
+        cell_residual_pair<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb,
+                                dg, dgf, ss, ft32, fb32);
+      } else {
+        cell_residual<YAK>(gr, i, j, c, Vt, Vb, gmap[c], (j == 0) ? vinb[i] : 0.0, ft, fb, dg,
+                           dgf);
+      }
+      emit(i, j, c, ft, fb, dg, dgf, ft32, fb32);
+      j += Sj;
+      i += Si;
+      if (j >= n) {
+        j -= n;
+        ++i;
+      }
     }
   }
   sd += f2d_bits(sdf);
