@@ -75,6 +75,10 @@ def parse_args():
     ap.add_argument("--batch-profile", choices=["c4", "small"], default=None,
                     help="only the persistent batched launch on the statistical mix (c4) "
                          "or its {64,128} subset (small), with per-phase timers")
+    ap.add_argument("--e2e-breakdown", action="store_true",
+                    help="only time one end-to-end call of the headline workload with device "
+                         "or host buffers, one or two passes per handle, with and without "
+                         "the voltage outputs, and the output copies alone")
     ap.add_argument("--table1", action="store_true",
                     help="GPU version of the paper's Table 1 (GMRES steps per preconditioner)")
     return ap.parse_args()
@@ -507,16 +511,19 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     ke = max(1, K // (2 * P))
+    call_ms = []
     e0.record(stream)
     for i in range(ke):
+        c0 = time.perf_counter()
         step_host(W + i * P)
+        call_ms.append(round(1e3 * (time.perf_counter() - c0), 1))
     e1.record(stream)
     torch.cuda.synchronize()
     te = job_time(e0.elapsed_time(e1) / 1000.0, pg)
     e2e = {"value": world * ke * P * S / te, "unit": "solves/s",
            "h2d_bytes_per_step": P * S * (m * 8 + 4),
            "d2h_bytes_per_step": P * S * (2 * m * n + n) * 8 + P * S * mca.ctypes.sizeof(mca.Stats),
-           "solves_per_call": P * S, "calls": ke,
+           "solves_per_call": P * S, "calls": ke, "call_ms": call_ms,
            "d2h_gbs_of_this_host": d2h_rate(torch, dev)}
 
     # ---- per-family kernel timing (CUDA events on the solve stream, separate pass of one
@@ -867,6 +874,74 @@ def committed_traffic(fam, fp):
     return ent.get("bytes_per_launch")
 
 
+def run_e2e_breakdown(args, reps=3):
+    """Where an end-to-end call spends its time: solve_many on --handles x --batch vectors
+    per pass (the headline's handles), outputs in device memory or pinned host memory, one
+    or two passes per handle per call, with and without the node-voltage outputs; then the
+    device-to-host copy of one call's voltages alone (one stream per handle).  Median
+    wall time of `reps` calls after one warm-up call, each call returning with its outputs
+    in place."""
+    import torch
+    import paper_2109_07929_gb300 as mca
+    torch.cuda.set_device(0)
+    B, H, m, n = args.batch, max(1, args.handles), args.size, args.size
+    ws = make_workload(args, 0, H * 2 * B)
+    params = params_for(mca, ws.params, mca.PREC_BF16_SPLIT, B, args.restart)
+    solvers = [mca.Solver(params, ws.gmaps) for _ in range(H)]
+    dev = torch.device("cuda", 0)
+    vin = {"device": torch.as_tensor(ws.vin, device=dev),
+           "host": torch.as_tensor(ws.vin).pin_memory()}
+    out = {"host_loadavg": os.getloadavg(), "host_cpus": os.cpu_count()}
+
+    def call(name, P, where, volt=True):
+        nv = P * B
+        vins = [vin[where][h * nv:(h + 1) * nv] for h in range(H)]
+        maps = [ws.map_index[h * nv:(h + 1) * nv] for h in range(H)]
+        if where == "device":
+            mk = lambda *s: torch.empty(*s, dtype=torch.float64, device=dev)
+        else:
+            mk = lambda *s: torch.empty(*s, dtype=torch.float64).pin_memory()
+        outs = [((mk(nv, m, n) if volt else None), (mk(nv, m, n) if volt else None),
+                 mk(nv, n)) for _ in range(H)]
+        ts = []
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = mca.solve_many(solvers, vins, map_indices=maps, n_threads=H, outs=outs)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+            for r in res:
+                for st in r[3]:
+                    assert st["status"] == 0 and st["rel_residual"] <= TOL, st
+        t = float(np.median(ts[1:]))
+        out[name] = {"ms_per_call": round(1e3 * t, 2), "solves_per_s": round(H * nv / t, 1),
+                     "solves_per_call": H * nv}
+        del outs
+
+    call("device_1_pass", 1, "device")
+    call("device_2_passes", 2, "device")
+    call("host_1_pass", 1, "host")
+    call("host_2_passes", 2, "host")
+    call("host_2_passes_currents_only", 2, "host", volt=False)
+    # the voltages of one two-pass call (both layers), device -> pinned host, alone
+    d = torch.empty(H, 2 * B, 2, m * n, dtype=torch.float64, device=dev)
+    hb = torch.empty(H, 2 * B, 2, m * n, dtype=torch.float64).pin_memory()
+    streams = [torch.cuda.Stream() for _ in range(H)]
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h in range(H):
+            with torch.cuda.stream(streams[h]):
+                hb[h].copy_(d[h], non_blocking=True)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    out["voltage_copies_alone"] = {"ms": round(1e3 * t, 1), "bytes": d.numel() * 8,
+                                   "GB/s": round(d.numel() * 8 / t / 1e9, 1)}
+    for s_ in solvers:
+        s_.close()
+    print(json.dumps({"e2e_breakdown": step_config(args), "results": out}), flush=True)
+
+
 def run_table1(args):
     """Table 1 of the paper on the GPU: GMRES iterations (and time) to relative residual
     1e-6 on the first Newton system J x = Y in the paper's normalised regime (wires and
@@ -914,6 +989,9 @@ def main():
         return run_batch_profile(args)
     if args.table1:
         run_table1(args)
+        return
+    if args.e2e_breakdown:
+        run_e2e_breakdown(args)
         return
     if args.profile_precond:
         run_profile_precond(args)
