@@ -193,6 +193,19 @@ def oracle_solves(ws, count, start=0, tol=TOL):
     return time.perf_counter() - t0
 
 
+def oracle_once(size, seed=0):
+    """Seconds of one oracle solve (Newton + FP64 preconditioned GMRES, NumPy/SciPy, BLAS on
+    every core) of the size^2 crossbar of seed `seed` with the workload's wiring, input
+    vector 0."""
+    from oracle import mca_oracle as O
+    ws = mi.config_large_set(size, seeds=(seed,), nvec=1)
+    t0 = time.perf_counter()
+    r = O.newton_solve(ws.params, ws.gmaps[0], ws.vin[0], tol=TOL, linear="pgmres")
+    t = time.perf_counter() - t0
+    assert r.rel_residual <= TOL
+    return t
+
+
 def workload_config(args, batch):
     dev = ("sinh devices b=2, V_in~U[0,0.3] V" if getattr(args, "device", "sinh") == "sinh" else
            f"Yakopcic-form devices b=2 a2/a1={args.neg_ratio:g}, V_in~U[-0.3,0.3] V")
@@ -650,6 +663,11 @@ def run_ours(args):
                                          f"GMRES, NumPy/SciPy) of the {m}^2 workload, vectors "
                                          f"0-{ncpu - 1} (crossbars 0-3), {tcpu:.1f} s",
                                "configs": oracle_configs_in_children()}
+        if not args.no_2048 and args.size == 1024:
+            t2 = oracle_once(2048)
+            out["cpu_baseline"]["c3_2048_pgmres"] = {
+                "value": 1.0 / t2, "unit": "solves/s", "solves": 1, "seconds": t2,
+                "seeds": "0", "threads": os.cpu_count()}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if pg:

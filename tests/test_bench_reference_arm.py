@@ -33,3 +33,10 @@ def test_reference_arm_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_oracle_once_times_one_converged_solve():
+    sys.path.insert(0, ROOT)
+    import bench
+    t = bench.oracle_once(32)
+    assert 0.0 < t < 60.0
