@@ -40,3 +40,16 @@ def test_oracle_once_times_one_converged_solve():
     import bench
     t = bench.oracle_once(32)
     assert 0.0 < t < 60.0
+
+
+def test_secondary_leg_records_a_failure_in_line():
+    sys.path.insert(0, ROOT)
+    import bench
+    out = {}
+    bench.secondary_leg(out, "ok", lambda: {"value": 1.0})
+
+    def fails():
+        raise RuntimeError("side figure failed")
+    bench.secondary_leg(out, "bad", fails)
+    assert out["ok"] == {"value": 1.0}
+    assert out["bad"] == {"error": "RuntimeError: side figure failed"}
