@@ -276,13 +276,12 @@ __device__ __forceinline__ void cell_residual_pair(const Grid& gr, int i, int j,
 
 // Column-strip walk of the pair cells with shared-memory halo staging.  The top layer
 // couples a node to j - 1 and j + 1 in its row, the bottom layer to i - 1 and i + 1 in its
-// column, and a pair cell needs all six voltages as FP32 pairs; splitting one costs about
-// a few dozen integer instructions, and a cell that splits its own
-// neighbours splits every voltage three times (those splits were a third of the pair
-// cell's instructions).  Here the block's cells are columns of
-// strips kThreads wide: block bx of nblk owns the units [U bx / nblk, U (bx + 1) / nblk) of
-// the strip-major list of U = m * strips (strip, row) units, and each thread walks down its
-// column of each strip segment.  The bottom layer's rows i - 1, i, i + 1 stay split in
+// column, and a pair cell needs all six voltages as FP32 pairs.  A split takes a few dozen
+// integer instructions, and a cell that splits its own neighbours splits every voltage three
+// times (those splits were a third of the pair cell's instructions).  Here the block's cells
+// are columns of strips kThreads wide: block bx of nblk owns the units
+// [U bx / nblk, U (bx + 1) / nblk) of the strip-major list of U = m * strips (strip, row)
+// units, and each thread walks down its column of each strip segment.  The bottom layer's rows i - 1, i, i + 1 stay split in
 // registers; the top layer's row is split once into shared memory, with one halo entry on
 // each side of the strip (threads 0 and kThreads - 1); the next row's voltages are loaded
 // before the current row is evaluated.  Each voltage is split about once (twice per segment
